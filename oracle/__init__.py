@@ -1,0 +1,251 @@
+"""CPU oracle for the symmetric-heap operations (ctypes wrapper over ``oracle.c``).
+
+TEST INFRASTRUCTURE ONLY: only ``tests/``, ``__graft_entry__.smoke()`` and the CPU
+baseline leg of ``bench.py`` import this package.  It never imports the GPU package and
+the GPU package never imports it; both take their inputs from ``workloads``.
+
+The heap is a numpy uint8 array of npes * H bytes; PE p's partition is bytes
+[p*H, (p+1)*H).  Each function applies one operation by its definition (see the C
+source for the reading of the paper each follows).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD, "liboracle.so")
+_lib = None
+_lock = threading.Lock()
+
+CFLAGS = ["-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared", "-Wall"]
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (plain C11, no fast-math, no FMA contraction)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+        tmp = _LIB_PATH + f".{os.getpid()}.tmp"
+        subprocess.check_call(["gcc", *CFLAGS, "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            L = C.CDLL(build())
+            P, I, U64, I64 = C.c_void_p, C.c_int, C.c_uint64, C.c_int64
+            sig = {
+                "or_copy": (I, [P, I, U64, I, U64, I, U64, U64]),
+                "or_amo64": (I, [P, I, U64, I, I, U64, I64, I64, P]),
+                "or_amo32": (I, [P, I, U64, I, I, U64, C.c_int32, C.c_int32, P]),
+                "or_put_signal": (I, [P, I, U64, I, U64, I, U64, U64, U64, I, U64]),
+                "or_signal_test": (I, [P, I, U64, I, U64, I, U64]),
+                "or_broadcast": (I, [P, I, U64, I, I, I, U64, U64, U64, I]),
+                "or_fcollect": (I, [P, I, U64, I, I, I, U64, U64, U64]),
+                "or_alltoall": (I, [P, I, U64, I, I, I, U64, U64, U64]),
+                "or_tree_sum_f32": (C.c_float, [P, I]),
+                "or_reduce": (I, [P, I, U64, I, I, I, U64, U64, U64, I, I]),
+                "or_reduce_f32_ref64": (I, [P, I, U64, I, I, I, U64, U64, P, P]),
+                "or_bf16_decode": (C.c_float, [C.c_uint16]),
+                "or_bf16_encode": (C.c_uint16, [C.c_float]),
+                "or_e4m3_decode": (C.c_double, [C.c_uint8]),
+                "or_e4m3_encode": (C.c_uint8, [C.c_float]),
+                "or_quantize": (I, [P, U64, I, P, P]),
+                "or_neumaier_f32": (C.c_float, [P, I]),
+                "or_qsum_reduce": (I, [P, I, U64, I, I, I, U64, U64, U64, I, U64]),
+                "or_qsum_ref64": (I, [P, I, U64, I, I, I, U64, U64, I, U64, P, P]),
+                "or_run_script": (I, [P, I, U64, P, I64, P, I, P, P]),
+                "or_cb64": (U64, [U64, U64]),
+                "or_amo_stream": (I, [P, U64, P, U64, U64, U64, U64, P]),
+                "or_check_serialisation": (I64, [I64, P, P, P, P, P, P, P, I, I64, P]),
+            }
+            for name, (res, args) in sig.items():
+                f = getattr(L, name)
+                f.restype = res
+                f.argtypes = args
+            _lib = L
+    return _lib
+
+
+class OracleError(RuntimeError):
+    pass
+
+
+def _chk(rc, what):
+    if rc != 0:
+        raise OracleError(f"{what}: oracle error {rc}")
+
+
+def _p(a: np.ndarray):
+    assert a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(C.c_void_p)
+
+
+class Heap:
+    """npes partitions of H bytes, initialised from ``init`` (bytes) or zero."""
+
+    def __init__(self, npes: int, H: int, init: np.ndarray = None):
+        self.npes, self.H = npes, H
+        if init is None:
+            self.mem = np.zeros(npes * H, dtype=np.uint8)
+        else:
+            assert init.nbytes == npes * H
+            self.mem = np.ascontiguousarray(init.view(np.uint8)).copy()
+
+    def pe(self, p: int) -> np.ndarray:
+        return self.mem[p * self.H:(p + 1) * self.H]
+
+    def view(self, p: int, off: int, count: int, dtype) -> np.ndarray:
+        dt = np.dtype(dtype)
+        return self.pe(p)[off:off + count * dt.itemsize].view(dt)
+
+    def _a(self):
+        return (_p(self.mem), self.npes, self.H)
+
+    # RMA (paper Sec. 2.1; blocking and _nbi forms share the final state)
+    def put(self, dst, src, nbytes, pe, issuer):
+        _chk(lib().or_copy(*self._a(), pe, dst, issuer, src, nbytes), "put")
+
+    def get(self, dst, src, nbytes, pe, issuer):
+        _chk(lib().or_copy(*self._a(), issuer, dst, pe, src, nbytes), "get")
+
+    def amo64(self, kind, pe, off, v, cond=0):
+        f = C.c_int64(0)
+        _chk(lib().or_amo64(*self._a(), kind, pe, off, v, cond, C.byref(f)), "amo64")
+        return f.value
+
+    def amo32(self, kind, pe, off, v, cond=0):
+        f = C.c_int32(0)
+        _chk(lib().or_amo32(*self._a(), kind, pe, off, v, cond, C.byref(f)), "amo32")
+        return f.value
+
+    def put_signal(self, dst, src, nbytes, sig, sig_op, v, pe, issuer):
+        _chk(lib().or_put_signal(*self._a(), pe, dst, issuer, src, nbytes, sig, sig_op, v),
+             "put_signal")
+
+    def signal_test(self, pe, off, cmp, v) -> bool:
+        r = lib().or_signal_test(*self._a(), pe, off, cmp, v)
+        if r < 0:
+            raise OracleError(f"signal_test: {r}")
+        return bool(r)
+
+    # collectives over a strided team (start, stride, size)
+    def broadcast(self, team, dst, src, nbytes, root):
+        _chk(lib().or_broadcast(*self._a(), *team, dst, src, nbytes, root), "broadcast")
+
+    def fcollect(self, team, dst, src, nbytes):
+        _chk(lib().or_fcollect(*self._a(), *team, dst, src, nbytes), "fcollect")
+
+    def alltoall(self, team, dst, src, m):
+        _chk(lib().or_alltoall(*self._a(), *team, dst, src, m), "alltoall")
+
+    def reduce(self, team, dst, src, nelems, dtype, op):
+        _chk(lib().or_reduce(*self._a(), *team, dst, src, nelems, dtype, op), "reduce")
+
+    def reduce_f32_ref64(self, team, src, nelems):
+        y = np.zeros(nelems, np.float64)
+        a = np.zeros(nelems, np.float64)
+        _chk(lib().or_reduce_f32_ref64(*self._a(), *team, src, nelems, _p(y), _p(a)), "ref64")
+        return y, a
+
+    def qsum_reduce(self, team, dst, q_off, s_off, fmt, n):
+        _chk(lib().or_qsum_reduce(*self._a(), *team, dst, q_off, s_off, fmt, n), "qsum_reduce")
+
+    def qsum_ref64(self, team, q_off, s_off, fmt, n):
+        y = np.zeros(n, np.float64)
+        a = np.zeros(n, np.float64)
+        _chk(lib().or_qsum_ref64(*self._a(), *team, q_off, s_off, fmt, n, _p(y), _p(a)), "qref64")
+        return y, a
+
+    def run_script(self, ops: np.ndarray, teams=None) -> np.ndarray:
+        """Apply a scripted op list in script order; returns fetched values (AMO ops)."""
+        ops = np.ascontiguousarray(ops)
+        assert ops.dtype.itemsize == 64
+        if teams is None:
+            teams = [(0, 1, self.npes)]
+        t = np.ascontiguousarray(np.array(teams, dtype=np.int32).reshape(-1))
+        fetched = np.zeros(len(ops), np.int64)
+        bad = C.c_int64(-1)
+        rc = lib().or_run_script(*self._a(), _p(ops), len(ops), _p(t), len(t) // 3, _p(fetched),
+                                 C.byref(bad))
+        if rc != 0:
+            raise OracleError(f"run_script: error {rc} at op {bad.value}")
+        return fetched
+
+
+def tree_sum_f32(values) -> np.float32:
+    v = np.ascontiguousarray(np.array(values, dtype=np.float32))
+    return np.float32(lib().or_tree_sum_f32(_p(v), len(v)))
+
+
+def neumaier_f32(values) -> np.float32:
+    v = np.ascontiguousarray(np.array(values, dtype=np.float32))
+    return np.float32(lib().or_neumaier_f32(_p(v), len(v)))
+
+
+def bf16_encode(x: float) -> int:
+    return int(lib().or_bf16_encode(float(np.float32(x))))
+
+
+def bf16_decode(q: int) -> float:
+    return float(lib().or_bf16_decode(q))
+
+
+def e4m3_encode(x: float) -> int:
+    return int(lib().or_e4m3_encode(float(np.float32(x))))
+
+
+def e4m3_decode(q: int) -> float:
+    return float(lib().or_e4m3_decode(q))
+
+
+def quantize(x: np.ndarray, fmt: int):
+    """Per-128-element block quantisation of one PE's floats -> (codes, scales)."""
+    x = np.ascontiguousarray(x, dtype=np.float32)
+    n = len(x)
+    q = np.zeros(n, np.uint8 if fmt == 1 else np.uint16)
+    s = np.zeros((n + 127) // 128, np.float32)
+    _chk(lib().or_quantize(_p(x), n, fmt, _p(q), _p(s)), "quantize")
+    return q, s
+
+
+def cb64(seed: int, i: int) -> int:
+    return int(lib().or_cb64(seed, i))
+
+
+def amo_stream(table: np.ndarray, ops: np.ndarray, op_seed: int, table_seed: int,
+               first_op: int = 0, want_fetched: bool = True):
+    """Apply a packed AMO stream sequentially to ``table`` (int64, modified in place)."""
+    assert table.dtype == np.int64 and ops.dtype == np.uint32
+    fetched = np.zeros(len(ops), np.int64) if want_fetched else None
+    _chk(lib().or_amo_stream(_p(table), len(table), _p(ops), len(ops), first_op, op_seed,
+                             table_seed, _p(fetched) if want_fetched else None), "amo_stream")
+    return fetched
+
+
+def check_serialisation(group, kind, operand, cond, fetched, w0, final=None,
+                        budget_per_group: int = 1 << 26):
+    """Number of word groups whose fetched values admit no valid serial order (0 = all
+    valid); -1 if the search was inconclusive.  Arrays are per op."""
+    n = len(kind)
+    group = np.ascontiguousarray(group, np.int64)
+    kind = np.ascontiguousarray(kind, np.int32)
+    operand = np.ascontiguousarray(operand, np.int64)
+    cond = np.ascontiguousarray(cond, np.int64)
+    fetched = np.ascontiguousarray(fetched, np.int64)
+    w0 = np.ascontiguousarray(w0, np.int64)
+    has_final = final is not None
+    fin = np.ascontiguousarray(final if has_final else np.zeros(n), np.int64)
+    bad = C.c_int64(-1)
+    r = lib().or_check_serialisation(n, _p(group), _p(kind), _p(operand), _p(cond), _p(fetched),
+                                     _p(w0), _p(fin), int(has_final), budget_per_group, C.byref(bad))
+    return int(r)

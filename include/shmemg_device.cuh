@@ -1,0 +1,668 @@
+/*
+ * shmemg_device.cuh -- device API of the one-GPU symmetric heap (sm_103a).
+ *
+ * Device-initiated operations (paper Sec. 6.3, "device-initiated path"): device code
+ * addresses PE p's copy of a symmetric object as heap + p*H + offset, without per-op
+ * pointer classification (Sec. 6.3: "should not require device code to perform
+ * dynamic pointer classification").  Scopes (Sec. 6.3, participation scopes):
+ *   thread  -- one thread issues the operation;
+ *   group   -- every thread of a shmemg_group (warp, block, cluster or grid) calls with
+ *              identical arguments (uniform participation, Sec. 6.3 normative excerpt)
+ *              and the work is split among them.
+ * Ordering (Sec. 6.4): fence orders, quiet completes the caller's operations; data
+ * moved with plain stores is complete once a GPU-scope fence follows it; bulk (TMA)
+ * stores also need their bulk group drained and a proxy fence.  Every wait is bounded
+ * by ctx.timeout_ns of %globaltimer; on expiry the first error is recorded in the
+ * device status word and the wait returns SHMEMG_ERR_TIMEOUT (no trap, no hang).
+ */
+#ifndef SHMEMG_DEVICE_CUH
+#define SHMEMG_DEVICE_CUH
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <type_traits>
+
+#include "shmemg.h"
+
+/* ------------------------------------------------------------ reserved prefix layout */
+#define SHMEMG_STATUS_OFF 0ull            /* int32 code, int32 pad, int64 detail */
+#define SHMEMG_TEAMS_OFF 4096ull          /* SHMEMG_MAX_TEAMS x shmemg_dteam_t */
+#define SHMEMG_BARRIERS_OFF (256ull << 10) /* SHMEMG_MAX_BARRIERS x shmemg_dbar_t */
+#define SHMEMG_MAX_BARRIERS 65536u
+#define SHMEMG_SCRATCH_OFF (2ull << 20)   /* library scratch words (2 MiB) */
+
+typedef struct {
+    int32_t start, stride, size;  /* members start + r*stride (+ group*gstride) */
+    int32_t ngroups, gstride;     /* SHARED: one group per cluster */
+    int32_t bar_base;             /* barrier slot of group 0 */
+    int32_t valid, pad;
+} shmemg_dteam_t;
+
+typedef struct {
+    uint32_t count;
+    uint32_t gen;
+    uint32_t pad[30];             /* one 128-byte line per barrier */
+} shmemg_dbar_t;
+
+typedef struct {
+    uint32_t rank;   /* this thread's rank in the cooperating group */
+    uint32_t size;   /* threads in the group */
+} shmemg_group;
+
+/* ------------------------------------------------------------------ PTX helpers */
+static __device__ __forceinline__ uint64_t shmemg_d_globaltimer() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+static __device__ __forceinline__ void shmemg_d_fence_gpu() {
+    asm volatile("fence.acq_rel.gpu;" ::: "memory");
+}
+static __device__ __forceinline__ void shmemg_d_fence_sys() {
+    asm volatile("fence.acq_rel.sys;" ::: "memory");
+}
+static __device__ __forceinline__ uint64_t shmemg_d_ld_acquire_u64(const uint64_t *p) {
+    uint64_t v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+static __device__ __forceinline__ uint32_t shmemg_d_ld_acquire_u32(const uint32_t *p) {
+    uint32_t v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+static __device__ __forceinline__ uint64_t shmemg_d_ld_acquire_sys_u64(const volatile uint64_t *p) {
+    uint64_t v;
+    asm volatile("ld.acquire.sys.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+static __device__ __forceinline__ void shmemg_d_st_release_u64(uint64_t *p, uint64_t v) {
+    asm volatile("st.release.gpu.global.u64 [%0], %1;" :: "l"(p), "l"(v) : "memory");
+}
+static __device__ __forceinline__ void shmemg_d_st_release_u32(uint32_t *p, uint32_t v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" :: "l"(p), "r"(v) : "memory");
+}
+static __device__ __forceinline__ void shmemg_d_red_release_add_u64(uint64_t *p, uint64_t v) {
+    asm volatile("red.release.gpu.global.add.u64 [%0], %1;" :: "l"(p), "l"(v) : "memory");
+}
+static __device__ __forceinline__ uint32_t shmemg_d_cluster_ctarank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+static __device__ __forceinline__ uint32_t shmemg_d_cluster_nctarank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
+    return r;
+}
+/* All threads of all CTAs of the cluster; release/acquire at cluster scope. */
+static __device__ __forceinline__ void shmemg_d_cluster_sync() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+/* ------------------------------------------------------------------ context access */
+static __device__ __forceinline__ uint8_t *shmemg_d_addr(const shmemg_device_ctx_t &c, int pe, uint64_t off) {
+    return c.heap + (uint64_t)pe * c.pe_stride + off;
+}
+static __device__ __forceinline__ uint64_t shmemg_d_offset(const shmemg_device_ctx_t &c, const void *sym) {
+    return (uint64_t)((const uint8_t *)sym - c.heap);
+}
+/* shmem_ptr analogue: device address of `sym` on `pe` (valid in device code only). */
+static __device__ __forceinline__ void *shmemg_d_ptr(const shmemg_device_ctx_t &c, const void *sym, int pe) {
+    return shmemg_d_addr(c, pe, shmemg_d_offset(c, sym));
+}
+static __device__ __forceinline__ int shmemg_d_n_pes(const shmemg_device_ctx_t &c) { return c.npes; }
+/* PE of the calling thread: its CTA (pe_mode CTA) or its cluster (pe_mode CLUSTER),
+ * for a 1-D grid launched with the library's PE layout. */
+static __device__ __forceinline__ int shmemg_d_my_pe(const shmemg_device_ctx_t &c) {
+    return c.pe_mode == SHMEMG_PE_MODE_CLUSTER ? (int)(blockIdx.x / (uint32_t)c.cluster_dim) : (int)blockIdx.x;
+}
+static __device__ __forceinline__ const shmemg_dteam_t *shmemg_d_team(const shmemg_device_ctx_t &c, int team) {
+    return (const shmemg_dteam_t *)(c.state + SHMEMG_TEAMS_OFF) + team;
+}
+/* Team rank of world PE `pe` in `team` and its group index; -1 if not a member. */
+static __device__ __forceinline__ int shmemg_d_team_rank(const shmemg_dteam_t &t, int pe, int *group) {
+    int rel = pe - t.start;
+    if (rel < 0) return -1;
+    int g = t.gstride > 0 ? rel / t.gstride : 0;
+    if (g >= t.ngroups) return -1;
+    rel -= g * t.gstride;
+    if (rel % t.stride) return -1;
+    int r = rel / t.stride;
+    if (r >= t.size) return -1;
+    if (group) *group = g;
+    return r;
+}
+static __device__ __forceinline__ int shmemg_d_team_member(const shmemg_dteam_t &t, int group, int r) {
+    return t.start + group * t.gstride + r * t.stride;
+}
+
+/* ------------------------------------------------------------------ groups */
+static __device__ __forceinline__ shmemg_group shmemg_d_group_thread() { return {0u, 1u}; }
+static __device__ __forceinline__ shmemg_group shmemg_d_group_warp() { return {threadIdx.x & 31u, 32u}; }
+static __device__ __forceinline__ shmemg_group shmemg_d_group_block() { return {threadIdx.x, blockDim.x}; }
+static __device__ __forceinline__ shmemg_group shmemg_d_group_cluster() {
+    return {shmemg_d_cluster_ctarank() * blockDim.x + threadIdx.x, shmemg_d_cluster_nctarank() * blockDim.x};
+}
+static __device__ __forceinline__ shmemg_group shmemg_d_group_grid() {
+    return {blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x};
+}
+/* the whole calling PE: its block, or its cluster in pe_mode CLUSTER */
+static __device__ __forceinline__ shmemg_group shmemg_d_group_pe(const shmemg_device_ctx_t &c) {
+    return c.pe_mode == SHMEMG_PE_MODE_CLUSTER ? shmemg_d_group_cluster() : shmemg_d_group_block();
+}
+static __device__ __forceinline__ void shmemg_d_pe_sync(const shmemg_device_ctx_t &c) {
+    if (c.pe_mode == SHMEMG_PE_MODE_CLUSTER) shmemg_d_cluster_sync();
+    else __syncthreads();
+}
+static __device__ __forceinline__ bool shmemg_d_pe_leader(const shmemg_device_ctx_t &c) {
+    return threadIdx.x == 0 && (c.pe_mode != SHMEMG_PE_MODE_CLUSTER || shmemg_d_cluster_ctarank() == 0);
+}
+
+/* ------------------------------------------------------------------ status word */
+/* Records the first device-side error (later ones are dropped). */
+static __device__ __forceinline__ void shmemg_d_set_status(const shmemg_device_ctx_t &c, int code, int64_t detail) {
+    int *st = (int *)(c.state + SHMEMG_STATUS_OFF);
+    if (atomicCAS(st, 0, code) == 0) {
+        *(volatile int64_t *)(c.state + SHMEMG_STATUS_OFF + 8) = detail;
+        shmemg_d_fence_gpu();
+    }
+}
+static __device__ __forceinline__ int shmemg_d_get_status(const shmemg_device_ctx_t &c) {
+    return *(volatile int *)(c.state + SHMEMG_STATUS_OFF);
+}
+
+/* ------------------------------------------------------------------ data movement */
+template <typename V>
+static __device__ __forceinline__ V shmemg_ld_cg(const V *p);
+template <> __device__ __forceinline__ uint4 shmemg_ld_cg<uint4>(const uint4 *p) { return __ldcg(p); }
+template <> __device__ __forceinline__ uint2 shmemg_ld_cg<uint2>(const uint2 *p) { return __ldcg(p); }
+template <> __device__ __forceinline__ uint32_t shmemg_ld_cg<uint32_t>(const uint32_t *p) { return __ldcg(p); }
+template <> __device__ __forceinline__ uint16_t shmemg_ld_cg<uint16_t>(const uint16_t *p) {
+    return __ldcg((const unsigned short *)p);
+}
+template <> __device__ __forceinline__ uint8_t shmemg_ld_cg<uint8_t>(const uint8_t *p) {
+    return (uint8_t)__ldcg((const unsigned char *)p);
+}
+template <> __device__ __forceinline__ int4 shmemg_ld_cg<int4>(const int4 *p) { return __ldcg(p); }
+template <> __device__ __forceinline__ longlong2 shmemg_ld_cg<longlong2>(const longlong2 *p) { return __ldcg(p); }
+template <> __device__ __forceinline__ float4 shmemg_ld_cg<float4>(const float4 *p) { return __ldcg(p); }
+template <> __device__ __forceinline__ int32_t shmemg_ld_cg<int32_t>(const int32_t *p) { return __ldcg(p); }
+template <> __device__ __forceinline__ int64_t shmemg_ld_cg<int64_t>(const int64_t *p) {
+    return (int64_t)__ldcg((const long long *)p);
+}
+template <> __device__ __forceinline__ float shmemg_ld_cg<float>(const float *p) { return __ldcg(p); }
+
+/* Group-wide copy of nvec vectors of type V; each thread keeps 4 loads in flight. */
+template <typename V>
+static __device__ __forceinline__ void shmemg_d_copy_vec(shmemg_group g, V *dst, const V *src, uint64_t nvec) {
+    uint64_t i = g.rank;
+    const uint64_t s = g.size;
+    for (; i + 3 * s < nvec; i += 4 * s) {
+        V a = shmemg_ld_cg(src + i), b = shmemg_ld_cg(src + i + s);
+        V d = shmemg_ld_cg(src + i + 2 * s), e = shmemg_ld_cg(src + i + 3 * s);
+        dst[i] = a;
+        dst[i + s] = b;
+        dst[i + 2 * s] = d;
+        dst[i + 3 * s] = e;
+    }
+    for (; i < nvec; i += s) dst[i] = shmemg_ld_cg(src + i);
+}
+
+/* widest power-of-two vector (<= 16 bytes) that both addresses and the length allow */
+static __device__ __forceinline__ int shmemg_d_vec_width(const void *a, const void *b, uint64_t n) {
+    uint64_t m = (uint64_t)a | (uint64_t)b | n;
+    return (m & 15) == 0 ? 16 : (m & 7) == 0 ? 8 : (m & 3) == 0 ? 4 : (m & 1) == 0 ? 2 : 1;
+}
+
+/* Group-wide byte copy dst <- src (no overlap). */
+static __device__ __forceinline__ void shmemg_d_copy_group(shmemg_group g, void *dst, const void *src, uint64_t n) {
+    switch (shmemg_d_vec_width(dst, src, n)) {
+    case 16: shmemg_d_copy_vec(g, (uint4 *)dst, (const uint4 *)src, n / 16); break;
+    case 8: shmemg_d_copy_vec(g, (uint2 *)dst, (const uint2 *)src, n / 8); break;
+    case 4: shmemg_d_copy_vec(g, (uint32_t *)dst, (const uint32_t *)src, n / 4); break;
+    case 2: shmemg_d_copy_vec(g, (uint16_t *)dst, (const uint16_t *)src, n / 2); break;
+    default: shmemg_d_copy_vec(g, (uint8_t *)dst, (const uint8_t *)src, n); break;
+    }
+}
+
+/* ------------------------------------------------------------------ RMA (Sec. 2.1) */
+/* put: n bytes of the caller PE's `src` -> `dst` on `pe`.  Group scope: every thread
+ * of g calls with the same arguments.  On return the caller's threads have read the
+ * source (local completion); remote visibility needs quiet (Sec. 6.3). */
+static __device__ __forceinline__ void shmemg_d_putmem_group(const shmemg_device_ctx_t &c, shmemg_group g,
+                                                             void *dst, const void *src, uint64_t n, int pe,
+                                                             int my_pe) {
+    shmemg_d_copy_group(g, shmemg_d_ptr(c, dst, pe), shmemg_d_ptr(c, src, my_pe), n);
+}
+/* get: n bytes of `src` on `pe` -> the caller PE's `dst`. */
+static __device__ __forceinline__ void shmemg_d_getmem_group(const shmemg_device_ctx_t &c, shmemg_group g,
+                                                             void *dst, const void *src, uint64_t n, int pe,
+                                                             int my_pe) {
+    shmemg_d_copy_group(g, shmemg_d_ptr(c, dst, my_pe), shmemg_d_ptr(c, src, pe), n);
+}
+/* block-scope forms for pe_mode CTA (the calling block is the PE) */
+static __device__ __forceinline__ void shmemg_d_putmem_block(const shmemg_device_ctx_t &c, void *dst,
+                                                             const void *src, uint64_t n, int pe) {
+    shmemg_d_putmem_group(c, shmemg_d_group_block(), dst, src, n, pe, shmemg_d_my_pe(c));
+    __syncthreads();
+}
+static __device__ __forceinline__ void shmemg_d_getmem_block(const shmemg_device_ctx_t &c, void *dst,
+                                                             const void *src, uint64_t n, int pe) {
+    shmemg_d_getmem_group(c, shmemg_d_group_block(), dst, src, n, pe, shmemg_d_my_pe(c));
+    __syncthreads();
+}
+/* thread-scope forms */
+static __device__ __forceinline__ void shmemg_d_putmem(const shmemg_device_ctx_t &c, void *dst, const void *src,
+                                                       uint64_t n, int pe) {
+    shmemg_d_putmem_group(c, shmemg_d_group_thread(), dst, src, n, pe, shmemg_d_my_pe(c));
+}
+static __device__ __forceinline__ void shmemg_d_getmem(const shmemg_device_ctx_t &c, void *dst, const void *src,
+                                                       uint64_t n, int pe) {
+    shmemg_d_getmem_group(c, shmemg_d_group_thread(), dst, src, n, pe, shmemg_d_my_pe(c));
+}
+
+/* ------------------------------------------------------------------ ordering (Sec. 6.4) */
+/* fence: later RMA/AMO of this thread are ordered after earlier ones (GPU scope). */
+static __device__ __forceinline__ void shmemg_d_fence() { shmemg_d_fence_gpu(); }
+/* quiet: this thread's earlier plain-store RMA and AMOs are complete and visible at GPU
+ * scope.  Host visibility additionally needs the host to synchronise (Fig. 3b). */
+static __device__ __forceinline__ void shmemg_d_quiet() { shmemg_d_fence_gpu(); }
+/* quiet for a whole PE (all its threads' operations): PE barrier, then a GPU-scope
+ * fence by the leader, whose later release covers the PE's writes (cumulativity). */
+static __device__ __forceinline__ void shmemg_d_quiet_pe(const shmemg_device_ctx_t &c) {
+    shmemg_d_pe_sync(c);
+    if (shmemg_d_pe_leader(c)) shmemg_d_fence_gpu();
+}
+
+/* ------------------------------------------------------------------ AMOs (Sec. 2.1) */
+/* Thread scope, relaxed at GPU scope ("atomicity does not imply ordering", Sec. 6.3). */
+static __device__ __forceinline__ int64_t shmemg_d_int64_atomic_fetch_add(const shmemg_device_ctx_t &c,
+                                                                          int64_t *target, int64_t v, int pe) {
+    return (int64_t)atomicAdd((unsigned long long *)shmemg_d_ptr(c, target, pe), (unsigned long long)v);
+}
+static __device__ __forceinline__ int64_t shmemg_d_int64_atomic_compare_swap(const shmemg_device_ctx_t &c,
+                                                                             int64_t *target, int64_t cond,
+                                                                             int64_t v, int pe) {
+    return (int64_t)atomicCAS((unsigned long long *)shmemg_d_ptr(c, target, pe), (unsigned long long)cond,
+                              (unsigned long long)v);
+}
+static __device__ __forceinline__ int64_t shmemg_d_int64_atomic_fetch_xor(const shmemg_device_ctx_t &c,
+                                                                          int64_t *target, int64_t v, int pe) {
+    return (int64_t)atomicXor((unsigned long long *)shmemg_d_ptr(c, target, pe), (unsigned long long)v);
+}
+static __device__ __forceinline__ int32_t shmemg_d_int32_atomic_fetch_add(const shmemg_device_ctx_t &c,
+                                                                          int32_t *target, int32_t v, int pe) {
+    return atomicAdd((int *)shmemg_d_ptr(c, target, pe), v);
+}
+static __device__ __forceinline__ int32_t shmemg_d_int32_atomic_compare_swap(const shmemg_device_ctx_t &c,
+                                                                             int32_t *target, int32_t cond,
+                                                                             int32_t v, int pe) {
+    return atomicCAS((int *)shmemg_d_ptr(c, target, pe), cond, v);
+}
+static __device__ __forceinline__ int32_t shmemg_d_int32_atomic_fetch_xor(const shmemg_device_ctx_t &c,
+                                                                          int32_t *target, int32_t v, int pe) {
+    return atomicXor((int *)shmemg_d_ptr(c, target, pe), v);
+}
+
+/* ------------------------------------------------------------------ signals */
+/* Signal update after the data (Sec. 7, put-signal): release at GPU scope so the data
+ * written before it by this thread -- and by the PE's threads synchronised with it --
+ * is visible to whoever acquires the signal. */
+static __device__ __forceinline__ void shmemg_d_signal_op(uint64_t *sig_addr, uint64_t v, int sig_op) {
+    if (sig_op == SHMEMG_SIGNAL_SET) shmemg_d_st_release_u64(sig_addr, v);
+    else shmemg_d_red_release_add_u64(sig_addr, v);
+}
+static __device__ __forceinline__ bool shmemg_d_cmp(uint64_t s, int cmp, uint64_t v) {
+    switch (cmp) {
+    case SHMEMG_CMP_EQ: return s == v;
+    case SHMEMG_CMP_NE: return s != v;
+    case SHMEMG_CMP_GT: return s > v;
+    case SHMEMG_CMP_GE: return s >= v;
+    case SHMEMG_CMP_LT: return s < v;
+    default: return s <= v;
+    }
+}
+/* put-with-signal at group scope: the put, a PE-wide completion, then one release
+ * update of the signal on `pe` by the group's rank 0. */
+static __device__ __forceinline__ void shmemg_d_putmem_signal_block(const shmemg_device_ctx_t &c, void *dst,
+                                                                    const void *src, uint64_t n, uint64_t *sig,
+                                                                    uint64_t v, int sig_op, int pe) {
+    shmemg_d_putmem_group(c, shmemg_d_group_block(), dst, src, n, pe, shmemg_d_my_pe(c));
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        shmemg_d_fence_gpu();
+        shmemg_d_signal_op((uint64_t *)shmemg_d_ptr(c, sig, pe), v, sig_op);
+    }
+    __syncthreads();
+}
+/* wait_until on the caller's own signal word (thread scope, Sec. 6.4 single unscoped
+ * contract), bounded: SHMEMG_SUCCESS or SHMEMG_ERR_TIMEOUT (recorded in the status
+ * word with `detail`).  Acquire: data published before the matching release is
+ * visible afterwards. */
+static __device__ __forceinline__ int shmemg_d_signal_wait_until(const shmemg_device_ctx_t &c, const uint64_t *sig_local,
+                                                                 int cmp, uint64_t v, int64_t detail) {
+    uint64_t t0 = 0;
+    uint32_t ns = 32;
+    for (uint32_t it = 0;; it++) {
+        if (shmemg_d_cmp(shmemg_d_ld_acquire_u64(sig_local), cmp, v)) return SHMEMG_SUCCESS;
+        if ((it & 63) == 0) {
+            uint64_t now = shmemg_d_globaltimer();
+            if (t0 == 0) t0 = now;
+            else if (now - t0 > c.timeout_ns) {
+                shmemg_d_set_status(c, SHMEMG_ERR_TIMEOUT, detail);
+                return SHMEMG_ERR_TIMEOUT;
+            }
+            if (shmemg_d_get_status(c) != 0) return SHMEMG_ERR_DEVICE;  /* another PE failed */
+        }
+        __nanosleep(ns);
+        if (ns < 1024) ns <<= 1;
+    }
+}
+
+/* ------------------------------------------------------------------ barriers */
+/* Barrier of one team group, entered by the leader thread of each member PE after the
+ * PE's own quiet.  Generation counting: read the generation, arrive; the last arrival
+ * resets the count and releases the next generation; the others acquire-spin on it
+ * (bounded).  Needs every member PE resident on the GPU at once. */
+static __device__ __forceinline__ int shmemg_d_team_barrier_leader(const shmemg_device_ctx_t &c, int bar_slot,
+                                                                   uint32_t size, int64_t detail) {
+    shmemg_dbar_t *b = (shmemg_dbar_t *)(c.state + SHMEMG_BARRIERS_OFF) + bar_slot;
+    shmemg_d_fence_gpu();
+    uint32_t gen = shmemg_d_ld_acquire_u32(&b->gen);
+    uint32_t arrived = atomicAdd(&b->count, 1u);
+    if (arrived == size - 1) {
+        b->count = 0;
+        shmemg_d_st_release_u32(&b->gen, gen + 1);
+        return SHMEMG_SUCCESS;
+    }
+    uint64_t t0 = 0;
+    uint32_t ns = 32;
+    for (uint32_t it = 0;; it++) {
+        if (shmemg_d_ld_acquire_u32(&b->gen) != gen) return SHMEMG_SUCCESS;
+        if ((it & 63) == 0) {
+            uint64_t now = shmemg_d_globaltimer();
+            if (t0 == 0) t0 = now;
+            else if (now - t0 > c.timeout_ns) {
+                shmemg_d_set_status(c, SHMEMG_ERR_TIMEOUT, detail);
+                return SHMEMG_ERR_TIMEOUT;
+            }
+            if (shmemg_d_get_status(c) != 0) return SHMEMG_ERR_DEVICE;
+        }
+        __nanosleep(ns);
+        if (ns < 512) ns <<= 1;
+    }
+}
+
+/* Team barrier at PE scope (all threads of the calling PE call it): quiet, then the
+ * leader runs the team barrier; the result is broadcast to the PE's threads. */
+static __device__ __forceinline__ int shmemg_d_team_sync_pe(const shmemg_device_ctx_t &c, int team, int64_t detail) {
+    __shared__ int shmemg_sync_rc;
+    const shmemg_dteam_t *t = shmemg_d_team(c, team);
+    int grp = 0;
+    int r = shmemg_d_team_rank(*t, shmemg_d_my_pe(c), &grp);
+    shmemg_d_pe_sync(c);
+    if (threadIdx.x == 0) {
+        int rc = SHMEMG_SUCCESS;
+        if (r >= 0 && shmemg_d_pe_leader(c)) rc = shmemg_d_team_barrier_leader(c, t->bar_base + grp, (uint32_t)t->size, detail);
+        shmemg_sync_rc = rc;
+    }
+    shmemg_d_pe_sync(c);
+    int rc = shmemg_sync_rc;
+    if (c.pe_mode == SHMEMG_PE_MODE_CLUSTER) {
+        /* the leader CTA's result reaches the other CTAs through the status word */
+        if (rc == SHMEMG_SUCCESS && shmemg_d_get_status(c) != 0) rc = SHMEMG_ERR_DEVICE;
+    }
+    return rc;
+}
+static __device__ __forceinline__ int shmemg_d_barrier_all_pe(const shmemg_device_ctx_t &c, int64_t detail) {
+    return shmemg_d_team_sync_pe(c, SHMEMG_TEAM_WORLD, detail);
+}
+
+
+/* ------------------------------------------------------------------ reductions */
+
+template <typename V> struct shmemg_vadd;
+template <> struct shmemg_vadd<float4> {
+    static __device__ __forceinline__ float4 add(float4 a, float4 b) {
+        return make_float4(__fadd_rn(a.x, b.x), __fadd_rn(a.y, b.y), __fadd_rn(a.z, b.z), __fadd_rn(a.w, b.w));
+    }
+};
+template <> struct shmemg_vadd<float> {
+    static __device__ __forceinline__ float add(float a, float b) { return __fadd_rn(a, b); }
+};
+
+/* Sum of member values over the aligned rank block [r0, r0 + 2^L), by recursive
+ * halving: the rank-pairwise tree restricted to that block. */
+template <int L, typename V>
+static __device__ __forceinline__ V shmemg_tree_block(const uint8_t *heap, uint64_t H, int pe0, int pstride, int r0,
+                                                      uint64_t off) {
+    if constexpr (L == 0) {
+        return shmemg_ld_cg((const V *)(heap + (uint64_t)(pe0 + r0 * pstride) * H + off));
+    } else {
+        V a = shmemg_tree_block<L - 1, V>(heap, H, pe0, pstride, r0, off);
+        V b = shmemg_tree_block<L - 1, V>(heap, H, pe0, pstride, r0 + (1 << (L - 1)), off);
+        return shmemg_vadd<V>::add(a, b);
+    }
+}
+
+/* Fixed float reduction order: the rank-pairwise tree over P members (level by level,
+ * pairs (2i, 2i+1), an odd last value carried up).  It equals the sum of the aligned
+ * power-of-two rank blocks of P's binary expansion, combined from the right, which is
+ * how it is evaluated here (bitwise identical, order fixed for every P). */
+template <typename V>
+static __device__ __forceinline__ V shmemg_tree_sum(const uint8_t *heap, uint64_t H, int pe0, int pstride, int P,
+                                                    uint64_t off) {
+    V acc{};
+    bool have = false;
+#define SHMEMG_TB(b)                                                                     \
+    if (P & (1 << b)) {                                                                  \
+        V t = shmemg_tree_block<b, V>(heap, H, pe0, pstride, P & ~((2 << b) - 1), off);  \
+        acc = have ? shmemg_vadd<V>::add(t, acc) : t;                                    \
+        have = true;                                                                     \
+    }
+    SHMEMG_TB(0) SHMEMG_TB(1) SHMEMG_TB(2) SHMEMG_TB(3) SHMEMG_TB(4) SHMEMG_TB(5) SHMEMG_TB(6) SHMEMG_TB(7)
+#undef SHMEMG_TB
+    for (int b = 8; b < 31; b++) {
+        if (!(P & (1 << b))) continue;
+        /* aligned block of 2^b ranks = pairwise tree over its 2^(b-7) blocks of 128 */
+        int s0 = P & ~((2 << b) - 1);
+        int nsub = 1 << (b - 7);
+        V stack[24];
+        V v{};
+        for (int q = 0; q < nsub; q++) {
+            v = shmemg_tree_block<7, V>(heap, H, pe0, pstride, s0 + q * 128, off);
+            int cnt = q, j = 0;
+            while (cnt & 1) {
+                v = shmemg_vadd<V>::add(stack[j], v);
+                cnt >>= 1;
+                j++;
+            }
+            stack[j] = v;
+        }
+        acc = have ? shmemg_vadd<V>::add(v, acc) : v;
+        have = true;
+    }
+    return acc;
+}
+
+template <typename T> static __device__ __forceinline__ T shmemg_comb(T a, T b, int op);
+template <> __device__ __forceinline__ int32_t shmemg_comb<int32_t>(int32_t a, int32_t b, int op) {
+    return op == SHMEMG_SUM ? (int32_t)((uint32_t)a + (uint32_t)b) : op == SHMEMG_MAX ? max(a, b) : min(a, b);
+}
+template <> __device__ __forceinline__ int64_t shmemg_comb<int64_t>(int64_t a, int64_t b, int op) {
+    return op == SHMEMG_SUM ? (int64_t)((uint64_t)a + (uint64_t)b) : op == SHMEMG_MAX ? max(a, b) : min(a, b);
+}
+template <> __device__ __forceinline__ float shmemg_comb<float>(float a, float b, int op) {
+    return op == SHMEMG_MAX ? (b > a ? b : a) : (b < a ? b : a);  /* sums use the tree */
+}
+
+/* Slice-owner reduce of vectors [v0, v1) (V = T or a 16-byte vector of T): each thread
+ * of g owns vectors, reads them from the P members pe0 + r*pstride, combines (integer
+ * sums wrap; float sums by the rank-pairwise tree; max/min exact) and writes the result
+ * to every member's dst. */
+template <typename T, typename V, int OP>
+static __device__ __forceinline__ void shmemg_d_reduce_vecs(shmemg_group g, uint8_t *heap, uint64_t H, int pe0,
+                                                           int pstride, int P, uint64_t dst_off, uint64_t src_off,
+                                                           uint64_t v0, uint64_t v1) {
+    constexpr int NL = sizeof(V) / sizeof(T);
+    for (uint64_t vi = v0 + g.rank; vi < v1; vi += g.size) {
+        const uint64_t off = src_off + vi * sizeof(V);
+        V acc;
+        if constexpr (OP == SHMEMG_SUM && std::is_floating_point<T>::value) {
+            acc = shmemg_tree_sum<V>(heap, H, pe0, pstride, P, off);
+        } else {
+            acc = shmemg_ld_cg((const V *)(heap + (uint64_t)pe0 * H + off));
+            int r = 1;
+            for (; r + 3 < P; r += 4) {
+                V a = shmemg_ld_cg((const V *)(heap + (uint64_t)(pe0 + r * pstride) * H + off));
+                V b = shmemg_ld_cg((const V *)(heap + (uint64_t)(pe0 + (r + 1) * pstride) * H + off));
+                V d = shmemg_ld_cg((const V *)(heap + (uint64_t)(pe0 + (r + 2) * pstride) * H + off));
+                V e = shmemg_ld_cg((const V *)(heap + (uint64_t)(pe0 + (r + 3) * pstride) * H + off));
+#pragma unroll
+                for (int l = 0; l < NL; l++) {
+                    T &s = reinterpret_cast<T *>(&acc)[l];
+                    s = shmemg_comb<T>(s, reinterpret_cast<T *>(&a)[l], OP);
+                    s = shmemg_comb<T>(s, reinterpret_cast<T *>(&b)[l], OP);
+                    s = shmemg_comb<T>(s, reinterpret_cast<T *>(&d)[l], OP);
+                    s = shmemg_comb<T>(s, reinterpret_cast<T *>(&e)[l], OP);
+                }
+            }
+            for (; r < P; r++) {
+                V a = shmemg_ld_cg((const V *)(heap + (uint64_t)(pe0 + r * pstride) * H + off));
+#pragma unroll
+                for (int l = 0; l < NL; l++) {
+                    T &s = reinterpret_cast<T *>(&acc)[l];
+                    s = shmemg_comb<T>(s, reinterpret_cast<T *>(&a)[l], OP);
+                }
+            }
+        }
+        const uint64_t doff = dst_off + vi * sizeof(V);
+        for (int r = 0; r < P; r++) *(V *)(heap + (uint64_t)(pe0 + r * pstride) * H + doff) = acc;
+    }
+}
+
+/* dispatch on element type, op and vector width (16-byte vectors when every address
+ * and the element range allow it) */
+template <typename T, typename V16>
+static __device__ __forceinline__ void shmemg_d_reduce_elems_t(shmemg_group g, uint8_t *heap, uint64_t H, int pe0,
+                                                              int pstride, int P, uint64_t dst_off, uint64_t src_off,
+                                                              uint64_t e0, uint64_t e1, int op) {
+    constexpr uint64_t L = sizeof(V16) / sizeof(T);
+    const bool v16 = ((dst_off | src_off | (e0 * sizeof(T)) | (e1 * sizeof(T)) | H) & 15) == 0;
+    if (v16) {
+        if (op == SHMEMG_SUM) shmemg_d_reduce_vecs<T, V16, SHMEMG_SUM>(g, heap, H, pe0, pstride, P, dst_off, src_off, e0 / L, e1 / L);
+        else if (op == SHMEMG_MAX) shmemg_d_reduce_vecs<T, V16, SHMEMG_MAX>(g, heap, H, pe0, pstride, P, dst_off, src_off, e0 / L, e1 / L);
+        else shmemg_d_reduce_vecs<T, V16, SHMEMG_MIN>(g, heap, H, pe0, pstride, P, dst_off, src_off, e0 / L, e1 / L);
+    } else {
+        if (op == SHMEMG_SUM) shmemg_d_reduce_vecs<T, T, SHMEMG_SUM>(g, heap, H, pe0, pstride, P, dst_off, src_off, e0, e1);
+        else if (op == SHMEMG_MAX) shmemg_d_reduce_vecs<T, T, SHMEMG_MAX>(g, heap, H, pe0, pstride, P, dst_off, src_off, e0, e1);
+        else shmemg_d_reduce_vecs<T, T, SHMEMG_MIN>(g, heap, H, pe0, pstride, P, dst_off, src_off, e0, e1);
+    }
+}
+static __device__ __forceinline__ void shmemg_d_reduce_elems(shmemg_group g, uint8_t *heap, uint64_t H, int pe0,
+                                                            int pstride, int P, uint64_t dst_off, uint64_t src_off,
+                                                            uint64_t e0, uint64_t e1, int dtype, int op) {
+    if (dtype == SHMEMG_INT32) shmemg_d_reduce_elems_t<int32_t, int4>(g, heap, H, pe0, pstride, P, dst_off, src_off, e0, e1, op);
+    else if (dtype == SHMEMG_INT64) shmemg_d_reduce_elems_t<int64_t, longlong2>(g, heap, H, pe0, pstride, P, dst_off, src_off, e0, e1, op);
+    else shmemg_d_reduce_elems_t<float, float4>(g, heap, H, pe0, pstride, P, dst_off, src_off, e0, e1, op);
+}
+
+/* Group-wide copy of src to the same offset `dst_off` of P members (one read, P
+ * writes per vector). */
+template <typename V>
+static __device__ __forceinline__ void shmemg_d_replicate_vec(shmemg_group g, uint8_t *heap, uint64_t H, int pe0,
+                                                             int pstride, int P, uint64_t dst_off, const V *src,
+                                                             uint64_t v0, uint64_t v1) {
+    for (uint64_t vi = v0 + g.rank; vi < v1; vi += g.size) {
+        V a = shmemg_ld_cg(src + vi);
+        for (int r = 0; r < P; r++) ((V *)(heap + (uint64_t)(pe0 + r * pstride) * H + dst_off))[vi] = a;
+    }
+}
+/* bytes [b0, b1) of src -> the same bytes of dst_off on every member */
+static __device__ __forceinline__ void shmemg_d_replicate_bytes(shmemg_group g, uint8_t *heap, uint64_t H, int pe0,
+                                                               int pstride, int P, uint64_t dst_off, const uint8_t *src,
+                                                               uint64_t b0, uint64_t b1) {
+    const int w = shmemg_d_vec_width((const void *)(heap + dst_off), src, b0 | b1 | H);
+    switch (w) {
+    case 16: shmemg_d_replicate_vec(g, heap, H, pe0, pstride, P, dst_off, (const uint4 *)src, b0 / 16, b1 / 16); break;
+    case 8: shmemg_d_replicate_vec(g, heap, H, pe0, pstride, P, dst_off, (const uint2 *)src, b0 / 8, b1 / 8); break;
+    case 4: shmemg_d_replicate_vec(g, heap, H, pe0, pstride, P, dst_off, (const uint32_t *)src, b0 / 4, b1 / 4); break;
+    case 2: shmemg_d_replicate_vec(g, heap, H, pe0, pstride, P, dst_off, (const uint16_t *)src, b0 / 2, b1 / 2); break;
+    default: shmemg_d_replicate_vec(g, heap, H, pe0, pstride, P, dst_off, (const uint8_t *)src, b0, b1); break;
+    }
+}
+
+/* slice [lo, hi) of `total` units owned by rank r of P, in multiples of `gran` units */
+static __device__ __forceinline__ void shmemg_d_slice(uint64_t total, int r, int P, uint64_t gran, uint64_t *lo,
+                                                      uint64_t *hi) {
+    uint64_t blocks = (total + gran - 1) / gran;
+    uint64_t b0 = blocks * (uint64_t)r / (uint64_t)P, b1 = blocks * (uint64_t)(r + 1) / (uint64_t)P;
+    *lo = b0 * gran < total ? b0 * gran : total;
+    *hi = b1 * gran < total ? b1 * gran : total;
+}
+
+/* ------------------------------------------------------------------ device collectives */
+/* PE-scope team collectives (every thread of every member PE calls with identical
+ * arguments: Sec. 6.3 uniform participation).  Each quiets and synchronises the team
+ * on entry and exit; in between, member r does its share: a slice of the elements or
+ * bytes (reduce, broadcast) or its own blocks (fcollect, alltoall).  Offsets are
+ * symmetric byte offsets.  Return SHMEMG_SUCCESS or a timeout / device error. */
+static __device__ __forceinline__ int shmemg_d_reduce_pe(const shmemg_device_ctx_t &c, int team, uint64_t dst_off,
+                                                         uint64_t src_off, uint64_t nelems, int dtype, int op,
+                                                         int64_t detail) {
+    const shmemg_dteam_t t = *shmemg_d_team(c, team);
+    int grp = 0, r = shmemg_d_team_rank(t, shmemg_d_my_pe(c), &grp);
+    if (r < 0) return SHMEMG_SUCCESS;
+    int rc = shmemg_d_team_sync_pe(c, team, detail);
+    if (rc) return rc;
+    uint64_t es = dtype == SHMEMG_INT64 ? 8 : 4, lo, hi;
+    shmemg_d_slice(nelems, r, t.size, 16 / es, &lo, &hi);
+    shmemg_d_reduce_elems(shmemg_d_group_pe(c), c.heap, c.pe_stride, shmemg_d_team_member(t, grp, 0), t.stride,
+                          t.size, dst_off, src_off, lo, hi, dtype, op);
+    return shmemg_d_team_sync_pe(c, team, detail);
+}
+static __device__ __forceinline__ int shmemg_d_broadcastmem_pe(const shmemg_device_ctx_t &c, int team, uint64_t dst_off,
+                                                               uint64_t src_off, uint64_t n, int root, int64_t detail) {
+    const shmemg_dteam_t t = *shmemg_d_team(c, team);
+    int grp = 0, r = shmemg_d_team_rank(t, shmemg_d_my_pe(c), &grp);
+    if (r < 0) return SHMEMG_SUCCESS;
+    int rc = shmemg_d_team_sync_pe(c, team, detail);
+    if (rc) return rc;
+    uint64_t lo, hi;
+    shmemg_d_slice(n, r, t.size, 16, &lo, &hi);
+    const uint8_t *src = shmemg_d_addr(c, shmemg_d_team_member(t, grp, root), src_off);
+    shmemg_d_replicate_bytes(shmemg_d_group_pe(c), c.heap, c.pe_stride, shmemg_d_team_member(t, grp, 0), t.stride,
+                             t.size, dst_off, src, lo, hi);
+    return shmemg_d_team_sync_pe(c, team, detail);
+}
+static __device__ __forceinline__ int shmemg_d_fcollectmem_pe(const shmemg_device_ctx_t &c, int team, uint64_t dst_off,
+                                                              uint64_t src_off, uint64_t n, int64_t detail) {
+    const shmemg_dteam_t t = *shmemg_d_team(c, team);
+    int grp = 0, r = shmemg_d_team_rank(t, shmemg_d_my_pe(c), &grp);
+    if (r < 0) return SHMEMG_SUCCESS;
+    int rc = shmemg_d_team_sync_pe(c, team, detail);
+    if (rc) return rc;
+    const uint8_t *src = shmemg_d_addr(c, shmemg_d_team_member(t, grp, r), src_off);
+    shmemg_d_replicate_bytes(shmemg_d_group_pe(c), c.heap, c.pe_stride, shmemg_d_team_member(t, grp, 0), t.stride,
+                             t.size, dst_off + (uint64_t)r * n, src, 0, n);
+    return shmemg_d_team_sync_pe(c, team, detail);
+}
+static __device__ __forceinline__ int shmemg_d_alltoallmem_pe(const shmemg_device_ctx_t &c, int team, uint64_t dst_off,
+                                                              uint64_t src_off, uint64_t n, int64_t detail) {
+    const shmemg_dteam_t t = *shmemg_d_team(c, team);
+    int grp = 0, r = shmemg_d_team_rank(t, shmemg_d_my_pe(c), &grp);
+    if (r < 0) return SHMEMG_SUCCESS;
+    int rc = shmemg_d_team_sync_pe(c, team, detail);
+    if (rc) return rc;
+    const int me = shmemg_d_team_member(t, grp, r);
+    for (int j = 0; j < t.size; j++) {
+        int pj = shmemg_d_team_member(t, grp, j);
+        shmemg_d_copy_group(shmemg_d_group_pe(c), shmemg_d_addr(c, pj, dst_off + (uint64_t)r * n),
+                            shmemg_d_addr(c, me, src_off + (uint64_t)j * n), n);
+    }
+    return shmemg_d_team_sync_pe(c, team, detail);
+}
+
+#endif /* SHMEMG_DEVICE_CUH */

@@ -1,0 +1,483 @@
+// Host-issued, stream-triggered operations (paper Sec. 6.3: "an implementation may
+// use internal GPU kernels to accelerate a host-issued or stream-triggered
+// operation"): RMA, AMOs, put-with-signal, wait, and the team collectives, each one
+// full-grid kernel on the caller's stream.
+//
+// Data movement is split into work items of one chunk (blockDim x 4 vectors); a CTA
+// takes items round-robin, each thread keeps its 4 vector loads in flight before it
+// stores them (to one destination, or to every team member for broadcast/fcollect).
+// Reductions use a slice-owner schedule: a thread owns a vector of elements, reads it
+// from every member, combines, and writes the result to every member.
+#include <cuda_runtime.h>
+
+#include <cstring>
+#include <type_traits>
+
+#include "internal.h"
+
+namespace shmemg {
+
+enum XKind { X_COPY = 0, X_A2A = 1, X_BCAST = 2, X_FCOLLECT = 3 };
+constexpr int XFER_THREADS = 512;
+constexpr int XFER_U = 4;
+constexpr int RED_THREADS = 256;
+constexpr int RED_U = 2;
+
+struct Xfer {
+    uint8_t *heap;
+    uint64_t H;
+    int kind;
+    int start, stride, size, gstride;  // team; blockIdx.y = group
+    int root;
+    int dst_pe, src_pe;                // X_COPY
+    uint64_t dst_off, src_off;
+    uint64_t seg_vec;                  // vectors per segment
+    uint64_t chunk_vec;                // vectors per item
+    uint64_t chunks_per_seg;
+    uint64_t nitems;                   // items per group
+};
+
+template <typename V>
+__device__ __forceinline__ void xfer_items(const Xfer &x, uint64_t first, uint64_t step) {
+    const int grp = blockIdx.y;
+    const int base_pe = x.start + grp * x.gstride;
+    for (uint64_t item = first; item < x.nitems; item += step) {
+        uint64_t seg = item / x.chunks_per_seg;
+        uint64_t ch = item - seg * x.chunks_per_seg;
+        uint64_t v0 = ch * x.chunk_vec;
+        uint64_t nv = x.seg_vec - v0 < x.chunk_vec ? x.seg_vec - v0 : x.chunk_vec;
+        const uint64_t segb = x.seg_vec * sizeof(V);
+        const V *src;
+        V *dst = nullptr;
+        uint64_t dst_off = x.dst_off;
+        bool replicate = false;
+        if (x.kind == X_COPY) {
+            src = (const V *)(x.heap + (uint64_t)x.src_pe * x.H + x.src_off);
+            dst = (V *)(x.heap + (uint64_t)x.dst_pe * x.H + x.dst_off);
+        } else if (x.kind == X_A2A) {
+            int i = (int)(seg / (uint64_t)x.size), j = (int)(seg - (uint64_t)i * x.size);
+            src = (const V *)(x.heap + (uint64_t)(base_pe + i * x.stride) * x.H + x.src_off + (uint64_t)j * segb);
+            dst = (V *)(x.heap + (uint64_t)(base_pe + j * x.stride) * x.H + x.dst_off + (uint64_t)i * segb);
+        } else if (x.kind == X_BCAST) {
+            src = (const V *)(x.heap + (uint64_t)(base_pe + x.root * x.stride) * x.H + x.src_off);
+            replicate = true;
+        } else {  // X_FCOLLECT: source = member seg, placed at block seg of every dst
+            src = (const V *)(x.heap + (uint64_t)(base_pe + (int)seg * x.stride) * x.H + x.src_off);
+            dst_off = x.dst_off + seg * segb;
+            replicate = true;
+        }
+        V buf[XFER_U];
+#pragma unroll
+        for (int u = 0; u < XFER_U; u++) {
+            uint64_t idx = threadIdx.x + (uint64_t)u * blockDim.x;
+            if (idx < nv) buf[u] = shmemg_ld_cg(src + v0 + idx);
+        }
+        if (!replicate) {
+#pragma unroll
+            for (int u = 0; u < XFER_U; u++) {
+                uint64_t idx = threadIdx.x + (uint64_t)u * blockDim.x;
+                if (idx < nv) dst[v0 + idx] = buf[u];
+            }
+        } else {
+            for (int r = 0; r < x.size; r++) {
+                V *d = (V *)(x.heap + (uint64_t)(base_pe + r * x.stride) * x.H + dst_off);
+#pragma unroll
+                for (int u = 0; u < XFER_U; u++) {
+                    uint64_t idx = threadIdx.x + (uint64_t)u * blockDim.x;
+                    if (idx < nv) d[v0 + idx] = buf[u];
+                }
+            }
+        }
+    }
+}
+
+template <typename V>
+__global__ void __launch_bounds__(XFER_THREADS) k_xfer(Xfer x) { xfer_items<V>(x, blockIdx.x, gridDim.x); }
+
+// put-with-signal: the copy, then the last CTA to finish releases the signal
+template <typename V>
+__global__ void __launch_bounds__(XFER_THREADS) k_put_signal(Xfer x, uint64_t *sig, uint64_t val, int op,
+                                                             uint32_t *done) {
+    xfer_items<V>(x, blockIdx.x, gridDim.x);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        shmemg_d_fence_gpu();
+        uint32_t d = atomicAdd(done, 1u);
+        if (d == gridDim.x - 1) {
+            *done = 0;
+            shmemg_d_fence_gpu();
+            shmemg_d_signal_op(sig, val, op);
+        }
+    }
+}
+
+// ------------------------------------------------------------------ reductions
+struct Red {
+    uint8_t *heap;
+    uint64_t H;
+    int start, stride, size, gstride;
+    uint64_t dst_off, src_off;
+    uint64_t nvec;        // vectors (V) per member
+    uint64_t chunk_vec;
+    uint64_t nitems;
+};
+
+template <typename T, typename V, int OP>
+__global__ void __launch_bounds__(RED_THREADS) k_reduce(Red x) {
+    const int pe0 = x.start + blockIdx.y * x.gstride;
+    const shmemg_group g = {threadIdx.x, blockDim.x};
+    for (uint64_t item = blockIdx.x; item < x.nitems; item += gridDim.x) {
+        const uint64_t v0 = item * x.chunk_vec;
+        const uint64_t v1 = v0 + x.chunk_vec < x.nvec ? v0 + x.chunk_vec : x.nvec;
+        shmemg_d_reduce_vecs<T, V, OP>(g, x.heap, x.H, pe0, x.stride, x.size, x.dst_off, x.src_off, v0, v1);
+    }
+}
+
+// ------------------------------------------------------------------ single-thread ops
+template <typename T>
+__global__ void k_amo(T *addr, int kind, T v, T cond, T *fetched) {
+    T old;
+    if (kind == SHMEMG_OP_FETCH_ADD) old = atomicAdd(addr, v);
+    else if (kind == SHMEMG_OP_COMPARE_SWAP) old = atomicCAS(addr, cond, v);
+    else old = atomicXor(addr, v);
+    if (fetched) *fetched = old;
+}
+
+__global__ void k_wait(shmemg_device_ctx_t c, const uint64_t *sig, int cmp, uint64_t val) {
+    shmemg_d_signal_wait_until(c, sig, cmp, val, -1);
+}
+
+// ------------------------------------------------------------------ launch helpers
+static int vec_width(uint64_t m) {
+    return (m & 15) == 0 ? 16 : (m & 7) == 0 ? 8 : (m & 3) == 0 ? 4 : (m & 1) == 0 ? 2 : 1;
+}
+
+template <typename V>
+static int launch_xfer_v(Xfer x, int ngroups, cudaStream_t s, uint64_t *sig, uint64_t val, int op, uint32_t *done) {
+    x.seg_vec /= sizeof(V);
+    x.chunk_vec = (uint64_t)XFER_THREADS * XFER_U;
+    x.chunks_per_seg = (x.seg_vec + x.chunk_vec - 1) / x.chunk_vec;
+    if (x.chunks_per_seg == 0) x.chunks_per_seg = 1;
+    uint64_t nseg = x.kind == X_A2A ? (uint64_t)x.size * x.size : x.kind == X_FCOLLECT ? (uint64_t)x.size : 1;
+    x.nitems = x.seg_vec ? nseg * x.chunks_per_seg : 0;
+    if (x.nitems == 0 && !sig) return SHMEMG_SUCCESS;
+    const void *kfn = sig ? (const void *)k_put_signal<V> : (const void *)k_xfer<V>;
+    uint64_t cap = (uint64_t)ctas_for(kfn, XFER_THREADS, 0);
+    uint64_t gx = x.nitems < cap ? x.nitems : cap;
+    if (gx == 0) gx = 1;
+    dim3 grid((unsigned)gx, (unsigned)ngroups);
+    if (sig) k_put_signal<V><<<grid, XFER_THREADS, 0, s>>>(x, sig, val, op, done);
+    else k_xfer<V><<<grid, XFER_THREADS, 0, s>>>(x);
+    return cuda_rc(cudaGetLastError());
+}
+
+// x.seg_vec carries the segment length in BYTES on entry
+static int launch_xfer(Xfer x, int ngroups, uint64_t align_bits, cudaStream_t s, uint64_t *sig = nullptr,
+                       uint64_t val = 0, int op = 0, uint32_t *done = nullptr) {
+    switch (vec_width(align_bits | x.seg_vec)) {
+    case 16: return launch_xfer_v<uint4>(x, ngroups, s, sig, val, op, done);
+    case 8: return launch_xfer_v<uint2>(x, ngroups, s, sig, val, op, done);
+    case 4: return launch_xfer_v<uint32_t>(x, ngroups, s, sig, val, op, done);
+    case 2: return launch_xfer_v<uint16_t>(x, ngroups, s, sig, val, op, done);
+    default: return launch_xfer_v<uint8_t>(x, ngroups, s, sig, val, op, done);
+    }
+}
+
+static Xfer xfer_base() {
+    Xfer x;
+    memset(&x, 0, sizeof(x));
+    x.heap = st().heap;
+    x.H = st().H;
+    x.stride = 1;
+    return x;
+}
+
+static int rma(void *dst, const void *src, uint64_t n, int dst_pe, int src_pe, void *stream) {
+    if (int rc = check_init()) return rc;
+    if (check_pe(dst_pe) || check_pe(src_pe)) return SHMEMG_ERR_INVALID_ARG;
+    uint64_t doff, soff;
+    if (sym_offset(dst, n, &doff) || sym_offset(src, n, &soff)) return SHMEMG_ERR_NOT_SYMMETRIC;
+    if (n == 0) return SHMEMG_SUCCESS;
+    Xfer x = xfer_base();
+    x.kind = X_COPY;
+    x.size = 1;
+    x.dst_pe = dst_pe;
+    x.src_pe = src_pe;
+    x.dst_off = doff;
+    x.src_off = soff;
+    x.seg_vec = n;
+    return launch_xfer(x, 1, doff | soff, to_stream(stream));
+}
+
+template <typename V, typename T, int OP>
+static int launch_red_v(Red r, int ngroups, cudaStream_t s) {
+    r.nvec /= (sizeof(V) / sizeof(T));
+    r.chunk_vec = (uint64_t)RED_THREADS * RED_U;
+    r.nitems = (r.nvec + r.chunk_vec - 1) / r.chunk_vec;
+    if (r.nitems == 0) return SHMEMG_SUCCESS;
+    const void *kfn = (const void *)k_reduce<T, V, OP>;
+    uint64_t cap = (uint64_t)ctas_for(kfn, RED_THREADS, 0);
+    dim3 grid((unsigned)(r.nitems < cap ? r.nitems : cap), (unsigned)ngroups);
+    k_reduce<T, V, OP><<<grid, RED_THREADS, 0, s>>>(r);
+    return cuda_rc(cudaGetLastError());
+}
+
+template <typename T, typename V16, int OP>
+static int launch_red(Red r, int ngroups, bool vec_ok, cudaStream_t s) {
+    return vec_ok ? launch_red_v<V16, T, OP>(r, ngroups, s) : launch_red_v<T, T, OP>(r, ngroups, s);
+}
+
+}  // namespace shmemg
+
+using namespace shmemg;
+
+// ================================================================== C ABI
+extern "C" {
+
+int shmemg_putmem(void *dst, const void *src, uint64_t n, int pe, int issuer, void *stream) {
+    return rma(dst, src, n, pe, issuer, stream);
+}
+int shmemg_putmem_nbi(void *dst, const void *src, uint64_t n, int pe, int issuer, void *stream) {
+    return rma(dst, src, n, pe, issuer, stream);
+}
+int shmemg_getmem(void *dst, const void *src, uint64_t n, int pe, int issuer, void *stream) {
+    return rma(dst, src, n, issuer, pe, stream);
+}
+int shmemg_getmem_nbi(void *dst, const void *src, uint64_t n, int pe, int issuer, void *stream) {
+    return rma(dst, src, n, issuer, pe, stream);
+}
+
+}  // extern "C"
+
+template <typename T>
+static int amo(T *target, int kind, T v, T cond, int pe, T *fetched, void *stream) {
+    if (int rc = check_init()) return rc;
+    if (check_pe(pe)) return SHMEMG_ERR_INVALID_ARG;
+    uint64_t off;
+    if (sym_offset(target, sizeof(T), &off)) return SHMEMG_ERR_NOT_SYMMETRIC;
+    if (off % sizeof(T)) return SHMEMG_ERR_INVALID_ARG;
+    T *addr = (T *)(st().heap + (uint64_t)pe * st().H + off);
+    k_amo<T><<<1, 1, 0, to_stream(stream)>>>(addr, kind, v, cond, fetched);
+    return cuda_rc(cudaGetLastError());
+}
+
+extern "C" {
+
+int shmemg_int64_atomic_fetch_add(int64_t *t, int64_t v, int pe, int64_t *f, void *s) {
+    return amo<unsigned long long>((unsigned long long *)t, SHMEMG_OP_FETCH_ADD, (unsigned long long)v, 0ull, pe,
+                                   (unsigned long long *)f, s);
+}
+int shmemg_int64_atomic_compare_swap(int64_t *t, int64_t c, int64_t v, int pe, int64_t *f, void *s) {
+    return amo<unsigned long long>((unsigned long long *)t, SHMEMG_OP_COMPARE_SWAP, (unsigned long long)v,
+                                   (unsigned long long)c, pe, (unsigned long long *)f, s);
+}
+int shmemg_int64_atomic_fetch_xor(int64_t *t, int64_t v, int pe, int64_t *f, void *s) {
+    return amo<unsigned long long>((unsigned long long *)t, SHMEMG_OP_FETCH_XOR, (unsigned long long)v, 0ull, pe,
+                                   (unsigned long long *)f, s);
+}
+int shmemg_int32_atomic_fetch_add(int32_t *t, int32_t v, int pe, int32_t *f, void *s) {
+    return amo<int>((int *)t, SHMEMG_OP_FETCH_ADD, v, 0, pe, (int *)f, s);
+}
+int shmemg_int32_atomic_compare_swap(int32_t *t, int32_t c, int32_t v, int pe, int32_t *f, void *s) {
+    return amo<int>((int *)t, SHMEMG_OP_COMPARE_SWAP, v, c, pe, (int *)f, s);
+}
+int shmemg_int32_atomic_fetch_xor(int32_t *t, int32_t v, int pe, int32_t *f, void *s) {
+    return amo<int>((int *)t, SHMEMG_OP_FETCH_XOR, v, 0, pe, (int *)f, s);
+}
+
+int shmemg_putmem_signal(void *dst, const void *src, uint64_t n, uint64_t *sig, uint64_t sigval, int sig_op,
+                         int pe, int issuer, void *stream) {
+    if (int rc = check_init()) return rc;
+    if (check_pe(pe) || check_pe(issuer)) return SHMEMG_ERR_INVALID_ARG;
+    if (sig_op != SHMEMG_SIGNAL_SET && sig_op != SHMEMG_SIGNAL_ADD) return SHMEMG_ERR_INVALID_ARG;
+    uint64_t doff, soff, goff;
+    if (sym_offset(dst, n, &doff) || sym_offset(src, n, &soff) || sym_offset(sig, 8, &goff))
+        return SHMEMG_ERR_NOT_SYMMETRIC;
+    if (goff & 7) return SHMEMG_ERR_INVALID_ARG;
+    State &S = st();
+    Xfer x = xfer_base();
+    x.kind = X_COPY;
+    x.size = 1;
+    x.dst_pe = pe;
+    x.src_pe = issuer;
+    x.dst_off = doff;
+    x.src_off = soff;
+    x.seg_vec = n;
+    uint32_t *done = (uint32_t *)(S.base + SHMEMG_SCRATCH_OFF + SCR_SIGNAL_DONE) +
+                     (S.call_seq++ % SCR_SIGNAL_DONE_SLOTS);
+    uint64_t *sig_addr = (uint64_t *)(S.heap + (uint64_t)pe * S.H + goff);
+    return launch_xfer(x, 1, doff | soff, to_stream(stream), sig_addr, sigval, sig_op, done);
+}
+
+int shmemg_signal_wait_until(uint64_t *sig, int pe, int cmp, uint64_t value, void *stream) {
+    if (int rc = check_init()) return rc;
+    if (check_pe(pe) || cmp < SHMEMG_CMP_EQ || cmp > SHMEMG_CMP_LE) return SHMEMG_ERR_INVALID_ARG;
+    uint64_t off;
+    if (sym_offset(sig, 8, &off) || (off & 7)) return SHMEMG_ERR_NOT_SYMMETRIC;
+    k_wait<<<1, 1, 0, to_stream(stream)>>>(device_ctx(), (const uint64_t *)(st().heap + (uint64_t)pe * st().H + off),
+                                          cmp, value);
+    return cuda_rc(cudaGetLastError());
+}
+
+// --------------------------------------------------------------- collectives
+static int coll_prep(shmemg_team_t team, HostTeam *t) {
+    if (int rc = check_init()) return rc;
+    if (team_get(team, t)) return SHMEMG_ERR_INVALID_ARG;
+    return SHMEMG_SUCCESS;
+}
+
+static Xfer team_xfer(const HostTeam &t, int kind) {
+    Xfer x = xfer_base();
+    x.kind = kind;
+    x.start = t.start;
+    x.stride = t.stride;
+    x.size = t.size;
+    x.gstride = t.gstride;
+    return x;
+}
+
+int shmemg_broadcastmem(shmemg_team_t team, void *dst, const void *src, uint64_t n, int root, void *stream) {
+    HostTeam t;
+    if (int rc = coll_prep(team, &t)) return rc;
+    if (root < 0 || root >= t.size) return SHMEMG_ERR_INVALID_ARG;
+    uint64_t doff, soff;
+    if (sym_offset(dst, n, &doff) || sym_offset(src, n, &soff)) return SHMEMG_ERR_NOT_SYMMETRIC;
+    if (n == 0) return SHMEMG_SUCCESS;
+    Xfer x = team_xfer(t, X_BCAST);
+    x.root = root;
+    x.dst_off = doff;
+    x.src_off = soff;
+    x.seg_vec = n;
+    return launch_xfer(x, t.ngroups, doff | soff, to_stream(stream));
+}
+
+int shmemg_fcollectmem(shmemg_team_t team, void *dst, const void *src, uint64_t n, void *stream) {
+    HostTeam t;
+    if (int rc = coll_prep(team, &t)) return rc;
+    uint64_t doff, soff;
+    if (sym_offset(dst, n * (uint64_t)t.size, &doff) || sym_offset(src, n, &soff)) return SHMEMG_ERR_NOT_SYMMETRIC;
+    if (n == 0) return SHMEMG_SUCCESS;
+    Xfer x = team_xfer(t, X_FCOLLECT);
+    x.dst_off = doff;
+    x.src_off = soff;
+    x.seg_vec = n;
+    return launch_xfer(x, t.ngroups, doff | soff, to_stream(stream));
+}
+
+int shmemg_alltoallmem(shmemg_team_t team, void *dst, const void *src, uint64_t n, void *stream) {
+    HostTeam t;
+    if (int rc = coll_prep(team, &t)) return rc;
+    uint64_t doff, soff;
+    uint64_t tot = n * (uint64_t)t.size;
+    if (sym_offset(dst, tot, &doff) || sym_offset(src, tot, &soff)) return SHMEMG_ERR_NOT_SYMMETRIC;
+    if (n == 0) return SHMEMG_SUCCESS;
+    Xfer x = team_xfer(t, X_A2A);
+    x.dst_off = doff;
+    x.src_off = soff;
+    x.seg_vec = n;
+    return launch_xfer(x, t.ngroups, doff | soff, to_stream(stream));
+}
+
+int shmemg_reduce(shmemg_team_t team, void *dst, const void *src, uint64_t nelems, int dtype, int op,
+                  void *stream) {
+    HostTeam t;
+    if (int rc = coll_prep(team, &t)) return rc;
+    if (op != SHMEMG_SUM && op != SHMEMG_MAX && op != SHMEMG_MIN) return SHMEMG_ERR_INVALID_ARG;
+    uint64_t es = dtype == SHMEMG_INT64 ? 8 : (dtype == SHMEMG_INT32 || dtype == SHMEMG_FLOAT) ? 4 : 0;
+    if (!es) return SHMEMG_ERR_INVALID_ARG;
+    uint64_t doff, soff;
+    if (sym_offset(dst, nelems * es, &doff) || sym_offset(src, nelems * es, &soff)) return SHMEMG_ERR_NOT_SYMMETRIC;
+    if (doff % es || soff % es) return SHMEMG_ERR_INVALID_ARG;
+    // dst == src (in place) is fine: each element is read by its owner before written;
+    // partial overlaps are undefined
+    if (doff != soff && doff < soff + nelems * es && soff < doff + nelems * es) return SHMEMG_ERR_INVALID_ARG;
+    if (nelems == 0) return SHMEMG_SUCCESS;
+    Red r;
+    memset(&r, 0, sizeof(r));
+    r.heap = st().heap;
+    r.H = st().H;
+    r.start = t.start;
+    r.stride = t.stride;
+    r.size = t.size;
+    r.gstride = t.gstride;
+    r.dst_off = doff;
+    r.src_off = soff;
+    r.nvec = nelems;
+    bool v16 = ((doff | soff | (nelems * es)) & 15) == 0;
+    cudaStream_t s = to_stream(stream);
+    int g = t.ngroups;
+#define SHMEMG_RED(T, V) \
+    (op == SHMEMG_SUM ? launch_red<T, V, SHMEMG_SUM>(r, g, v16, s) \
+     : op == SHMEMG_MAX ? launch_red<T, V, SHMEMG_MAX>(r, g, v16, s) : launch_red<T, V, SHMEMG_MIN>(r, g, v16, s))
+    if (dtype == SHMEMG_INT32) return SHMEMG_RED(int32_t, int4);
+    if (dtype == SHMEMG_INT64) return SHMEMG_RED(int64_t, longlong2);
+    return SHMEMG_RED(float, float4);
+#undef SHMEMG_RED
+}
+
+#define SHMEMG_NAMED_REDUCE(name, T, DT, OP)                                                          \
+    int shmemg_##name##_reduce(shmemg_team_t team, T *dst, const T *src, uint64_t n, void *stream) { \
+        return shmemg_reduce(team, dst, src, n, DT, OP, stream);                                      \
+    }
+SHMEMG_NAMED_REDUCE(int32_sum, int32_t, SHMEMG_INT32, SHMEMG_SUM)
+SHMEMG_NAMED_REDUCE(int32_max, int32_t, SHMEMG_INT32, SHMEMG_MAX)
+SHMEMG_NAMED_REDUCE(int32_min, int32_t, SHMEMG_INT32, SHMEMG_MIN)
+SHMEMG_NAMED_REDUCE(int64_sum, int64_t, SHMEMG_INT64, SHMEMG_SUM)
+SHMEMG_NAMED_REDUCE(int64_max, int64_t, SHMEMG_INT64, SHMEMG_MAX)
+SHMEMG_NAMED_REDUCE(int64_min, int64_t, SHMEMG_INT64, SHMEMG_MIN)
+SHMEMG_NAMED_REDUCE(float_sum, float, SHMEMG_FLOAT, SHMEMG_SUM)
+SHMEMG_NAMED_REDUCE(float_max, float, SHMEMG_FLOAT, SHMEMG_MAX)
+SHMEMG_NAMED_REDUCE(float_min, float, SHMEMG_FLOAT, SHMEMG_MIN)
+
+// --------------------------------------------------------------- host script runner
+int shmemg_run_script_host(const shmemg_op_t *ops, int64_t nops, int64_t *fetched, void *stream) {
+    if (int rc = check_init()) return rc;
+    if (nops < 0 || (nops && !ops)) return SHMEMG_ERR_INVALID_ARG;
+    State &S = st();
+    for (int64_t i = 0; i < nops; i++) {
+        const shmemg_op_t &o = ops[i];
+        uint8_t *dst = S.heap + o.dst, *src = S.heap + o.src;
+        int rc = SHMEMG_SUCCESS;
+        switch (o.kind) {
+        case SHMEMG_OP_PUT: rc = shmemg_putmem(dst, src, o.n, o.pe, o.issuer, stream); break;
+        case SHMEMG_OP_PUT_NBI: rc = shmemg_putmem_nbi(dst, src, o.n, o.pe, o.issuer, stream); break;
+        case SHMEMG_OP_GET: rc = shmemg_getmem(dst, src, o.n, o.pe, o.issuer, stream); break;
+        case SHMEMG_OP_GET_NBI: rc = shmemg_getmem_nbi(dst, src, o.n, o.pe, o.issuer, stream); break;
+        case SHMEMG_OP_FETCH_ADD:
+        case SHMEMG_OP_COMPARE_SWAP:
+        case SHMEMG_OP_FETCH_XOR:
+            if (o.dtype == SHMEMG_INT64) {
+                if (o.kind == SHMEMG_OP_FETCH_ADD)
+                    rc = shmemg_int64_atomic_fetch_add((int64_t *)dst, o.operand, o.pe, fetched ? fetched + i : nullptr, stream);
+                else if (o.kind == SHMEMG_OP_COMPARE_SWAP)
+                    rc = shmemg_int64_atomic_compare_swap((int64_t *)dst, o.cond, o.operand, o.pe,
+                                                          fetched ? fetched + i : nullptr, stream);
+                else
+                    rc = shmemg_int64_atomic_fetch_xor((int64_t *)dst, o.operand, o.pe, fetched ? fetched + i : nullptr, stream);
+            } else {
+                rc = SHMEMG_ERR_UNSUPPORTED;  // int32 AMOs are host calls of their own
+            }
+            break;
+        case SHMEMG_OP_PUT_SIGNAL:
+            rc = shmemg_putmem_signal(dst, src, o.n, (uint64_t *)(S.heap + o.aux), (uint64_t)o.operand, o.sub, o.pe,
+                                      o.issuer, stream);
+            break;
+        case SHMEMG_OP_WAIT_UNTIL:
+            rc = shmemg_signal_wait_until((uint64_t *)dst, o.issuer, o.sub, (uint64_t)o.operand, stream);
+            break;
+        case SHMEMG_OP_BARRIER_ALL: rc = shmemg_barrier_all(stream); break;
+        case SHMEMG_OP_QUIET: rc = shmemg_quiet(stream); break;
+        case SHMEMG_OP_FENCE: rc = shmemg_fence(stream); break;
+        case SHMEMG_OP_TEAM_SYNC: rc = shmemg_team_sync(o.team, stream); break;
+        case SHMEMG_OP_BROADCAST: rc = shmemg_broadcastmem(o.team, dst, src, o.n, o.pe, stream); break;
+        case SHMEMG_OP_FCOLLECT: rc = shmemg_fcollectmem(o.team, dst, src, o.n, stream); break;
+        case SHMEMG_OP_ALLTOALL: rc = shmemg_alltoallmem(o.team, dst, src, o.n, stream); break;
+        case SHMEMG_OP_REDUCE: rc = shmemg_reduce(o.team, dst, src, o.n, o.dtype, o.sub, stream); break;
+        default: rc = SHMEMG_ERR_INVALID_ARG;
+        }
+        if (rc) return rc;
+    }
+    return SHMEMG_SUCCESS;
+}
+
+}  // extern "C"

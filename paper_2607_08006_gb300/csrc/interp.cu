@@ -1,0 +1,237 @@
+// Device-initiated execution of a scripted operation list (paper Sec. 6.3,
+// device-initiated path; Fig. 6b: put -> fence -> quiet issued by GPU threads).
+//
+// One cooperative launch holds every PE (a CTA, or a cluster of CTAs in pe_mode
+// CLUSTER).  Every PE walks the whole list; it issues, in list order, the RMA/AMO/signal
+// ops whose issuer it is, and its share of every collective of a team it belongs to.
+// Blocking RMA ends with a PE barrier (local completion, and later ops of the PE see
+// it); collectives and barriers quiet and synchronise their team on entry and exit.
+#include <cuda_runtime.h>
+
+#include <cstdlib>
+
+#include "internal.h"
+
+namespace shmemg {
+
+constexpr int INTERP_THREADS = 512;
+
+__global__ void __launch_bounds__(INTERP_THREADS) k_interp(shmemg_device_ctx_t c, const shmemg_op_t *ops,
+                                                           int64_t nops, int64_t *fetched) {
+    const int me = shmemg_d_my_pe(c);
+    const shmemg_group g = shmemg_d_group_pe(c);
+    const bool leader = shmemg_d_pe_leader(c);
+    __shared__ int s_rc;
+    for (int64_t i = 0; i < nops; i++) {
+        const shmemg_op_t o = ops[i];
+        int rc = SHMEMG_SUCCESS;
+        switch (o.kind) {
+        case SHMEMG_OP_PUT:
+        case SHMEMG_OP_PUT_NBI:
+            if (o.issuer == me) {
+                shmemg_d_copy_group(g, shmemg_d_addr(c, o.pe, o.dst), shmemg_d_addr(c, me, o.src), o.n);
+                if (o.kind == SHMEMG_OP_PUT) shmemg_d_pe_sync(c);
+            }
+            break;
+        case SHMEMG_OP_GET:
+        case SHMEMG_OP_GET_NBI:
+            if (o.issuer == me) {
+                shmemg_d_copy_group(g, shmemg_d_addr(c, me, o.dst), shmemg_d_addr(c, o.pe, o.src), o.n);
+                if (o.kind == SHMEMG_OP_GET) shmemg_d_pe_sync(c);
+            }
+            break;
+        case SHMEMG_OP_FETCH_ADD:
+        case SHMEMG_OP_COMPARE_SWAP:
+        case SHMEMG_OP_FETCH_XOR:
+            if (o.issuer == me && leader) {
+                int64_t old;
+                if (o.dtype == SHMEMG_INT64) {
+                    int64_t *t = (int64_t *)shmemg_d_addr(c, o.pe, o.dst);
+                    if (o.kind == SHMEMG_OP_FETCH_ADD)
+                        old = (int64_t)atomicAdd((unsigned long long *)t, (unsigned long long)o.operand);
+                    else if (o.kind == SHMEMG_OP_COMPARE_SWAP)
+                        old = (int64_t)atomicCAS((unsigned long long *)t, (unsigned long long)o.cond,
+                                                 (unsigned long long)o.operand);
+                    else
+                        old = (int64_t)atomicXor((unsigned long long *)t, (unsigned long long)o.operand);
+                } else {
+                    int *t = (int *)shmemg_d_addr(c, o.pe, o.dst);
+                    if (o.kind == SHMEMG_OP_FETCH_ADD) old = atomicAdd(t, (int)o.operand);
+                    else if (o.kind == SHMEMG_OP_COMPARE_SWAP) old = atomicCAS(t, (int)o.cond, (int)o.operand);
+                    else old = atomicXor(t, (int)o.operand);
+                }
+                if (fetched) fetched[i] = old;
+            }
+            break;
+        case SHMEMG_OP_PUT_SIGNAL:
+            if (o.issuer == me) {
+                shmemg_d_copy_group(g, shmemg_d_addr(c, o.pe, o.dst), shmemg_d_addr(c, me, o.src), o.n);
+                shmemg_d_pe_sync(c);
+                if (leader) {
+                    shmemg_d_fence_gpu();
+                    shmemg_d_signal_op((uint64_t *)shmemg_d_addr(c, o.pe, o.aux), (uint64_t)o.operand, o.sub);
+                }
+            }
+            break;
+        case SHMEMG_OP_WAIT_UNTIL:
+            if (o.issuer == me) {
+                if (threadIdx.x == 0) {
+                    int w = SHMEMG_SUCCESS;
+                    if (leader) w = shmemg_d_signal_wait_until(c, (const uint64_t *)shmemg_d_addr(c, me, o.dst), o.sub,
+                                                               (uint64_t)o.operand, i);
+                    s_rc = w;
+                }
+                shmemg_d_pe_sync(c);
+                rc = s_rc;
+                if (c.pe_mode == SHMEMG_PE_MODE_CLUSTER && shmemg_d_get_status(c) != 0) rc = SHMEMG_ERR_DEVICE;
+            }
+            break;
+        case SHMEMG_OP_QUIET:
+        case SHMEMG_OP_FENCE:
+            if (o.issuer == me || o.issuer < 0) shmemg_d_quiet_pe(c);
+            break;
+        case SHMEMG_OP_BARRIER_ALL:
+            rc = shmemg_d_barrier_all_pe(c, i);
+            break;
+        case SHMEMG_OP_TEAM_SYNC: {
+            int grp;
+            if (shmemg_d_team_rank(*shmemg_d_team(c, o.team), me, &grp) >= 0) rc = shmemg_d_team_sync_pe(c, o.team, i);
+            break;
+        }
+        case SHMEMG_OP_BROADCAST:
+            rc = shmemg_d_broadcastmem_pe(c, o.team, o.dst, o.src, o.n, o.pe, i);
+            break;
+        case SHMEMG_OP_FCOLLECT:
+            rc = shmemg_d_fcollectmem_pe(c, o.team, o.dst, o.src, o.n, i);
+            break;
+        case SHMEMG_OP_ALLTOALL:
+            rc = shmemg_d_alltoallmem_pe(c, o.team, o.dst, o.src, o.n, i);
+            break;
+        case SHMEMG_OP_REDUCE:
+            rc = shmemg_d_reduce_pe(c, o.team, o.dst, o.src, o.n, o.dtype, o.sub, i);
+            break;
+        default:
+            if (leader) shmemg_d_set_status(c, SHMEMG_ERR_INVALID_ARG, i);
+            rc = SHMEMG_ERR_INVALID_ARG;
+        }
+        if (rc != SHMEMG_SUCCESS) break;
+    }
+    shmemg_d_quiet_pe(c);
+}
+
+// host-side validation of one op (ranges, PEs, teams); returns SHMEMG_* code
+static int validate_op(const shmemg_op_t &o) {
+    State &S = st();
+    auto in = [&](uint64_t off, uint64_t n) { return off <= S.H && n <= S.H - off; };
+    auto pe_ok = [&](int p) { return p >= 0 && p < S.npes; };
+    switch (o.kind) {
+    case SHMEMG_OP_PUT: case SHMEMG_OP_PUT_NBI: case SHMEMG_OP_GET: case SHMEMG_OP_GET_NBI:
+        return pe_ok(o.pe) && pe_ok(o.issuer) && in(o.dst, o.n) && in(o.src, o.n) ? 0 : SHMEMG_ERR_INVALID_ARG;
+    case SHMEMG_OP_FETCH_ADD: case SHMEMG_OP_COMPARE_SWAP: case SHMEMG_OP_FETCH_XOR: {
+        uint64_t es = o.dtype == SHMEMG_INT64 ? 8 : o.dtype == SHMEMG_INT32 ? 4 : 0;
+        return es && pe_ok(o.pe) && pe_ok(o.issuer) && in(o.dst, es) && o.dst % es == 0 ? 0 : SHMEMG_ERR_INVALID_ARG;
+    }
+    case SHMEMG_OP_PUT_SIGNAL:
+        return pe_ok(o.pe) && pe_ok(o.issuer) && in(o.dst, o.n) && in(o.src, o.n) && in(o.aux, 8) && o.aux % 8 == 0 &&
+                       o.sub <= SHMEMG_SIGNAL_ADD ? 0 : SHMEMG_ERR_INVALID_ARG;
+    case SHMEMG_OP_WAIT_UNTIL:
+        return pe_ok(o.issuer) && in(o.dst, 8) && o.dst % 8 == 0 && o.sub <= SHMEMG_CMP_LE ? 0 : SHMEMG_ERR_INVALID_ARG;
+    case SHMEMG_OP_QUIET: case SHMEMG_OP_FENCE: case SHMEMG_OP_BARRIER_ALL:
+        return 0;
+    default: break;
+    }
+    HostTeam t;
+    if (team_get(o.team, &t)) return SHMEMG_ERR_INVALID_ARG;
+    switch (o.kind) {
+    case SHMEMG_OP_TEAM_SYNC: return 0;
+    case SHMEMG_OP_BROADCAST:
+        return o.pe >= 0 && o.pe < t.size && in(o.dst, o.n) && in(o.src, o.n) ? 0 : SHMEMG_ERR_INVALID_ARG;
+    case SHMEMG_OP_FCOLLECT:
+        return in(o.dst, o.n * (uint64_t)t.size) && in(o.src, o.n) ? 0 : SHMEMG_ERR_INVALID_ARG;
+    case SHMEMG_OP_ALLTOALL:
+        return in(o.dst, o.n * (uint64_t)t.size) && in(o.src, o.n * (uint64_t)t.size) ? 0 : SHMEMG_ERR_INVALID_ARG;
+    case SHMEMG_OP_REDUCE: {
+        uint64_t es = o.dtype == SHMEMG_INT64 ? 8 : (o.dtype == SHMEMG_INT32 || o.dtype == SHMEMG_FLOAT) ? 4 : 0;
+        return es && o.sub <= SHMEMG_MIN && in(o.dst, o.n * es) && in(o.src, o.n * es) && o.dst % es == 0 &&
+                       o.src % es == 0 ? 0 : SHMEMG_ERR_INVALID_ARG;
+    }
+    default: return SHMEMG_ERR_INVALID_ARG;
+    }
+}
+
+int interp_threads() {
+    static int t = 0;
+    if (!t) {
+        const char *e = getenv("SHMEMG_INTERP_THREADS");
+        t = e && *e ? atoi(e) : INTERP_THREADS;
+        if (t < 32 || t > INTERP_THREADS || t % 32) t = INTERP_THREADS;
+    }
+    return t;
+}
+
+// Cooperative launch of `kernel` with one CTA (or cluster) per PE.
+int launch_pe_grid(const void *kernel, void **args, size_t smem, cudaStream_t s) {
+    State &S = st();
+    const int threads = interp_threads();
+    const int cd = S.cluster_dim;
+    const unsigned grid = S.pe_mode == SHMEMG_PE_MODE_CLUSTER ? (unsigned)(S.npes * cd) : (unsigned)S.npes;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(threads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[2];
+    int na = 0;
+    attr[na].id = cudaLaunchAttributeCooperative;
+    attr[na].val.cooperative = 1;
+    na++;
+    if (cd > 1) {
+        attr[na].id = cudaLaunchAttributeClusterDimension;
+        attr[na].val.clusterDim.x = cd;
+        attr[na].val.clusterDim.y = 1;
+        attr[na].val.clusterDim.z = 1;
+        na++;
+        int nclusters = 0;
+        cudaLaunchConfig_t q = cfg;
+        q.attrs = attr + 1;
+        q.numAttrs = 1;
+        if (cudaOccupancyMaxActiveClusters(&nclusters, kernel, &q) != cudaSuccess) {
+            cudaGetLastError();
+            return SHMEMG_ERR_UNSUPPORTED;
+        }
+        if ((int64_t)nclusters * cd < (int64_t)grid) return SHMEMG_ERR_UNSUPPORTED;
+    } else {
+        int per_sm = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem);
+        if ((int64_t)per_sm * S.sm_count < (int64_t)grid) return SHMEMG_ERR_UNSUPPORTED;
+    }
+    cfg.attrs = attr;
+    cfg.numAttrs = na;
+    cudaError_t e = cudaLaunchKernelExC(&cfg, kernel, args);
+    if (e == cudaErrorCooperativeLaunchTooLarge) {
+        cudaGetLastError();
+        return SHMEMG_ERR_UNSUPPORTED;
+    }
+    return cuda_rc(e);
+}
+
+}  // namespace shmemg
+
+using namespace shmemg;
+
+extern "C" int shmemg_run_script(const shmemg_op_t *ops, int64_t nops, int64_t *fetched, void *stream) {
+    if (int rc = check_init()) return rc;
+    if (nops < 0 || (nops && !ops)) return SHMEMG_ERR_INVALID_ARG;
+    if (nops == 0) return SHMEMG_SUCCESS;
+    // validate on the host (a copy of the device list) before anything runs
+    std::vector<shmemg_op_t> h((size_t)nops);
+    int rc = cuda_rc(cudaMemcpyAsync(h.data(), ops, sizeof(shmemg_op_t) * (size_t)nops, cudaMemcpyDeviceToHost,
+                                     to_stream(stream)));
+    if (rc) return rc;
+    if ((rc = cuda_rc(cudaStreamSynchronize(to_stream(stream))))) return rc;
+    for (int64_t i = 0; i < nops; i++)
+        if ((rc = validate_op(h[i]))) return rc;
+    shmemg_device_ctx_t c = device_ctx();
+    void *args[] = {(void *)&c, (void *)&ops, (void *)&nops, (void *)&fetched};
+    return launch_pe_grid((const void *)k_interp, args, 0, to_stream(stream));
+}

@@ -19,3 +19,34 @@ def orc():
 
     oracle.build()
     return oracle
+
+
+@pytest.fixture(scope="session")
+def sg():
+    """The GPU library (built in-tree); GPU tests only."""
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    from paper_2607_08006_gb300.builder import build
+
+    build()
+    import paper_2607_08006_gb300 as pkg
+
+    pkg.lib()
+    return pkg
+
+
+@pytest.fixture
+def heapf(sg):
+    """Factory of initialised heaps; finalises whatever it created."""
+    made = []
+
+    def make(npes, H, **kw):
+        h = sg.Heap(npes, H, **kw)
+        made.append(h)
+        return h
+
+    yield make
+    for h in made:
+        h.close()

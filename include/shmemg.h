@@ -343,7 +343,9 @@ int shmemg_run_script_host(const shmemg_op_t *ops, int64_t nops, int64_t *fetche
  * (r mod 2^20) + 1, compare_swap swaps in r if the word equals its initial value
  * splitmix64(table_seed ^ w), fetch_xor xors r (1 if r is 0).  fetched[i] (device, may
  * be NULL) gets the old value.  flags bit 0: warp-aggregate fetch_add/fetch_xor on
- * equal targets (the aggregated ops are consecutive in the serial order). */
+ * equal targets (the aggregated ops are consecutive in the serial order).  An op whose
+ * word is >= npes*words_per_pe (or whose code is 3) is skipped and recorded in the
+ * status word (SHMEMG_ERR_INVALID_ARG, detail = op index). */
 #define SHMEMG_AMO_AGGREGATE 1u
 int shmemg_amo_stream(int64_t *table, uint64_t words_per_pe, const uint32_t *ops, uint64_t nops,
                       uint64_t op_seed, uint64_t table_seed, int64_t *fetched, uint32_t flags,
@@ -352,9 +354,10 @@ int shmemg_amo_stream(int64_t *table, uint64_t words_per_pe, const uint32_t *ops
 /* Put-with-signal ping-pong between PE pairs (2k, 2k+1), one CTA per PE, cooperative
  * launch: for t in 0..iters-1 PE 2k puts `payload` bytes of its `buf` into the peer's
  * `buf` + payload and adds 1 to the peer's signal `sig`, then waits for its own signal
- * to reach t+1; PE 2k+1 answers in kind.  lat_ns[k] (device, npairs uint64) receives
- * the total round-trip time of pair k in ns (globaltimer).  buf must hold 2*payload
- * bytes per PE; sig one uint64 per PE. */
+ * to reach t+1; PE 2k+1 answers in kind.  lat_ns[k*iters + t] (device, npairs*iters
+ * uint64, may be NULL) receives round trip t of pair k in ns (globaltimer).  buf must
+ * hold 2*payload bytes per PE; sig one uint64 per PE, zero before the call.  Needs
+ * pe_mode CTA and 2*npairs co-resident CTAs (else SHMEMG_ERR_UNSUPPORTED). */
 int shmemg_pingpong(void *buf, uint64_t *sig, uint64_t payload, int npairs, int iters,
                     uint64_t *lat_ns, void *stream);
 

@@ -1,0 +1,267 @@
+// Batched uneven collectives: many teams' sum all-reduces in one persistent launch
+// captured in a CUDA graph (a batching extension of the team reductions the paper
+// inherits from OpenSHMEM 1.6, Sec. 6.3).
+//
+// Work items are (team, tile) pairs planned on the host, largest team first (cost =
+// members x elements x bytes); CTAs of a persistent grid take items from a device
+// counter.  Each item is a slice-owner reduction of one tile over the team's members:
+// fp32 by the fixed rank-pairwise tree, int64 exactly, bf16/e4m3 payloads dequantised
+// and accumulated with Neumaier's compensated sum.  The last CTA to leave resets the
+// counters, so graph replays need no memset node.  The autotuner times candidate
+// (tile, CTAs per SM) plans with CUDA events and keeps the fastest.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
+#include "internal.h"
+#include "quant_dev.cuh"
+
+namespace shmemg {
+
+constexpr int B_THREADS = 256;
+enum BKind { BK_F32 = 0, BK_I64 = 1, BK_BF16 = 2, BK_E4M3 = 3 };
+
+struct BTeam {
+    int32_t start, size, kind, vec;
+    uint64_t n, d_off, s_off, sc_off;
+};
+
+struct BArgs {
+    uint8_t *heap;
+    uint64_t H;
+    const BTeam *teams;
+    const uint2 *items;   // (team, tile)
+    uint32_t nitems;
+    uint32_t tile;        // elements per item
+    uint32_t *counter;    // [0] next item, [1] CTAs done
+};
+
+__device__ __forceinline__ void batch_item(const BArgs &a, const BTeam &t, uint64_t e0, uint64_t e1) {
+    const shmemg_group g = {threadIdx.x, blockDim.x};
+    if (t.kind == BK_F32) {
+        shmemg_d_reduce_elems_t<float, float4>(g, a.heap, a.H, t.start, 1, t.size, t.d_off, t.s_off, e0, e1, SHMEMG_SUM);
+    } else if (t.kind == BK_I64) {
+        shmemg_d_reduce_elems_t<int64_t, longlong2>(g, a.heap, a.H, t.start, 1, t.size, t.d_off, t.s_off, e0, e1,
+                                                    SHMEMG_SUM);
+    } else {
+        for (uint64_t q = e0 / 4 + threadIdx.x; q * 4 < e1; q += blockDim.x) {
+            const uint64_t f = q * 4;
+            const bool vec = t.vec && f + 4 <= t.n;
+            if (t.kind == BK_E4M3) qsum4<SHMEMG_FMT_E4M3>(a.heap, a.H, t.start, 1, t.size, t.d_off, t.s_off, t.sc_off, f, t.n, vec);
+            else qsum4<SHMEMG_FMT_BF16>(a.heap, a.H, t.start, 1, t.size, t.d_off, t.s_off, t.sc_off, f, t.n, vec);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(B_THREADS) k_batch(BArgs a) {
+    __shared__ uint32_t s_item;
+    for (;;) {
+        if (threadIdx.x == 0) s_item = atomicAdd(&a.counter[0], 1u);
+        __syncthreads();
+        const uint32_t it = s_item;
+        __syncthreads();
+        if (it >= a.nitems) break;
+        const uint2 item = a.items[it];
+        const BTeam t = a.teams[item.x];
+        const uint64_t e0 = (uint64_t)item.y * a.tile;
+        const uint64_t e1 = e0 + a.tile < t.n ? e0 + a.tile : t.n;
+        batch_item(a, t, e0, e1);
+    }
+    if (threadIdx.x == 0) {
+        // every CTA has drawn its final (out-of-range) item before it counts itself
+        // done, so the last one can reset both words for the next launch
+        __threadfence();
+        if (atomicAdd(&a.counter[1], 1u) == gridDim.x - 1) {
+            a.counter[0] = 0;
+            a.counter[1] = 0;
+            __threadfence();
+        }
+    }
+}
+
+}  // namespace shmemg
+
+using namespace shmemg;
+
+struct shmemg_batch_s {
+    std::vector<BTeam> teams;
+    std::vector<uint64_t> cost;
+    BTeam *d_teams = nullptr;
+    uint2 *d_items = nullptr;
+    uint32_t *d_counter = nullptr;
+    uint32_t nitems = 0;
+    shmemg_tune_t tune{};
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int grid = 0;
+};
+
+static void free_graph(shmemg_batch_s *b) {
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    b->exec = nullptr;
+    b->graph = nullptr;
+}
+
+// (re)plan items for the batch's tile size, upload them and capture the graph
+static int plan_and_capture(shmemg_batch_s *b) {
+    State &S = st();
+    const uint32_t tile = (uint32_t)b->tune.tile_elems;
+    std::vector<int> order(b->teams.size());
+    for (size_t i = 0; i < order.size(); i++) order[i] = (int)i;
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return b->cost[x] > b->cost[y]; });
+    std::vector<uint2> items;
+    for (int t : order) {
+        uint64_t tiles = (b->teams[t].n + tile - 1) / tile;
+        for (uint64_t k = 0; k < tiles; k++) items.push_back(make_uint2((unsigned)t, (unsigned)k));
+    }
+    if (items.size() >= (1ull << 31)) return SHMEMG_ERR_INVALID_ARG;
+    if (b->d_items) cudaFree(b->d_items);
+    b->d_items = nullptr;
+    int rc = cuda_rc(cudaMalloc(&b->d_items, sizeof(uint2) * (items.size() ? items.size() : 1)));
+    if (rc) return rc;
+    if ((rc = cuda_rc(cudaMemcpy(b->d_items, items.data(), sizeof(uint2) * items.size(), cudaMemcpyHostToDevice))))
+        return rc;
+    b->nitems = (uint32_t)items.size();
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch, B_THREADS, 0);
+    if (per_sm < 1) per_sm = 1;
+    int want = b->tune.ctas_per_sm > 0 ? std::min(b->tune.ctas_per_sm, per_sm) : per_sm;
+    b->grid = want * S.sm_count;
+    if ((uint32_t)b->grid > b->nitems) b->grid = (int)std::max<uint32_t>(b->nitems, 1u);
+    free_graph(b);
+    cudaStream_t cs;
+    if ((rc = cuda_rc(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking)))) return rc;
+    BArgs a;
+    a.heap = S.heap;
+    a.H = S.H;
+    a.teams = b->d_teams;
+    a.items = b->d_items;
+    a.nitems = b->nitems;
+    a.tile = tile;
+    a.counter = b->d_counter;
+    rc = cuda_rc(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    if (!rc) {
+        k_batch<<<b->grid, B_THREADS, 0, cs>>>(a);
+        cudaError_t le = cudaGetLastError();
+        cudaError_t ee = cudaStreamEndCapture(cs, &b->graph);
+        rc = cuda_rc(le != cudaSuccess ? le : ee);
+    }
+    if (!rc) rc = cuda_rc(cudaGraphInstantiate(&b->exec, b->graph, 0));
+    cudaStreamDestroy(cs);
+    return rc;
+}
+
+extern "C" {
+
+int shmemg_batch_create(const shmemg_coll_desc_t *descs, int count, const shmemg_tune_t *tune, shmemg_batch_t *out) {
+    if (int rc = check_init()) return rc;
+    if (!out || count < 1 || !descs) return SHMEMG_ERR_INVALID_ARG;
+    State &S = st();
+    auto *b = new shmemg_batch_s();
+    for (int i = 0; i < count; i++) {
+        const shmemg_coll_desc_t &d = descs[i];
+        BTeam t;
+        memset(&t, 0, sizeof(t));
+        if (d.size < 1 || d.start < 0 || d.start + d.size > S.npes || d.n == 0) { delete b; return SHMEMG_ERR_INVALID_ARG; }
+        t.start = d.start;
+        t.size = d.size;
+        t.n = d.n;
+        uint64_t in_es, out_es = 4;
+        if (d.dtype == SHMEMG_INT64) { t.kind = BK_I64; in_es = 8; out_es = 8; }
+        else if (d.dtype == SHMEMG_FLOAT && d.fmt < 0) { t.kind = BK_F32; in_es = 4; }
+        else if (d.dtype == SHMEMG_FLOAT && d.fmt == SHMEMG_FMT_BF16) { t.kind = BK_BF16; in_es = 2; }
+        else if (d.dtype == SHMEMG_FLOAT && d.fmt == SHMEMG_FMT_E4M3) { t.kind = BK_E4M3; in_es = 1; }
+        else { delete b; return SHMEMG_ERR_INVALID_ARG; }
+        if (sym_offset(d.dst, d.n * out_es, &t.d_off) || sym_offset(d.src, d.n * in_es, &t.s_off)) {
+            delete b;
+            return SHMEMG_ERR_NOT_SYMMETRIC;
+        }
+        if ((t.d_off % out_es) || (t.s_off % in_es)) { delete b; return SHMEMG_ERR_INVALID_ARG; }
+        if (t.kind >= BK_BF16) {
+            if (!d.scales || sym_offset(d.scales, (d.n + 127) / 128 * 4, &t.sc_off) || (t.sc_off & 3)) {
+                delete b;
+                return SHMEMG_ERR_NOT_SYMMETRIC;
+            }
+            t.vec = (t.d_off & 15) == 0 && (t.s_off & (t.kind == BK_E4M3 ? 3 : 7)) == 0;
+        }
+        b->teams.push_back(t);
+        b->cost.push_back((uint64_t)d.size * d.n * (in_es + out_es));
+    }
+    b->tune.tile_elems = tune && tune->tile_elems > 0 ? tune->tile_elems : 16384;
+    b->tune.ctas_per_sm = tune ? tune->ctas_per_sm : 0;
+    b->tune.threads = B_THREADS;
+    if (b->tune.tile_elems % 128) { delete b; return SHMEMG_ERR_INVALID_ARG; }
+    int rc = cuda_rc(cudaMalloc(&b->d_teams, sizeof(BTeam) * b->teams.size()));
+    if (!rc) rc = cuda_rc(cudaMemcpy(b->d_teams, b->teams.data(), sizeof(BTeam) * b->teams.size(), cudaMemcpyHostToDevice));
+    if (!rc) rc = cuda_rc(cudaMalloc(&b->d_counter, 2 * sizeof(uint32_t)));
+    if (!rc) rc = cuda_rc(cudaMemset(b->d_counter, 0, 2 * sizeof(uint32_t)));
+    if (!rc) rc = plan_and_capture(b);
+    if (rc) {
+        shmemg_batch_destroy(b);
+        return rc;
+    }
+    *out = b;
+    return SHMEMG_SUCCESS;
+}
+
+int shmemg_batch_launch(shmemg_batch_t b, void *stream) {
+    if (int rc = check_init()) return rc;
+    if (!b || !b->exec) return SHMEMG_ERR_INVALID_ARG;
+    return cuda_rc(cudaGraphLaunch(b->exec, to_stream(stream)));
+}
+
+int shmemg_batch_autotune(shmemg_batch_t b, void *stream, shmemg_tune_t *chosen) {
+    if (int rc = check_init()) return rc;
+    if (!b) return SHMEMG_ERR_INVALID_ARG;
+    cudaStream_t s = to_stream(stream);
+    const int tiles[] = {2048, 8192, 32768, 131072};
+    const int ctas[] = {1, 2, 0};
+    shmemg_tune_t best = b->tune;
+    float best_ms = 1e30f;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    int rc = SHMEMG_SUCCESS;
+    for (int t : tiles) {
+        for (int c : ctas) {
+            b->tune.tile_elems = t;
+            b->tune.ctas_per_sm = c;
+            if ((rc = plan_and_capture(b))) break;
+            cudaGraphLaunch(b->exec, s);  // warm-up
+            cudaEventRecord(e0, s);
+            for (int k = 0; k < 3; k++) cudaGraphLaunch(b->exec, s);
+            cudaEventRecord(e1, s);
+            if ((rc = cuda_rc(cudaEventSynchronize(e1)))) break;
+            float ms = 0;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ms < best_ms) {
+                best_ms = ms;
+                best = b->tune;
+            }
+        }
+        if (rc) break;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc) return rc;
+    b->tune = best;
+    if ((rc = plan_and_capture(b))) return rc;
+    if (chosen) *chosen = best;
+    return SHMEMG_SUCCESS;
+}
+
+int shmemg_batch_destroy(shmemg_batch_t b) {
+    if (!b) return SHMEMG_ERR_INVALID_ARG;
+    cudaDeviceSynchronize();
+    free_graph(b);
+    if (b->d_items) cudaFree(b->d_items);
+    if (b->d_teams) cudaFree(b->d_teams);
+    if (b->d_counter) cudaFree(b->d_counter);
+    delete b;
+    return SHMEMG_SUCCESS;
+}
+
+}  // extern "C"

@@ -1,0 +1,102 @@
+// Device-side codecs and compensated accumulation of the reduced-precision float
+// payloads, shared by the quantised all-reduce and the batched collective engine.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include "internal.h"
+
+namespace shmemg {
+
+// ---------------------------------------------------------------- codecs
+// E4M3 decode from the format: 1 sign, 4 exponent bits (bias 7), 3 mantissa bits;
+// exponent field 0 holds subnormals m/8 * 2^-6 (exact in binary32).
+__device__ __forceinline__ float e4m3_decode(uint32_t q) {
+    const uint32_t s = (q >> 7) & 1u, e = (q >> 3) & 15u, m = q & 7u;
+    float v;
+    if (e == 0) {
+        v = (float)m * 0.001953125f;  // m * 2^-9, exact
+    } else {
+        v = __uint_as_float(((e + 120u) << 23) | (m << 20));  // (1 + m/8) * 2^(e-7)
+    }
+    return s ? -v : v;
+}
+__device__ __forceinline__ float bf16_decode(uint32_t q) { return __uint_as_float(q << 16); }
+
+// two floats -> two E4M3 codes (round to nearest even, saturate to +-448); `lo` is the
+// element at the lower address
+__device__ __forceinline__ uint16_t e4m3x2_encode(float lo, float hi) {
+    uint16_t r;
+    asm("cvt.rn.satfinite.e4m3x2.f32 %0, %1, %2;" : "=h"(r) : "f"(hi), "f"(lo));
+    return r;
+}
+__device__ __forceinline__ uint16_t bf16_encode(float x) {
+    return __bfloat16_as_ushort(__float2bfloat16_rn(x));
+}
+
+// ---------------------------------------------------------------- compensated sum
+// Neumaier: t = sum + x; c += (sum - t) + x if |sum| >= |x| else (x - t) + sum; sum = t.
+struct Neu {
+    float sum, c;
+    __device__ __forceinline__ void add(float x) {
+        const float t = __fadd_rn(sum, x);
+        if (fabsf(sum) >= fabsf(x)) c = __fadd_rn(c, __fadd_rn(__fsub_rn(sum, t), x));
+        else c = __fadd_rn(c, __fadd_rn(__fsub_rn(x, t), sum));
+        sum = t;
+    }
+    __device__ __forceinline__ float result() const { return __fadd_rn(sum, c); }
+};
+
+// Dequantised sum of elements [e0, e0+4) over the team members, written to every
+// member's dst.  Vector path: 4 codes and 4 floats per access (aligned offsets).
+template <int FMT>
+__device__ __forceinline__ void qsum4(uint8_t *heap, uint64_t H, int pe0, int pstride, int P, uint64_t d_off,
+                                      uint64_t q_off, uint64_t s_off, uint64_t e0, uint64_t n, bool vec) {
+    Neu acc[4];
+#pragma unroll
+    for (int j = 0; j < 4; j++) acc[j] = {0.0f, 0.0f};
+    for (int r = 0; r < P; r++) {
+        const uint8_t *base = heap + (uint64_t)(pe0 + r * pstride) * H;
+        float d[4];
+        if (vec) {
+            const float s = __ldcg((const float *)(base + s_off) + e0 / 128);
+            if (FMT == SHMEMG_FMT_E4M3) {
+                const uint32_t w = __ldcg((const unsigned int *)(base + q_off + e0));
+#pragma unroll
+                for (int j = 0; j < 4; j++) d[j] = __fmul_rn(e4m3_decode((w >> (8 * j)) & 0xFFu), s);
+            } else {
+                const uint2 w = __ldcg((const uint2 *)(base + q_off + 2 * e0));
+                d[0] = __fmul_rn(bf16_decode(w.x & 0xFFFFu), s);
+                d[1] = __fmul_rn(bf16_decode(w.x >> 16), s);
+                d[2] = __fmul_rn(bf16_decode(w.y & 0xFFFFu), s);
+                d[3] = __fmul_rn(bf16_decode(w.y >> 16), s);
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < 4; j++) {
+                const uint64_t e = e0 + j;
+                if (e >= n) { d[j] = 0.0f; continue; }
+                const float s = ((const float *)(base + s_off))[e / 128];
+                const float v = FMT == SHMEMG_FMT_E4M3 ? e4m3_decode(base[q_off + e])
+                                                       : bf16_decode(((const uint16_t *)(base + q_off))[e]);
+                d[j] = __fmul_rn(v, s);
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < 4; j++) acc[j].add(d[j]);
+    }
+    if (vec) {
+        const float4 o = make_float4(acc[0].result(), acc[1].result(), acc[2].result(), acc[3].result());
+        for (int r = 0; r < P; r++) *(float4 *)(heap + (uint64_t)(pe0 + r * pstride) * H + d_off + 4 * e0) = o;
+    } else {
+        for (int r = 0; r < P; r++) {
+            float *dst = (float *)(heap + (uint64_t)(pe0 + r * pstride) * H + d_off);
+#pragma unroll
+            for (int j = 0; j < 4; j++)
+                if (e0 + j < n) dst[e0 + j] = acc[j].result();
+        }
+    }
+}
+
+}  // namespace shmemg

@@ -391,6 +391,28 @@ int shmemg_batch_launch(shmemg_batch_t batch, void *stream);
 int shmemg_batch_autotune(shmemg_batch_t batch, void *stream, shmemg_tune_t *chosen);
 int shmemg_batch_destroy(shmemg_batch_t batch);
 
+/* Allocation-free batched sum reduce.  The paper has no counterpart: this is a
+ * service of this library for callers that cannot allocate device memory -- a host
+ * framework whose caching allocator already holds the GPU's memory, or a
+ * latency-critical loop that must not call cudaMalloc/cudaFree (cudaFree synchronises
+ * the whole device).  It computes exactly what shmemg_batch_create + shmemg_batch_launch
+ * compute for the same descriptors and tile size (largest-first work items, one launch
+ * of the same kernel on `stream`), but keeps the team table, the work items and the two
+ * work counters in one array compiled into the library (about 560 KiB, held by every GPU
+ * that loads the library until the process exits) instead of allocating them.  The
+ * caller still passes the inputs and outputs (symmetric objects in the descriptors).
+ * Limits: at most SHMEMG_NOALLOC_MAX_TEAMS descriptors and SHMEMG_NOALLOC_MAX_ITEMS work
+ * items (sum over teams of ceil(n / tile)); larger requests return
+ * SHMEMG_ERR_INVALID_ARG and launch nothing.  tile_elems: a multiple of 128, 0 = 16384.
+ * The first call on a device looks the array's device address up (cudaGetSymbolAddress)
+ * with that device current; make that first call before any stream capture.  Every
+ * call overwrites the array (the counters are cleared on `stream` before the launch):
+ * calls whose work overlaps on the GPU -- on different streams, or on different host
+ * threads -- race on it and give wrong results; order them (one stream, or events). */
+#define SHMEMG_NOALLOC_MAX_TEAMS 1024
+#define SHMEMG_NOALLOC_MAX_ITEMS 65536
+int shmemg_batch_reduce_noalloc(const shmemg_coll_desc_t *descs, int count, int tile_elems, void *stream);
+
 /* ----------------------------------------------------------------- serving */
 /* A persistent, device-resident progress kernel that drains a request ring written by
  * the host, admits requests against free symmetric-heap pages, runs admitted requests

@@ -13,6 +13,7 @@
 
 #include <algorithm>
 #include <cstring>
+#include <mutex>
 #include <vector>
 
 #include "internal.h"
@@ -265,3 +266,110 @@ int shmemg_batch_destroy(shmemg_batch_t b) {
 }
 
 }  // extern "C"
+
+// ================================================================ allocation-free variant
+// The batched reduce above keeps its team table, work items and work counters in
+// device memory that shmemg_batch_create allocates.  shmemg_batch_reduce_noalloc runs
+// the same kernel with those three in one fixed array compiled into the library, so a
+// call allocates nothing.  Every GPU that loads the library holds the array until the
+// process exits; all calls share it.
+namespace shmemg {
+
+struct NoallocScratch {
+    BTeam teams[SHMEMG_NOALLOC_MAX_TEAMS];
+    uint2 items[SHMEMG_NOALLOC_MAX_ITEMS];
+    uint32_t counter[2];
+};
+
+static __device__ __align__(256) uint8_t g_noalloc_scratch[sizeof(NoallocScratch)];
+
+// host staging of one call's table and items (no host heap allocation per call)
+static BTeam g_noalloc_teams_h[SHMEMG_NOALLOC_MAX_TEAMS];
+static uint2 g_noalloc_items_h[SHMEMG_NOALLOC_MAX_ITEMS];
+static uint64_t g_noalloc_cost_h[SHMEMG_NOALLOC_MAX_TEAMS];
+static int g_noalloc_order_h[SHMEMG_NOALLOC_MAX_TEAMS];
+static std::mutex g_noalloc_mu;
+constexpr int NOALLOC_MAX_DEVICES = 64;
+static NoallocScratch *g_noalloc_dev[NOALLOC_MAX_DEVICES];
+
+// device address of the array on the current device; looked up once per device
+static int noalloc_scratch(NoallocScratch **out) {
+    int dev = 0;
+    int rc = cuda_rc(cudaGetDevice(&dev));
+    if (rc) return rc;
+    if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return SHMEMG_ERR_UNSUPPORTED;
+    if (!g_noalloc_dev[dev]) {
+        void *p = nullptr;
+        if ((rc = cuda_rc(cudaGetSymbolAddress(&p, g_noalloc_scratch)))) return rc;
+        g_noalloc_dev[dev] = (NoallocScratch *)p;
+    }
+    *out = g_noalloc_dev[dev];
+    return SHMEMG_SUCCESS;
+}
+
+}  // namespace shmemg
+
+extern "C" int shmemg_batch_reduce_noalloc(const shmemg_coll_desc_t *descs, int count, int tile_elems, void *stream) {
+    if (int rc = check_init()) return rc;
+    if (!descs || count < 1) return SHMEMG_ERR_INVALID_ARG;
+    if (count > SHMEMG_NOALLOC_MAX_TEAMS) return SHMEMG_ERR_INVALID_ARG;  // more teams than the array holds
+    const uint32_t tile = tile_elems > 0 ? (uint32_t)tile_elems : 16384u;
+    if (tile % 128) return SHMEMG_ERR_INVALID_ARG;
+    State &S = st();
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    NoallocScratch *d = nullptr;
+    if (int rc = noalloc_scratch(&d)) return rc;
+    uint64_t nitems = 0;
+    for (int i = 0; i < count; i++) {
+        const shmemg_coll_desc_t &c = descs[i];
+        BTeam &t = g_noalloc_teams_h[i];
+        memset(&t, 0, sizeof(t));
+        if (c.size < 1 || c.start < 0 || c.start + c.size > S.npes || c.n == 0) return SHMEMG_ERR_INVALID_ARG;
+        t.start = c.start;
+        t.size = c.size;
+        t.n = c.n;
+        uint64_t in_es, out_es = 4;
+        if (c.dtype == SHMEMG_INT64) { t.kind = BK_I64; in_es = 8; out_es = 8; }
+        else if (c.dtype == SHMEMG_FLOAT && c.fmt < 0) { t.kind = BK_F32; in_es = 4; }
+        else if (c.dtype == SHMEMG_FLOAT && c.fmt == SHMEMG_FMT_BF16) { t.kind = BK_BF16; in_es = 2; }
+        else if (c.dtype == SHMEMG_FLOAT && c.fmt == SHMEMG_FMT_E4M3) { t.kind = BK_E4M3; in_es = 1; }
+        else return SHMEMG_ERR_INVALID_ARG;
+        if (sym_offset(c.dst, c.n * out_es, &t.d_off) || sym_offset(c.src, c.n * in_es, &t.s_off))
+            return SHMEMG_ERR_NOT_SYMMETRIC;
+        if ((t.d_off % out_es) || (t.s_off % in_es)) return SHMEMG_ERR_INVALID_ARG;
+        if (t.kind >= BK_BF16) {
+            if (!c.scales || sym_offset(c.scales, (c.n + 127) / 128 * 4, &t.sc_off) || (t.sc_off & 3))
+                return SHMEMG_ERR_NOT_SYMMETRIC;
+            t.vec = (t.d_off & 15) == 0 && (t.s_off & (t.kind == BK_E4M3 ? 3 : 7)) == 0;
+        }
+        g_noalloc_cost_h[i] = (uint64_t)c.size * c.n * (in_es + out_es);
+        g_noalloc_order_h[i] = i;
+        nitems += (c.n + tile - 1) / tile;
+    }
+    if (nitems > SHMEMG_NOALLOC_MAX_ITEMS) return SHMEMG_ERR_INVALID_ARG;  // more work items than the array holds
+    std::stable_sort(g_noalloc_order_h, g_noalloc_order_h + count,
+                     [](int x, int y) { return g_noalloc_cost_h[x] > g_noalloc_cost_h[y]; });
+    uint32_t k = 0;
+    for (int j = 0; j < count; j++) {
+        const int t = g_noalloc_order_h[j];
+        const uint64_t tiles = (g_noalloc_teams_h[t].n + tile - 1) / tile;
+        for (uint64_t q = 0; q < tiles; q++) g_noalloc_items_h[k++] = make_uint2((unsigned)t, (unsigned)q);
+    }
+    cudaStream_t s = to_stream(stream);
+    int rc = cuda_rc(cudaMemcpyAsync(d->teams, g_noalloc_teams_h, sizeof(BTeam) * count, cudaMemcpyHostToDevice, s));
+    if (!rc) rc = cuda_rc(cudaMemcpyAsync(d->items, g_noalloc_items_h, sizeof(uint2) * k, cudaMemcpyHostToDevice, s));
+    if (!rc) rc = cuda_rc(cudaMemsetAsync(d->counter, 0, sizeof(d->counter), s));  // work counters start at zero
+    if (rc) return rc;
+    BArgs a;
+    a.heap = S.heap;
+    a.H = S.H;
+    a.teams = d->teams;
+    a.items = d->items;
+    a.nitems = k;
+    a.tile = tile;
+    a.counter = d->counter;
+    int grid = ctas_for((const void *)k_batch, B_THREADS, 0);
+    if ((uint32_t)grid > k) grid = (int)k;
+    k_batch<<<grid, B_THREADS, 0, s>>>(a);
+    return cuda_rc(cudaGetLastError());
+}

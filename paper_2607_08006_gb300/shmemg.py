@@ -140,6 +140,7 @@ _SIGS = {
     "shmemg_batch_launch": [P, P],
     "shmemg_batch_autotune": [P, P, P],
     "shmemg_batch_destroy": [P],
+    "shmemg_batch_reduce_noalloc": [P, I, I, P],
     "shmemg_server_start": [P, P, P],
     "shmemg_server_submit": [P, P, P],
     "shmemg_server_poll": [P, P, I, P],
@@ -461,6 +462,12 @@ class Batch:
         if self.h:
             _call("shmemg_batch_destroy", self.h)
             self.h = None
+
+
+def batch_reduce_noalloc(descs, tile_elems=0, stream=None):
+    """The batched sum reduce without any device allocation (library-held scratch)."""
+    arr = (CollDesc * len(descs))(*descs)
+    _call("shmemg_batch_reduce_noalloc", C.cast(arr, C.c_void_p), len(descs), tile_elems, _stream(stream))
 
 
 # serving -----------------------------------------------------------------------------

@@ -414,56 +414,101 @@ int shmemg_batch_destroy(shmemg_batch_t batch);
 int shmemg_batch_reduce_noalloc(const shmemg_coll_desc_t *descs, int count, int tile_elems, void *stream);
 
 /* ----------------------------------------------------------------- serving */
-/* A persistent, device-resident progress kernel that drains a request ring written by
- * the host, admits requests against free symmetric-heap pages, runs admitted requests
- * concurrently on its worker CTAs and writes completion records to mapped host memory.
- * Request kinds reuse shmemg_op_t kinds (PUT, GET, FETCH_ADD, COMPARE_SWAP, FETCH_XOR,
- * REDUCE, ALLTOALL). */
+/* A persistent, device-resident progress kernel (paper Sec. 3 and 7: persistent
+ * kernels; the paper leaves their progress guarantee to the implementation, this one
+ * documents it below).  CTA 0 admits: it acquire-polls a request ring in mapped host
+ * memory, gives each request a slot and its destination pages (the same page range on
+ * every PE the request writes, first fit in per-PE page bitmaps), and publishes it to a
+ * device work queue.  The other CTAs take (request, tile) work items from the head of
+ * that queue, so requests admitted while others run share the GPU tile by tile
+ * (continuous batching).  The CTA that finishes a request's last tile writes its
+ * completion record to mapped host memory and frees its pages and slot.
+ *
+ * Request kinds (SHMEMG_OP_*):
+ *   PUT      n bytes of `src` on `issuer` -> fresh pages on `pe`
+ *   GET      n bytes of `src` on `pe`     -> fresh pages on `issuer`
+ *   FETCH_ADD / COMPARE_SWAP / FETCH_XOR  int64 on table word `word` (word w lives on
+ *            PE w / amo_words at amo_offset + 8*(w % amo_words)); operand, cond
+ *   REDUCE   sum all-reduce over PEs pe .. pe+issuer-1 of n elements at `src`
+ *            (dtype SHMEMG_FLOAT with fmt 0xFF: fp32 by the rank-pairwise tree; dtype
+ *            SHMEMG_FLOAT with fmt SHMEMG_FMT_BF16: bf16 codes at src, per-128 scales at
+ *            symmetric offset `cond`, Neumaier fp32 accumulation; dtype SHMEMG_INT64:
+ *            exact) into fresh pages on every member
+ *   ALLTOALL blocks of n bytes over PEs pe .. pe+issuer-1 from `src` into fresh pages
+ * Offsets `src` (and `cond` for bf16 scales) are symmetric byte offsets of caller data
+ * the server only reads: 16-byte aligned; n a multiple of 8 (RMA), 4 (REDUCE) or 16
+ * (ALLTOALL).  The result is the fetched value (AMO) or a checksum of the output:
+ * sum over its little-endian 32-bit words w_i (members' outputs concatenated in team
+ * rank order) of w_i * (2i + 1), modulo 2^64.  Invalid requests complete with an error
+ * status.  Progress: the kernel needs no host action to progress; it exits on stop,
+ * after idle_ns without requests, or after max_ns in total. */
 typedef struct {
     uint32_t kind;
-    uint8_t dtype;      /* REDUCE: SHMEMG_FLOAT or SHMEMG_INT64; AMO: SHMEMG_INT64 */
-    uint8_t fmt;        /* REDUCE float: 0xFF fp32, else SHMEMG_FMT_BF16 */
+    uint8_t dtype;
+    uint8_t fmt;
     uint16_t reserved0;
-    int32_t pe;         /* RMA/AMO target PE; REDUCE/ALLTOALL first team PE */
+    int32_t pe;
     int32_t issuer;     /* RMA/AMO issuing PE; REDUCE/ALLTOALL team size */
-    uint64_t n;         /* RMA bytes; REDUCE elements; ALLTOALL bytes per pair */
-    uint64_t word;      /* AMO: word index inside the AMO table */
+    uint64_t n;
+    uint64_t word;
     int64_t operand;
     int64_t cond;
-    uint64_t seed;      /* input data of the request is derived from this seed */
+    uint64_t src;       /* symmetric offset of the request's input */
     uint64_t ticket;    /* set by submit */
 } shmemg_req_t;
 typedef struct {
     uint64_t ticket;
-    uint64_t t_admit_ns;   /* globaltimer at admission */
+    uint64_t t_admit_ns;   /* globaltimer when the request was admitted (or its kernel began) */
     uint64_t t_done_ns;    /* globaltimer at completion */
     uint64_t result;       /* AMO: fetched value; others: checksum of the output */
     int32_t status;        /* SHMEMG_SUCCESS or an error */
-    int32_t reserved0;
+    uint32_t seq;          /* record sequence number + 1, written last */
 } shmemg_completion_t;
 typedef struct {
-    int32_t workers;          /* worker CTAs (0 = 2 per SM) */
-    int32_t threads;          /* threads per worker CTA (0 = 256) */
-    int32_t ring_slots;       /* request ring capacity (power of two, 0 = 65536) */
-    int32_t max_inflight;     /* admitted-but-unfinished request limit (0 = 4096) */
-    uint64_t page_bytes;      /* admission page size (0 = 65536) */
-    uint64_t arena_offset;    /* symmetric offset of the pageable arena */
-    uint64_t arena_bytes;     /* per-PE bytes of the arena */
+    int32_t workers;          /* worker CTAs (0 = every CTA the GPU holds at once, minus one) */
+    int32_t ring_slots;       /* request / completion ring capacity (power of two, 0 = 65536) */
+    int32_t max_inflight;     /* admitted-but-unfinished request limit (0 = 1024) */
+    int32_t reserved0;
+    uint64_t page_bytes;      /* admission page size (multiple of 256, 0 = 65536) */
+    uint64_t arena_offset;    /* symmetric offset of the pageable arena (destinations) */
+    uint64_t arena_bytes;     /* per-PE bytes of the arena (<= 4096 pages) */
     uint64_t amo_offset;      /* symmetric offset of the AMO table */
     uint64_t amo_words;       /* AMO table words per PE */
+    uint64_t idle_ns;         /* exit after this long without a request (0 = 60 s) */
+    uint64_t max_ns;          /* exit after this long in total (0 = 600 s) */
 } shmemg_server_cfg_t;
 typedef struct shmemg_server_s *shmemg_server_t;
+/* Launches the progress kernel (a cooperative launch; it occupies `stream` until it
+ * exits, so give it a stream of its own).  Allocates the server's device queues and
+ * mapped host rings. */
 int shmemg_server_start(const shmemg_server_cfg_t *cfg, void *stream, shmemg_server_t *out);
 /* Publishes one request (release store of the ring tail to device-visible memory);
- * SHMEMG_ERR_BUSY if the ring is full.  *ticket gets the request's ticket. */
+ * SHMEMG_ERR_BUSY if the ring is full.  *ticket (may be NULL) gets its ticket. */
 int shmemg_server_submit(shmemg_server_t s, const shmemg_req_t *req, uint64_t *ticket);
-/* Copies up to `max` new completion records; *got = how many. */
+/* Submits reqs[i] at host time t0 + arrival_ns[i] (CLOCK_MONOTONIC; spins, retries while
+ * the ring is full); *t0_ns receives t0.  A native feeder for open-loop arrivals. */
+int shmemg_server_feed(shmemg_server_t s, const shmemg_req_t *reqs, int count, const uint64_t *arrival_ns,
+                       uint64_t *t0_ns);
+/* Copies up to `max` new completion records in completion order; *got = how many. */
 int shmemg_server_poll(shmemg_server_t s, shmemg_completion_t *out, int max, int *got);
-/* globaltimer value now (ns), read by a tiny kernel; for clock calibration. */
-int shmemg_device_time_ns(uint64_t *out);
-/* Sets the stop flag, waits (bounded) for the kernel to drain and exit, frees the
- * server's host rings. */
+/* Sets the stop flag and waits (bounded by 60 s) for the kernel to drain and exit;
+ * frees the server.  SHMEMG_ERR_TIMEOUT if it did not exit in time. */
 int shmemg_server_stop(shmemg_server_t s);
+
+/* The plain launch-per-op path for the same requests: one full-grid kernel per request
+ * on `stream`, destinations at cfg->arena_offset (requests on one stream never
+ * overlap), completion record written to `rec` (host-mapped or device memory). */
+int shmemg_request_run(const shmemg_req_t *req, const shmemg_server_cfg_t *cfg, shmemg_completion_t *rec,
+                       void *stream);
+/* Launches reqs[i] at host time t0 + arrival_ns[i] (CLOCK_MONOTONIC), one kernel each on
+ * `stream`; recs (count records, host-mapped) receive the completions; *t0_ns gets t0. */
+int shmemg_plain_feed(const shmemg_req_t *reqs, int count, const uint64_t *arrival_ns,
+                      const shmemg_server_cfg_t *cfg, shmemg_completion_t *recs, void *stream, uint64_t *t0_ns);
+/* globaltimer value now (ns), read by a tiny kernel. */
+int shmemg_device_time_ns(uint64_t *out);
+/* Offset between the device globaltimer and the host CLOCK_MONOTONIC (device - host,
+ * ns), from the tightest of `rounds` launch round trips; *err_ns = half that round trip. */
+int shmemg_clock_offset(int rounds, int64_t *offset_ns, uint64_t *err_ns);
 
 #ifdef __cplusplus
 }

@@ -218,6 +218,45 @@ def quantize(x: np.ndarray, fmt: int):
     return q, s
 
 
+def checksum32(buf: np.ndarray) -> int:
+    """Result encoding of a served request's output: sum over its little-endian 32-bit
+    words w_i of w_i * (2i + 1), modulo 2^64."""
+    w = np.frombuffer(np.ascontiguousarray(buf).tobytes(), dtype="<u4").astype(np.uint64)
+    i = np.arange(len(w), dtype=np.uint64)
+    with np.errstate(over="ignore"):
+        return int(np.sum(w * (np.uint64(2) * i + np.uint64(1)), dtype=np.uint64))
+
+
+def serve_request(heap: "Heap", r, amo_offset: int, amo_words: int, scratch_off: int):
+    """Expected result of one served request applied alone to `heap` (its output is built
+    at scratch_off): the fetched value for an AMO, else the output's checksum32."""
+    kind = int(r["kind"])
+    if kind in (5, 6, 7):
+        w = int(r["word"])
+        return heap.amo64(kind, w // amo_words, amo_offset + 8 * (w % amo_words), int(r["operand"]), int(r["cond"]))
+    pe, iss, n, src = int(r["pe"]), int(r["issuer"]), int(r["n"]), int(r["src"])
+    if kind in (1, 2):
+        sp, dp = (iss, pe) if kind == 1 else (pe, iss)
+        heap.put(scratch_off, src, n, dp, sp)
+        return checksum32(heap.pe(dp)[scratch_off:scratch_off + n])
+    team = (pe, 1, iss)
+    if kind == 16:
+        if int(r["dtype"]) == 1:
+            heap.reduce(team, scratch_off, src, n, 1, 0)
+            nb = 8 * n
+        elif int(r["fmt"]) == 0:
+            heap.qsum_reduce(team, scratch_off, src, int(r["cond"]), 0, n)
+            nb = 4 * n
+        else:
+            heap.reduce(team, scratch_off, src, n, 2, 0)
+            nb = 4 * n
+        return checksum32(heap.pe(pe)[scratch_off:scratch_off + nb])
+    if kind == 15:
+        heap.alltoall(team, scratch_off, src, n)
+        return checksum32(np.concatenate([heap.pe(pe + j)[scratch_off:scratch_off + iss * n] for j in range(iss)]))
+    raise ValueError(kind)
+
+
 def cb64(seed: int, i: int) -> int:
     return int(lib().or_cb64(seed, i))
 

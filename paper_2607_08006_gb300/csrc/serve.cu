@@ -1,0 +1,818 @@
+// Serving: a persistent, device-resident progress kernel draining a host request ring
+// with memory-based admission and tile-level continuous batching, and the plain
+// launch-per-request path it is compared with.  (Persistent kernels and their progress:
+// paper Sec. 3 and 7; the operations are the RMA, AMO and collectives of Sec. 6.3.)
+//
+// Roles in the server kernel:
+//  * CTA 0, thread 0 -- the admitter: acquire-polls the ring tail in mapped host memory,
+//    validates the request, finds a free slot and its destination pages (one page range
+//    free on every PE the request writes: OR of the per-PE page bitmaps, first fit), marks
+//    them, fills the slot and publishes (slot, generation) to the device work queue.
+//  * CTAs 1..W -- workers: take tiles of queued requests (a window of the queue's oldest
+//    entries, spread by CTA index so small requests run beside big ones), claim a tile by
+//    compare-and-swap on the slot's (generation, next tile) word, run it, add its output
+//    checksum, and count it done.  The CTA that completes the last tile writes the
+//    completion record to mapped host memory, frees the pages and releases the slot.
+// Every wait is bounded: the kernel exits on the stop flag once drained, after idle_ns
+// without work, or after max_ns.
+#include <cuda_runtime.h>
+#include <time.h>
+
+#include <cstring>
+#include <thread>
+
+#include "internal.h"
+#include "quant_dev.cuh"
+
+namespace shmemg {
+
+constexpr int SV_THREADS = 256;
+constexpr uint64_t RMA_TILE = 128ull << 10;   // bytes per put/get tile
+constexpr uint64_t RED_TILE = 16384;          // elements per reduce tile
+constexpr uint64_t A2A_TILE = 64ull << 10;    // bytes per alltoall block chunk
+constexpr uint32_t WINDOW = 32;               // queue entries workers spread over
+constexpr uint8_t FMT_F32 = 0xFF;
+
+struct SvHost {                      // mapped host memory
+    volatile uint64_t tail;          // requests published by the host
+    uint8_t p0[120];
+    volatile uint64_t head;          // requests taken by the admitter
+    uint8_t p1[120];
+    volatile uint32_t stop;
+    uint8_t p2[124];
+    volatile uint64_t consumed;      // completion records read by the host
+    uint8_t p3[120];
+};
+
+struct SvCtl {                       // device memory
+    unsigned long long fifo_head;
+    uint8_t p0[120];
+    unsigned long long fifo_tail;
+    uint8_t p1[120];
+    unsigned int exit_flag;
+    uint8_t p2[124];
+    unsigned long long comp_pos;
+    uint8_t p3[120];
+    unsigned long long inflight;
+    uint8_t p4[120];
+};
+
+struct SvSlot {
+    shmemg_req_t req;
+    uint64_t dst_off;
+    uint32_t page0, npages;
+    uint32_t ntiles, gen;
+    unsigned long long claim;        // (gen << 32) | next tile
+    unsigned int done;
+    unsigned int busy;
+    unsigned long long checksum;
+    uint64_t t_admit;
+    int32_t status;
+    int32_t pad;
+};
+
+struct SvArgs {
+    uint8_t *heap;
+    uint64_t H;
+    int npes;
+    shmemg_server_cfg_t cfg;
+    uint32_t pages_per_pe, bm_words;
+    unsigned long long *bitmaps;     // npes * bm_words
+    SvSlot *slots;
+    uint32_t nslots;
+    unsigned long long *fifo;        // (gen << 32) | slot
+    uint32_t fifo_cap;
+    SvCtl *ctl;
+    SvHost *host;
+    shmemg_req_t *ring;
+    shmemg_completion_t *comp;
+    uint32_t ring_slots;
+};
+
+__device__ __forceinline__ uint64_t now_dev() { return shmemg_d_globaltimer(); }
+
+// ------------------------------------------------------------------ request geometry
+struct Geo {
+    int first, count;       // PEs whose destination pages the request writes
+    uint64_t bytes;         // destination bytes per such PE
+    uint32_t ntiles;
+    int valid;
+};
+
+__host__ __device__ inline Geo geometry(const shmemg_req_t &r, int npes, uint64_t H, uint64_t amo_words) {
+    Geo g = {0, 0, 0, 0, 0};
+    switch (r.kind) {
+    case SHMEMG_OP_PUT:
+    case SHMEMG_OP_GET: {
+        int w = r.kind == SHMEMG_OP_PUT ? r.pe : r.issuer;
+        if (r.pe < 0 || r.pe >= npes || r.issuer < 0 || r.issuer >= npes || r.n == 0 || (r.n & 7) ||
+            (r.src & 15) || r.src > H || r.n > H - r.src)
+            return g;
+        g.first = w;
+        g.count = 1;
+        g.bytes = r.n;
+        g.ntiles = (uint32_t)((r.n + RMA_TILE - 1) / RMA_TILE);
+        break;
+    }
+    case SHMEMG_OP_FETCH_ADD:
+    case SHMEMG_OP_COMPARE_SWAP:
+    case SHMEMG_OP_FETCH_XOR:
+        if (r.dtype != SHMEMG_INT64 || amo_words == 0 || r.word >= (uint64_t)npes * amo_words) return g;
+        g.ntiles = 1;
+        break;
+    case SHMEMG_OP_REDUCE: {
+        int P = r.issuer;
+        uint64_t in_es, out_es;
+        if (r.dtype == SHMEMG_INT64) { in_es = 8; out_es = 8; }
+        else if (r.dtype == SHMEMG_FLOAT && r.fmt == FMT_F32) { in_es = 4; out_es = 4; }
+        else if (r.dtype == SHMEMG_FLOAT && r.fmt == SHMEMG_FMT_BF16) { in_es = 2; out_es = 4; }
+        else return g;
+        if (P < 1 || r.pe < 0 || r.pe + P > npes || r.n == 0 || (r.n & 3) || (r.src & 15) || r.src > H ||
+            r.n * in_es > H - r.src)
+            return g;
+        if (r.fmt == SHMEMG_FMT_BF16 && r.dtype == SHMEMG_FLOAT) {
+            uint64_t sb = (r.n + 127) / 128 * 4;
+            if (r.cond < 0 || ((uint64_t)r.cond & 3) || (uint64_t)r.cond > H || sb > H - (uint64_t)r.cond) return g;
+        }
+        g.first = r.pe;
+        g.count = P;
+        g.bytes = r.n * out_es;
+        g.ntiles = (uint32_t)((r.n + RED_TILE - 1) / RED_TILE);
+        break;
+    }
+    case SHMEMG_OP_ALLTOALL: {
+        int P = r.issuer;
+        if (P < 1 || r.pe < 0 || r.pe + P > npes || r.n == 0 || (r.n & 15) || (r.src & 15) || r.src > H ||
+            r.n * (uint64_t)P > H - r.src)
+            return g;
+        g.first = r.pe;
+        g.count = P;
+        g.bytes = r.n * (uint64_t)P;
+        g.ntiles = (uint32_t)((uint64_t)P * P * ((r.n + A2A_TILE - 1) / A2A_TILE));
+        break;
+    }
+    default:
+        return g;
+    }
+    g.valid = 1;
+    return g;
+}
+
+// ------------------------------------------------------------------ tiles
+__device__ __forceinline__ uint64_t ck4(uint4 x, uint64_t i) {
+    return (uint64_t)x.x * (2 * i + 1) + (uint64_t)x.y * (2 * i + 3) + (uint64_t)x.z * (2 * i + 5) +
+           (uint64_t)x.w * (2 * i + 7);
+}
+__device__ __forceinline__ uint64_t ck2(uint2 x, uint64_t i) {
+    return (uint64_t)x.x * (2 * i + 1) + (uint64_t)x.y * (2 * i + 3);
+}
+
+// bytes [b0, b1) of src -> dst; returns this thread's checksum terms, word index of
+// byte b of the output = wbase + b / 4
+__device__ __forceinline__ uint64_t copy_ck(uint8_t *dst, const uint8_t *src, uint64_t b0, uint64_t b1, uint64_t wbase) {
+    uint64_t acc = 0;
+    if (((uint64_t)dst | (uint64_t)src | b0 | b1) % 16 == 0) {
+        const uint4 *s = (const uint4 *)src;
+        uint4 *d = (uint4 *)dst;
+        uint64_t v = b0 / 16 + threadIdx.x;
+        const uint64_t e = b1 / 16, st = blockDim.x;
+        for (; v + 3 * st < e; v += 4 * st) {
+            uint4 a = __ldcg(s + v), b = __ldcg(s + v + st), c = __ldcg(s + v + 2 * st), f = __ldcg(s + v + 3 * st);
+            d[v] = a;
+            d[v + st] = b;
+            d[v + 2 * st] = c;
+            d[v + 3 * st] = f;
+            acc += ck4(a, wbase + 4 * v) + ck4(b, wbase + 4 * (v + st)) + ck4(c, wbase + 4 * (v + 2 * st)) +
+                   ck4(f, wbase + 4 * (v + 3 * st));
+        }
+        for (; v < e; v += st) {
+            uint4 a = __ldcg(s + v);
+            d[v] = a;
+            acc += ck4(a, wbase + 4 * v);
+        }
+    } else {
+        const uint2 *s = (const uint2 *)src;
+        uint2 *d = (uint2 *)dst;
+        for (uint64_t v = b0 / 8 + threadIdx.x; v < b1 / 8; v += blockDim.x) {
+            uint2 a = __ldcg(s + v);
+            d[v] = a;
+            acc += ck2(a, wbase + 2 * v);
+        }
+    }
+    return acc;
+}
+
+// one tile of a request (all threads of the CTA); returns this thread's checksum terms
+// (AMO: thread 0 stores the fetched value through *amo_out)
+__device__ uint64_t run_tile(const SvArgs &a, const shmemg_req_t &r, uint64_t dst_off, uint32_t k,
+                             unsigned long long *amo_out) {
+    uint8_t *heap = a.heap;
+    const uint64_t H = a.H;
+    switch (r.kind) {
+    case SHMEMG_OP_PUT:
+    case SHMEMG_OP_GET: {
+        const int sp = r.kind == SHMEMG_OP_PUT ? r.issuer : r.pe, dp = r.kind == SHMEMG_OP_PUT ? r.pe : r.issuer;
+        const uint64_t b0 = (uint64_t)k * RMA_TILE, b1 = b0 + RMA_TILE < r.n ? b0 + RMA_TILE : r.n;
+        return copy_ck(heap + (uint64_t)dp * H + dst_off, heap + (uint64_t)sp * H + r.src, b0, b1, 0);
+    }
+    case SHMEMG_OP_FETCH_ADD:
+    case SHMEMG_OP_COMPARE_SWAP:
+    case SHMEMG_OP_FETCH_XOR: {
+        if (threadIdx.x == 0) {
+            const uint64_t pe = r.word / a.cfg.amo_words, idx = r.word - pe * a.cfg.amo_words;
+            unsigned long long *t = (unsigned long long *)(heap + pe * H + a.cfg.amo_offset + idx * 8);
+            unsigned long long old;
+            if (r.kind == SHMEMG_OP_FETCH_ADD) old = atomicAdd(t, (unsigned long long)r.operand);
+            else if (r.kind == SHMEMG_OP_COMPARE_SWAP) old = atomicCAS(t, (unsigned long long)r.cond, (unsigned long long)r.operand);
+            else old = atomicXor(t, (unsigned long long)r.operand);
+            *amo_out = old;
+        }
+        return 0;
+    }
+    case SHMEMG_OP_REDUCE: {
+        const int P = r.issuer, pe0 = r.pe;
+        const uint64_t e0 = (uint64_t)k * RED_TILE, e1 = e0 + RED_TILE < r.n ? e0 + RED_TILE : r.n;
+        uint64_t acc = 0;
+        if (r.dtype == SHMEMG_INT64) {
+            for (uint64_t v = e0 / 2 + threadIdx.x; v < e1 / 2; v += blockDim.x) {
+                const uint64_t off = r.src + 16 * v;
+                longlong2 s = __ldcg((const longlong2 *)(heap + (uint64_t)pe0 * H + off));
+                for (int m = 1; m < P; m++) {
+                    longlong2 x = __ldcg((const longlong2 *)(heap + (uint64_t)(pe0 + m) * H + off));
+                    s.x = (long long)((unsigned long long)s.x + (unsigned long long)x.x);
+                    s.y = (long long)((unsigned long long)s.y + (unsigned long long)x.y);
+                }
+                for (int m = 0; m < P; m++) *(longlong2 *)(heap + (uint64_t)(pe0 + m) * H + dst_off + 16 * v) = s;
+                uint4 w;
+                memcpy(&w, &s, 16);
+                acc += ck4(w, 4 * v);
+            }
+        } else if (r.fmt == FMT_F32) {
+            for (uint64_t v = e0 / 4 + threadIdx.x; v < e1 / 4; v += blockDim.x) {
+                const float4 s = shmemg_tree_sum<float4>(heap, H, pe0, 1, P, r.src + 16 * v);
+                for (int m = 0; m < P; m++) *(float4 *)(heap + (uint64_t)(pe0 + m) * H + dst_off + 16 * v) = s;
+                uint4 w;
+                memcpy(&w, &s, 16);
+                acc += ck4(w, 4 * v);
+            }
+        } else {
+            for (uint64_t q = e0 / 4 + threadIdx.x; q < e1 / 4; q += blockDim.x) {
+                qsum4<SHMEMG_FMT_BF16>(heap, H, pe0, 1, P, dst_off, r.src, (uint64_t)r.cond, 4 * q, r.n, true);
+                uint4 w = __ldcg((const uint4 *)(heap + (uint64_t)pe0 * H + dst_off + 16 * q));
+                acc += ck4(w, 4 * q);
+            }
+        }
+        return acc;
+    }
+    case SHMEMG_OP_ALLTOALL: {
+        const int P = r.issuer, pe0 = r.pe;
+        const uint64_t chunks = (r.n + A2A_TILE - 1) / A2A_TILE;
+        const uint64_t pair = k / chunks, ch = k - pair * chunks;
+        const int i = (int)(pair / (uint64_t)P), j = (int)(pair - (uint64_t)i * P);
+        const uint64_t b0 = ch * A2A_TILE, b1 = b0 + A2A_TILE < r.n ? b0 + A2A_TILE : r.n;
+        const uint64_t wbase = ((uint64_t)j * P * r.n + (uint64_t)i * r.n) / 4;
+        return copy_ck(heap + (uint64_t)(pe0 + j) * H + dst_off + (uint64_t)i * r.n,
+                       heap + (uint64_t)(pe0 + i) * H + r.src + (uint64_t)j * r.n, b0, b1, wbase);
+    }
+    default:
+        return 0;
+    }
+}
+
+__device__ __forceinline__ uint64_t block_sum_u64(uint64_t v) {
+    __shared__ uint64_t s_part[32];
+    for (int o = 16; o; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) s_part[threadIdx.x >> 5] = v;
+    __syncthreads();
+    uint64_t t = 0;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < (int)(blockDim.x >> 5); w++) t += s_part[w];
+    __syncthreads();
+    return t;  // valid in thread 0
+}
+
+// completion record to mapped host memory (thread scope); bounded wait for ring room
+__device__ void write_completion(const SvArgs &a, uint64_t ticket, uint64_t t_admit, uint64_t result, int status) {
+    const unsigned long long pos = atomicAdd(&a.ctl->comp_pos, 1ull);
+    const uint64_t t0 = now_dev();
+    while (pos - a.host->consumed >= a.ring_slots) {
+        if (now_dev() - t0 > 2000000000ull) return;  // host stopped reading: drop the record
+        __nanosleep(1000);
+    }
+    volatile shmemg_completion_t *c = a.comp + (pos % a.ring_slots);
+    c->ticket = ticket;
+    c->t_admit_ns = t_admit;
+    c->t_done_ns = now_dev();
+    c->result = result;
+    c->status = status;
+    shmemg_d_fence_sys();
+    asm volatile("st.release.sys.global.u32 [%0], %1;" ::"l"((const uint32_t *)&c->seq), "r"((uint32_t)(pos + 1))
+                 : "memory");
+}
+
+// ------------------------------------------------------------------ admitter
+__device__ bool find_pages(const SvArgs &a, const Geo &g, uint32_t need, uint32_t *first) {
+    if (need == 0) { *first = 0; return true; }
+    if (need > a.pages_per_pe) return false;
+    uint32_t run = 0;
+    for (uint32_t w = 0; w < a.bm_words; w++) {
+        unsigned long long occ = 0;
+        for (int m = 0; m < g.count; m++)
+            occ |= *(volatile unsigned long long *)&a.bitmaps[(uint64_t)(g.first + m) * a.bm_words + w];
+        for (int b = 0; b < 64; b++) {
+            const uint32_t page = w * 64 + b;
+            if (page >= a.pages_per_pe) return false;
+            if ((occ >> b) & 1ull) {
+                run = 0;
+            } else if (++run == need) {
+                *first = page + 1 - need;
+                return true;
+            }
+        }
+    }
+    return false;
+}
+
+__device__ void mark_pages(const SvArgs &a, int first_pe, int count, uint32_t p0, uint32_t np, bool set) {
+    for (int m = 0; m < count; m++) {
+        unsigned long long *bm = a.bitmaps + (uint64_t)(first_pe + m) * a.bm_words;
+        for (uint32_t p = p0; p < p0 + np;) {
+            const uint32_t w = p / 64, b = p % 64;
+            const uint32_t nb = (64 - b) < (p0 + np - p) ? (64 - b) : (p0 + np - p);
+            const unsigned long long mask = (nb == 64 ? ~0ull : ((1ull << nb) - 1)) << b;
+            if (set) atomicOr(bm + w, mask);
+            else atomicAnd(bm + w, ~mask);
+            p += nb;
+        }
+    }
+}
+
+__device__ void admitter(const SvArgs &a) {
+    uint64_t head = 0, fifo_tail = 0;
+    uint32_t rot = 0;
+    const uint64_t t_start = now_dev();
+    uint64_t t_last = t_start;
+    bool have = false;
+    shmemg_req_t r;
+    uint32_t sleep_ns = 64;
+    for (;;) {
+        const uint64_t now = now_dev();
+        if (now - t_start > a.cfg.max_ns) break;
+        if (!have) {
+            const uint64_t tail = shmemg_d_ld_acquire_sys_u64(&a.host->tail);
+            if (head < tail) {
+                volatile const shmemg_req_t *src = a.ring + (head % a.ring_slots);
+                r.kind = src->kind;
+                r.dtype = src->dtype;
+                r.fmt = src->fmt;
+                r.pe = src->pe;
+                r.issuer = src->issuer;
+                r.n = src->n;
+                r.word = src->word;
+                r.operand = src->operand;
+                r.cond = src->cond;
+                r.src = src->src;
+                r.ticket = src->ticket;
+                have = true;
+                t_last = now;
+            } else {
+                const bool idle = *(volatile unsigned long long *)&a.ctl->inflight == 0;
+                if (idle && a.host->stop) break;
+                if (idle && now - t_last > a.cfg.idle_ns) break;
+                __nanosleep(sleep_ns);
+                if (sleep_ns < 2048) sleep_ns <<= 1;
+                continue;
+            }
+        }
+        sleep_ns = 64;
+        const Geo g = geometry(r, a.npes, a.H, a.cfg.amo_words);
+        if (!g.valid) {
+            write_completion(a, r.ticket, now, 0, SHMEMG_ERR_INVALID_ARG);
+            head++;
+            asm volatile("st.release.sys.global.u64 [%0], %1;" ::"l"((const uint64_t *)&a.host->head), "l"(head) : "memory");
+            have = false;
+            continue;
+        }
+        const uint32_t need = (uint32_t)((g.bytes + a.cfg.page_bytes - 1) / a.cfg.page_bytes);
+        if (need > a.pages_per_pe) {
+            write_completion(a, r.ticket, now, 0, SHMEMG_ERR_OUT_OF_HEAP);
+            head++;
+            asm volatile("st.release.sys.global.u64 [%0], %1;" ::"l"((const uint64_t *)&a.host->head), "l"(head) : "memory");
+            have = false;
+            continue;
+        }
+        // a free slot and room in the queue
+        if (fifo_tail - *(volatile unsigned long long *)&a.ctl->fifo_head >= a.fifo_cap) { __nanosleep(256); continue; }
+        int slot = -1;
+        for (uint32_t i = 0; i < a.nslots; i++) {
+            const uint32_t s = (rot + i) % a.nslots;
+            if (*(volatile unsigned int *)&a.slots[s].busy == 0) { slot = (int)s; break; }
+        }
+        if (slot < 0) { __nanosleep(256); continue; }
+        uint32_t p0 = 0;
+        if (!find_pages(a, g, need, &p0)) { __nanosleep(256); continue; }
+        shmemg_d_fence_gpu();  // page frees and slot releases seen above happen before reuse
+        mark_pages(a, g.first, g.count, p0, need, true);
+        SvSlot &s = a.slots[slot];
+        const uint32_t gen = s.gen + 1;
+        s.req = r;
+        s.dst_off = a.cfg.arena_offset + (uint64_t)p0 * a.cfg.page_bytes;
+        s.page0 = p0;
+        s.npages = need;
+        s.ntiles = g.ntiles;
+        s.gen = gen;
+        s.done = 0;
+        s.checksum = 0;
+        s.t_admit = now;
+        s.status = 0;
+        s.busy = 1;
+        atomicAdd(&a.ctl->inflight, 1ull);
+        shmemg_d_fence_gpu();
+        asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(&s.claim), "l"((unsigned long long)gen << 32) : "memory");
+        a.fifo[fifo_tail % a.fifo_cap] = ((unsigned long long)gen << 32) | (unsigned)slot;
+        fifo_tail++;
+        asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(&a.ctl->fifo_tail), "l"((unsigned long long)fifo_tail) : "memory");
+        rot = (uint32_t)slot + 1;
+        head++;
+        asm volatile("st.release.sys.global.u64 [%0], %1;" ::"l"((const uint64_t *)&a.host->head), "l"(head) : "memory");
+        have = false;
+        t_last = now;
+    }
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(&a.ctl->exit_flag), "r"(1u) : "memory");
+}
+
+// ------------------------------------------------------------------ workers
+__device__ void finalize(const SvArgs &a, SvSlot &s) {
+    shmemg_d_fence_gpu();
+    const shmemg_req_t r = s.req;
+    const Geo g = geometry(r, a.npes, a.H, a.cfg.amo_words);
+    if (s.npages) mark_pages(a, g.first, g.count, s.page0, s.npages, false);
+    write_completion(a, r.ticket, s.t_admit, s.checksum, s.status);
+    atomicAdd(&a.ctl->inflight, ~0ull);  // -1
+    shmemg_d_fence_gpu();
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(&s.busy), "r"(0u) : "memory");
+}
+
+__device__ void worker(const SvArgs &a) {
+    __shared__ int s_cmd;
+    __shared__ uint32_t s_slot, s_tile;
+    __shared__ unsigned long long s_amo;
+    const uint32_t me = blockIdx.x - 1;
+    uint32_t sleep_ns = 32;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            int cmd = 0;
+            for (int tries = 0; tries < 64 && cmd == 0; tries++) {
+                if (*(volatile unsigned int *)&a.ctl->exit_flag) { cmd = -1; break; }
+                const unsigned long long h = shmemg_d_ld_acquire_u64((const uint64_t *)&a.ctl->fifo_head);
+                const unsigned long long t = shmemg_d_ld_acquire_u64((const uint64_t *)&a.ctl->fifo_tail);
+                if (h >= t) break;
+                const uint32_t live = (uint32_t)((t - h) < WINDOW ? (t - h) : WINDOW);
+                const uint32_t start = me % live;
+                for (uint32_t j = 0; j < live && cmd == 0; j++) {
+                    const unsigned long long pos = h + (start + j) % live;
+                    const unsigned long long e = *(volatile unsigned long long *)&a.fifo[pos % a.fifo_cap];
+                    const uint32_t slot = (uint32_t)e, gen = (uint32_t)(e >> 32);
+                    SvSlot &s = a.slots[slot];
+                    unsigned long long c = shmemg_d_ld_acquire_u64((const uint64_t *)&s.claim);
+                    for (;;) {
+                        if ((uint32_t)(c >> 32) != gen || (uint32_t)c >= *(volatile uint32_t *)&s.ntiles) {
+                            if (pos == h) atomicCAS(&a.ctl->fifo_head, h, h + 1);  // exhausted or stale head
+                            break;
+                        }
+                        const unsigned long long seen = atomicCAS(&s.claim, c, c + 1);
+                        if (seen == c) {
+                            s_slot = slot;
+                            s_tile = (uint32_t)c;
+                            cmd = 1;
+                            break;
+                        }
+                        c = seen;
+                    }
+                }
+            }
+            s_cmd = cmd;
+        }
+        __syncthreads();
+        const int cmd = s_cmd;
+        if (cmd < 0) break;
+        if (cmd == 0) {
+            __syncthreads();
+            __nanosleep(sleep_ns);
+            if (sleep_ns < 1024) sleep_ns <<= 1;
+            continue;
+        }
+        sleep_ns = 32;
+        SvSlot &s = a.slots[s_slot];
+        const shmemg_req_t r = s.req;
+        const uint64_t part = run_tile(a, r, s.dst_off, s_tile, &s_amo);
+        const uint64_t sum = block_sum_u64(part);
+        if (threadIdx.x == 0) {
+            if (r.kind == SHMEMG_OP_FETCH_ADD || r.kind == SHMEMG_OP_COMPARE_SWAP || r.kind == SHMEMG_OP_FETCH_XOR)
+                s.checksum = s_amo;
+            else
+                atomicAdd(&s.checksum, (unsigned long long)sum);
+            shmemg_d_fence_gpu();
+            if (atomicAdd(&s.done, 1u) == s.ntiles - 1) finalize(a, s);
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(SV_THREADS) k_server(SvArgs a) {
+    if (blockIdx.x == 0) {
+        if (threadIdx.x == 0) admitter(a);
+        return;
+    }
+    worker(a);
+}
+
+// ------------------------------------------------------------------ plain path
+struct PlainScratch {
+    unsigned long long checksum, amo;
+    unsigned int done, pad;
+    uint64_t t_start;
+};
+
+__global__ void __launch_bounds__(SV_THREADS) k_plain(SvArgs a, shmemg_req_t r, uint32_t ntiles, int status,
+                                                      PlainScratch *sc, shmemg_completion_t *rec) {
+    __shared__ unsigned long long s_amo;
+    if (blockIdx.x == 0 && threadIdx.x == 0) sc->t_start = now_dev();
+    uint64_t part = 0;
+    if (status == SHMEMG_SUCCESS)
+        for (uint32_t k = blockIdx.x; k < ntiles; k += gridDim.x) {
+            part += run_tile(a, r, a.cfg.arena_offset, k, &s_amo);
+            __syncthreads();
+            if (threadIdx.x == 0 && (r.kind == SHMEMG_OP_FETCH_ADD || r.kind == SHMEMG_OP_COMPARE_SWAP ||
+                                     r.kind == SHMEMG_OP_FETCH_XOR))
+                sc->amo = s_amo;
+        }
+    const uint64_t sum = block_sum_u64(part);
+    if (threadIdx.x == 0) {
+        atomicAdd(&sc->checksum, (unsigned long long)sum);
+        shmemg_d_fence_gpu();
+        if (atomicAdd(&sc->done, 1u) == gridDim.x - 1) {
+            shmemg_d_fence_gpu();
+            const bool amo = r.kind == SHMEMG_OP_FETCH_ADD || r.kind == SHMEMG_OP_COMPARE_SWAP ||
+                             r.kind == SHMEMG_OP_FETCH_XOR;
+            volatile shmemg_completion_t *c = rec;
+            c->ticket = r.ticket;
+            c->t_admit_ns = sc->t_start;
+            c->result = amo ? sc->amo : sc->checksum;
+            c->status = status;
+            c->t_done_ns = now_dev();
+            c->seq = 1;
+            sc->checksum = 0;
+            sc->amo = 0;
+            sc->done = 0;
+            shmemg_d_fence_sys();
+        }
+    }
+}
+
+__global__ void k_stamp(uint64_t *out) { *out = shmemg_d_globaltimer(); }
+
+static uint64_t host_ns() {
+    timespec t;
+    clock_gettime(CLOCK_MONOTONIC, &t);
+    return (uint64_t)t.tv_sec * 1000000000ull + (uint64_t)t.tv_nsec;
+}
+
+static int cfg_check(const shmemg_server_cfg_t &c0, shmemg_server_cfg_t *out) {
+    State &S = st();
+    shmemg_server_cfg_t c = c0;
+    if (c.page_bytes == 0) c.page_bytes = 65536;
+    if (c.ring_slots == 0) c.ring_slots = 65536;
+    if (c.max_inflight == 0) c.max_inflight = 1024;
+    if (c.idle_ns == 0) c.idle_ns = 60ull * 1000000000ull;
+    if (c.max_ns == 0) c.max_ns = 600ull * 1000000000ull;
+    if (c.page_bytes % 256 || c.ring_slots < 2 || (c.ring_slots & (c.ring_slots - 1)) || c.max_inflight < 1)
+        return SHMEMG_ERR_INVALID_ARG;
+    if (c.arena_offset % 256 || c.arena_offset > S.H || c.arena_bytes > S.H - c.arena_offset) return SHMEMG_ERR_INVALID_ARG;
+    if (c.arena_bytes / c.page_bytes > 4096) return SHMEMG_ERR_INVALID_ARG;
+    if (c.amo_words && (c.amo_offset % 8 || c.amo_offset > S.H || c.amo_words * 8 > S.H - c.amo_offset))
+        return SHMEMG_ERR_INVALID_ARG;
+    *out = c;
+    return SHMEMG_SUCCESS;
+}
+
+}  // namespace shmemg
+
+using namespace shmemg;
+
+struct shmemg_server_s {
+    SvArgs args;
+    SvHost *host = nullptr;            // mapped host control
+    shmemg_req_t *ring = nullptr;      // mapped host ring
+    shmemg_completion_t *comp = nullptr;
+    void *dev_mem = nullptr;           // bitmaps, slots, fifo, ctl
+    uint64_t tail = 0, comp_next = 0, ticket = 0;
+    cudaStream_t stream = nullptr;
+};
+
+static void server_free(shmemg_server_s *s) {
+    if (s->dev_mem) cudaFree(s->dev_mem);
+    if (s->host) cudaFreeHost(s->host);
+    if (s->ring) cudaFreeHost(s->ring);
+    if (s->comp) cudaFreeHost(s->comp);
+    delete s;
+}
+
+extern "C" {
+
+int shmemg_server_start(const shmemg_server_cfg_t *cfg_in, void *stream, shmemg_server_t *out) {
+    if (int rc = check_init()) return rc;
+    if (!cfg_in || !out) return SHMEMG_ERR_INVALID_ARG;
+    State &S = st();
+    shmemg_server_cfg_t cfg;
+    if (int rc = cfg_check(*cfg_in, &cfg)) return rc;
+    auto *s = new shmemg_server_s();
+    SvArgs &a = s->args;
+    memset(&a, 0, sizeof(a));
+    a.heap = S.heap;
+    a.H = S.H;
+    a.npes = S.npes;
+    a.cfg = cfg;
+    a.pages_per_pe = (uint32_t)(cfg.arena_bytes / cfg.page_bytes);
+    a.bm_words = (a.pages_per_pe + 63) / 64;
+    a.nslots = (uint32_t)cfg.max_inflight;
+    a.fifo_cap = 1;
+    while (a.fifo_cap < 2 * a.nslots) a.fifo_cap <<= 1;
+    a.ring_slots = (uint32_t)cfg.ring_slots;
+    size_t bm_bytes = (size_t)S.npes * (a.bm_words ? a.bm_words : 1) * 8;
+    size_t off_slots = (bm_bytes + 255) & ~(size_t)255;
+    size_t off_fifo = off_slots + (((size_t)a.nslots * sizeof(SvSlot) + 255) & ~(size_t)255);
+    size_t off_ctl = off_fifo + (((size_t)a.fifo_cap * 8 + 255) & ~(size_t)255);
+    size_t total = off_ctl + sizeof(SvCtl);
+    int rc = cuda_rc(cudaMalloc(&s->dev_mem, total));
+    if (!rc) rc = cuda_rc(cudaMemset(s->dev_mem, 0, total));
+    if (!rc) rc = cuda_rc(cudaHostAlloc((void **)&s->host, sizeof(SvHost), cudaHostAllocMapped));
+    if (!rc) rc = cuda_rc(cudaHostAlloc((void **)&s->ring, sizeof(shmemg_req_t) * a.ring_slots, cudaHostAllocMapped));
+    if (!rc) rc = cuda_rc(cudaHostAlloc((void **)&s->comp, sizeof(shmemg_completion_t) * a.ring_slots, cudaHostAllocMapped));
+    if (rc) { server_free(s); return rc; }
+    memset((void *)s->host, 0, sizeof(SvHost));
+    memset(s->ring, 0, sizeof(shmemg_req_t) * a.ring_slots);
+    memset(s->comp, 0, sizeof(shmemg_completion_t) * a.ring_slots);
+    uint8_t *d = (uint8_t *)s->dev_mem;
+    a.bitmaps = (unsigned long long *)d;
+    a.slots = (SvSlot *)(d + off_slots);
+    a.fifo = (unsigned long long *)(d + off_fifo);
+    a.ctl = (SvCtl *)(d + off_ctl);
+    void *p;
+    if ((rc = cuda_rc(cudaHostGetDevicePointer(&p, (void *)s->host, 0)))) { server_free(s); return rc; }
+    a.host = (SvHost *)p;
+    if ((rc = cuda_rc(cudaHostGetDevicePointer(&p, s->ring, 0)))) { server_free(s); return rc; }
+    a.ring = (shmemg_req_t *)p;
+    if ((rc = cuda_rc(cudaHostGetDevicePointer(&p, s->comp, 0)))) { server_free(s); return rc; }
+    a.comp = (shmemg_completion_t *)p;
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_server, SV_THREADS, 0);
+    int cap = per_sm * S.sm_count;
+    int workers = cfg.workers > 0 ? cfg.workers : cap - 1;
+    if (workers < 1 || workers + 1 > cap) { server_free(s); return SHMEMG_ERR_UNSUPPORTED; }
+    s->stream = to_stream(stream);
+    cudaLaunchConfig_t lc = {};
+    lc.gridDim = dim3(workers + 1);
+    lc.blockDim = dim3(SV_THREADS);
+    lc.stream = s->stream;
+    cudaLaunchAttribute at;
+    at.id = cudaLaunchAttributeCooperative;
+    at.val.cooperative = 1;
+    lc.attrs = &at;
+    lc.numAttrs = 1;
+    void *kargs[] = {(void *)&a};
+    if ((rc = cuda_rc(cudaLaunchKernelExC(&lc, (const void *)k_server, kargs)))) { server_free(s); return rc; }
+    *out = s;
+    return SHMEMG_SUCCESS;
+}
+
+int shmemg_server_submit(shmemg_server_t s, const shmemg_req_t *req, uint64_t *ticket) {
+    if (!s || !req) return SHMEMG_ERR_INVALID_ARG;
+    const uint64_t head = __atomic_load_n(&s->host->head, __ATOMIC_ACQUIRE);
+    if (s->tail - head >= s->args.ring_slots) return SHMEMG_ERR_BUSY;
+    shmemg_req_t r = *req;
+    r.ticket = s->ticket++;
+    s->ring[s->tail % s->args.ring_slots] = r;
+    s->tail++;
+    __atomic_store_n(&s->host->tail, s->tail, __ATOMIC_RELEASE);
+    if (ticket) *ticket = r.ticket;
+    return SHMEMG_SUCCESS;
+}
+
+int shmemg_server_feed(shmemg_server_t s, const shmemg_req_t *reqs, int count, const uint64_t *arrival_ns,
+                       uint64_t *t0_ns) {
+    if (!s || count < 0 || (count && (!reqs || !arrival_ns))) return SHMEMG_ERR_INVALID_ARG;
+    const uint64_t t0 = host_ns();
+    if (t0_ns) *t0_ns = t0;
+    for (int i = 0; i < count; i++) {
+        const uint64_t target = t0 + arrival_ns[i];
+        while (host_ns() < target) {
+        }
+        const uint64_t give_up = host_ns() + 60ull * 1000000000ull;
+        while (shmemg_server_submit(s, &reqs[i], nullptr) == SHMEMG_ERR_BUSY) {
+            if (host_ns() > give_up) return SHMEMG_ERR_TIMEOUT;
+        }
+    }
+    return SHMEMG_SUCCESS;
+}
+
+int shmemg_server_poll(shmemg_server_t s, shmemg_completion_t *out, int max, int *got) {
+    if (!s || !got || max < 0 || (max && !out)) return SHMEMG_ERR_INVALID_ARG;
+    int n = 0;
+    while (n < max) {
+        shmemg_completion_t *c = s->comp + (s->comp_next % s->args.ring_slots);
+        const uint32_t seq = __atomic_load_n(&c->seq, __ATOMIC_ACQUIRE);
+        if (seq != (uint32_t)(s->comp_next + 1)) break;
+        out[n++] = *c;
+        s->comp_next++;
+    }
+    __atomic_store_n(&s->host->consumed, s->comp_next, __ATOMIC_RELEASE);
+    *got = n;
+    return SHMEMG_SUCCESS;
+}
+
+int shmemg_server_stop(shmemg_server_t s) {
+    if (!s) return SHMEMG_ERR_INVALID_ARG;
+    __atomic_store_n(&s->host->stop, 1u, __ATOMIC_RELEASE);
+    const uint64_t give_up = host_ns() + 60ull * 1000000000ull;
+    int rc = SHMEMG_SUCCESS;
+    for (;;) {
+        // keep reading completions so a kernel waiting for ring room can finish
+        shmemg_completion_t tmp[256];
+        int got = 0;
+        shmemg_server_poll(s, tmp, 256, &got);
+        cudaError_t e = cudaStreamQuery(s->stream);
+        if (e == cudaSuccess) break;
+        if (e != cudaErrorNotReady) { rc = cuda_rc(e); break; }
+        if (host_ns() > give_up) return SHMEMG_ERR_TIMEOUT;  // kernel still running: keep its memory
+        std::this_thread::sleep_for(std::chrono::microseconds(200));
+    }
+    server_free(s);
+    return rc;
+}
+
+int shmemg_request_run(const shmemg_req_t *req, const shmemg_server_cfg_t *cfg_in, shmemg_completion_t *rec,
+                       void *stream) {
+    if (int rc = check_init()) return rc;
+    if (!req || !cfg_in || !rec) return SHMEMG_ERR_INVALID_ARG;
+    State &S = st();
+    shmemg_server_cfg_t cfg;
+    if (int rc = cfg_check(*cfg_in, &cfg)) return rc;
+    SvArgs a;
+    memset(&a, 0, sizeof(a));
+    a.heap = S.heap;
+    a.H = S.H;
+    a.npes = S.npes;
+    a.cfg = cfg;
+    const Geo g = geometry(*req, S.npes, S.H, cfg.amo_words);
+    int status = g.valid ? SHMEMG_SUCCESS : SHMEMG_ERR_INVALID_ARG;
+    if (g.valid && g.bytes > cfg.arena_bytes) status = SHMEMG_ERR_OUT_OF_HEAP;
+    PlainScratch *sc = (PlainScratch *)(S.base + SHMEMG_SCRATCH_OFF + SCR_WORK) + (S.call_seq++ % 1024);
+    int cap = ctas_for((const void *)k_plain, SV_THREADS, 0);
+    int grid = (int)(g.ntiles < (uint32_t)cap ? (g.ntiles ? g.ntiles : 1) : (uint32_t)cap);
+    SvArgs ka = a;
+    k_plain<<<grid, SV_THREADS, 0, to_stream(stream)>>>(ka, *req, g.ntiles, status, sc, rec);
+    return cuda_rc(cudaGetLastError());
+}
+
+int shmemg_plain_feed(const shmemg_req_t *reqs, int count, const uint64_t *arrival_ns, const shmemg_server_cfg_t *cfg,
+                      shmemg_completion_t *recs, void *stream, uint64_t *t0_ns) {
+    if (int rc = check_init()) return rc;
+    if (count < 0 || (count && (!reqs || !arrival_ns || !recs)) || !cfg) return SHMEMG_ERR_INVALID_ARG;
+    const uint64_t t0 = host_ns();
+    if (t0_ns) *t0_ns = t0;
+    for (int i = 0; i < count; i++) {
+        const uint64_t target = t0 + arrival_ns[i];
+        while (host_ns() < target) {
+        }
+        shmemg_req_t r = reqs[i];
+        r.ticket = (uint64_t)i;
+        if (int rc = shmemg_request_run(&r, cfg, recs + i, stream)) return rc;
+    }
+    return SHMEMG_SUCCESS;
+}
+
+int shmemg_clock_offset(int rounds, int64_t *offset_ns, uint64_t *err_ns) {
+    if (rounds < 1 || !offset_ns || !err_ns) return SHMEMG_ERR_INVALID_ARG;
+    uint64_t *d = nullptr;
+    int rc = cuda_rc(cudaHostAlloc((void **)&d, 8, cudaHostAllocMapped));
+    if (rc) return rc;
+    uint64_t *dd = nullptr;
+    cudaHostGetDevicePointer((void **)&dd, d, 0);
+    uint64_t best = ~0ull;
+    for (int i = 0; i < rounds; i++) {
+        const uint64_t h0 = host_ns();
+        k_stamp<<<1, 1>>>(dd);
+        if ((rc = cuda_rc(cudaDeviceSynchronize()))) break;
+        const uint64_t h1 = host_ns();
+        if (h1 - h0 < best) {
+            best = h1 - h0;
+            *offset_ns = (int64_t)(*(volatile uint64_t *)d - (h0 + (h1 - h0) / 2));
+        }
+    }
+    cudaFreeHost(d);
+    *err_ns = best / 2;
+    return rc;
+}
+
+}  // extern "C"

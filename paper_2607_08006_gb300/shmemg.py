@@ -77,18 +77,27 @@ class Tune(C.Structure):
 class Req(C.Structure):
     _fields_ = [("kind", C.c_uint32), ("dtype", C.c_uint8), ("fmt", C.c_uint8), ("reserved0", C.c_uint16),
                 ("pe", C.c_int32), ("issuer", C.c_int32), ("n", C.c_uint64), ("word", C.c_uint64),
-                ("operand", C.c_int64), ("cond", C.c_int64), ("seed", C.c_uint64), ("ticket", C.c_uint64)]
+                ("operand", C.c_int64), ("cond", C.c_int64), ("src", C.c_uint64), ("ticket", C.c_uint64)]
+
+
+REQ_DTYPE = np.dtype([("kind", "<u4"), ("dtype", "u1"), ("fmt", "u1"), ("reserved0", "<u2"), ("pe", "<i4"),
+                      ("issuer", "<i4"), ("n", "<u8"), ("word", "<u8"), ("operand", "<i8"), ("cond", "<i8"),
+                      ("src", "<u8"), ("ticket", "<u8")])
+COMPLETION_DTYPE = np.dtype([("ticket", "<u8"), ("t_admit_ns", "<u8"), ("t_done_ns", "<u8"), ("result", "<u8"),
+                             ("status", "<i4"), ("seq", "<u4")])
+FMT_F32 = 0xFF
 
 
 class Completion(C.Structure):
     _fields_ = [("ticket", C.c_uint64), ("t_admit_ns", C.c_uint64), ("t_done_ns", C.c_uint64),
-                ("result", C.c_uint64), ("status", C.c_int32), ("reserved0", C.c_int32)]
+                ("result", C.c_uint64), ("status", C.c_int32), ("seq", C.c_uint32)]
 
 
 class ServerCfg(C.Structure):
-    _fields_ = [("workers", C.c_int32), ("threads", C.c_int32), ("ring_slots", C.c_int32),
-                ("max_inflight", C.c_int32), ("page_bytes", C.c_uint64), ("arena_offset", C.c_uint64),
-                ("arena_bytes", C.c_uint64), ("amo_offset", C.c_uint64), ("amo_words", C.c_uint64)]
+    _fields_ = [("workers", C.c_int32), ("ring_slots", C.c_int32), ("max_inflight", C.c_int32),
+                ("reserved0", C.c_int32), ("page_bytes", C.c_uint64), ("arena_offset", C.c_uint64),
+                ("arena_bytes", C.c_uint64), ("amo_offset", C.c_uint64), ("amo_words", C.c_uint64),
+                ("idle_ns", C.c_uint64), ("max_ns", C.c_uint64)]
 
 
 P, I, U64, I64, U32 = C.c_void_p, C.c_int, C.c_uint64, C.c_int64, C.c_uint32
@@ -145,6 +154,10 @@ _SIGS = {
     "shmemg_server_submit": [P, P, P],
     "shmemg_server_poll": [P, P, I, P],
     "shmemg_server_stop": [P],
+    "shmemg_server_feed": [P, P, I, P, P],
+    "shmemg_request_run": [P, P, P, P],
+    "shmemg_plain_feed": [P, I, P, P, P, P, P],
+    "shmemg_clock_offset": [I, P, P],
     "shmemg_device_time_ns": [P],
 }
 for _dt in ("int32", "int64", "float"):
@@ -487,10 +500,21 @@ class Server:
             raise ShmemgError(rc, "shmemg_server_submit")
         return t.value
 
-    def poll(self, out_array, max_n) -> int:
+    def poll(self, out: np.ndarray) -> int:
+        """Fills out (COMPLETION_DTYPE records) with new completions; returns how many."""
         got = C.c_int(0)
-        _call("shmemg_server_poll", self.h, C.cast(out_array, C.c_void_p), max_n, C.byref(got))
+        _call("shmemg_server_poll", self.h, out.ctypes.data_as(C.c_void_p), len(out), C.byref(got))
         return got.value
+
+    def feed(self, reqs: np.ndarray, arrival_ns: np.ndarray) -> int:
+        """Submits reqs (REQ_DTYPE) at host times t0 + arrival_ns (native spin loop);
+        returns t0 (CLOCK_MONOTONIC ns)."""
+        reqs = np.ascontiguousarray(reqs, REQ_DTYPE)
+        arr = np.ascontiguousarray(arrival_ns, np.uint64)
+        t0 = C.c_uint64(0)
+        _call("shmemg_server_feed", self.h, reqs.ctypes.data_as(C.c_void_p), len(reqs),
+              arr.ctypes.data_as(C.c_void_p), C.byref(t0))
+        return t0.value
 
     def stop(self):
         if self.h:
@@ -502,3 +526,31 @@ def device_time_ns() -> int:
     v = C.c_uint64(0)
     _call("shmemg_device_time_ns", C.byref(v))
     return v.value
+
+
+def request_run(req, cfg: ServerCfg, rec_ptr: int, stream=None):
+    """Plain path: one kernel for one request (REQ_DTYPE record or Req)."""
+    if isinstance(req, np.ndarray):
+        req = np.ascontiguousarray(req, REQ_DTYPE)
+        rp = req.ctypes.data_as(C.c_void_p)
+    else:
+        rp = C.byref(req)
+    _call("shmemg_request_run", rp, C.byref(cfg), rec_ptr, _stream(stream))
+
+
+def plain_feed(reqs: np.ndarray, arrival_ns: np.ndarray, cfg: ServerCfg, recs_ptr: int, stream=None) -> int:
+    """Plain path under open-loop arrivals: one kernel per request launched at its
+    arrival time; completion records to recs_ptr (host-mapped). Returns t0."""
+    reqs = np.ascontiguousarray(reqs, REQ_DTYPE)
+    arr = np.ascontiguousarray(arrival_ns, np.uint64)
+    t0 = C.c_uint64(0)
+    _call("shmemg_plain_feed", reqs.ctypes.data_as(C.c_void_p), len(reqs), arr.ctypes.data_as(C.c_void_p),
+          C.byref(cfg), recs_ptr, _stream(stream), C.byref(t0))
+    return t0.value
+
+
+def clock_offset(rounds=50):
+    """(device globaltimer - host CLOCK_MONOTONIC) in ns, and its error bound."""
+    off, err = C.c_int64(0), C.c_uint64(0)
+    _call("shmemg_clock_offset", rounds, C.byref(off), C.byref(err))
+    return off.value, err.value

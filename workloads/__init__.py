@@ -459,6 +459,127 @@ def gen_batch_teams(seed: int = None, n_teams: int = 256, world: int = 128, p_lo
                       np.array(ii, bool))
 
 
+# --------------------------------------------------------------------------- serving
+# One served request = one 64-byte record (same layout as shmemg_req_t).
+REQ_DTYPE = np.dtype([("kind", "<u4"), ("dtype", "u1"), ("fmt", "u1"), ("reserved0", "<u2"), ("pe", "<i4"),
+                      ("issuer", "<i4"), ("n", "<u8"), ("word", "<u8"), ("operand", "<i8"), ("cond", "<i8"),
+                      ("src", "<u8"), ("ticket", "<u8")])
+assert REQ_DTYPE.itemsize == 64
+FMT_F32 = 0xFF
+
+
+@dataclass
+class ServeLayout:
+    """Per-PE layout of a served heap: AMO table, read-only source zone, page arena."""
+    H: int
+    amo_offset: int
+    amo_words: int
+    ro_offset: int
+    ro_bytes: int
+    arena_offset: int
+    arena_bytes: int
+    page_bytes: int = 65536
+
+
+def serve_layout(H: int = 32 << 20, amo_words: int = 8192) -> ServeLayout:
+    amo = amo_words * 8
+    half = H // 2
+    return ServeLayout(H=H, amo_offset=0, amo_words=amo_words, ro_offset=amo, ro_bytes=half - amo,
+                       arena_offset=half, arena_bytes=half)
+
+
+def serve_source_words(seed: int, pe: int, nwords: int) -> np.ndarray:
+    """Read-only source zone of one PE: binary32 words (k - 128) / 128, k = top byte of a
+    counter draw -- values in [-1, 1) that are also exact in bfloat16 (low 16 bits 0)."""
+    k = (cb64_np(seed, np.arange(nwords, dtype=np.uint64) + np.uint64(pe << 40)) >> np.uint64(56)).astype(np.int64)
+    return ((k - 128).astype(np.float32) / np.float32(128.0))
+
+
+def serve_source_words_torch(seed: int, pe: int, nwords: int, device="cuda"):
+    """Torch twin of ``serve_source_words`` (same bits)."""
+    import torch
+
+    idx = torch.arange(nwords, dtype=torch.int64, device=device) + (pe << 40)
+    z = cb64_torch(seed, idx)
+    k = (z >> 56) & 0xFF
+    return (k - 128).to(torch.float32) / 128.0
+
+
+def gen_serve_requests(seed: int, count: int, npes: int, lay: ServeLayout, rma_max: int = 4 << 20,
+                       red_lo: int = 1 << 16, red_hi: int = 2 << 20, a2a_lo: int = 4096, a2a_hi: int = 256 << 10,
+                       p_hi: int = 64, mix=(0.60, 0.25, 0.10, 0.05), distinct_amo_words: bool = False,
+                       bf16_frac: float = 0.5) -> np.ndarray:
+    """Mixed served requests: put/get of 8 B..rma_max (log-uniform, multiples of 8), int64
+    AMOs (fetch_add 50 %, compare_swap 25 %, fetch_xor 25 %), fp32 or bf16-payload sum
+    reductions over teams of log-uniform 2..p_hi PEs with red_lo..red_hi elements, and
+    alltoall of a2a_lo..a2a_hi bytes per pair (multiples of 16).  Destination footprints are
+    kept within the arena (alltoall: P*m <= arena/2, reduce: 4n <= arena/2); sources lie in
+    the read-only zone at 16-byte aligned offsets."""
+    rng = SplitMix64(seed)
+    out = np.zeros(count, REQ_DTYPE)
+    cum = np.cumsum(mix)
+    words = npes * lay.amo_words
+    amo_perm = None
+    if distinct_amo_words:
+        amo_perm = np.random.default_rng(seed & 0xFFFFFFFF).permutation(words)
+    amo_i = 0
+    ro_lo, ro_hi = lay.ro_offset, lay.ro_offset + lay.ro_bytes
+
+    def src_off(nbytes):
+        span = (ro_hi - ro_lo - nbytes) // 16
+        return ro_lo + 16 * rng.below(max(span, 1))
+
+    for i in range(count):
+        u = rng.uniform()
+        r = out[i]
+        if u < cum[0]:
+            n = 8 * rng.log_uniform_int(1, rma_max // 8)
+            r["kind"] = 1 if rng.below(2) == 0 else 2
+            r["pe"], r["issuer"] = rng.below(npes), rng.below(npes)
+            r["n"] = n
+            r["src"] = src_off(n)
+        elif u < cum[1]:
+            v = rng.uniform()
+            r["kind"] = 5 if v < 0.5 else (6 if v < 0.75 else 7)
+            r["dtype"] = DT_INT64
+            if amo_perm is not None:
+                r["word"] = int(amo_perm[amo_i % words])
+                amo_i += 1
+            else:
+                r["word"] = rng.below(words)
+            r["operand"] = rng.next() - (1 << 63) if r["kind"] != 5 else rng.randint(1, 1 << 20)
+            r["cond"] = rng.next() - (1 << 63)
+        elif u < cum[2]:
+            P = rng.log_uniform_int(2, min(p_hi, npes))
+            n = 4 * (rng.log_uniform_int(red_lo, red_hi) // 4)
+            n = min(n, (lay.arena_bytes // 2) // 4)
+            bf = rng.uniform() < bf16_frac
+            r["kind"] = 16
+            r["dtype"] = DT_FLOAT
+            r["fmt"] = FMT_BF16 if bf else FMT_F32
+            r["pe"], r["issuer"] = rng.below(npes - P + 1), P
+            r["n"] = n
+            r["src"] = src_off(n * (2 if bf else 4))
+            if bf:
+                r["cond"] = src_off(4 * ((n + 127) // 128))
+        else:
+            P = rng.log_uniform_int(2, min(p_hi, npes))
+            m = 16 * (rng.log_uniform_int(a2a_lo, a2a_hi) // 16)
+            m = min(m, 16 * ((lay.arena_bytes // 2) // P // 16))
+            r["kind"] = 15
+            r["pe"], r["issuer"] = rng.below(npes - P + 1), P
+            r["n"] = m
+            r["src"] = src_off(m * P)
+    return out
+
+
+def poisson_arrivals_ns(seed: int, count: int, rate_per_s: float) -> np.ndarray:
+    """Cumulative Poisson arrival times (ns) at the given rate."""
+    u = 1.0 - u01_np(cb64_np(seed, np.arange(count, dtype=np.uint64)))
+    gaps = -np.log(u) / rate_per_s * 1e9
+    return np.cumsum(gaps).astype(np.uint64)
+
+
 # --------------------------------------------------------------------------- sweep points
 KiB, MiB = 1 << 10, 1 << 20
 SWEEP_ELEMS = [1 << 10, 1 << 12, 1 << 14, 1 << 16, 1 << 18, 1 << 20, 1 << 22, 1 << 24]

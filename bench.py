@@ -443,6 +443,355 @@ def run_reference(args, rank, world):
             "e2e": {"value": round(value, 3), "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+# ----------------------------------------------------------------------------- AMO / signal stress
+def _events(torch):
+    return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+
+def run_amo(torch, sg, nops_log2=26, reps=3):
+    """1024 PEs (one CTA each) over a 2^27-word int64 table; uniform and Zipf(1.1)
+    streams of 2^nops_log2 fetch_add/compare_swap/fetch_xor; GUPS with and without warp
+    aggregation, against an L2-resident table and the HBM-sector ceiling; then 512
+    put_signal/wait_until ping-pong pairs."""
+    npes, wpp = 1024, 1 << 17
+    Hh = wpp * 8 + 16384
+    heap = sg.Heap(npes, Hh)
+    out = {"npes": npes, "table_words": npes * wpp, "ops": 1 << nops_log2}
+    try:
+        parts = heap.partitions()
+        tseed, oseed = W.derive_seed("amo-table"), W.derive_seed("amo-ops")
+        for p0 in range(0, npes, 128):
+            idx = torch.arange(p0 * wpp, (p0 + 128) * wpp, dtype=torch.int64, device="cuda")
+            parts[p0:p0 + 128, :wpp * 8].view(torch.int64).copy_(W.cb64_torch(tseed, idx).view(128, wpp))
+        nops = 1 << nops_log2
+        s = torch.cuda.current_stream()
+        for dist in ("uniform", "zipf"):
+            t0 = time.perf_counter()
+            ops = np.empty(nops, np.uint32)
+            ch = 1 << 24
+            for c in range(0, nops, ch):
+                ops[c:c + ch] = W.amo_stream_np(W.derive_seed("amo-" + dist), min(ch, nops - c), 27, dist=dist, offset=c)
+            gen_s = time.perf_counter() - t0
+            dops = torch.from_numpy(ops.view(np.int32)).cuda()
+            fetched = torch.empty(nops, dtype=torch.int64, device="cuda")
+            for agg in (0, 1):
+                sg.amo_stream(heap.base, wpp, dops, nops, oseed, tseed, fetched, flags=agg)
+                e0, e1 = _events(torch)
+                e0.record(s)
+                for _ in range(reps):
+                    sg.amo_stream(heap.base, wpp, dops, nops, oseed, tseed, fetched, flags=agg)
+                e1.record(s)
+                torch.cuda.synchronize()
+                ms = e0.elapsed_time(e1) / reps
+                out[f"{dist}_{'agg' if agg else 'plain'}"] = {"GUPS": round(nops / (ms * 1e-3) / 1e9, 3),
+                                                              "ms": round(ms, 3)}
+            out[f"{dist}_generation_s"] = round(gen_s, 2)
+            del dops, fetched
+        # L2-resident reference: the same kernel on a table of 2^21 words (16 MiB)
+        small_wpp = (1 << 21) // npes
+        ops = W.amo_stream_np(5, nops, 21, dist="uniform")
+        dops = torch.from_numpy(ops.view(np.int32)).cuda()
+        sg.amo_stream(heap.base, small_wpp, dops, nops, oseed, tseed, None, flags=0)
+        e0, e1 = _events(torch)
+        e0.record(s)
+        for _ in range(reps):
+            sg.amo_stream(heap.base, small_wpp, dops, nops, oseed, tseed, None, flags=0)
+        e1.record(s)
+        torch.cuda.synchronize()
+        l2 = nops / (e0.elapsed_time(e1) / reps * 1e-3) / 1e9
+        hbm, _ = measured_peaks()
+        sector = hbm * 1e9 / (4 + 8 + 64) / 1e9
+        out["l2_resident_GUPS"] = round(l2, 3)
+        out["hbm_sector_ceiling_GUPS"] = round(sector, 2)
+        best = max(out["uniform_plain"]["GUPS"], out["uniform_agg"]["GUPS"])
+        out["uniform_frac_of_l2_resident"] = round(best / l2, 3)
+        out["uniform_frac_of_hbm_sector_ceiling"] = round(best / sector, 3)
+        del dops
+        # ping-pong: 512 pairs, 10^4 round trips, payload sweep
+        sg.get_status()
+        sig_off = wpp * 8 + 8192
+        pp = {}
+        iters = 10000
+        lat = torch.zeros(512 * iters, dtype=torch.int64, device="cuda")
+        for payload in (8, 64, 512, 4096):
+            parts[:, sig_off:sig_off + 8].zero_()
+            torch.cuda.synchronize()
+            sg.pingpong(heap.base + wpp * 8, heap.base + sig_off, payload, 512, iters, lat)
+            torch.cuda.synchronize()
+            rt = lat.cpu().numpy().astype(np.float64)
+            half = rt / 2 / 1e3
+            pp[str(payload)] = {"half_rtt_us_p50": round(float(np.percentile(half, 50)), 3),
+                                "half_rtt_us_p99": round(float(np.percentile(half, 99)), 3),
+                                "payload_GBps": round(512 * 2 * payload * iters / (rt.reshape(512, iters).sum(1).max() * 1e-9) / 1e9, 3)}
+        code, _ = sg.get_status()
+        out["pingpong_512_pairs"] = pp
+        out["status"] = code
+    finally:
+        heap.close()
+    return out
+
+
+# ----------------------------------------------------------------------------- batched teams
+def run_batch(torch, sg, reps=5, check_teams=32, check_elems=4096):
+    """256 teams of log-uniform 2-128 PEs (128-PE world), n log-uniform 256-4 Mi, 25 %
+    int64; fp32 N(0,1) payloads vs bf16 / E4M3 payloads with per-128 scales.  One
+    graph-captured persistent launch per format, autotuned; compared with one launch per
+    team and with the untuned plan; error against binary64 on sampled elements."""
+    bt = W.gen_batch_teams()
+    world = 128
+    P, n = bt.size.astype(np.int64), bt.n.astype(np.int64)
+    need = np.where(bt.is_int, 16 * n, 10 * n + 4 * ((n + 127) // 128) + 1024)
+    order = np.argsort(-need, kind="stable")
+    hw = np.zeros(world, np.int64)
+    off = np.zeros(len(P), np.int64)
+    for t in order:
+        s0, e = bt.start[t], bt.start[t] + P[t]
+        o = (int(hw[s0:e].max()) + 255) // 256 * 256
+        off[t] = o
+        hw[s0:e] = o + need[t]
+    Hb = int((hw.max() + (1 << 20)) // (1 << 20) * (1 << 20))
+    heap = sg.Heap(world, Hb)
+    out = {"teams": len(P), "world": world, "heap_bytes_per_pe": Hb}
+    try:
+        base = heap.base
+        gen = torch.Generator(device="cuda")
+        gen.manual_seed(W.derive_seed("batch-values") & 0x7FFFFFFF)
+        lay = []
+        for t in range(len(P)):
+            o = int(off[t])
+            nt = int(n[t])
+            if bt.is_int[t]:
+                src, dst = o, o + 8 * nt
+                for p in range(bt.start[t], bt.start[t] + P[t]):
+                    v = torch.randint(-(1 << 20), (1 << 20) + 1, (nt,), dtype=torch.int64, device="cuda", generator=gen)
+                    heap.view(src, p, torch.int64, nt).copy_(v)
+                lay.append(("i64", src, dst, None, None))
+            else:
+                src = o
+                codes = o + 4 * nt
+                dst = (codes + 2 * nt + 255) // 256 * 256
+                sc = (dst + 4 * nt + 255) // 256 * 256
+                for p in range(bt.start[t], bt.start[t] + P[t]):
+                    heap.view(src, p, torch.float32, nt).normal_(generator=gen)
+                lay.append(("f", src, dst, codes, sc))
+        torch.cuda.synchronize()
+        teams_h = {}
+
+        def descs(fmt):
+            d = []
+            for t, (k, src, dst, codes, sc) in enumerate(lay):
+                st0, sz, nt = int(bt.start[t]), int(P[t]), int(n[t])
+                if k == "i64":
+                    d.append(sg.CollDesc(st0, sz, sg.INT64, -1, nt, base + dst, base + src, None))
+                elif fmt < 0:
+                    d.append(sg.CollDesc(st0, sz, sg.FLOAT, -1, nt, base + dst, base + src, None))
+                else:
+                    d.append(sg.CollDesc(st0, sz, sg.FLOAT, fmt, nt, base + dst, base + codes, base + sc))
+            return d
+
+        def algo_bytes(fmt):
+            tot = 0
+            for t, (k, *_r) in enumerate(lay):
+                e_in = 8 if k == "i64" else (4 if fmt < 0 else (2 if fmt == 0 else 1))
+                e_out = 8 if k == "i64" else 4
+                sc = 0 if (k == "i64" or fmt < 0) else 4 / 128
+                tot += P[t] * n[t] * (e_in + e_out + sc)
+            return float(tot)
+
+        s = torch.cuda.current_stream()
+
+        def time_graph(b):
+            b.launch()
+            e0, e1 = _events(torch)
+            e0.record(s)
+            for _ in range(reps):
+                b.launch()
+            e1.record(s)
+            torch.cuda.synchronize()
+            return e0.elapsed_time(e1) / reps
+
+        hbm, src_kind = measured_peaks()
+        for fmt, name in ((-1, "fp32"), (0, "bf16"), (1, "e4m3")):
+            if fmt >= 0:   # quantise every float team's fp32 input into its codes + scales
+                for t, (k, src, dst, codes, sc) in enumerate(lay):
+                    if k == "i64":
+                        continue
+                    key = (int(bt.start[t]), int(P[t]))
+                    if key not in teams_h:
+                        teams_h[key] = sg.team_split_strided(sg.TEAM_WORLD, key[0], 1, key[1])
+                    sg.quantize(teams_h[key], base + codes, base + sc, base + src, fmt, int(n[t]))
+                torch.cuda.synchronize()
+            ab = algo_bytes(fmt)
+            b = sg.Batch(descs(fmt), sg.Tune(16384, 0, 0, 0))
+            untuned = time_graph(b)
+            tune = b.autotune()
+            tuned = time_graph(b)
+            # one launch per team (plain path)
+            for key in {(int(bt.start[t]), int(P[t])) for t in range(len(P))}:
+                if key not in teams_h:
+                    teams_h[key] = sg.team_split_strided(sg.TEAM_WORLD, key[0], 1, key[1])
+            e0, e1 = _events(torch)
+            e0.record(s)
+            for _ in range(reps):
+                for t, (k, src, dst, codes, sc) in enumerate(lay):
+                    tm = teams_h[(int(bt.start[t]), int(P[t]))]
+                    if k == "i64":
+                        sg.reduce(tm, base + dst, base + src, int(n[t]), sg.INT64, sg.SUM, s)
+                    elif fmt < 0:
+                        sg.reduce(tm, base + dst, base + src, int(n[t]), sg.FLOAT, sg.SUM, s)
+                    else:
+                        sg.qsum_reduce(tm, base + dst, base + codes, base + sc, fmt, int(n[t]), s)
+            e1.record(s)
+            torch.cuda.synchronize()
+            per_team = e0.elapsed_time(e1) / reps
+            b.launch()
+            torch.cuda.synchronize()
+            err = batch_errors(torch, heap, bt, lay, fmt, check_teams, check_elems)
+            out[name] = {"GBps": round(ab / (tuned * 1e-3) / 1e9, 1), "ms": round(tuned, 3),
+                         "frac_of_hbm": round(ab / (tuned * 1e-3) / 1e9 / hbm, 3),
+                         "untuned_ms": round(untuned, 3), "launch_per_team_ms": round(per_team, 3),
+                         "speedup_vs_launch_per_team": round(per_team / tuned, 2),
+                         "tune": {"tile_elems": tune.tile_elems, "ctas_per_sm": tune.ctas_per_sm},
+                         "algorithmic_bytes": ab, "error_vs_fp64": err}
+            b.destroy()
+        for tm in teams_h.values():
+            sg.team_destroy(tm)
+    finally:
+        heap.close()
+    return out
+
+
+def batch_errors(torch, heap, bt, lay, fmt, nteams, nel):
+    """Normwise error of the float teams' outputs against binary64 sums of the original
+    fp32 inputs (sampled: the first nteams float teams, first nel elements)."""
+    rel_max, sq_num, sq_den, i64_ok = 0.0, 0.0, 0.0, True
+    seen = 0
+    for t, (k, src, dst, codes, sc) in enumerate(lay):
+        m = min(int(bt.n[t]), nel)
+        members = range(int(bt.start[t]), int(bt.start[t] + bt.size[t]))
+        if k == "i64":
+            if seen < nteams:
+                x = np.stack([heap.view(src, p, torch.int64, m).cpu().numpy() for p in members])
+                y = heap.view(dst, int(bt.start[t]), torch.int64, m).cpu().numpy()
+                i64_ok &= bool(np.array_equal(x.sum(0), y))
+            continue
+        if seen >= nteams:
+            continue
+        seen += 1
+        x = np.stack([heap.view(src, p, torch.float32, m).cpu().numpy().astype(np.float64) for p in members])
+        y64 = x.sum(0)
+        y = heap.view(dst, int(bt.start[t]), torch.float32, m).cpu().numpy().astype(np.float64)
+        num, den = np.linalg.norm(y - y64), np.linalg.norm(y64)
+        rel_max = max(rel_max, num / den if den else 0.0)
+        sq_num += num * num
+        sq_den += den * den
+    return {"normwise_rel_max": float(f"{rel_max:.3e}"), "normwise_rel_rms": float(f"{math.sqrt(sq_num / sq_den):.3e}"),
+            "int64_teams_exact": i64_ok, "sampled_float_teams": seen, "elements_per_team": nel}
+
+
+# ----------------------------------------------------------------------------- serving
+def serve_latency(recs, t0_host, arrivals, offset_ns):
+    """Per-request latency (us) from the intended arrival (host clock) to device
+    completion, through the measured clock offset."""
+    done_host = recs["t_done_ns"].astype(np.int64) - offset_ns
+    return (done_host - (t0_host + arrivals[recs["ticket"].astype(np.int64)].astype(np.int64))) / 1e3
+
+
+def run_serve(torch, sg, nreq=4096, rates=None, npes=512, Hs=32 << 20):
+    """512 PEs x 32 MiB (16 GiB).  Mixed Poisson arrivals: 60 % put/get 8 B-4 MiB, 25 %
+    int64 AMOs, 10 % fp32/bf16 team reductions, 5 % alltoall; served by the persistent
+    engine and by one launch per request, same arrivals; throughput and p50/p99 latency."""
+    lay = W.serve_layout(H=Hs, amo_words=8192)
+    heap = sg.Heap(npes, Hs)
+    out = {"npes": npes, "heap_bytes": npes * Hs, "requests_per_point": nreq}
+    try:
+        parts = heap.partitions()
+        seed = W.derive_seed("serve-inputs")
+        for p in range(npes):
+            parts[p, lay.ro_offset:lay.ro_offset + lay.ro_bytes].view(torch.float32).copy_(
+                W.serve_source_words_torch(seed, p, lay.ro_bytes // 4))
+        torch.cuda.synchronize()
+        cfg = sg.ServerCfg()
+        cfg.page_bytes = lay.page_bytes
+        cfg.arena_offset, cfg.arena_bytes = lay.arena_offset, lay.arena_bytes
+        cfg.amo_offset, cfg.amo_words = lay.amo_offset, lay.amo_words
+        cfg.max_ns = 300 * 10**9
+        reqs = W.gen_serve_requests(W.derive_seed("serve-reqs"), nreq, npes, lay)
+        mb = float(np.mean(reqs["n"][np.isin(reqs["kind"], (1, 2))])) / 1e6
+        out["mix_counts"] = {k: int(v) for k, v in zip(("rma", "amo", "reduce", "alltoall"), (
+            np.isin(reqs["kind"], (1, 2)).sum(), np.isin(reqs["kind"], (5, 6, 7)).sum(),
+            (reqs["kind"] == 16).sum(), (reqs["kind"] == 15).sum()))}
+        out["mean_rma_MB"] = round(mb, 3)
+        offset, err = sg.clock_offset(50)
+        out["clock_offset_err_us"] = round(err / 1e3, 2)
+        sstream = torch.cuda.Stream()
+        comp_buf = np.zeros(8192, sg.COMPLETION_DTYPE)
+
+        def serve_once(arr):
+            srv = sg.Server(cfg, sstream)
+            t0 = srv.feed(reqs, arr)
+            recs = np.zeros(nreq, sg.COMPLETION_DTYPE)
+            got, tl = 0, time.time()
+            while got < nreq:
+                k = srv.poll(comp_buf)
+                recs[got:got + k] = comp_buf[:k]
+                got += k
+                if k == 0:
+                    if time.time() - tl > 120:
+                        break
+                    time.sleep(0.0002)
+            srv.stop()
+            return recs[:got], t0
+
+        rec_t = torch.zeros(nreq * sg.COMPLETION_DTYPE.itemsize, dtype=torch.uint8).pin_memory()
+
+        def plain_once(arr):
+            rec_t.zero_()
+            pstream = torch.cuda.Stream()
+            t0 = sg.plain_feed(reqs, arr, cfg, rec_t.data_ptr(), pstream)
+            pstream.synchronize()
+            return np.frombuffer(rec_t.numpy().tobytes(), sg.COMPLETION_DTYPE).copy(), t0
+
+        classes = {"rma": (1, 2), "amo": (5, 6, 7), "reduce": (16,), "alltoall": (15,)}
+
+        def summarise(recs, t0, arr):
+            ok = recs[recs["status"] == 0]
+            lat = serve_latency(ok, t0, arr, offset)
+            span = (int(ok["t_done_ns"].max()) - offset - t0) / 1e9
+            svc = (ok["t_done_ns"].astype(np.int64) - ok["t_admit_ns"].astype(np.int64)) / 1e3
+            kinds = reqs["kind"][ok["ticket"].astype(np.int64)]
+            per = {}
+            for cname, ks in classes.items():
+                m = np.isin(kinds, ks)
+                if m.any():
+                    per[cname] = {"p50_us": round(float(np.percentile(lat[m], 50)), 1),
+                                  "p99_us": round(float(np.percentile(lat[m], 99)), 1),
+                                  "service_p50_us": round(float(np.percentile(svc[m], 50)), 1)}
+            return {"req_per_s": round(len(ok) / span, 1), "p50_us": round(float(np.percentile(lat, 50)), 1),
+                    "p99_us": round(float(np.percentile(lat, 99)), 1), "completed": int(len(ok)),
+                    "errors": int((recs["status"] != 0).sum()), "per_class": per}
+
+        # saturation rate: everything at t = 0
+        zero = np.zeros(nreq, np.uint64)
+        r_s, t_s = serve_once(zero)
+        sat = summarise(r_s, t_s, zero)
+        out["burst_server"] = sat
+        r_p, t_p = plain_once(zero)
+        out["burst_plain"] = summarise(r_p, t_p, zero)
+        lam_sat = sat["req_per_s"]
+        pts = rates or [0.5 * lam_sat, 0.9 * lam_sat, 1e6, 1e7]
+        out["points"] = []
+        for lam in pts:
+            arr = W.poisson_arrivals_ns(W.derive_seed("serve-arrivals"), nreq, lam)
+            rs, ts = serve_once(arr)
+            rp, tp = plain_once(arr)
+            out["points"].append({"rate_req_per_s": round(lam, 1), "server": summarise(rs, ts, arr),
+                                  "plain": summarise(rp, tp, arr)})
+    finally:
+        heap.close()
+    return out
+
+
 # ----------------------------------------------------------------------------- distributed
 def dist_init():
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -480,6 +829,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="shmemg", choices=["shmemg", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--secondary", default="amo,batch,serve",
+                    help="extra workloads measured after the sweep (comma list of amo,batch,serve or 'none')")
+    ap.add_argument("--amo-ops-log2", type=int, default=26)
+    ap.add_argument("--serve-requests", type=int, default=4096)
     args = ap.parse_args()
     rank, world = dist_init()
     if args.impl == "reference":
@@ -490,6 +843,25 @@ def main():
     if rank == 0:
         if not args.no_cpu_baseline and world == 1:
             out["cpu_baseline"] = cpu_baseline()
+        sec = [s for s in args.secondary.split(",") if s and s != "none"]
+        if sec:
+            import torch
+
+            import paper_2607_08006_gb300 as sg
+
+            out["secondary"] = {}
+            for name in sec:
+                t0 = time.perf_counter()
+                if name == "amo":
+                    r = run_amo(torch, sg, args.amo_ops_log2)
+                elif name == "batch":
+                    r = run_batch(torch, sg)
+                elif name == "serve":
+                    r = run_serve(torch, sg, args.serve_requests)
+                else:
+                    continue
+                r["wall_s"] = round(time.perf_counter() - t0, 1)
+                out["secondary"][name] = r
         print(json.dumps(out), flush=True)
 
 

@@ -112,7 +112,8 @@ __global__ void __launch_bounds__(AMO_THREADS) k_amo_stream(AmoArgs a) {
 
 // Ping-pong between PEs 2k and 2k+1 (one CTA each): put the payload into the peer's
 // buf + payload, release-add 1 to the peer's signal, acquire-wait for the own signal.
-__global__ void __launch_bounds__(PP_THREADS) k_pingpong(shmemg_device_ctx_t c, uint64_t buf_off, uint64_t sig_off,
+// (at most 64 registers: 1024 ping-pong CTAs must be co-resident)
+__global__ void __launch_bounds__(PP_THREADS, 8) k_pingpong(shmemg_device_ctx_t c, uint64_t buf_off, uint64_t sig_off,
                                                          uint64_t payload, int iters, uint64_t *lat) {
     __shared__ int s_stop;
     const int me = blockIdx.x, peer = me ^ 1, pair = me >> 1;

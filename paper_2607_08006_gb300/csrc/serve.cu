@@ -27,9 +27,9 @@
 namespace shmemg {
 
 constexpr int SV_THREADS = 256;
-constexpr uint64_t RMA_TILE = 128ull << 10;   // bytes per put/get tile
-constexpr uint64_t RED_TILE = 16384;          // elements per reduce tile
-constexpr uint64_t A2A_TILE = 64ull << 10;    // bytes per alltoall block chunk
+constexpr uint64_t RMA_TILE = 64ull << 10;    // bytes per put/get tile
+constexpr uint64_t RED_TILE = 8192;           // elements per reduce tile
+constexpr uint64_t A2A_TILE = 32ull << 10;    // bytes per alltoall block chunk
 constexpr uint32_t WINDOW = 32;               // queue entries workers spread over
 constexpr uint8_t FMT_F32 = 0xFF;
 
@@ -55,6 +55,8 @@ struct SvCtl {                       // device memory
     uint8_t p3[120];
     unsigned long long inflight;
     uint8_t p4[120];
+    unsigned long long consumed_cache;  // last host `consumed` value seen by the device
+    uint8_t p5[120];
 };
 
 struct SvSlot {
@@ -294,10 +296,18 @@ __device__ __forceinline__ uint64_t block_sum_u64(uint64_t v) {
 // completion record to mapped host memory (thread scope); bounded wait for ring room
 __device__ void write_completion(const SvArgs &a, uint64_t ticket, uint64_t t_admit, uint64_t result, int status) {
     const unsigned long long pos = atomicAdd(&a.ctl->comp_pos, 1ull);
-    const uint64_t t0 = now_dev();
-    while (pos - a.host->consumed >= a.ring_slots) {
-        if (now_dev() - t0 > 2000000000ull) return;  // host stopped reading: drop the record
-        __nanosleep(1000);
+    if (pos - *(volatile unsigned long long *)&a.ctl->consumed_cache >= a.ring_slots) {
+        // ring looks full from the cached credit: ask the host how far it has read
+        const uint64_t t0 = now_dev();
+        for (;;) {
+            const unsigned long long cons = a.host->consumed;
+            if (pos - cons < a.ring_slots) {
+                atomicMax(&a.ctl->consumed_cache, cons);
+                break;
+            }
+            if (now_dev() - t0 > 2000000000ull) return;  // host stopped reading: drop the record
+            __nanosleep(1000);
+        }
     }
     volatile shmemg_completion_t *c = a.comp + (pos % a.ring_slots);
     c->ticket = ticket;
@@ -305,7 +315,7 @@ __device__ void write_completion(const SvArgs &a, uint64_t ticket, uint64_t t_ad
     c->t_done_ns = now_dev();
     c->result = result;
     c->status = status;
-    shmemg_d_fence_sys();
+    // the release orders the record's fields before its sequence number
     asm volatile("st.release.sys.global.u32 [%0], %1;" ::"l"((const uint32_t *)&c->seq), "r"((uint32_t)(pos + 1))
                  : "memory");
 }
@@ -347,98 +357,161 @@ __device__ void mark_pages(const SvArgs &a, int first_pe, int count, uint32_t p0
     }
 }
 
-__device__ void admitter(const SvArgs &a) {
-    uint64_t head = 0, fifo_tail = 0;
-    uint32_t rot = 0;
+// Admission state of the admitter (lane 0 of CTA 0's first warp).
+struct AdmState {
+    uint64_t fifo_tail, fifo_published;
+    uint32_t rot;
+};
+
+// Publishes the slots admitted since the last flush: one GPU-scope fence orders every
+// slot field and claim word before the queue tail that workers acquire.
+__device__ __forceinline__ void adm_flush(const SvArgs &a, AdmState &st) {
+    if (st.fifo_published == st.fifo_tail) return;
+    shmemg_d_fence_gpu();
+    asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(&a.ctl->fifo_tail), "l"((unsigned long long)st.fifo_tail)
+                 : "memory");
+    st.fifo_published = st.fifo_tail;
+}
+
+// Tries to admit one request: 1 = admitted (or completed with an error), 0 = no slot,
+// queue room or pages yet (retry later).
+__device__ int adm_try(const SvArgs &a, AdmState &st, const shmemg_req_t &r, uint64_t now) {
+    const Geo g = geometry(r, a.npes, a.H, a.cfg.amo_words);
+    if (!g.valid) {
+        write_completion(a, r.ticket, now, 0, SHMEMG_ERR_INVALID_ARG);
+        return 1;
+    }
+    const uint32_t need = (uint32_t)((g.bytes + a.cfg.page_bytes - 1) / a.cfg.page_bytes);
+    if (need > a.pages_per_pe) {
+        write_completion(a, r.ticket, now, 0, SHMEMG_ERR_OUT_OF_HEAP);
+        return 1;
+    }
+    if (st.fifo_tail - *(volatile unsigned long long *)&a.ctl->fifo_head >= a.fifo_cap) return 0;
+    int slot = -1;
+    for (uint32_t i = 0; i < a.nslots; i++) {
+        const uint32_t s = (st.rot + i) % a.nslots;
+        if (*(volatile unsigned int *)&a.slots[s].busy == 0) { slot = (int)s; break; }
+    }
+    if (slot < 0) return 0;
+    uint32_t p0 = 0;
+    if (!find_pages(a, g, need, &p0)) return 0;
+    shmemg_d_fence_gpu();  // page frees and slot releases seen above happen before reuse
+    mark_pages(a, g.first, g.count, p0, need, true);
+    SvSlot &s = a.slots[slot];
+    const uint32_t gen = s.gen + 1;
+    s.req = r;
+    s.dst_off = a.cfg.arena_offset + (uint64_t)p0 * a.cfg.page_bytes;
+    s.page0 = p0;
+    s.npages = need;
+    s.ntiles = g.ntiles;
+    s.gen = gen;
+    s.done = 0;
+    s.checksum = 0;
+    s.t_admit = now;
+    s.status = 0;
+    s.busy = 1;
+    // release: a worker whose fetch-and-add sees this generation also sees the fields above
+    asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(&s.claim), "l"((unsigned long long)gen << 32) : "memory");
+    atomicAdd(&a.ctl->inflight, 1ull);
+    a.fifo[st.fifo_tail % a.fifo_cap] = ((unsigned long long)gen << 32) | (unsigned)slot;
+    st.fifo_tail++;
+    st.rot = (uint32_t)slot + 1;
+    return 1;
+}
+
+// The admitter warp: each round it acquires the ring tail, reads up to 8 requests with
+// one 16-byte system-scope load per lane (4 lanes per 64-byte request), admits them in
+// order on lane 0 and publishes the batch with one fence.
+// The admitter warp keeps up to PEND requests taken from the ring and admits any of
+// them that fits now (oldest first), so a request waiting for pages does not hold back
+// later ones; once the oldest has waited AGE_NS, only it is tried until it is admitted
+// (no starvation).  Each round the warp acquires the ring tail and reads up to 8 new
+// requests with one 16-byte system-scope load per lane (4 lanes per 64-byte request);
+// admitted requests are published with one fence per round.
+constexpr int PEND = 32;
+constexpr uint64_t AGE_NS = 2000000;
+
+__device__ void admitter_warp(const SvArgs &a) {
+    __shared__ __align__(16) shmemg_req_t s_pend[PEND];  // 16-byte stores below
+    __shared__ uint64_t s_since[PEND];
+    __shared__ int s_ctl[2];
+    __shared__ int s_npend, s_adm;
+    const int lane = threadIdx.x & 31;
+    uint64_t head = 0;
+    AdmState st = {0, 0, 0};
     const uint64_t t_start = now_dev();
     uint64_t t_last = t_start;
-    bool have = false;
-    shmemg_req_t r;
     uint32_t sleep_ns = 64;
+    if (lane == 0) s_npend = 0;
+    __syncwarp();
     for (;;) {
-        const uint64_t now = now_dev();
-        if (now - t_start > a.cfg.max_ns) break;
-        if (!have) {
+        if (lane == 0) {
+            const uint64_t now = now_dev();
             const uint64_t tail = shmemg_d_ld_acquire_sys_u64(&a.host->tail);
-            if (head < tail) {
-                volatile const shmemg_req_t *src = a.ring + (head % a.ring_slots);
-                r.kind = src->kind;
-                r.dtype = src->dtype;
-                r.fmt = src->fmt;
-                r.pe = src->pe;
-                r.issuer = src->issuer;
-                r.n = src->n;
-                r.word = src->word;
-                r.operand = src->operand;
-                r.cond = src->cond;
-                r.src = src->src;
-                r.ticket = src->ticket;
-                have = true;
-                t_last = now;
-            } else {
+            const uint64_t room = (uint64_t)(PEND - s_npend) < 8 ? (uint64_t)(PEND - s_npend) : 8;
+            int nnew = (int)(tail - head < room ? tail - head : room), stop = 0;
+            if (now - t_start > a.cfg.max_ns) stop = 1;
+            if (nnew == 0 && s_npend == 0 && !stop) {
                 const bool idle = *(volatile unsigned long long *)&a.ctl->inflight == 0;
-                if (idle && a.host->stop) break;
-                if (idle && now - t_last > a.cfg.idle_ns) break;
-                __nanosleep(sleep_ns);
-                if (sleep_ns < 2048) sleep_ns <<= 1;
-                continue;
+                if (idle && (a.host->stop || now - t_last > a.cfg.idle_ns)) stop = 1;
             }
+            s_ctl[0] = nnew;
+            s_ctl[1] = stop;
         }
-        sleep_ns = 64;
-        const Geo g = geometry(r, a.npes, a.H, a.cfg.amo_words);
-        if (!g.valid) {
-            write_completion(a, r.ticket, now, 0, SHMEMG_ERR_INVALID_ARG);
-            head++;
-            asm volatile("st.release.sys.global.u64 [%0], %1;" ::"l"((const uint64_t *)&a.host->head), "l"(head) : "memory");
-            have = false;
-            continue;
+        __syncwarp();
+        const int nnew = s_ctl[0];
+        if (s_ctl[1]) break;
+        if (nnew > 0) {
+            const int q = lane >> 2, part = lane & 3, base = s_npend;
+            if (q < nnew) {
+                const uint32_t *p = (const uint32_t *)(a.ring + ((head + q) % a.ring_slots)) + 4 * part;
+                uint4 v;
+                asm volatile("ld.relaxed.sys.global.v4.u32 {%0, %1, %2, %3}, [%4];"
+                             : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+                             : "l"(p)
+                             : "memory");
+                reinterpret_cast<uint4 *>(&s_pend[base + q])[part] = v;
+            }
+            head += (uint64_t)nnew;  // every lane: the next read uses it
         }
-        const uint32_t need = (uint32_t)((g.bytes + a.cfg.page_bytes - 1) / a.cfg.page_bytes);
-        if (need > a.pages_per_pe) {
-            write_completion(a, r.ticket, now, 0, SHMEMG_ERR_OUT_OF_HEAP);
-            head++;
-            asm volatile("st.release.sys.global.u64 [%0], %1;" ::"l"((const uint64_t *)&a.host->head), "l"(head) : "memory");
-            have = false;
-            continue;
+        __syncwarp();
+        int admitted = 0;
+        if (lane == 0) {
+            const uint64_t now = now_dev();
+            for (int i = s_npend; i < s_npend + nnew; i++) s_since[i] = now;
+            int n = s_npend + nnew;
+            const bool aged = n > 0 && now - s_since[0] > AGE_NS;
+            int k = 0;
+            for (int i = 0; i < n; i++) {
+                const bool try_it = !aged || i == 0;
+                if (try_it && adm_try(a, st, s_pend[i], now)) {
+                    admitted++;
+                    continue;
+                }
+                if (k != i) {
+                    s_pend[k] = s_pend[i];
+                    s_since[k] = s_since[i];
+                }
+                k++;
+            }
+            s_npend = k;
+            adm_flush(a, st);
+            if (nnew > 0)
+                asm volatile("st.release.sys.global.u64 [%0], %1;" ::"l"((const uint64_t *)&a.host->head), "l"(head)
+                             : "memory");
+            if (nnew > 0 || admitted) t_last = now;
+            s_adm = admitted;
         }
-        // a free slot and room in the queue
-        if (fifo_tail - *(volatile unsigned long long *)&a.ctl->fifo_head >= a.fifo_cap) { __nanosleep(256); continue; }
-        int slot = -1;
-        for (uint32_t i = 0; i < a.nslots; i++) {
-            const uint32_t s = (rot + i) % a.nslots;
-            if (*(volatile unsigned int *)&a.slots[s].busy == 0) { slot = (int)s; break; }
+        __syncwarp();
+        if (nnew == 0 && s_adm == 0) {
+            __nanosleep(sleep_ns);
+            if (sleep_ns < 1024) sleep_ns <<= 1;
+        } else {
+            sleep_ns = 64;
         }
-        if (slot < 0) { __nanosleep(256); continue; }
-        uint32_t p0 = 0;
-        if (!find_pages(a, g, need, &p0)) { __nanosleep(256); continue; }
-        shmemg_d_fence_gpu();  // page frees and slot releases seen above happen before reuse
-        mark_pages(a, g.first, g.count, p0, need, true);
-        SvSlot &s = a.slots[slot];
-        const uint32_t gen = s.gen + 1;
-        s.req = r;
-        s.dst_off = a.cfg.arena_offset + (uint64_t)p0 * a.cfg.page_bytes;
-        s.page0 = p0;
-        s.npages = need;
-        s.ntiles = g.ntiles;
-        s.gen = gen;
-        s.done = 0;
-        s.checksum = 0;
-        s.t_admit = now;
-        s.status = 0;
-        s.busy = 1;
-        atomicAdd(&a.ctl->inflight, 1ull);
-        shmemg_d_fence_gpu();
-        asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(&s.claim), "l"((unsigned long long)gen << 32) : "memory");
-        a.fifo[fifo_tail % a.fifo_cap] = ((unsigned long long)gen << 32) | (unsigned)slot;
-        fifo_tail++;
-        asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(&a.ctl->fifo_tail), "l"((unsigned long long)fifo_tail) : "memory");
-        rot = (uint32_t)slot + 1;
-        head++;
-        asm volatile("st.release.sys.global.u64 [%0], %1;" ::"l"((const uint64_t *)&a.host->head), "l"(head) : "memory");
-        have = false;
-        t_last = now;
     }
-    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(&a.ctl->exit_flag), "r"(1u) : "memory");
+    if (lane == 0)
+        asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(&a.ctl->exit_flag), "r"(1u) : "memory");
 }
 
 // ------------------------------------------------------------------ workers
@@ -453,15 +526,38 @@ __device__ void finalize(const SvArgs &a, SvSlot &s) {
     asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(&s.busy), "r"(0u) : "memory");
 }
 
+// Claims tile k of whatever request slot s holds now: fetch-and-add on the slot's
+// (generation, next tile) word, then an acquire fence (the admitter published the slot
+// with a release store of that word).  A claimed k < ntiles is always executed, even by
+// a worker that came from an older queue entry of the same slot, so no index is lost.
+__device__ __forceinline__ bool claim_tile(const SvArgs &a, uint32_t slot, uint32_t *tile) {
+    SvSlot &s = a.slots[slot];
+    const unsigned long long c = atomicAdd(&s.claim, 1ull);
+    shmemg_d_fence_gpu();
+    if ((uint32_t)c < *(volatile uint32_t *)&s.ntiles) {
+        *tile = (uint32_t)c;
+        return true;
+    }
+    return false;
+}
+
 __device__ void worker(const SvArgs &a) {
     __shared__ int s_cmd;
     __shared__ uint32_t s_slot, s_tile;
     __shared__ unsigned long long s_amo;
     const uint32_t me = blockIdx.x - 1;
     uint32_t sleep_ns = 32;
+    int sticky = -1;  // slot of the last claim: try it again first
     for (;;) {
         if (threadIdx.x == 0) {
             int cmd = 0;
+            uint32_t tile;
+            if (sticky >= 0 && claim_tile(a, (uint32_t)sticky, &tile)) {
+                s_slot = (uint32_t)sticky;
+                s_tile = tile;
+                cmd = 1;
+            }
+            sticky = -1;
             for (int tries = 0; tries < 64 && cmd == 0; tries++) {
                 if (*(volatile unsigned int *)&a.ctl->exit_flag) { cmd = -1; break; }
                 const unsigned long long h = shmemg_d_ld_acquire_u64((const uint64_t *)&a.ctl->fifo_head);
@@ -474,23 +570,20 @@ __device__ void worker(const SvArgs &a) {
                     const unsigned long long e = *(volatile unsigned long long *)&a.fifo[pos % a.fifo_cap];
                     const uint32_t slot = (uint32_t)e, gen = (uint32_t)(e >> 32);
                     SvSlot &s = a.slots[slot];
-                    unsigned long long c = shmemg_d_ld_acquire_u64((const uint64_t *)&s.claim);
-                    for (;;) {
-                        if ((uint32_t)(c >> 32) != gen || (uint32_t)c >= *(volatile uint32_t *)&s.ntiles) {
-                            if (pos == h) atomicCAS(&a.ctl->fifo_head, h, h + 1);  // exhausted or stale head
-                            break;
-                        }
-                        const unsigned long long seen = atomicCAS(&s.claim, c, c + 1);
-                        if (seen == c) {
-                            s_slot = slot;
-                            s_tile = (uint32_t)c;
-                            cmd = 1;
-                            break;
-                        }
-                        c = seen;
+                    const unsigned long long c = *(volatile unsigned long long *)&s.claim;
+                    if ((uint32_t)(c >> 32) != gen || (uint32_t)c >= *(volatile uint32_t *)&s.ntiles) {
+                        if (pos == h) atomicCAS(&a.ctl->fifo_head, h, h + 1);  // exhausted or stale head
+                        continue;
+                    }
+                    if (claim_tile(a, slot, &tile)) {
+                        s_slot = slot;
+                        s_tile = tile;
+                        sticky = (int)slot;
+                        cmd = 1;
                     }
                 }
             }
+            if (cmd == 1) sticky = (int)s_slot;
             s_cmd = cmd;
         }
         __syncthreads();
@@ -519,9 +612,9 @@ __device__ void worker(const SvArgs &a) {
     }
 }
 
-__global__ void __launch_bounds__(SV_THREADS) k_server(SvArgs a) {
+__global__ void __launch_bounds__(SV_THREADS, 2) k_server(SvArgs a) {
     if (blockIdx.x == 0) {
-        if (threadIdx.x == 0) admitter(a);
+        if (threadIdx.x < 32) admitter_warp(a);
         return;
     }
     worker(a);
@@ -534,7 +627,7 @@ struct PlainScratch {
     uint64_t t_start;
 };
 
-__global__ void __launch_bounds__(SV_THREADS) k_plain(SvArgs a, shmemg_req_t r, uint32_t ntiles, int status,
+__global__ void __launch_bounds__(SV_THREADS, 2) k_plain(SvArgs a, shmemg_req_t r, uint32_t ntiles, int status,
                                                       PlainScratch *sc, shmemg_completion_t *rec) {
     __shared__ unsigned long long s_amo;
     if (blockIdx.x == 0 && threadIdx.x == 0) sc->t_start = now_dev();

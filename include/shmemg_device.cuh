@@ -227,6 +227,101 @@ static __device__ __forceinline__ void shmemg_d_copy_group(shmemg_group g, void 
     }
 }
 
+/* ------------------------------------------------------------------ bulk (TMA) copies */
+/* Large aligned copies go through the Tensor Memory Accelerator's non-tensor bulk path:
+ * one thread streams chunks global -> shared (cp.async.bulk, completion counted in bytes
+ * on an mbarrier) and shared -> global (cp.async.bulk, bulk groups) through a ring of
+ * SHMEMG_BULK_STAGES shared-memory stages, so each SM keeps several chunks in flight
+ * without occupying registers.  Generic-proxy writes made before the copy are made
+ * visible to the async proxy first, and the copy's writes to the generic proxy after. */
+#define SHMEMG_BULK_STAGES 4
+#define SHMEMG_BULK_CHUNK (32u << 10)
+#define SHMEMG_BULK_SMEM (SHMEMG_BULK_STAGES * SHMEMG_BULK_CHUNK)
+#define SHMEMG_BULK_MIN (64u << 10) /* smaller copies use vector loads and stores */
+
+static __device__ __forceinline__ uint32_t shmemg_smem_u32(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+static __device__ __forceinline__ void shmemg_bulk_load(void *smem, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(shmemg_smem_u32(bar)), "r"(bytes)
+                 : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     shmemg_smem_u32(smem)),
+                 "l"(src), "r"(bytes), "r"(shmemg_smem_u32(bar))
+                 : "memory");
+}
+static __device__ __forceinline__ void shmemg_bulk_store(void *dst, const void *smem, uint32_t bytes) {
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst), "r"(shmemg_smem_u32(smem)),
+                 "r"(bytes)
+                 : "memory");
+    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+/* bounded wait for an mbarrier phase: false after ~timeout_ns */
+static __device__ __forceinline__ bool shmemg_mbar_wait(uint64_t *bar, uint32_t parity, uint64_t timeout_ns) {
+    uint64_t t0 = 0;
+    for (uint32_t it = 0;; it++) {
+        uint32_t done;
+        asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+                     : "=r"(done)
+                     : "r"(shmemg_smem_u32(bar)), "r"(parity)
+                     : "memory");
+        if (done) return true;
+        if ((it & 255) == 255) {
+            const uint64_t now = shmemg_d_globaltimer();
+            if (t0 == 0) t0 = now;
+            else if (now - t0 > timeout_ns) return false;
+        }
+    }
+}
+
+/* Thread-scope bulk copy of the chunks first, first+stride, ... of (dst <- src, n bytes);
+ * dst, src and n multiples of 16.  smem: SHMEMG_BULK_SMEM bytes (128-byte aligned);
+ * bars: SHMEMG_BULK_STAGES mbarriers.  Returns once the data is written (blocking put
+ * semantics); SHMEMG_ERR_TIMEOUT (recorded in the status word) if a stage never fills. */
+static __device__ int shmemg_d_bulk_copy_thread(const shmemg_device_ctx_t &c, uint8_t *dst, const uint8_t *src,
+                                                uint64_t n, uint32_t first, uint32_t stride, uint8_t *smem,
+                                                uint64_t *bars) {
+    const uint64_t nch = (n + SHMEMG_BULK_CHUNK - 1) / SHMEMG_BULK_CHUNK;
+    if (first >= nch) return SHMEMG_SUCCESS;
+    const uint32_t count = (uint32_t)((nch - first + stride - 1) / stride);
+    for (int s = 0; s < SHMEMG_BULK_STAGES; s++)
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(shmemg_smem_u32(&bars[s])) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.global;" ::: "memory");  /* earlier generic writes -> async proxy */
+    auto chunk = [&](uint32_t j, uint64_t *off) -> uint32_t {
+        *off = (uint64_t)(first + (uint64_t)j * stride) * SHMEMG_BULK_CHUNK;
+        const uint64_t left = n - *off;
+        return (uint32_t)(left < SHMEMG_BULK_CHUNK ? left : SHMEMG_BULK_CHUNK);
+    };
+    for (uint32_t j = 0; j < count && j < SHMEMG_BULK_STAGES; j++) {
+        uint64_t off;
+        const uint32_t b = chunk(j, &off);
+        shmemg_bulk_load(smem + (uint64_t)j * SHMEMG_BULK_CHUNK, src + off, b, &bars[j]);
+    }
+    int rc = SHMEMG_SUCCESS;
+    for (uint32_t j = 0; j < count; j++) {
+        const uint32_t s = j % SHMEMG_BULK_STAGES;
+        if (!shmemg_mbar_wait(&bars[s], (j / SHMEMG_BULK_STAGES) & 1u, c.timeout_ns)) {
+            shmemg_d_set_status(c, SHMEMG_ERR_TIMEOUT, -2);
+            rc = SHMEMG_ERR_TIMEOUT;
+            break;
+        }
+        uint64_t off;
+        const uint32_t b = chunk(j, &off);
+        shmemg_bulk_store(dst + off, smem + (uint64_t)s * SHMEMG_BULK_CHUNK, b);
+        if (j + SHMEMG_BULK_STAGES < count) {
+            /* the stage is refilled once the store just issued has read it */
+            asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+            uint64_t off2;
+            const uint32_t b2 = chunk(j + SHMEMG_BULK_STAGES, &off2);
+            shmemg_bulk_load(smem + (uint64_t)s * SHMEMG_BULK_CHUNK, src + off2, b2, &bars[s]);
+        }
+    }
+    asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+    asm volatile("fence.proxy.async.global;" ::: "memory");  /* async-proxy writes -> generic readers */
+    return rc;
+}
+
 /* ------------------------------------------------------------------ RMA (Sec. 2.1) */
 /* put: n bytes of the caller PE's `src` -> `dst` on `pe`.  Group scope: every thread
  * of g calls with the same arguments.  On return the caller's threads have read the

@@ -16,12 +16,29 @@ namespace shmemg {
 
 constexpr int INTERP_THREADS = 512;
 
+// Large aligned puts and gets (>= SHMEMG_BULK_MIN) run on the bulk (TMA) engine when the
+// launch provides its shared-memory ring (use_bulk): thread 0 of each CTA of the PE
+// streams every ncta-th chunk.
+__device__ __forceinline__ void pe_copy(const shmemg_device_ctx_t &c, shmemg_group g, uint8_t *d, const uint8_t *s,
+                                        uint64_t n, int use_bulk, uint8_t *ring, uint64_t *bars) {
+    if (use_bulk && n >= SHMEMG_BULK_MIN && (((uint64_t)d | (uint64_t)s | n) & 15) == 0) {
+        const bool cl = c.pe_mode == SHMEMG_PE_MODE_CLUSTER;
+        if (threadIdx.x == 0)
+            shmemg_d_bulk_copy_thread(c, d, s, n, cl ? shmemg_d_cluster_ctarank() : 0u, cl ? (uint32_t)c.cluster_dim : 1u,
+                                      ring, bars);
+    } else {
+        shmemg_d_copy_group(g, d, s, n);
+    }
+}
+
 __global__ void __launch_bounds__(INTERP_THREADS) k_interp(shmemg_device_ctx_t c, const shmemg_op_t *ops,
-                                                           int64_t nops, int64_t *fetched) {
+                                                           int64_t nops, int64_t *fetched, int use_bulk) {
     const int me = shmemg_d_my_pe(c);
     const shmemg_group g = shmemg_d_group_pe(c);
     const bool leader = shmemg_d_pe_leader(c);
     __shared__ int s_rc;
+    extern __shared__ __align__(128) uint8_t s_ring[];
+    __shared__ __align__(8) uint64_t s_bars[SHMEMG_BULK_STAGES];
     for (int64_t i = 0; i < nops; i++) {
         const shmemg_op_t o = ops[i];
         int rc = SHMEMG_SUCCESS;
@@ -29,14 +46,14 @@ __global__ void __launch_bounds__(INTERP_THREADS) k_interp(shmemg_device_ctx_t c
         case SHMEMG_OP_PUT:
         case SHMEMG_OP_PUT_NBI:
             if (o.issuer == me) {
-                shmemg_d_copy_group(g, shmemg_d_addr(c, o.pe, o.dst), shmemg_d_addr(c, me, o.src), o.n);
+                pe_copy(c, g, shmemg_d_addr(c, o.pe, o.dst), shmemg_d_addr(c, me, o.src), o.n, use_bulk, s_ring, s_bars);
                 if (o.kind == SHMEMG_OP_PUT) shmemg_d_pe_sync(c);
             }
             break;
         case SHMEMG_OP_GET:
         case SHMEMG_OP_GET_NBI:
             if (o.issuer == me) {
-                shmemg_d_copy_group(g, shmemg_d_addr(c, me, o.dst), shmemg_d_addr(c, o.pe, o.src), o.n);
+                pe_copy(c, g, shmemg_d_addr(c, me, o.dst), shmemg_d_addr(c, o.pe, o.src), o.n, use_bulk, s_ring, s_bars);
                 if (o.kind == SHMEMG_OP_GET) shmemg_d_pe_sync(c);
             }
             break;
@@ -232,6 +249,18 @@ extern "C" int shmemg_run_script(const shmemg_op_t *ops, int64_t nops, int64_t *
     for (int64_t i = 0; i < nops; i++)
         if ((rc = validate_op(h[i]))) return rc;
     shmemg_device_ctx_t c = device_ctx();
-    void *args[] = {(void *)&c, (void *)&ops, (void *)&nops, (void *)&fetched};
-    return launch_pe_grid((const void *)k_interp, args, 0, to_stream(stream));
+    // the bulk engine's shared-memory ring (disable with SHMEMG_BULK=0)
+    static int bulk = -1;
+    if (bulk < 0) {
+        const char *e = getenv("SHMEMG_BULK");
+        bulk = (e && *e == '0') ? 0 : 1;
+        if (bulk && cudaFuncSetAttribute((const void *)k_interp, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         SHMEMG_BULK_SMEM) != cudaSuccess) {
+            cudaGetLastError();
+            bulk = 0;
+        }
+    }
+    int use_bulk = bulk;
+    void *args[] = {(void *)&c, (void *)&ops, (void *)&nops, (void *)&fetched, (void *)&use_bulk};
+    return launch_pe_grid((const void *)k_interp, args, use_bulk ? SHMEMG_BULK_SMEM : 0, to_stream(stream));
 }

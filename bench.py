@@ -792,6 +792,83 @@ def run_serve(torch, sg, nreq=4096, rates=None, npes=512, Hs=32 << 20):
     return out
 
 
+# ----------------------------------------------------------------------------- profiling cases
+PROFILE_CASES = ("interp_ring", "reduce", "reduce_f32", "broadcast", "alltoall", "amo", "batch_bf16", "qsum")
+
+
+def run_profile_case(name, launches=4):
+    """Small cases of single kernels for ncu captures: inputs larger than the 129 MB L2,
+    at most ~2 GB on the device, `launches` launches of the kernel of interest."""
+    import torch
+
+    import paper_2607_08006_gb300 as sg
+
+    sg.build()
+    torch.cuda.set_device(0)
+    s = torch.cuda.current_stream()
+    if name == "interp_ring":      # 64 PEs (clusters of 2 CTAs), ring put_nbi of 8 MiB, bulk engine
+        m = 8 * MiB
+        heap = sg.Heap(64, 2 * m, pe_mode=sg.PE_MODE_CLUSTER, cluster_dim=2)
+        ops = np.zeros(65, W.OP_DTYPE)
+        for p in range(64):
+            ops[p] = (W.OP_PUT_NBI, 0, 0, 0, (p + 1) % 64, p, m, 0, m, 0, 0, 0)
+        ops[64] = (W.OP_QUIET, 0, 0, 0, 0, -1, 0, 0, 0, 0, 0, 0)
+        dev = torch.from_numpy(ops.view(np.uint8).copy()).cuda()
+        for _ in range(launches):
+            sg.run_script(dev, 65, None, s)
+    elif name in ("reduce", "reduce_f32"):  # 64 PEs, 1 Mi elements
+        n = 1 << 20
+        heap = sg.Heap(64, 16 * n)
+        heap.partitions().random_(0, 255)
+        dt = sg.INT64 if name == "reduce" else sg.FLOAT
+        if dt == sg.FLOAT:
+            heap.partitions()[:, :8 * n].view(torch.float32).normal_()
+        for _ in range(launches):
+            sg.reduce(sg.TEAM_WORLD, heap.base + 8 * n, heap.base, n, dt, sg.SUM, s)
+    elif name == "broadcast":      # 64 PEs, 8 MiB
+        m = 8 * MiB
+        heap = sg.Heap(64, 2 * m)
+        for _ in range(launches):
+            sg.broadcastmem(sg.TEAM_WORLD, heap.base + m, heap.base, m, 63, s)
+    elif name == "alltoall":       # 64 PEs, 128 KiB per pair
+        m = 128 * KiB
+        heap = sg.Heap(64, 2 * 64 * m)
+        for _ in range(launches):
+            sg.alltoallmem(sg.TEAM_WORLD, heap.base + 64 * m, heap.base, m, s)
+    elif name == "amo":            # 1024 PEs, 2^27-word table (1 GiB), 2^22 uniform ops
+        wpp = 1 << 17
+        heap = sg.Heap(1024, wpp * 8)
+        nops = 1 << 22
+        ops = torch.from_numpy(W.amo_stream_np(1, nops, 27).view(np.int32)).cuda()
+        f = torch.empty(nops, dtype=torch.int64, device="cuda")
+        for _ in range(launches):
+            sg.amo_stream(heap.base, wpp, ops, nops, 1, 2, f, 0, s)
+    elif name in ("batch_bf16", "qsum"):   # 64 PEs, bf16 payloads of 1 Mi elements
+        n = 1 << 20
+        heap = sg.Heap(64, 12 * n)
+        x = heap.partitions()[:, :4 * n].view(torch.float32)
+        x.normal_()
+        sg.quantize(sg.TEAM_WORLD, heap.base + 4 * n, heap.base + 6 * n, heap.base, sg.FMT_BF16, n, s)
+        if name == "qsum":
+            for _ in range(launches):
+                sg.qsum_reduce(sg.TEAM_WORLD, heap.base + 7 * n, heap.base + 4 * n, heap.base + 6 * n, sg.FMT_BF16, n, s)
+        else:
+            d = [sg.CollDesc(0, 64, sg.FLOAT, sg.FMT_BF16, n, heap.base + 7 * n, heap.base + 4 * n, heap.base + 6 * n)]
+            b = sg.Batch(d, sg.Tune(8192, 0, 0, 0))
+            for _ in range(launches):
+                b.launch(s)
+            torch.cuda.synchronize()
+            b.destroy()
+    else:
+        raise SystemExit(f"unknown profile case {name}")
+    torch.cuda.synchronize()
+    code, detail = sg.get_status()
+    heap.close()
+    if code != 0:
+        raise SystemExit(f"device status {code} detail {detail}")
+    print(json.dumps({"profile_case": name, "launches": launches, "status": "ok"}))
+
+
 # ----------------------------------------------------------------------------- distributed
 def dist_init():
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -833,7 +910,11 @@ def main():
                     help="extra workloads measured after the sweep (comma list of amo,batch,serve or 'none')")
     ap.add_argument("--amo-ops-log2", type=int, default=26)
     ap.add_argument("--serve-requests", type=int, default=4096)
+    ap.add_argument("--profile", choices=PROFILE_CASES, help="run one small single-kernel case (for ncu) and exit")
     args = ap.parse_args()
+    if args.profile:
+        run_profile_case(args.profile)
+        return
     rank, world = dist_init()
     if args.impl == "reference":
         if rank == 0:

@@ -557,17 +557,18 @@ static __device__ __forceinline__ V shmemg_tree_sum(const uint8_t *heap, uint64_
         acc = have ? shmemg_vadd<V>::add(t, acc) : t;                                    \
         have = true;                                                                     \
     }
-    SHMEMG_TB(0) SHMEMG_TB(1) SHMEMG_TB(2) SHMEMG_TB(3) SHMEMG_TB(4) SHMEMG_TB(5) SHMEMG_TB(6) SHMEMG_TB(7)
+    SHMEMG_TB(0) SHMEMG_TB(1) SHMEMG_TB(2) SHMEMG_TB(3) SHMEMG_TB(4) SHMEMG_TB(5)
 #undef SHMEMG_TB
-    for (int b = 8; b < 31; b++) {
+    for (int b = 6; b < 31; b++) {
         if (!(P & (1 << b))) continue;
-        /* aligned block of 2^b ranks = pairwise tree over its 2^(b-7) blocks of 128 */
+        /* aligned block of 2^b ranks = pairwise tree over its 2^(b-5) blocks of 32,
+         * combined with a carry stack (binary counter): the same pairing */
         int s0 = P & ~((2 << b) - 1);
-        int nsub = 1 << (b - 7);
-        V stack[24];
+        int nsub = 1 << (b - 5);
+        V stack[26];
         V v{};
         for (int q = 0; q < nsub; q++) {
-            v = shmemg_tree_block<7, V>(heap, H, pe0, pstride, s0 + q * 128, off);
+            v = shmemg_tree_block<5, V>(heap, H, pe0, pstride, s0 + q * 32, off);
             int cnt = q, j = 0;
             while (cnt & 1) {
                 v = shmemg_vadd<V>::add(stack[j], v);
@@ -610,6 +611,18 @@ static __device__ __forceinline__ void shmemg_d_reduce_vecs(shmemg_group g, uint
         } else {
             acc = shmemg_ld_cg((const V *)(heap + (uint64_t)pe0 * H + off));
             int r = 1;
+            for (; r + 7 < P; r += 8) {  /* eight members' loads in flight */
+                V x[8];
+#pragma unroll
+                for (int u = 0; u < 8; u++) x[u] = shmemg_ld_cg((const V *)(heap + (uint64_t)(pe0 + (r + u) * pstride) * H + off));
+#pragma unroll
+                for (int u = 0; u < 8; u++)
+#pragma unroll
+                    for (int l = 0; l < NL; l++) {
+                        T &s = reinterpret_cast<T *>(&acc)[l];
+                        s = shmemg_comb<T>(s, reinterpret_cast<T *>(&x[u])[l], OP);
+                    }
+            }
             for (; r + 3 < P; r += 4) {
                 V a = shmemg_ld_cg((const V *)(heap + (uint64_t)(pe0 + r * pstride) * H + off));
                 V b = shmemg_ld_cg((const V *)(heap + (uint64_t)(pe0 + (r + 1) * pstride) * H + off));

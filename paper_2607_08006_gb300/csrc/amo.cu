@@ -43,6 +43,43 @@ __global__ void __launch_bounds__(AMO_THREADS) k_amo_stream(AmoArgs a) {
     const int p = blockIdx.x;
     const uint64_t lo = a.nops * (uint64_t)p / (uint64_t)a.npes;
     const uint64_t hi = a.nops * (uint64_t)(p + 1) / (uint64_t)a.npes;
+    if (!(a.flags & SHMEMG_AMO_AGGREGATE)) {
+        // each thread keeps four independent atomics in flight (ops i, i+B, i+2B, i+3B)
+        constexpr int U = 4;
+        for (uint64_t base = lo + threadIdx.x; base < hi; base += (uint64_t)blockDim.x * U) {
+            unsigned long long old[U];
+            bool act[U];
+#pragma unroll
+            for (int k = 0; k < U; k++) {
+                const uint64_t i = base + (uint64_t)k * blockDim.x;
+                act[k] = i < hi;
+                old[k] = 0;
+                if (!act[k]) continue;
+                const uint32_t op = __ldcs(a.ops + i);
+                const uint64_t w = op & ((1u << 27) - 1u);
+                const uint32_t code = (op >> 27) & 3u;
+                if (w >= a.nwords || code == 3u) {
+                    int *stw = (int *)(a.state + SHMEMG_STATUS_OFF);
+                    if (atomicCAS(stw, 0, SHMEMG_ERR_INVALID_ARG) == 0) *(volatile int64_t *)(a.state + SHMEMG_STATUS_OFF + 8) = (int64_t)i;
+                    act[k] = false;
+                    continue;
+                }
+                const uint64_t r = cb64(a.op_seed, i);
+                const uint64_t pe = a.wpp_log2 >= 0 ? w >> a.wpp_log2 : w / a.wpp;
+                const uint64_t idx = w - pe * a.wpp;
+                unsigned long long *addr = (unsigned long long *)(a.heap + pe * a.H + a.table_off + idx * 8);
+                if (code == 1u) old[k] = atomicCAS(addr, (unsigned long long)cb64(a.table_seed, w), (unsigned long long)r);
+                else if (code == 0u) old[k] = atomicAdd(addr, (unsigned long long)((r & ((1u << 20) - 1u)) + 1u));
+                else old[k] = atomicXor(addr, (unsigned long long)(r ? r : 1ull));
+            }
+            if (a.fetched) {
+#pragma unroll
+                for (int k = 0; k < U; k++)
+                    if (act[k]) __stcs((unsigned long long *)a.fetched + base + (uint64_t)k * blockDim.x, old[k]);
+            }
+        }
+        return;
+    }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     const uint32_t lt = (1u << lane) - 1u;
     uint64_t *sv = s_val + warp * 32, *so = s_old + warp * 32;

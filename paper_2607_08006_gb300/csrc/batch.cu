@@ -39,6 +39,23 @@ struct BArgs {
     uint32_t *counter;    // [0] next item, [1] CTAs done
 };
 
+// quantised tile: E elements per thread on the wide path (bit 1 of t.vec), 4-element
+// steps for ragged or unaligned groups
+template <int FMT>
+__device__ __forceinline__ void batch_qsum(const BArgs &a, const BTeam &t, uint64_t e0, uint64_t e1) {
+    constexpr int E = QWide<FMT>::E;
+    for (uint64_t q = e0 / E + threadIdx.x; q * E < e1; q += blockDim.x) {
+        const uint64_t f = q * E;
+        if ((t.vec & 2) && f + E <= e1) {
+            qsum_wide<FMT>(a.heap, a.H, t.start, 1, t.size, t.d_off, t.s_off, t.sc_off, f);
+        } else {
+            for (int k = 0; k < E / 4 && f + 4 * k < e1; k++)
+                qsum4<FMT>(a.heap, a.H, t.start, 1, t.size, t.d_off, t.s_off, t.sc_off, f + 4 * k, t.n,
+                           (t.vec & 1) && f + 4 * k + 4 <= t.n);
+        }
+    }
+}
+
 __device__ __forceinline__ void batch_item(const BArgs &a, const BTeam &t, uint64_t e0, uint64_t e1) {
     const shmemg_group g = {threadIdx.x, blockDim.x};
     if (t.kind == BK_F32) {
@@ -47,12 +64,8 @@ __device__ __forceinline__ void batch_item(const BArgs &a, const BTeam &t, uint6
         shmemg_d_reduce_elems_t<int64_t, longlong2>(g, a.heap, a.H, t.start, 1, t.size, t.d_off, t.s_off, e0, e1,
                                                     SHMEMG_SUM);
     } else {
-        for (uint64_t q = e0 / 4 + threadIdx.x; q * 4 < e1; q += blockDim.x) {
-            const uint64_t f = q * 4;
-            const bool vec = t.vec && f + 4 <= t.n;
-            if (t.kind == BK_E4M3) qsum4<SHMEMG_FMT_E4M3>(a.heap, a.H, t.start, 1, t.size, t.d_off, t.s_off, t.sc_off, f, t.n, vec);
-            else qsum4<SHMEMG_FMT_BF16>(a.heap, a.H, t.start, 1, t.size, t.d_off, t.s_off, t.sc_off, f, t.n, vec);
-        }
+        if (t.kind == BK_E4M3) batch_qsum<SHMEMG_FMT_E4M3>(a, t, e0, e1);
+        else batch_qsum<SHMEMG_FMT_BF16>(a, t, e0, e1);
     }
 }
 
@@ -186,7 +199,8 @@ int shmemg_batch_create(const shmemg_coll_desc_t *descs, int count, const shmemg
                 delete b;
                 return SHMEMG_ERR_NOT_SYMMETRIC;
             }
-            t.vec = (t.d_off & 15) == 0 && (t.s_off & (t.kind == BK_E4M3 ? 3 : 7)) == 0;
+            t.vec = ((t.d_off & 15) == 0 && (t.s_off & (t.kind == BK_E4M3 ? 3 : 7)) == 0 ? 1 : 0) |
+                    ((t.d_off & 15) == 0 && (t.s_off & 15) == 0 ? 2 : 0);
         }
         b->teams.push_back(t);
         b->cost.push_back((uint64_t)d.size * d.n * (in_es + out_es));
@@ -340,7 +354,8 @@ extern "C" int shmemg_batch_reduce_noalloc(const shmemg_coll_desc_t *descs, int 
         if (t.kind >= BK_BF16) {
             if (!c.scales || sym_offset(c.scales, (c.n + 127) / 128 * 4, &t.sc_off) || (t.sc_off & 3))
                 return SHMEMG_ERR_NOT_SYMMETRIC;
-            t.vec = (t.d_off & 15) == 0 && (t.s_off & (t.kind == BK_E4M3 ? 3 : 7)) == 0;
+            t.vec = ((t.d_off & 15) == 0 && (t.s_off & (t.kind == BK_E4M3 ? 3 : 7)) == 0 ? 1 : 0) |
+                    ((t.d_off & 15) == 0 && (t.s_off & 15) == 0 ? 2 : 0);
         }
         g_noalloc_cost_h[i] = (uint64_t)c.size * c.n * (in_es + out_es);
         g_noalloc_order_h[i] = i;

@@ -94,6 +94,96 @@ __device__ __forceinline__ void xfer_items(const Xfer &x, uint64_t first, uint64
 template <typename V>
 __global__ void __launch_bounds__(XFER_THREADS) k_xfer(Xfer x) { xfer_items<V>(x, blockIdx.x, gridDim.x); }
 
+// ------------------------------------------------------------------ bulk (TMA) variant
+// One thread per CTA streams the CTA's items (chunks of XB_CHUNK bytes) through an
+// XB_STAGES-deep shared-memory ring: a bulk load per chunk, then one bulk store (copy,
+// alltoall) or one per team member (broadcast, fcollect) from the same stage.
+constexpr int XB_STAGES = 6;
+constexpr uint32_t XB_CHUNK = 32u << 10;
+constexpr uint32_t XB_SMEM = XB_STAGES * XB_CHUNK;
+
+struct XChunk {
+    const uint8_t *src;
+    uint8_t *dst;        // single destination (copy, alltoall)
+    uint64_t dst_off;    // replicate: byte offset inside every member's partition
+    uint32_t bytes;
+    bool replicate;
+};
+
+__device__ __forceinline__ XChunk xchunk(const Xfer &x, uint64_t item, int base_pe) {
+    XChunk c;
+    const uint64_t seg = item / x.chunks_per_seg, ch = item - seg * x.chunks_per_seg;
+    const uint64_t segb = x.seg_vec, off = ch * XB_CHUNK;
+    c.bytes = (uint32_t)(segb - off < XB_CHUNK ? segb - off : XB_CHUNK);
+    c.replicate = false;
+    c.dst = nullptr;
+    c.dst_off = 0;
+    if (x.kind == X_COPY) {
+        c.src = x.heap + (uint64_t)x.src_pe * x.H + x.src_off + off;
+        c.dst = x.heap + (uint64_t)x.dst_pe * x.H + x.dst_off + off;
+    } else if (x.kind == X_A2A) {
+        const int i = (int)(seg / (uint64_t)x.size), j = (int)(seg - (uint64_t)i * x.size);
+        c.src = x.heap + (uint64_t)(base_pe + i * x.stride) * x.H + x.src_off + (uint64_t)j * segb + off;
+        c.dst = x.heap + (uint64_t)(base_pe + j * x.stride) * x.H + x.dst_off + (uint64_t)i * segb + off;
+    } else if (x.kind == X_BCAST) {
+        c.src = x.heap + (uint64_t)(base_pe + x.root * x.stride) * x.H + x.src_off + off;
+        c.dst_off = x.dst_off + off;
+        c.replicate = true;
+    } else {
+        c.src = x.heap + (uint64_t)(base_pe + (int)seg * x.stride) * x.H + x.src_off + off;
+        c.dst_off = x.dst_off + seg * segb + off;
+        c.replicate = true;
+    }
+    return c;
+}
+
+__global__ void __launch_bounds__(32) k_xfer_bulk(Xfer x, uint8_t *state, uint64_t timeout_ns) {
+    extern __shared__ __align__(128) uint8_t ring[];
+    __shared__ __align__(8) uint64_t bars[XB_STAGES];
+    if (threadIdx.x != 0) return;
+    const int base_pe = x.start + blockIdx.y * x.gstride;
+    if (x.nitems <= blockIdx.x) return;
+    const uint64_t count = (x.nitems - blockIdx.x + gridDim.x - 1) / gridDim.x;
+    for (int s = 0; s < XB_STAGES; s++)
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(shmemg_smem_u32(&bars[s])) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+    for (uint64_t j = 0; j < count && j < XB_STAGES; j++) {
+        const XChunk c = xchunk(x, blockIdx.x + j * gridDim.x, base_pe);
+        shmemg_bulk_load(ring + j * XB_CHUNK, c.src, c.bytes, &bars[j]);
+    }
+    for (uint64_t j = 0; j < count; j++) {
+        const uint32_t s = (uint32_t)(j % XB_STAGES);
+        if (!shmemg_mbar_wait(&bars[s], (uint32_t)((j / XB_STAGES) & 1), timeout_ns)) {
+            int *st = (int *)(state + SHMEMG_STATUS_OFF);
+            if (atomicCAS(st, 0, SHMEMG_ERR_TIMEOUT) == 0) *(volatile int64_t *)(state + SHMEMG_STATUS_OFF + 8) = -3;
+            break;
+        }
+        const XChunk c = xchunk(x, blockIdx.x + j * gridDim.x, base_pe);
+        uint8_t *stage = ring + (uint64_t)s * XB_CHUNK;
+        if (!c.replicate) {
+            asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(c.dst),
+                         "r"(shmemg_smem_u32(stage)), "r"(c.bytes)
+                         : "memory");
+        } else {
+            for (int r = 0; r < x.size; r++) {
+                uint8_t *d = x.heap + (uint64_t)(base_pe + r * x.stride) * x.H + c.dst_off;
+                asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(d),
+                             "r"(shmemg_smem_u32(stage)), "r"(c.bytes)
+                             : "memory");
+            }
+        }
+        asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+        if (j + XB_STAGES < count) {
+            asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+            const XChunk n2 = xchunk(x, blockIdx.x + (j + XB_STAGES) * gridDim.x, base_pe);
+            shmemg_bulk_load(stage, n2.src, n2.bytes, &bars[s]);
+        }
+    }
+    asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+}
+
 // put-with-signal: the copy, then the last CTA to finish releases the signal
 template <typename V>
 __global__ void __launch_bounds__(XFER_THREADS) k_put_signal(Xfer x, uint64_t *sig, uint64_t val, int op,
@@ -171,9 +261,37 @@ static int launch_xfer_v(Xfer x, int ngroups, cudaStream_t s, uint64_t *sig, uin
     return cuda_rc(cudaGetLastError());
 }
 
+static bool bulk_enabled() {
+    static int on = -1;
+    if (on < 0) {
+        const char *e = getenv("SHMEMG_BULK");
+        on = (e && *e == '0') ? 0 : 1;
+        if (on && cudaFuncSetAttribute((const void *)k_xfer_bulk, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       XB_SMEM) != cudaSuccess) {
+            cudaGetLastError();
+            on = 0;
+        }
+    }
+    return on == 1;
+}
+
+// segments of >= one chunk with 16-byte aligned addresses and lengths go to the bulk engine
+static int launch_xfer_bulk(Xfer x, int ngroups, cudaStream_t s) {
+    x.chunks_per_seg = (x.seg_vec + XB_CHUNK - 1) / XB_CHUNK;
+    const uint64_t nseg = x.kind == X_A2A ? (uint64_t)x.size * x.size : x.kind == X_FCOLLECT ? (uint64_t)x.size : 1;
+    x.nitems = nseg * x.chunks_per_seg;
+    uint64_t cap = (uint64_t)ctas_for((const void *)k_xfer_bulk, 32, XB_SMEM);
+    dim3 grid((unsigned)(x.nitems < cap ? x.nitems : cap), (unsigned)ngroups);
+    k_xfer_bulk<<<grid, 32, XB_SMEM, s>>>(x, st().base, st().timeout_ns);
+    return cuda_rc(cudaGetLastError());
+}
+
 // x.seg_vec carries the segment length in BYTES on entry
 static int launch_xfer(Xfer x, int ngroups, uint64_t align_bits, cudaStream_t s, uint64_t *sig = nullptr,
                        uint64_t val = 0, int op = 0, uint32_t *done = nullptr) {
+    // (alltoall's many smaller segments measured faster on the vector path)
+    if (!sig && x.kind != X_A2A && ((align_bits | x.seg_vec) & 15) == 0 && x.seg_vec >= XB_CHUNK && bulk_enabled())
+        return launch_xfer_bulk(x, ngroups, s);
     switch (vec_width(align_bits | x.seg_vec)) {
     case 16: return launch_xfer_v<uint4>(x, ngroups, s, sig, val, op, done);
     case 8: return launch_xfer_v<uint2>(x, ngroups, s, sig, val, op, done);

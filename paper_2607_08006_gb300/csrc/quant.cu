@@ -85,16 +85,27 @@ struct QSumArgs {
     int start, stride, size, gstride;
     uint64_t d_off, q_off, s_off;
     uint64_t n;
-    bool vec;
+    bool vec;   // 4-element vector path allowed
+    bool wide;  // 16-byte code path allowed
 };
 
+// Each thread owns QWide<FMT>::E consecutive elements (one 16-byte code load per member);
+// a ragged or unaligned group falls back to 4-element steps.
 template <int FMT>
 __global__ void __launch_bounds__(Q_THREADS) k_qsum(QSumArgs a) {
+    constexpr int E = QWide<FMT>::E;
     const int pe0 = a.start + blockIdx.y * a.gstride;
-    const uint64_t nq = (a.n + 3) / 4;
-    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nq; i += (uint64_t)gridDim.x * blockDim.x) {
-        const uint64_t e0 = i * 4;
-        qsum4<FMT>(a.heap, a.H, pe0, a.stride, a.size, a.d_off, a.q_off, a.s_off, e0, a.n, a.vec && e0 + 4 <= a.n);
+    const uint64_t ng = (a.n + E - 1) / E;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < ng; i += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t e0 = i * E;
+        if (a.wide && e0 + E <= a.n) {
+            qsum_wide<FMT>(a.heap, a.H, pe0, a.stride, a.size, a.d_off, a.q_off, a.s_off, e0);
+        } else {
+            for (int k = 0; k < E / 4 && e0 + 4 * k < a.n; k++) {
+                const uint64_t f = e0 + 4 * k;
+                qsum4<FMT>(a.heap, a.H, pe0, a.stride, a.size, a.d_off, a.q_off, a.s_off, f, a.n, a.vec && f + 4 <= a.n);
+            }
+        }
     }
 }
 
@@ -163,9 +174,11 @@ int shmemg_qsum_reduce(shmemg_team_t team, float *dst, const void *q, const floa
     a.s_off = so;
     a.n = n;
     a.vec = (d & 15) == 0 && (qo & (fmt == SHMEMG_FMT_E4M3 ? 3 : 7)) == 0;
+    a.wide = (d & 15) == 0 && (qo & 15) == 0;
     const void *kfn = fmt == SHMEMG_FMT_E4M3 ? (const void *)k_qsum<SHMEMG_FMT_E4M3> : (const void *)k_qsum<SHMEMG_FMT_BF16>;
     uint64_t cap = (uint64_t)ctas_for(kfn, Q_THREADS, 0);
-    uint64_t need = ((n + 3) / 4 + Q_THREADS - 1) / Q_THREADS;
+    const uint64_t E = fmt == SHMEMG_FMT_E4M3 ? 16 : 8;
+    uint64_t need = ((n + E - 1) / E + Q_THREADS - 1) / Q_THREADS;
     dim3 grid((unsigned)(need < cap ? need : cap), (unsigned)t.ngroups);
     if (fmt == SHMEMG_FMT_E4M3) k_qsum<SHMEMG_FMT_E4M3><<<grid, Q_THREADS, 0, to_stream(stream)>>>(a);
     else k_qsum<SHMEMG_FMT_BF16><<<grid, Q_THREADS, 0, to_stream(stream)>>>(a);

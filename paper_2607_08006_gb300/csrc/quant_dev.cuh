@@ -50,6 +50,65 @@ struct Neu {
 
 // Dequantised sum of elements [e0, e0+4) over the team members, written to every
 // member's dst.  Vector path: 4 codes and 4 floats per access (aligned offsets).
+// Elements per thread of the wide path: one 16-byte code load per member.
+template <int FMT> struct QWide { static constexpr int E = FMT == SHMEMG_FMT_E4M3 ? 16 : 8; };
+
+template <int FMT>
+__device__ __forceinline__ void qdecode16(uint4 w, float s, float *d) {
+    const uint32_t v[4] = {w.x, w.y, w.z, w.w};
+    if (FMT == SHMEMG_FMT_E4M3) {
+#pragma unroll
+        for (int j = 0; j < 16; j++) d[j] = __fmul_rn(e4m3_decode((v[j >> 2] >> (8 * (j & 3))) & 0xFFu), s);
+    } else {
+#pragma unroll
+        for (int j = 0; j < 8; j++) d[j] = __fmul_rn(bf16_decode((v[j >> 1] >> (16 * (j & 1))) & 0xFFFFu), s);
+    }
+}
+
+// Wide form of qsum4: elements [e0, e0+E) with E = QWide<FMT>::E, e0 a multiple of E,
+// q_off and d_off 16-byte aligned, e0 + E <= n.  Two members' loads are in flight at a
+// time; accumulation stays in team-rank order.
+template <int FMT>
+__device__ __forceinline__ void qsum_wide(uint8_t *heap, uint64_t H, int pe0, int pstride, int P, uint64_t d_off,
+                                          uint64_t q_off, uint64_t s_off, uint64_t e0) {
+    constexpr int E = QWide<FMT>::E;
+    constexpr uint64_t QS = FMT == SHMEMG_FMT_E4M3 ? 1 : 2;
+    Neu acc[E];
+#pragma unroll
+    for (int j = 0; j < E; j++) acc[j] = {0.0f, 0.0f};
+    float d[E];
+    int r = 0;
+    for (; r + 1 < P; r += 2) {
+        const uint8_t *b0 = heap + (uint64_t)(pe0 + r * pstride) * H;
+        const uint8_t *b1 = heap + (uint64_t)(pe0 + (r + 1) * pstride) * H;
+        const uint4 w0 = __ldcg((const uint4 *)(b0 + q_off + e0 * QS));
+        const uint4 w1 = __ldcg((const uint4 *)(b1 + q_off + e0 * QS));
+        const float s0 = __ldcg((const float *)(b0 + s_off) + e0 / 128);
+        const float s1 = __ldcg((const float *)(b1 + s_off) + e0 / 128);
+        qdecode16<FMT>(w0, s0, d);
+#pragma unroll
+        for (int j = 0; j < E; j++) acc[j].add(d[j]);
+        qdecode16<FMT>(w1, s1, d);
+#pragma unroll
+        for (int j = 0; j < E; j++) acc[j].add(d[j]);
+    }
+    if (r < P) {
+        const uint8_t *b0 = heap + (uint64_t)(pe0 + r * pstride) * H;
+        qdecode16<FMT>(__ldcg((const uint4 *)(b0 + q_off + e0 * QS)), __ldcg((const float *)(b0 + s_off) + e0 / 128), d);
+#pragma unroll
+        for (int j = 0; j < E; j++) acc[j].add(d[j]);
+    }
+    float4 o[E / 4];
+#pragma unroll
+    for (int k = 0; k < E / 4; k++)
+        o[k] = make_float4(acc[4 * k].result(), acc[4 * k + 1].result(), acc[4 * k + 2].result(), acc[4 * k + 3].result());
+    for (int m = 0; m < P; m++) {
+        float4 *dst = (float4 *)(heap + (uint64_t)(pe0 + m * pstride) * H + d_off + 4 * e0);
+#pragma unroll
+        for (int k = 0; k < E / 4; k++) dst[k] = o[k];
+    }
+}
+
 template <int FMT>
 __device__ __forceinline__ void qsum4(uint8_t *heap, uint64_t H, int pe0, int pstride, int P, uint64_t d_off,
                                       uint64_t q_off, uint64_t s_off, uint64_t e0, uint64_t n, bool vec) {

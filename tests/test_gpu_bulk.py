@@ -38,3 +38,30 @@ def test_bulk_ring_put_get(sg, heapf, orc, mode, cd, m):
     ref.run_script(ops)
     d = first_diff(download(h), ref.mem)
     assert d is None, d
+
+
+def test_bulk_host_collectives(sg, heapf, orc):
+    """Host-issued broadcast / fcollect / alltoall / put large enough for the bulk engine
+    (ragged last chunk, strided team, per-cluster SHARED groups) against the oracle."""
+    npes, H = 8, 4 * MiB
+    h = heapf(npes, H, pe_mode=0, cluster_dim=4)
+    init = random_heap(npes, H, 77)
+    upload(h, init)
+    ref = orc.Heap(npes, H, init)
+    b = h.base
+    sg.broadcastmem(sg.TEAM_WORLD, b + 2 * MiB, b + 0, 100 * 1024 + 16, 5)
+    ref.broadcast((0, 1, npes), 2 * MiB, 0, 100 * 1024 + 16, 5)
+    t = sg.team_split_strided(sg.TEAM_WORLD, 1, 2, 4)       # PEs 1, 3, 5, 7
+    sg.fcollectmem(t, b + 3 * MiB, b + 160 * 1024, 48 * 1024)
+    ref.fcollect((1, 2, 4), 3 * MiB, 160 * 1024, 48 * 1024)
+    sg.alltoallmem(t, b + 512 * 1024, b + 1024 * 1024, 40 * 1024)
+    ref.alltoall((1, 2, 4), 512 * 1024, 1024 * 1024, 40 * 1024)
+    sg.team_destroy(t)
+    sg.broadcastmem(sg.TEAM_SHARED, b + 1536 * 1024, b + 1024 * 1024, 64 * 1024, 2)
+    for g in range(2):
+        ref.broadcast((4 * g, 1, 4), 1536 * 1024, 1024 * 1024, 64 * 1024, 2)
+    sg.putmem(b + 3584 * 1024, b + 0, 512 * 1024 - 32, 6, 1)
+    ref.put(3584 * 1024, 0, 512 * 1024 - 32, 6, 1)
+    sg.quiet()
+    d = first_diff(download(h), ref.mem)
+    assert d is None, d

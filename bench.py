@@ -806,8 +806,8 @@ def run_profile_case(name, launches=4):
     sg.build()
     torch.cuda.set_device(0)
     s = torch.cuda.current_stream()
-    if name == "interp_ring":      # 64 PEs (clusters of 2 CTAs), ring put_nbi of 8 MiB, bulk engine
-        m = 8 * MiB
+    if name == "interp_ring":      # 64 PEs (clusters of 2 CTAs), ring put_nbi of 24 MiB, bulk engine
+        m = 24 * MiB
         heap = sg.Heap(64, 2 * m, pe_mode=sg.PE_MODE_CLUSTER, cluster_dim=2)
         ops = np.zeros(65, W.OP_DTYPE)
         for p in range(64):

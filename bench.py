@@ -806,16 +806,18 @@ def run_profile_case(name, launches=4):
     sg.build()
     torch.cuda.set_device(0)
     s = torch.cuda.current_stream()
-    if name == "interp_ring":      # 64 PEs (clusters of 2 CTAs), ring put_nbi of 24 MiB, bulk engine
-        m = 24 * MiB
-        heap = sg.Heap(64, 2 * m, pe_mode=sg.PE_MODE_CLUSTER, cluster_dim=2)
-        ops = np.zeros(65, W.OP_DTYPE)
-        for p in range(64):
-            ops[p] = (W.OP_PUT_NBI, 0, 0, 0, (p + 1) % 64, p, m, 0, m, 0, 0, 0)
-        ops[64] = (W.OP_QUIET, 0, 0, 0, 0, -1, 0, 0, 0, 0, 0, 0)
+    if name == "interp_ring":      # 128 PEs of one CTA each, ring put_nbi of 12 MiB, bulk engine
+        # (one CTA per PE: the bench's 64 two-CTA clusters give each SM the same share,
+        # and a cluster launch is profiled without its cluster shape)
+        m, npes = 12 * MiB, 128
+        heap = sg.Heap(npes, 2 * m, pe_mode=sg.PE_MODE_CTA, cluster_dim=1)
+        ops = np.zeros(npes + 1, W.OP_DTYPE)
+        for p in range(npes):
+            ops[p] = (W.OP_PUT_NBI, 0, 0, 0, (p + 1) % npes, p, m, 0, m, 0, 0, 0)
+        ops[npes] = (W.OP_QUIET, 0, 0, 0, 0, -1, 0, 0, 0, 0, 0, 0)
         dev = torch.from_numpy(ops.view(np.uint8).copy()).cuda()
         for _ in range(launches):
-            sg.run_script(dev, 65, None, s)
+            sg.run_script(dev, npes + 1, None, s)
     elif name in ("reduce", "reduce_f32"):  # 64 PEs, 1 Mi elements
         n = 1 << 20
         heap = sg.Heap(64, 16 * n)

@@ -327,8 +327,11 @@ typedef struct {
  * their team on entry and exit.  Ops between two synchronising ops run concurrently
  * on different PEs: the script must be race-free there for a deterministic heap.
  * fetched[i] (caller's device array of nops) receives the old value of AMO op i.
- * `ops` is a device array.  Needs every PE co-resident: SHMEMG_ERR_UNSUPPORTED if the
- * GPU cannot hold them. */
+ * `ops` is a device array, checked on the device as it is read: an invalid op (a PE or
+ * byte range outside the heap, a misaligned AMO target, a destroyed team) ends the
+ * script at that op and records SHMEMG_ERR_INVALID_ARG with the op's index in the
+ * status word; the ops before it have run.  Needs every PE co-resident:
+ * SHMEMG_ERR_UNSUPPORTED if the GPU cannot hold them. */
 int shmemg_run_script(const shmemg_op_t *ops, int64_t nops, int64_t *fetched, void *stream);
 /* The plain launch-per-op path: the same list, from HOST memory, executed in list
  * order by one stream-triggered host call per op on `stream`. */

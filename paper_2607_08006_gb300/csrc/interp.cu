@@ -15,6 +15,7 @@
 namespace shmemg {
 
 constexpr int INTERP_THREADS = 512;
+constexpr int OP_BATCH = 64;  // op records staged in shared memory at a time
 
 // Large aligned puts and gets (>= SHMEMG_BULK_MIN) run on the bulk (TMA) engine when the
 // launch provides its shared-memory ring (use_bulk): thread 0 of each CTA of the PE
@@ -22,12 +23,55 @@ constexpr int INTERP_THREADS = 512;
 __device__ __forceinline__ void pe_copy(const shmemg_device_ctx_t &c, shmemg_group g, uint8_t *d, const uint8_t *s,
                                         uint64_t n, int use_bulk, uint8_t *ring, uint64_t *bars) {
     if (use_bulk && n >= SHMEMG_BULK_MIN && (((uint64_t)d | (uint64_t)s | n) & 15) == 0) {
+        // the split follows the hardware cluster shape: a launch without clusters (each
+        // CTA its own cluster of one) still copies every chunk
         const bool cl = c.pe_mode == SHMEMG_PE_MODE_CLUSTER;
         if (threadIdx.x == 0)
-            shmemg_d_bulk_copy_thread(c, d, s, n, cl ? shmemg_d_cluster_ctarank() : 0u, cl ? (uint32_t)c.cluster_dim : 1u,
-                                      ring, bars);
+            shmemg_d_bulk_copy_thread(c, d, s, n, cl ? shmemg_d_cluster_ctarank() : 0u,
+                                      cl ? shmemg_d_cluster_nctarank() : 1u, ring, bars);
     } else {
         shmemg_d_copy_group(g, d, s, n);
+    }
+}
+
+// Device-side check of one op (the same rules as the host's argument checks): PEs in
+// range, byte ranges inside a partition, AMO alignment, live teams.  Every thread of
+// every PE evaluates it on the same record, so the verdict is uniform.
+__device__ __forceinline__ bool op_valid(const shmemg_device_ctx_t &c, const shmemg_op_t &o) {
+    const uint64_t H = c.pe_stride;
+    auto in = [&](uint64_t off, uint64_t n) { return off <= H && n <= H - off; };
+    auto pe_ok = [&](int p) { return p >= 0 && p < c.npes; };
+    switch (o.kind) {
+    case SHMEMG_OP_PUT: case SHMEMG_OP_PUT_NBI: case SHMEMG_OP_GET: case SHMEMG_OP_GET_NBI:
+        return pe_ok(o.pe) && pe_ok(o.issuer) && in(o.dst, o.n) && in(o.src, o.n);
+    case SHMEMG_OP_FETCH_ADD: case SHMEMG_OP_COMPARE_SWAP: case SHMEMG_OP_FETCH_XOR: {
+        const uint64_t es = o.dtype == SHMEMG_INT64 ? 8 : o.dtype == SHMEMG_INT32 ? 4 : 0;
+        return es && pe_ok(o.pe) && pe_ok(o.issuer) && in(o.dst, es) && o.dst % es == 0;
+    }
+    case SHMEMG_OP_PUT_SIGNAL:
+        return pe_ok(o.pe) && pe_ok(o.issuer) && in(o.dst, o.n) && in(o.src, o.n) && in(o.aux, 8) && o.aux % 8 == 0 &&
+               o.sub <= SHMEMG_SIGNAL_ADD;
+    case SHMEMG_OP_WAIT_UNTIL:
+        return pe_ok(o.issuer) && in(o.dst, 8) && o.dst % 8 == 0 && o.sub <= SHMEMG_CMP_LE;
+    case SHMEMG_OP_QUIET: case SHMEMG_OP_FENCE: case SHMEMG_OP_BARRIER_ALL:
+        return true;
+    default:
+        break;
+    }
+    if (o.team >= SHMEMG_MAX_TEAMS) return false;
+    const shmemg_dteam_t t = *shmemg_d_team(c, o.team);
+    if (!t.valid) return false;
+    switch (o.kind) {
+    case SHMEMG_OP_TEAM_SYNC: return true;
+    case SHMEMG_OP_BROADCAST: return o.pe >= 0 && o.pe < t.size && in(o.dst, o.n) && in(o.src, o.n);
+    case SHMEMG_OP_FCOLLECT: return in(o.dst, o.n * (uint64_t)t.size) && in(o.src, o.n);
+    case SHMEMG_OP_ALLTOALL: return in(o.dst, o.n * (uint64_t)t.size) && in(o.src, o.n * (uint64_t)t.size);
+    case SHMEMG_OP_REDUCE: {
+        const uint64_t es = o.dtype == SHMEMG_INT64 ? 8 : (o.dtype == SHMEMG_INT32 || o.dtype == SHMEMG_FLOAT) ? 4 : 0;
+        return es && o.sub <= SHMEMG_MIN && in(o.dst, o.n * es) && in(o.src, o.n * es) && o.dst % es == 0 &&
+               o.src % es == 0;
+    }
+    default: return false;
     }
 }
 
@@ -39,9 +83,25 @@ __global__ void __launch_bounds__(INTERP_THREADS) k_interp(shmemg_device_ctx_t c
     __shared__ int s_rc;
     extern __shared__ __align__(128) uint8_t s_ring[];
     __shared__ __align__(8) uint64_t s_bars[SHMEMG_BULK_STAGES];
-    for (int64_t i = 0; i < nops; i++) {
-        const shmemg_op_t o = ops[i];
+    // the op list is staged through shared memory OP_BATCH records at a time (one
+    // coalesced copy per batch instead of a dependent global load per op and thread)
+    __shared__ __align__(16) shmemg_op_t s_ops[OP_BATCH];
+    bool failed = false;
+    for (int64_t base = 0; base < nops && !failed; base += OP_BATCH) {
+    const int cnt = (int)(nops - base < OP_BATCH ? nops - base : OP_BATCH);
+    __syncthreads();
+    for (int q = threadIdx.x; q < cnt * 4; q += blockDim.x)
+        reinterpret_cast<uint4 *>(s_ops)[q] = __ldcg(reinterpret_cast<const uint4 *>(ops + base) + q);
+    __syncthreads();
+    for (int k = 0; k < cnt; k++) {
+        const int64_t i = base + k;
+        const shmemg_op_t o = s_ops[k];
         int rc = SHMEMG_SUCCESS;
+        if (!op_valid(c, o)) {  // an invalid op ends the script there, recorded with its index
+            if (leader) shmemg_d_set_status(c, SHMEMG_ERR_INVALID_ARG, i);
+            failed = true;
+            break;
+        }
         switch (o.kind) {
         case SHMEMG_OP_PUT:
         case SHMEMG_OP_PUT_NBI:
@@ -131,49 +191,13 @@ __global__ void __launch_bounds__(INTERP_THREADS) k_interp(shmemg_device_ctx_t c
             if (leader) shmemg_d_set_status(c, SHMEMG_ERR_INVALID_ARG, i);
             rc = SHMEMG_ERR_INVALID_ARG;
         }
-        if (rc != SHMEMG_SUCCESS) break;
+        if (rc != SHMEMG_SUCCESS) {
+            failed = true;  // uniform across the PE: every thread leaves both loops
+            break;
+        }
+    }
     }
     shmemg_d_quiet_pe(c);
-}
-
-// host-side validation of one op (ranges, PEs, teams); returns SHMEMG_* code
-static int validate_op(const shmemg_op_t &o) {
-    State &S = st();
-    auto in = [&](uint64_t off, uint64_t n) { return off <= S.H && n <= S.H - off; };
-    auto pe_ok = [&](int p) { return p >= 0 && p < S.npes; };
-    switch (o.kind) {
-    case SHMEMG_OP_PUT: case SHMEMG_OP_PUT_NBI: case SHMEMG_OP_GET: case SHMEMG_OP_GET_NBI:
-        return pe_ok(o.pe) && pe_ok(o.issuer) && in(o.dst, o.n) && in(o.src, o.n) ? 0 : SHMEMG_ERR_INVALID_ARG;
-    case SHMEMG_OP_FETCH_ADD: case SHMEMG_OP_COMPARE_SWAP: case SHMEMG_OP_FETCH_XOR: {
-        uint64_t es = o.dtype == SHMEMG_INT64 ? 8 : o.dtype == SHMEMG_INT32 ? 4 : 0;
-        return es && pe_ok(o.pe) && pe_ok(o.issuer) && in(o.dst, es) && o.dst % es == 0 ? 0 : SHMEMG_ERR_INVALID_ARG;
-    }
-    case SHMEMG_OP_PUT_SIGNAL:
-        return pe_ok(o.pe) && pe_ok(o.issuer) && in(o.dst, o.n) && in(o.src, o.n) && in(o.aux, 8) && o.aux % 8 == 0 &&
-                       o.sub <= SHMEMG_SIGNAL_ADD ? 0 : SHMEMG_ERR_INVALID_ARG;
-    case SHMEMG_OP_WAIT_UNTIL:
-        return pe_ok(o.issuer) && in(o.dst, 8) && o.dst % 8 == 0 && o.sub <= SHMEMG_CMP_LE ? 0 : SHMEMG_ERR_INVALID_ARG;
-    case SHMEMG_OP_QUIET: case SHMEMG_OP_FENCE: case SHMEMG_OP_BARRIER_ALL:
-        return 0;
-    default: break;
-    }
-    HostTeam t;
-    if (team_get(o.team, &t)) return SHMEMG_ERR_INVALID_ARG;
-    switch (o.kind) {
-    case SHMEMG_OP_TEAM_SYNC: return 0;
-    case SHMEMG_OP_BROADCAST:
-        return o.pe >= 0 && o.pe < t.size && in(o.dst, o.n) && in(o.src, o.n) ? 0 : SHMEMG_ERR_INVALID_ARG;
-    case SHMEMG_OP_FCOLLECT:
-        return in(o.dst, o.n * (uint64_t)t.size) && in(o.src, o.n) ? 0 : SHMEMG_ERR_INVALID_ARG;
-    case SHMEMG_OP_ALLTOALL:
-        return in(o.dst, o.n * (uint64_t)t.size) && in(o.src, o.n * (uint64_t)t.size) ? 0 : SHMEMG_ERR_INVALID_ARG;
-    case SHMEMG_OP_REDUCE: {
-        uint64_t es = o.dtype == SHMEMG_INT64 ? 8 : (o.dtype == SHMEMG_INT32 || o.dtype == SHMEMG_FLOAT) ? 4 : 0;
-        return es && o.sub <= SHMEMG_MIN && in(o.dst, o.n * es) && in(o.src, o.n * es) && o.dst % es == 0 &&
-                       o.src % es == 0 ? 0 : SHMEMG_ERR_INVALID_ARG;
-    }
-    default: return SHMEMG_ERR_INVALID_ARG;
-    }
 }
 
 int interp_threads() {
@@ -240,14 +264,6 @@ extern "C" int shmemg_run_script(const shmemg_op_t *ops, int64_t nops, int64_t *
     if (int rc = check_init()) return rc;
     if (nops < 0 || (nops && !ops)) return SHMEMG_ERR_INVALID_ARG;
     if (nops == 0) return SHMEMG_SUCCESS;
-    // validate on the host (a copy of the device list) before anything runs
-    std::vector<shmemg_op_t> h((size_t)nops);
-    int rc = cuda_rc(cudaMemcpyAsync(h.data(), ops, sizeof(shmemg_op_t) * (size_t)nops, cudaMemcpyDeviceToHost,
-                                     to_stream(stream)));
-    if (rc) return rc;
-    if ((rc = cuda_rc(cudaStreamSynchronize(to_stream(stream))))) return rc;
-    for (int64_t i = 0; i < nops; i++)
-        if ((rc = validate_op(h[i]))) return rc;
     shmemg_device_ctx_t c = device_ctx();
     // the bulk engine's shared-memory ring (disable with SHMEMG_BULK=0)
     static int bulk = -1;

@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include "internal.h"
@@ -48,8 +49,6 @@ struct Neu {
     __device__ __forceinline__ float result() const { return __fadd_rn(sum, c); }
 };
 
-// Dequantised sum of elements [e0, e0+4) over the team members, written to every
-// member's dst.  Vector path: 4 codes and 4 floats per access (aligned offsets).
 // Elements per thread of the wide path: one 16-byte code load per member.
 template <int FMT> struct QWide { static constexpr int E = FMT == SHMEMG_FMT_E4M3 ? 16 : 8; };
 
@@ -57,8 +56,16 @@ template <int FMT>
 __device__ __forceinline__ void qdecode16(uint4 w, float s, float *d) {
     const uint32_t v[4] = {w.x, w.y, w.z, w.w};
     if (FMT == SHMEMG_FMT_E4M3) {
+        // hardware conversion of code pairs to f16 (exact: every E4M3 value is an f16
+        // value), then to binary32
 #pragma unroll
-        for (int j = 0; j < 16; j++) d[j] = __fmul_rn(e4m3_decode((v[j >> 2] >> (8 * (j & 3))) & 0xFFu), s);
+        for (int j = 0; j < 16; j += 2) {
+            const uint16_t pair = (uint16_t)((v[j >> 2] >> (8 * (j & 3))) & 0xFFFFu);
+            uint32_t h2;
+            asm("cvt.rn.f16x2.e4m3x2 %0, %1;" : "=r"(h2) : "h"(pair));
+            d[j] = __fmul_rn(__half2float(__ushort_as_half((unsigned short)(h2 & 0xFFFFu))), s);
+            d[j + 1] = __fmul_rn(__half2float(__ushort_as_half((unsigned short)(h2 >> 16))), s);
+        }
     } else {
 #pragma unroll
         for (int j = 0; j < 8; j++) d[j] = __fmul_rn(bf16_decode((v[j >> 1] >> (16 * (j & 1))) & 0xFFFFu), s);
@@ -66,8 +73,8 @@ __device__ __forceinline__ void qdecode16(uint4 w, float s, float *d) {
 }
 
 // Wide form of qsum4: elements [e0, e0+E) with E = QWide<FMT>::E, e0 a multiple of E,
-// q_off and d_off 16-byte aligned, e0 + E <= n.  Two members' loads are in flight at a
-// time; accumulation stays in team-rank order.
+// q_off and d_off 16-byte aligned, e0 + E <= n.  Eight members' codes and scales are
+// loaded ahead of their accumulation, which stays in team-rank order.
 template <int FMT>
 __device__ __forceinline__ void qsum_wide(uint8_t *heap, uint64_t H, int pe0, int pstride, int P, uint64_t d_off,
                                           uint64_t q_off, uint64_t s_off, uint64_t e0) {
@@ -77,22 +84,25 @@ __device__ __forceinline__ void qsum_wide(uint8_t *heap, uint64_t H, int pe0, in
 #pragma unroll
     for (int j = 0; j < E; j++) acc[j] = {0.0f, 0.0f};
     float d[E];
+    constexpr int M = 8;  // members whose codes and scales are loaded ahead
     int r = 0;
-    for (; r + 1 < P; r += 2) {
-        const uint8_t *b0 = heap + (uint64_t)(pe0 + r * pstride) * H;
-        const uint8_t *b1 = heap + (uint64_t)(pe0 + (r + 1) * pstride) * H;
-        const uint4 w0 = __ldcg((const uint4 *)(b0 + q_off + e0 * QS));
-        const uint4 w1 = __ldcg((const uint4 *)(b1 + q_off + e0 * QS));
-        const float s0 = __ldcg((const float *)(b0 + s_off) + e0 / 128);
-        const float s1 = __ldcg((const float *)(b1 + s_off) + e0 / 128);
-        qdecode16<FMT>(w0, s0, d);
+    for (; r + M <= P; r += M) {
+        uint4 w[M];
+        float sc[M];
 #pragma unroll
-        for (int j = 0; j < E; j++) acc[j].add(d[j]);
-        qdecode16<FMT>(w1, s1, d);
+        for (int u = 0; u < M; u++) {
+            const uint8_t *b = heap + (uint64_t)(pe0 + (r + u) * pstride) * H;
+            w[u] = __ldcg((const uint4 *)(b + q_off + e0 * QS));
+            sc[u] = __ldcg((const float *)(b + s_off) + e0 / 128);
+        }
 #pragma unroll
-        for (int j = 0; j < E; j++) acc[j].add(d[j]);
+        for (int u = 0; u < M; u++) {
+            qdecode16<FMT>(w[u], sc[u], d);
+#pragma unroll
+            for (int j = 0; j < E; j++) acc[j].add(d[j]);
+        }
     }
-    if (r < P) {
+    for (; r < P; r++) {
         const uint8_t *b0 = heap + (uint64_t)(pe0 + r * pstride) * H;
         qdecode16<FMT>(__ldcg((const uint4 *)(b0 + q_off + e0 * QS)), __ldcg((const float *)(b0 + s_off) + e0 / 128), d);
 #pragma unroll
@@ -109,6 +119,8 @@ __device__ __forceinline__ void qsum_wide(uint8_t *heap, uint64_t H, int pe0, in
     }
 }
 
+// Dequantised sum of elements [e0, e0+4) over the team members, written to every
+// member's dst.  Vector path: 4 codes and 4 floats per access (aligned offsets).
 template <int FMT>
 __device__ __forceinline__ void qsum4(uint8_t *heap, uint64_t H, int pe0, int pstride, int P, uint64_t d_off,
                                       uint64_t q_off, uint64_t s_off, uint64_t e0, uint64_t n, bool vec) {

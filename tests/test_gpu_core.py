@@ -285,3 +285,30 @@ def test_device_barrier_timeout_is_bounded(sg, heapf):
     sg.clear_status()
     x = torch.ones(4, device="cuda")
     assert float(x.sum()) == 4.0
+
+
+def test_device_script_rejects_invalid_op(sg, heapf, orc):
+    """An op outside the heap stops the device-initiated script at that op; the status
+    word names it and the ops before it have run."""
+    npes, H = 4, 1 << 16
+    h = heapf(npes, H)
+    init = random_heap(npes, H, 5)
+    upload(h, init)
+    ops = np.zeros(5, W.OP_DTYPE)
+    ops[0] = (W.OP_PUT, 0, 0, 0, 1, 0, 4096, 0, 512, 0, 0, 0)
+    ops[1] = (W.OP_BARRIER_ALL, 0, 0, 0, 0, -1, 0, 0, 0, 0, 0, 0)
+    ops[2] = (W.OP_FADD, W.DT_INT64, 0, 0, 2, 3, 8192, 0, 0, 7, 0, 0)
+    ops[3] = (W.OP_PUT, 0, 0, 0, 9, 0, 0, 0, 8, 0, 0, 0)            # PE 9 does not exist
+    ops[4] = (W.OP_PUT, 0, 0, 0, 2, 1, 0, 0, 8, 0, 0, 0)
+    sg.clear_status()
+    dev = torch.from_numpy(ops.view(np.uint8).copy()).cuda()
+    fetched = torch.zeros(5, dtype=torch.int64, device="cuda")
+    sg.run_script(dev, 5, fetched)
+    torch.cuda.synchronize()
+    code, detail = sg.get_status()
+    assert code == sg.ERR_INVALID_ARG and detail == 3
+    sg.clear_status()
+    ref = orc.Heap(npes, H, init)
+    want = ref.run_script(ops[:3])
+    assert first_diff(download(h), ref.mem) is None
+    assert int(fetched[2]) == want[2]

@@ -568,7 +568,7 @@ def run_batch(torch, sg, reps=5, check_teams=32, check_elems=4096):
                 lay.append(("i64", src, dst, None, None))
             else:
                 src = o
-                codes = o + 4 * nt
+                codes = (o + 4 * nt + 255) // 256 * 256      # 16-byte aligned codes: the wide path
                 dst = (codes + 2 * nt + 255) // 256 * 256
                 sc = (dst + 4 * nt + 255) // 256 * 256
                 for p in range(bt.start[t], bt.start[t] + P[t]):

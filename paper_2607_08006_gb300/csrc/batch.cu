@@ -39,12 +39,22 @@ struct BArgs {
     uint32_t *counter;    // [0] next item, [1] CTAs done
 };
 
-// quantised tile: E elements per thread on the wide path (bit 1 of t.vec), 4-element
-// steps for ragged or unaligned groups
+// quantised tile: full chunks of blockDim x E elements accumulate into shared memory and
+// are bulk-stored to every member (bit 1 of t.vec: 16-byte aligned codes and outputs);
+// the rest runs E (or 4) elements per thread
 template <int FMT>
-__device__ __forceinline__ void batch_qsum(const BArgs &a, const BTeam &t, uint64_t e0, uint64_t e1) {
+__device__ __forceinline__ void batch_qsum(const BArgs &a, const BTeam &t, uint64_t e0, uint64_t e1, float *s_out) {
     constexpr int E = QWide<FMT>::E;
-    for (uint64_t q = e0 / E + threadIdx.x; q * E < e1; q += blockDim.x) {
+    const uint64_t CH = (uint64_t)blockDim.x * E;
+    uint64_t f0 = e0;
+    if (t.vec & 2) {
+        for (; f0 + CH <= e1; f0 += CH) {
+            if (threadIdx.x == 0) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");  // s_out free
+            __syncthreads();
+            qsum_chunk_tma<FMT>(a.heap, a.H, t.start, 1, t.size, t.d_off, t.s_off, t.sc_off, f0, s_out);
+        }
+    }
+    for (uint64_t q = f0 / E + threadIdx.x; q * E < e1; q += blockDim.x) {
         const uint64_t f = q * E;
         if ((t.vec & 2) && f + E <= e1) {
             qsum_wide<FMT>(a.heap, a.H, t.start, 1, t.size, t.d_off, t.s_off, t.sc_off, f);
@@ -56,7 +66,7 @@ __device__ __forceinline__ void batch_qsum(const BArgs &a, const BTeam &t, uint6
     }
 }
 
-__device__ __forceinline__ void batch_item(const BArgs &a, const BTeam &t, uint64_t e0, uint64_t e1) {
+__device__ __forceinline__ void batch_item(const BArgs &a, const BTeam &t, uint64_t e0, uint64_t e1, float *s_out) {
     const shmemg_group g = {threadIdx.x, blockDim.x};
     if (t.kind == BK_F32) {
         shmemg_d_reduce_elems_t<float, float4>(g, a.heap, a.H, t.start, 1, t.size, t.d_off, t.s_off, e0, e1, SHMEMG_SUM);
@@ -64,13 +74,14 @@ __device__ __forceinline__ void batch_item(const BArgs &a, const BTeam &t, uint6
         shmemg_d_reduce_elems_t<int64_t, longlong2>(g, a.heap, a.H, t.start, 1, t.size, t.d_off, t.s_off, e0, e1,
                                                     SHMEMG_SUM);
     } else {
-        if (t.kind == BK_E4M3) batch_qsum<SHMEMG_FMT_E4M3>(a, t, e0, e1);
-        else batch_qsum<SHMEMG_FMT_BF16>(a, t, e0, e1);
+        if (t.kind == BK_E4M3) batch_qsum<SHMEMG_FMT_E4M3>(a, t, e0, e1, s_out);
+        else batch_qsum<SHMEMG_FMT_BF16>(a, t, e0, e1, s_out);
     }
 }
 
 __global__ void __launch_bounds__(B_THREADS) k_batch(BArgs a) {
     __shared__ uint32_t s_item;
+    __shared__ __align__(128) float s_out[B_THREADS * 16];  // one quantised chunk (E <= 16)
     for (;;) {
         if (threadIdx.x == 0) s_item = atomicAdd(&a.counter[0], 1u);
         __syncthreads();
@@ -81,9 +92,10 @@ __global__ void __launch_bounds__(B_THREADS) k_batch(BArgs a) {
         const BTeam t = a.teams[item.x];
         const uint64_t e0 = (uint64_t)item.y * a.tile;
         const uint64_t e1 = e0 + a.tile < t.n ? e0 + a.tile : t.n;
-        batch_item(a, t, e0, e1);
+        batch_item(a, t, e0, e1, s_out);
     }
     if (threadIdx.x == 0) {
+        asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");  // this CTA's bulk stores are done
         // every CTA has drawn its final (out-of-range) item before it counts itself
         // done, so the last one can reset both words for the next launch
         __threadfence();

@@ -89,24 +89,26 @@ struct QSumArgs {
     bool wide;  // 16-byte code path allowed
 };
 
-// Each thread owns QWide<FMT>::E consecutive elements (one 16-byte code load per member);
-// a ragged or unaligned group falls back to 4-element steps.
+// Full, aligned chunks of blockDim x E elements: each thread accumulates E elements
+// (one 16-byte code load per member) into shared memory and thread 0 bulk-stores the
+// chunk to every member.  The ragged tail runs in 4-element steps.
 template <int FMT>
 __global__ void __launch_bounds__(Q_THREADS) k_qsum(QSumArgs a) {
     constexpr int E = QWide<FMT>::E;
+    __shared__ __align__(128) float s_out[Q_THREADS * E];
     const int pe0 = a.start + blockIdx.y * a.gstride;
-    const uint64_t ng = (a.n + E - 1) / E;
-    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < ng; i += (uint64_t)gridDim.x * blockDim.x) {
-        const uint64_t e0 = i * E;
-        if (a.wide && e0 + E <= a.n) {
-            qsum_wide<FMT>(a.heap, a.H, pe0, a.stride, a.size, a.d_off, a.q_off, a.s_off, e0);
-        } else {
-            for (int k = 0; k < E / 4 && e0 + 4 * k < a.n; k++) {
-                const uint64_t f = e0 + 4 * k;
-                qsum4<FMT>(a.heap, a.H, pe0, a.stride, a.size, a.d_off, a.q_off, a.s_off, f, a.n, a.vec && f + 4 <= a.n);
-            }
-        }
+    const uint64_t CH = (uint64_t)blockDim.x * E;
+    const uint64_t nfull = a.wide ? a.n / CH : 0;
+    for (uint64_t ch = blockIdx.x; ch < nfull; ch += gridDim.x) {
+        if (threadIdx.x == 0) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");  // s_out free again
+        __syncthreads();
+        qsum_chunk_tma<FMT>(a.heap, a.H, pe0, a.stride, a.size, a.d_off, a.q_off, a.s_off, ch * CH, s_out);
     }
+    if (threadIdx.x == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+    const uint64_t t0 = nfull * CH;
+    for (uint64_t f = t0 + 4 * ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x); f < a.n;
+         f += 4 * (uint64_t)gridDim.x * blockDim.x)
+        qsum4<FMT>(a.heap, a.H, pe0, a.stride, a.size, a.d_off, a.q_off, a.s_off, f, a.n, a.vec && f + 4 <= a.n);
 }
 
 }  // namespace shmemg
@@ -178,7 +180,7 @@ int shmemg_qsum_reduce(shmemg_team_t team, float *dst, const void *q, const floa
     const void *kfn = fmt == SHMEMG_FMT_E4M3 ? (const void *)k_qsum<SHMEMG_FMT_E4M3> : (const void *)k_qsum<SHMEMG_FMT_BF16>;
     uint64_t cap = (uint64_t)ctas_for(kfn, Q_THREADS, 0);
     const uint64_t E = fmt == SHMEMG_FMT_E4M3 ? 16 : 8;
-    uint64_t need = ((n + E - 1) / E + Q_THREADS - 1) / Q_THREADS;
+    uint64_t need = (n + Q_THREADS * E - 1) / (Q_THREADS * E);
     dim3 grid((unsigned)(need < cap ? need : cap), (unsigned)t.ngroups);
     if (fmt == SHMEMG_FMT_E4M3) k_qsum<SHMEMG_FMT_E4M3><<<grid, Q_THREADS, 0, to_stream(stream)>>>(a);
     else k_qsum<SHMEMG_FMT_BF16><<<grid, Q_THREADS, 0, to_stream(stream)>>>(a);

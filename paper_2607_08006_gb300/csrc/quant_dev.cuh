@@ -76,8 +76,26 @@ __device__ __forceinline__ void qdecode16(uint4 w, float s, float *d) {
 // q_off and d_off 16-byte aligned, e0 + E <= n.  Eight members' codes and scales are
 // loaded ahead of their accumulation, which stays in team-rank order.
 template <int FMT>
+__device__ __forceinline__ void qsum_wide_acc(const uint8_t *heap, uint64_t H, int pe0, int pstride, int P,
+                                              uint64_t q_off, uint64_t s_off, uint64_t e0, float4 *o);
+
+template <int FMT>
 __device__ __forceinline__ void qsum_wide(uint8_t *heap, uint64_t H, int pe0, int pstride, int P, uint64_t d_off,
                                           uint64_t q_off, uint64_t s_off, uint64_t e0) {
+    constexpr int E = QWide<FMT>::E;
+    float4 o[E / 4];
+    qsum_wide_acc<FMT>(heap, H, pe0, pstride, P, q_off, s_off, e0, o);
+    for (int m = 0; m < P; m++) {
+        float4 *dst = (float4 *)(heap + (uint64_t)(pe0 + m * pstride) * H + d_off + 4 * e0);
+#pragma unroll
+        for (int k = 0; k < E / 4; k++) dst[k] = o[k];
+    }
+}
+
+// The accumulation of qsum_wide: the E compensated sums of elements [e0, e0+E) into o.
+template <int FMT>
+__device__ __forceinline__ void qsum_wide_acc(const uint8_t *heap, uint64_t H, int pe0, int pstride, int P,
+                                              uint64_t q_off, uint64_t s_off, uint64_t e0, float4 *o) {
     constexpr int E = QWide<FMT>::E;
     constexpr uint64_t QS = FMT == SHMEMG_FMT_E4M3 ? 1 : 2;
     Neu acc[E];
@@ -108,14 +126,34 @@ __device__ __forceinline__ void qsum_wide(uint8_t *heap, uint64_t H, int pe0, in
 #pragma unroll
         for (int j = 0; j < E; j++) acc[j].add(d[j]);
     }
-    float4 o[E / 4];
 #pragma unroll
     for (int k = 0; k < E / 4; k++)
         o[k] = make_float4(acc[4 * k].result(), acc[4 * k + 1].result(), acc[4 * k + 2].result(), acc[4 * k + 3].result());
-    for (int m = 0; m < P; m++) {
-        float4 *dst = (float4 *)(heap + (uint64_t)(pe0 + m * pstride) * H + d_off + 4 * e0);
+}
+
+// One CTA's chunk of blockDim.x * E elements starting at c0 (full, aligned): every thread
+// accumulates its E elements into shared memory, then thread 0 bulk-stores the chunk to
+// every member (one TMA store per member instead of P x E/4 vector stores per thread).
+// `out` holds blockDim.x * E floats (128-byte aligned).  Returns with the stores issued;
+// the caller waits (bulk wait_group.read) before it reuses `out`.
+template <int FMT>
+__device__ __forceinline__ void qsum_chunk_tma(uint8_t *heap, uint64_t H, int pe0, int pstride, int P, uint64_t d_off,
+                                               uint64_t q_off, uint64_t s_off, uint64_t c0, float *out) {
+    constexpr int E = QWide<FMT>::E;
+    float4 o[E / 4];
+    qsum_wide_acc<FMT>(heap, H, pe0, pstride, P, q_off, s_off, c0 + (uint64_t)threadIdx.x * E, o);
 #pragma unroll
-        for (int k = 0; k < E / 4; k++) dst[k] = o[k];
+    for (int k = 0; k < E / 4; k++) reinterpret_cast<float4 *>(out)[threadIdx.x * (E / 4) + k] = o[k];
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // generic smem writes -> bulk copy engine
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const uint32_t bytes = blockDim.x * E * 4;
+        for (int m = 0; m < P; m++)
+            asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(
+                             heap + (uint64_t)(pe0 + m * pstride) * H + d_off + 4 * c0),
+                         "r"((uint32_t)__cvta_generic_to_shared(out)), "r"(bytes)
+                         : "memory");
+        asm volatile("cp.async.bulk.commit_group;" ::: "memory");
     }
 }
 

@@ -307,7 +307,9 @@ def roofline_for(summary, hbm, src):
         with open(TRAFFIC_FILE) as f:
             t = json.load(f).get(name)
         if t:
-            traffic = t.get("dram_bytes_per_launch")
+            # the captured launch's DRAM bytes, scaled by algorithmic bytes to one average
+            # launch of this workload (traffic grows in proportion to the bytes moved)
+            traffic = round(t["capture_dram_bytes"] / t["capture_algorithmic_bytes"] * d["bytes"] / d["launches"])
     total_ms = sum(v["ms"] for v in per_k.values())
     return {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
             "frac": round(achieved / hbm, 4), "traffic": traffic, "kernel": name,
@@ -441,6 +443,49 @@ def run_reference(args, rank, world):
             "cpu_baseline": {"value": round(value, 3), "unit": "GB/s", "cores": 1, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": round(value, 3), "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+# ----------------------------------------------------------------------------- scripted stream
+def run_script_leg(torch, sg, reps=5):
+    """The 4-PE x 1 MiB scripted stream of 10,000 ops (+20 barriers): device-initiated
+    (one cooperative launch) and launch-per-op, each checked against the oracle's final
+    heap, with the oracle's own time (single thread)."""
+    import oracle as orc
+
+    s = W.gen_plain_script()
+    heap = sg.Heap(s.npes, s.heap_bytes)
+    out = {"ops": int(len(s.ops))}
+    try:
+        parts = heap.partitions()
+        init = torch.from_numpy(s.heap.reshape(s.npes, s.heap_bytes)).cuda()
+        dev_ops = torch.from_numpy(s.ops.view(np.uint8).copy()).cuda()
+        fetched = torch.zeros(len(s.ops), dtype=torch.int64, device="cuda")
+        stream = torch.cuda.current_stream()
+        ref = orc.Heap(s.npes, s.heap_bytes, s.heap)
+        t0 = time.perf_counter()
+        ref.run_script(s.ops)
+        out["oracle_ms"] = round((time.perf_counter() - t0) * 1e3, 3)
+        for mode in ("device", "host"):
+            times = []
+            for _ in range(reps + 1):
+                parts.copy_(init)
+                torch.cuda.synchronize()
+                e0, e1 = _events(torch)
+                e0.record(stream)
+                if mode == "device":
+                    sg.run_script(dev_ops, len(s.ops), fetched, stream)
+                else:
+                    sg.run_script_host(s.ops, fetched, stream)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                times.append(e0.elapsed_time(e1))
+            ok = bool(np.array_equal(parts.cpu().numpy().reshape(-1), ref.mem))
+            ms = float(np.median(times[1:]))
+            out[mode] = {"ms": round(ms, 3), "ops_per_s": round(len(s.ops) / (ms * 1e-3), 1), "heap_matches_oracle": ok}
+        out["status"] = sg.get_status()[0]
+    finally:
+        heap.close()
+    return out
 
 
 # ----------------------------------------------------------------------------- AMO / signal stress
@@ -908,8 +953,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="shmemg", choices=["shmemg", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--secondary", default="amo,batch,serve",
-                    help="extra workloads measured after the sweep (comma list of amo,batch,serve or 'none')")
+    ap.add_argument("--secondary", default="script,amo,batch,serve",
+                    help="extra workloads measured after the sweep (comma list of script,amo,batch,serve or 'none')")
     ap.add_argument("--amo-ops-log2", type=int, default=26)
     ap.add_argument("--serve-requests", type=int, default=4096)
     ap.add_argument("--profile", choices=PROFILE_CASES, help="run one small single-kernel case (for ncu) and exit")
@@ -935,7 +980,9 @@ def main():
             out["secondary"] = {}
             for name in sec:
                 t0 = time.perf_counter()
-                if name == "amo":
+                if name == "script":
+                    r = run_script_leg(torch, sg)
+                elif name == "amo":
                     r = run_amo(torch, sg, args.amo_ops_log2)
                 elif name == "batch":
                     r = run_batch(torch, sg)

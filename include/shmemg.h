@@ -364,6 +364,19 @@ int shmemg_amo_stream(int64_t *table, uint64_t words_per_pe, const uint32_t *ops
 int shmemg_pingpong(void *buf, uint64_t *sig, uint64_t payload, int npairs, int iters,
                     uint64_t *lat_ns, void *stream);
 
+/* The ping-pong of shmemg_pingpong between the two CTAs of each pair inside one
+ * thread-block cluster, through distributed shared memory (Sec. 5.3 direct pointers,
+ * Sec. 6.3 device shared team): the payload goes into the peer's shared-memory window
+ * and the signal is a word of that window (cluster-scope release add, acquire poll).
+ * At the end PE p writes the last payload it received to its buf + payload and adds
+ * the rounds it received to its `sig`: the heap ends exactly as after shmemg_pingpong.
+ * Needs pe_mode CTA with cluster_dim >= 2 (each pair inside one device shared team),
+ * 2*npairs a multiple of cluster_dim, payload <= SHMEMG_PINGPONG_CLUSTER_MAX, and every
+ * CTA co-resident (else SHMEMG_ERR_UNSUPPORTED); other arguments as shmemg_pingpong. */
+#define SHMEMG_PINGPONG_CLUSTER_MAX (64u << 10)
+int shmemg_pingpong_cluster(void *buf, uint64_t *sig, uint64_t payload, int npairs, int iters,
+                            uint64_t *lat_ns, void *stream);
+
 /* ----------------------------------------------------------------- batched collectives */
 /* Many teams' uneven collectives in one persistent launch captured in a CUDA graph. */
 typedef struct {

@@ -216,7 +216,8 @@ static __device__ __forceinline__ int shmemg_d_vec_width(const void *a, const vo
     return (m & 15) == 0 ? 16 : (m & 7) == 0 ? 8 : (m & 3) == 0 ? 4 : (m & 1) == 0 ? 2 : 1;
 }
 
-/* Group-wide byte copy dst <- src (no overlap). */
+/* Group-wide byte copy dst <- src (no overlap).  src must be global memory (the loads
+ * are ld.global.cg); dst may be global or the caller's own shared memory. */
 static __device__ __forceinline__ void shmemg_d_copy_group(shmemg_group g, void *dst, const void *src, uint64_t n) {
     switch (shmemg_d_vec_width(dst, src, n)) {
     case 16: shmemg_d_copy_vec(g, (uint4 *)dst, (const uint4 *)src, n / 16); break;
@@ -490,9 +491,183 @@ static __device__ __forceinline__ int shmemg_d_team_barrier_leader(const shmemg_
     }
 }
 
+/* ------------------------------------------------------------------ cluster (DSMEM) */
+/* The device shared team (Sec. 6.3: the peers that share a GPU memory locality domain)
+ * of a CTA-mode heap with cluster_dim > 1 is one hardware thread-block cluster when a
+ * kernel is launched with clusters of cluster_dim CTAs: its members can load and store
+ * each other's shared memory (distributed shared memory, DSMEM) directly, the direct
+ * pointer idea of shmem_ptr (Sec. 5.3) applied to on-chip memory.
+ *
+ * A kernel using this path keeps one shmemg_cluster_state_t in shared memory and calls
+ * shmemg_d_cluster_begin first and shmemg_d_cluster_end last, with every thread of
+ * every CTA: a CTA may touch a peer's shared memory only after the peer has started and
+ * before it exits, and both calls are hardware cluster barriers.  Every wait in between
+ * is bounded, so every CTA reaches the final barrier. */
+typedef struct {
+    uint32_t flag[8];  /* flag[j]: last barrier generation cluster rank j has reached */
+    uint32_t gen;      /* cluster barriers this CTA has entered (thread 0) */
+    int rc;            /* last barrier result, for the CTA's other threads */
+} shmemg_cluster_state_t;
+
+/* Every DSMEM access below names its state space: a peer's copy of a shared-memory
+ * object is addressed by its 32-bit shared::cluster address (mapa), the CTA's own copy
+ * by its shared::cta address; no generic address points into the cluster window. */
+static __device__ __forceinline__ uint32_t shmemg_d_cluster_addr(const void *local, uint32_t rank) {
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(shmemg_smem_u32(local)), "r"(rank));
+    return r;
+}
+static __device__ __forceinline__ void shmemg_d_st_release_cluster_u32(uint32_t dsm, uint32_t v) {
+    asm volatile("st.release.cluster.shared::cluster.u32 [%0], %1;" ::"r"(dsm), "r"(v) : "memory");
+}
+static __device__ __forceinline__ void shmemg_d_st_release_cluster_u64(uint32_t dsm, uint64_t v) {
+    asm volatile("st.release.cluster.shared::cluster.u64 [%0], %1;" ::"r"(dsm), "l"(v) : "memory");
+}
+static __device__ __forceinline__ void shmemg_d_red_release_cluster_add_u64(uint32_t dsm, uint64_t v) {
+    asm volatile("red.release.cluster.shared::cluster.add.u64 [%0], %1;" ::"r"(dsm), "l"(v) : "memory");
+}
+static __device__ __forceinline__ uint32_t shmemg_d_ld_acquire_cluster_u32(const uint32_t *own) {
+    uint32_t v;
+    asm volatile("ld.acquire.cluster.shared::cta.u32 %0, [%1];" : "=r"(v) : "r"(shmemg_smem_u32(own)) : "memory");
+    return v;
+}
+static __device__ __forceinline__ uint64_t shmemg_d_ld_acquire_cluster_u64(const uint64_t *own) {
+    uint64_t v;
+    asm volatile("ld.acquire.cluster.shared::cta.u64 %0, [%1];" : "=l"(v) : "r"(shmemg_smem_u32(own)) : "memory");
+    return v;
+}
+/* plain DSMEM loads and stores of 1, 2, 4, 8 or 16 bytes */
+template <int B> struct shmemg_dsm;
+template <> struct shmemg_dsm<16> {
+    typedef uint4 W;
+    static __device__ __forceinline__ W ld(uint32_t a) {
+        W v;
+        asm volatile("ld.shared::cluster.v4.u32 {%0, %1, %2, %3}, [%4];" : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+                     : "r"(a) : "memory");
+        return v;
+    }
+    static __device__ __forceinline__ void st(uint32_t a, W v) {
+        asm volatile("st.shared::cluster.v4.u32 [%0], {%1, %2, %3, %4};" ::"r"(a), "r"(v.x), "r"(v.y), "r"(v.z),
+                     "r"(v.w) : "memory");
+    }
+};
+template <> struct shmemg_dsm<8> {
+    typedef uint2 W;
+    static __device__ __forceinline__ W ld(uint32_t a) {
+        W v;
+        asm volatile("ld.shared::cluster.v2.u32 {%0, %1}, [%2];" : "=r"(v.x), "=r"(v.y) : "r"(a) : "memory");
+        return v;
+    }
+    static __device__ __forceinline__ void st(uint32_t a, W v) {
+        asm volatile("st.shared::cluster.v2.u32 [%0], {%1, %2};" ::"r"(a), "r"(v.x), "r"(v.y) : "memory");
+    }
+};
+template <> struct shmemg_dsm<4> {
+    typedef uint32_t W;
+    static __device__ __forceinline__ W ld(uint32_t a) {
+        W v;
+        asm volatile("ld.shared::cluster.u32 %0, [%1];" : "=r"(v) : "r"(a) : "memory");
+        return v;
+    }
+    static __device__ __forceinline__ void st(uint32_t a, W v) {
+        asm volatile("st.shared::cluster.u32 [%0], %1;" ::"r"(a), "r"(v) : "memory");
+    }
+};
+template <> struct shmemg_dsm<2> {
+    typedef uint16_t W;
+    static __device__ __forceinline__ W ld(uint32_t a) {
+        W v;
+        asm volatile("ld.shared::cluster.u16 %0, [%1];" : "=h"(v) : "r"(a) : "memory");
+        return v;
+    }
+    static __device__ __forceinline__ void st(uint32_t a, W v) {
+        asm volatile("st.shared::cluster.u16 [%0], %1;" ::"r"(a), "h"(v) : "memory");
+    }
+};
+template <> struct shmemg_dsm<1> {
+    typedef uint8_t W;
+    static __device__ __forceinline__ W ld(uint32_t a) {
+        uint32_t v;
+        asm volatile("ld.shared::cluster.u8 %0, [%1];" : "=r"(v) : "r"(a) : "memory");
+        return (W)v;
+    }
+    static __device__ __forceinline__ void st(uint32_t a, W v) {
+        asm volatile("st.shared::cluster.u8 [%0], %1;" ::"r"(a), "r"((uint32_t)v) : "memory");
+    }
+};
+template <typename V>
+static __device__ __forceinline__ V shmemg_d_ld_cluster(uint32_t a) {
+    typename shmemg_dsm<sizeof(V)>::W w = shmemg_dsm<sizeof(V)>::ld(a);
+    V v;
+    memcpy(&v, &w, sizeof(V));
+    return v;
+}
+template <typename V>
+static __device__ __forceinline__ void shmemg_d_st_cluster(uint32_t a, V v) {
+    typename shmemg_dsm<sizeof(V)>::W w;
+    memcpy(&w, &v, sizeof(V));
+    shmemg_dsm<sizeof(V)>::st(a, w);
+}
+
+static __device__ __forceinline__ void shmemg_d_cluster_begin(shmemg_cluster_state_t &cs) {
+    if (threadIdx.x < 8) cs.flag[threadIdx.x] = 0;
+    if (threadIdx.x == 0) cs.gen = 0;
+    shmemg_d_cluster_sync();
+}
+static __device__ __forceinline__ void shmemg_d_cluster_end() { shmemg_d_cluster_sync(); }
+
+/* Is `team` the hardware cluster of this launch (its barrier and data can go through
+ * DSMEM)?  Only when the kernel keeps a cluster state and the heap's shared team is a
+ * cluster of CTAs. */
+static __device__ __forceinline__ bool shmemg_d_team_is_cluster(const shmemg_device_ctx_t &c,
+                                                                const shmemg_cluster_state_t *cs, int team) {
+    return cs && team == SHMEMG_TEAM_SHARED && c.pe_mode == SHMEMG_PE_MODE_CTA && c.cluster_dim > 1;
+}
+
+/* Barrier of the cluster's CTAs, entered by thread 0 of each: it stores its new
+ * generation into every member's flag[own rank] (release, cluster scope) and polls its
+ * own flags (acquire) until every member has reached the generation: no atomics, and
+ * each CTA spins only on its own shared memory.  Bounded like every wait here. */
+static __device__ __forceinline__ int shmemg_d_cluster_barrier_leader(const shmemg_device_ctx_t &c,
+                                                                      shmemg_cluster_state_t &cs, int64_t detail) {
+    const uint32_t n = shmemg_d_cluster_nctarank(), me = shmemg_d_cluster_ctarank();
+    const uint32_t gen = ++cs.gen;
+    for (uint32_t j = 0; j < n; j++) shmemg_d_st_release_cluster_u32(shmemg_d_cluster_addr(&cs.flag[me], j), gen);
+    uint64_t t0 = 0;
+    for (uint32_t j = 0; j < n; j++) {
+        for (uint32_t it = 0; (int32_t)(shmemg_d_ld_acquire_cluster_u32(&cs.flag[j]) - gen) < 0; it++) {
+            if ((it & 255) == 255) {
+                const uint64_t now = shmemg_d_globaltimer();
+                if (t0 == 0) t0 = now;
+                else if (now - t0 > c.timeout_ns) {
+                    shmemg_d_set_status(c, SHMEMG_ERR_TIMEOUT, detail);
+                    return SHMEMG_ERR_TIMEOUT;
+                }
+                if (shmemg_d_get_status(c) != 0) return SHMEMG_ERR_DEVICE;
+            }
+        }
+    }
+    return SHMEMG_SUCCESS;
+}
+/* Cluster barrier at CTA scope (every thread calls); `quiet` first makes the CTA's
+ * earlier writes visible GPU-wide, as a team barrier does. */
+static __device__ __noinline__ int shmemg_d_cluster_sync_pe(const shmemg_device_ctx_t &c,
+                                                               shmemg_cluster_state_t &cs, bool quiet, int64_t detail) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (quiet) shmemg_d_fence_gpu();
+        cs.rc = shmemg_d_cluster_barrier_leader(c, cs, detail);
+    }
+    __syncthreads();
+    return cs.rc;
+}
+
 /* Team barrier at PE scope (all threads of the calling PE call it): quiet, then the
- * leader runs the team barrier; the result is broadcast to the PE's threads. */
-static __device__ __forceinline__ int shmemg_d_team_sync_pe(const shmemg_device_ctx_t &c, int team, int64_t detail) {
+ * leader runs the team barrier; the result is broadcast to the PE's threads.  With a
+ * cluster state and the cluster's own team, the barrier goes through DSMEM. */
+static __device__ __forceinline__ int shmemg_d_team_sync_pe(const shmemg_device_ctx_t &c, int team, int64_t detail,
+                                                            shmemg_cluster_state_t *cs = nullptr) {
+    if (shmemg_d_team_is_cluster(c, cs, team)) return shmemg_d_cluster_sync_pe(c, *cs, true, detail);
     __shared__ int shmemg_sync_rc;
     const shmemg_dteam_t *t = shmemg_d_team(c, team);
     int grp = 0;
@@ -719,50 +894,54 @@ static __device__ __forceinline__ void shmemg_d_slice(uint64_t total, int r, int
  * symmetric byte offsets.  Return SHMEMG_SUCCESS or a timeout / device error. */
 static __device__ __forceinline__ int shmemg_d_reduce_pe(const shmemg_device_ctx_t &c, int team, uint64_t dst_off,
                                                          uint64_t src_off, uint64_t nelems, int dtype, int op,
-                                                         int64_t detail) {
+                                                         int64_t detail,
+                                                         shmemg_cluster_state_t *cs = nullptr) {
     const shmemg_dteam_t t = *shmemg_d_team(c, team);
     int grp = 0, r = shmemg_d_team_rank(t, shmemg_d_my_pe(c), &grp);
     if (r < 0) return SHMEMG_SUCCESS;
-    int rc = shmemg_d_team_sync_pe(c, team, detail);
+    int rc = shmemg_d_team_sync_pe(c, team, detail, cs);
     if (rc) return rc;
     uint64_t es = dtype == SHMEMG_INT64 ? 8 : 4, lo, hi;
     shmemg_d_slice(nelems, r, t.size, 16 / es, &lo, &hi);
     shmemg_d_reduce_elems(shmemg_d_group_pe(c), c.heap, c.pe_stride, shmemg_d_team_member(t, grp, 0), t.stride,
                           t.size, dst_off, src_off, lo, hi, dtype, op);
-    return shmemg_d_team_sync_pe(c, team, detail);
+    return shmemg_d_team_sync_pe(c, team, detail, cs);
 }
 static __device__ __forceinline__ int shmemg_d_broadcastmem_pe(const shmemg_device_ctx_t &c, int team, uint64_t dst_off,
-                                                               uint64_t src_off, uint64_t n, int root, int64_t detail) {
+                                                               uint64_t src_off, uint64_t n, int root, int64_t detail,
+                                                               shmemg_cluster_state_t *cs = nullptr) {
     const shmemg_dteam_t t = *shmemg_d_team(c, team);
     int grp = 0, r = shmemg_d_team_rank(t, shmemg_d_my_pe(c), &grp);
     if (r < 0) return SHMEMG_SUCCESS;
-    int rc = shmemg_d_team_sync_pe(c, team, detail);
+    int rc = shmemg_d_team_sync_pe(c, team, detail, cs);
     if (rc) return rc;
     uint64_t lo, hi;
     shmemg_d_slice(n, r, t.size, 16, &lo, &hi);
     const uint8_t *src = shmemg_d_addr(c, shmemg_d_team_member(t, grp, root), src_off);
     shmemg_d_replicate_bytes(shmemg_d_group_pe(c), c.heap, c.pe_stride, shmemg_d_team_member(t, grp, 0), t.stride,
                              t.size, dst_off, src, lo, hi);
-    return shmemg_d_team_sync_pe(c, team, detail);
+    return shmemg_d_team_sync_pe(c, team, detail, cs);
 }
 static __device__ __forceinline__ int shmemg_d_fcollectmem_pe(const shmemg_device_ctx_t &c, int team, uint64_t dst_off,
-                                                              uint64_t src_off, uint64_t n, int64_t detail) {
+                                                              uint64_t src_off, uint64_t n, int64_t detail,
+                                                              shmemg_cluster_state_t *cs = nullptr) {
     const shmemg_dteam_t t = *shmemg_d_team(c, team);
     int grp = 0, r = shmemg_d_team_rank(t, shmemg_d_my_pe(c), &grp);
     if (r < 0) return SHMEMG_SUCCESS;
-    int rc = shmemg_d_team_sync_pe(c, team, detail);
+    int rc = shmemg_d_team_sync_pe(c, team, detail, cs);
     if (rc) return rc;
     const uint8_t *src = shmemg_d_addr(c, shmemg_d_team_member(t, grp, r), src_off);
     shmemg_d_replicate_bytes(shmemg_d_group_pe(c), c.heap, c.pe_stride, shmemg_d_team_member(t, grp, 0), t.stride,
                              t.size, dst_off + (uint64_t)r * n, src, 0, n);
-    return shmemg_d_team_sync_pe(c, team, detail);
+    return shmemg_d_team_sync_pe(c, team, detail, cs);
 }
 static __device__ __forceinline__ int shmemg_d_alltoallmem_pe(const shmemg_device_ctx_t &c, int team, uint64_t dst_off,
-                                                              uint64_t src_off, uint64_t n, int64_t detail) {
+                                                              uint64_t src_off, uint64_t n, int64_t detail,
+                                                              shmemg_cluster_state_t *cs = nullptr) {
     const shmemg_dteam_t t = *shmemg_d_team(c, team);
     int grp = 0, r = shmemg_d_team_rank(t, shmemg_d_my_pe(c), &grp);
     if (r < 0) return SHMEMG_SUCCESS;
-    int rc = shmemg_d_team_sync_pe(c, team, detail);
+    int rc = shmemg_d_team_sync_pe(c, team, detail, cs);
     if (rc) return rc;
     const int me = shmemg_d_team_member(t, grp, r);
     for (int j = 0; j < t.size; j++) {
@@ -770,7 +949,245 @@ static __device__ __forceinline__ int shmemg_d_alltoallmem_pe(const shmemg_devic
         shmemg_d_copy_group(shmemg_d_group_pe(c), shmemg_d_addr(c, pj, dst_off + (uint64_t)r * n),
                             shmemg_d_addr(c, me, src_off + (uint64_t)j * n), n);
     }
-    return shmemg_d_team_sync_pe(c, team, detail);
+    return shmemg_d_team_sync_pe(c, team, detail, cs);
+}
+
+/* ------------------------------------------------------------------ cluster collectives */
+/* Shared-team collectives staged through DSMEM (CTA-mode heaps, the team = the launch's
+ * cluster).  `win` is a shared-memory window of `win_bytes` at the same offset in every
+ * CTA (16-byte aligned).  After the entry barrier (a quiet and a team barrier) each
+ * member copies what the others need into its own window, the cluster synchronises,
+ * and each member builds ITS OWN destination from the members' windows read through
+ * DSMEM; an exit barrier keeps every window until all have read it.  The only HBM
+ * traffic is each member's own source read and destination write; every byte that
+ * moves between PEs crosses the cluster's DSMEM. */
+
+/* group-wide copies between global memory and a cluster peer's shared memory: the
+ * peer's copy of the shared object at `local` in cluster rank `rank` */
+template <typename V>
+static __device__ __forceinline__ void shmemg_d_copy_vec_from_cluster(shmemg_group g, V *dst, uint32_t src,
+                                                                     uint64_t nvec) {
+    uint64_t i = g.rank;
+    const uint64_t s = g.size;
+    for (; i + 3 * s < nvec; i += 4 * s) {
+        V a = shmemg_d_ld_cluster<V>(src + (uint32_t)(i * sizeof(V)));
+        V b = shmemg_d_ld_cluster<V>(src + (uint32_t)((i + s) * sizeof(V)));
+        V d = shmemg_d_ld_cluster<V>(src + (uint32_t)((i + 2 * s) * sizeof(V)));
+        V e = shmemg_d_ld_cluster<V>(src + (uint32_t)((i + 3 * s) * sizeof(V)));
+        dst[i] = a;
+        dst[i + s] = b;
+        dst[i + 2 * s] = d;
+        dst[i + 3 * s] = e;
+    }
+    for (; i < nvec; i += s) dst[i] = shmemg_d_ld_cluster<V>(src + (uint32_t)(i * sizeof(V)));
+}
+static __device__ __forceinline__ void shmemg_d_copy_from_cluster(shmemg_group g, void *dst, const void *local,
+                                                                 uint32_t rank, uint64_t n) {
+    const uint32_t a = shmemg_d_cluster_addr(local, rank);
+    switch (shmemg_d_vec_width(dst, local, n)) {
+    case 16: shmemg_d_copy_vec_from_cluster(g, (uint4 *)dst, a, n / 16); break;
+    case 8: shmemg_d_copy_vec_from_cluster(g, (uint2 *)dst, a, n / 8); break;
+    case 4: shmemg_d_copy_vec_from_cluster(g, (uint32_t *)dst, a, n / 4); break;
+    case 2: shmemg_d_copy_vec_from_cluster(g, (uint16_t *)dst, a, n / 2); break;
+    default: shmemg_d_copy_vec_from_cluster(g, (uint8_t *)dst, a, n); break;
+    }
+}
+template <typename V>
+static __device__ __forceinline__ void shmemg_d_copy_vec_to_cluster(shmemg_group g, uint32_t dst, const V *src,
+                                                                   uint64_t nvec) {
+    uint64_t i = g.rank;
+    const uint64_t s = g.size;
+    for (; i + 3 * s < nvec; i += 4 * s) {
+        V a = shmemg_ld_cg(src + i), b = shmemg_ld_cg(src + i + s);
+        V d = shmemg_ld_cg(src + i + 2 * s), e = shmemg_ld_cg(src + i + 3 * s);
+        shmemg_d_st_cluster<V>(dst + (uint32_t)(i * sizeof(V)), a);
+        shmemg_d_st_cluster<V>(dst + (uint32_t)((i + s) * sizeof(V)), b);
+        shmemg_d_st_cluster<V>(dst + (uint32_t)((i + 2 * s) * sizeof(V)), d);
+        shmemg_d_st_cluster<V>(dst + (uint32_t)((i + 3 * s) * sizeof(V)), e);
+    }
+    for (; i < nvec; i += s) shmemg_d_st_cluster<V>(dst + (uint32_t)(i * sizeof(V)), shmemg_ld_cg(src + i));
+}
+static __device__ __forceinline__ void shmemg_d_copy_to_cluster(shmemg_group g, void *local, uint32_t rank,
+                                                               const void *src, uint64_t n) {
+    const uint32_t a = shmemg_d_cluster_addr(local, rank);
+    switch (shmemg_d_vec_width(local, src, n)) {
+    case 16: shmemg_d_copy_vec_to_cluster(g, a, (const uint4 *)src, n / 16); break;
+    case 8: shmemg_d_copy_vec_to_cluster(g, a, (const uint2 *)src, n / 8); break;
+    case 4: shmemg_d_copy_vec_to_cluster(g, a, (const uint32_t *)src, n / 4); break;
+    case 2: shmemg_d_copy_vec_to_cluster(g, a, (const uint16_t *)src, n / 2); break;
+    default: shmemg_d_copy_vec_to_cluster(g, a, (const uint8_t *)src, n); break;
+    }
+}
+
+/* the rank-pairwise tree (the fixed float order above) over P <= 8 members, values from
+ * a loader ld(r) */
+template <int L, typename V, typename Ld>
+static __device__ __forceinline__ V shmemg_tree_block_ld(const Ld &ld, int r0) {
+    if constexpr (L == 0) {
+        return ld(r0);
+    } else {
+        V a = shmemg_tree_block_ld<L - 1, V>(ld, r0);
+        V b = shmemg_tree_block_ld<L - 1, V>(ld, r0 + (1 << (L - 1)));
+        return shmemg_vadd<V>::add(a, b);
+    }
+}
+template <typename V, typename Ld>
+static __device__ __forceinline__ V shmemg_tree_sum8(const Ld &ld, int P) {
+    V acc{};
+    bool have = false;
+#define SHMEMG_TB8(b)                                                    \
+    if (P & (1 << b)) {                                                  \
+        V t = shmemg_tree_block_ld<b, V>(ld, P & ~((2 << b) - 1));       \
+        acc = have ? shmemg_vadd<V>::add(t, acc) : t;                    \
+        have = true;                                                     \
+    }
+    SHMEMG_TB8(0) SHMEMG_TB8(1) SHMEMG_TB8(2) SHMEMG_TB8(3)
+#undef SHMEMG_TB8
+    return acc;
+}
+
+/* dst[v] = combination over the P members' windows of vector v (team-rank order) */
+template <typename T, typename V, int OP>
+static __device__ __forceinline__ void shmemg_d_cluster_reduce_vecs(const uint8_t *win, int P, V *dst, uint64_t nvec) {
+    constexpr int NL = sizeof(V) / sizeof(T);
+    for (uint64_t vi = threadIdx.x; vi < nvec; vi += blockDim.x) {
+        auto ld = [&](int r) { return shmemg_d_ld_cluster<V>(shmemg_d_cluster_addr(win, (uint32_t)r) + (uint32_t)(vi * sizeof(V))); };
+        V acc;
+        if constexpr (OP == SHMEMG_SUM && std::is_floating_point<T>::value) {
+            acc = shmemg_tree_sum8<V>(ld, P);
+        } else {
+            acc = ld(0);
+            for (int r = 1; r < P; r++) {
+                V x = ld(r);
+#pragma unroll
+                for (int l = 0; l < NL; l++) {
+                    T &s = reinterpret_cast<T *>(&acc)[l];
+                    s = shmemg_comb<T>(s, reinterpret_cast<T *>(&x)[l], OP);
+                }
+            }
+        }
+        dst[vi] = acc;
+    }
+}
+template <typename T, typename V16>
+static __device__ __forceinline__ void shmemg_d_cluster_reduce_t(const uint8_t *win, int P, uint8_t *dst,
+                                                                uint64_t nelems, int op) {
+    const bool v16 = (((uint64_t)dst | (nelems * sizeof(T))) & 15) == 0;
+    if (v16) {
+        const uint64_t nv = nelems * sizeof(T) / 16;
+        if (op == SHMEMG_SUM) shmemg_d_cluster_reduce_vecs<T, V16, SHMEMG_SUM>(win, P, (V16 *)dst, nv);
+        else if (op == SHMEMG_MAX) shmemg_d_cluster_reduce_vecs<T, V16, SHMEMG_MAX>(win, P, (V16 *)dst, nv);
+        else shmemg_d_cluster_reduce_vecs<T, V16, SHMEMG_MIN>(win, P, (V16 *)dst, nv);
+    } else {
+        if (op == SHMEMG_SUM) shmemg_d_cluster_reduce_vecs<T, T, SHMEMG_SUM>(win, P, (T *)dst, nelems);
+        else if (op == SHMEMG_MAX) shmemg_d_cluster_reduce_vecs<T, T, SHMEMG_MAX>(win, P, (T *)dst, nelems);
+        else shmemg_d_cluster_reduce_vecs<T, T, SHMEMG_MIN>(win, P, (T *)dst, nelems);
+    }
+}
+
+/* Bytes a staged collective needs in each member's window (0: too large to stage). */
+static __device__ __forceinline__ uint64_t shmemg_d_cluster_stage_bytes(int kind, uint64_t n, int dtype, int P) {
+    switch (kind) {
+    case SHMEMG_OP_REDUCE: return n * (dtype == SHMEMG_INT64 ? 8 : 4);
+    case SHMEMG_OP_BROADCAST: case SHMEMG_OP_FCOLLECT: return n;
+    case SHMEMG_OP_ALLTOALL: return n * (uint64_t)P;
+    default: return 0;
+    }
+}
+
+static __device__ __noinline__ int shmemg_d_cluster_reduce_pe(const shmemg_device_ctx_t &c, shmemg_cluster_state_t &cs,
+                                                                 uint8_t *win, uint64_t dst_off, uint64_t src_off,
+                                                                 uint64_t nelems, int dtype, int op, int64_t detail) {
+    const int me = shmemg_d_my_pe(c), P = (int)shmemg_d_cluster_nctarank();
+    int rc = shmemg_d_cluster_sync_pe(c, cs, true, detail);
+    if (rc) return rc;
+    shmemg_d_copy_group(shmemg_d_group_block(), win, shmemg_d_addr(c, me, src_off),
+                        shmemg_d_cluster_stage_bytes(SHMEMG_OP_REDUCE, nelems, dtype, P));
+    if ((rc = shmemg_d_cluster_sync_pe(c, cs, false, detail))) return rc;
+    uint8_t *dst = shmemg_d_addr(c, me, dst_off);
+    if (dtype == SHMEMG_INT32) shmemg_d_cluster_reduce_t<int32_t, int4>(win, P, dst, nelems, op);
+    else if (dtype == SHMEMG_INT64) shmemg_d_cluster_reduce_t<int64_t, longlong2>(win, P, dst, nelems, op);
+    else shmemg_d_cluster_reduce_t<float, float4>(win, P, dst, nelems, op);
+    return shmemg_d_cluster_sync_pe(c, cs, false, detail);
+}
+/* root (team rank) stages n bytes; every member copies the root's window */
+static __device__ __noinline__ int shmemg_d_cluster_broadcastmem_pe(const shmemg_device_ctx_t &c,
+                                                                       shmemg_cluster_state_t &cs, uint8_t *win,
+                                                                       uint64_t dst_off, uint64_t src_off, uint64_t n,
+                                                                       int root, int64_t detail) {
+    const int me = shmemg_d_my_pe(c);
+    int rc = shmemg_d_cluster_sync_pe(c, cs, true, detail);
+    if (rc) return rc;
+    if ((int)shmemg_d_cluster_ctarank() == root)
+        shmemg_d_copy_group(shmemg_d_group_block(), win, shmemg_d_addr(c, me, src_off), n);
+    if ((rc = shmemg_d_cluster_sync_pe(c, cs, false, detail))) return rc;
+    shmemg_d_copy_from_cluster(shmemg_d_group_block(), shmemg_d_addr(c, me, dst_off), win, (uint32_t)root, n);
+    return shmemg_d_cluster_sync_pe(c, cs, false, detail);
+}
+/* each member stages its n bytes; member r's dst block j = member j's window */
+static __device__ __noinline__ int shmemg_d_cluster_fcollectmem_pe(const shmemg_device_ctx_t &c,
+                                                                      shmemg_cluster_state_t &cs, uint8_t *win,
+                                                                      uint64_t dst_off, uint64_t src_off, uint64_t n,
+                                                                      int64_t detail) {
+    const int me = shmemg_d_my_pe(c), P = (int)shmemg_d_cluster_nctarank();
+    int rc = shmemg_d_cluster_sync_pe(c, cs, true, detail);
+    if (rc) return rc;
+    shmemg_d_copy_group(shmemg_d_group_block(), win, shmemg_d_addr(c, me, src_off), n);
+    if ((rc = shmemg_d_cluster_sync_pe(c, cs, false, detail))) return rc;
+    for (int j = 0; j < P; j++)
+        shmemg_d_copy_from_cluster(shmemg_d_group_block(), shmemg_d_addr(c, me, dst_off + (uint64_t)j * n), win,
+                                   (uint32_t)j, n);
+    return shmemg_d_cluster_sync_pe(c, cs, false, detail);
+}
+/* each member stages its P blocks; member r's dst block j = block r of member j's window */
+static __device__ __noinline__ int shmemg_d_cluster_alltoallmem_pe(const shmemg_device_ctx_t &c,
+                                                                      shmemg_cluster_state_t &cs, uint8_t *win,
+                                                                      uint64_t dst_off, uint64_t src_off, uint64_t n,
+                                                                      int64_t detail) {
+    const int me = shmemg_d_my_pe(c), P = (int)shmemg_d_cluster_nctarank(), r = (int)shmemg_d_cluster_ctarank();
+    int rc = shmemg_d_cluster_sync_pe(c, cs, true, detail);
+    if (rc) return rc;
+    shmemg_d_copy_group(shmemg_d_group_block(), win, shmemg_d_addr(c, me, src_off), n * (uint64_t)P);
+    if ((rc = shmemg_d_cluster_sync_pe(c, cs, false, detail))) return rc;
+    for (int j = 0; j < P; j++)
+        shmemg_d_copy_from_cluster(shmemg_d_group_block(), shmemg_d_addr(c, me, dst_off + (uint64_t)j * n),
+                                   win + (uint64_t)r * n, (uint32_t)j, n);
+    return shmemg_d_cluster_sync_pe(c, cs, false, detail);
+}
+
+/* put-with-signal into a cluster peer's shared memory (group scope: every thread of g
+ * calls; g's rank-0 thread updates the signal after the group has written): n bytes
+ * from `src` (global memory) to the peer's copy of the shared object `dst_local`,
+ * then a cluster-scope release update of the peer's copy of `sig_local`. */
+static __device__ __forceinline__ void shmemg_d_putmem_signal_cluster_block(void *dst_local, const void *src, uint64_t n,
+                                                                            uint64_t *sig_local, uint64_t v, int sig_op,
+                                                                            uint32_t peer_rank) {
+    shmemg_d_copy_to_cluster(shmemg_d_group_block(), dst_local, peer_rank, src, n);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const uint32_t s = shmemg_d_cluster_addr(sig_local, peer_rank);
+        if (sig_op == SHMEMG_SIGNAL_SET) shmemg_d_st_release_cluster_u64(s, v);
+        else shmemg_d_red_release_cluster_add_u64(s, v);
+    }
+}
+/* wait_until on the caller's own shared-memory signal word (thread scope, acquire at
+ * cluster scope), bounded like shmemg_d_signal_wait_until. */
+static __device__ __forceinline__ int shmemg_d_signal_wait_until_cluster(const shmemg_device_ctx_t &c,
+                                                                         const uint64_t *sig_local, int cmp, uint64_t v,
+                                                                         int64_t detail) {
+    uint64_t t0 = 0;
+    for (uint32_t it = 0;; it++) {
+        if (shmemg_d_cmp(shmemg_d_ld_acquire_cluster_u64(sig_local), cmp, v)) return SHMEMG_SUCCESS;
+        if ((it & 255) == 255) {
+            const uint64_t now = shmemg_d_globaltimer();
+            if (t0 == 0) t0 = now;
+            else if (now - t0 > c.timeout_ns) {
+                shmemg_d_set_status(c, SHMEMG_ERR_TIMEOUT, detail);
+                return SHMEMG_ERR_TIMEOUT;
+            }
+            if (shmemg_d_get_status(c) != 0) return SHMEMG_ERR_DEVICE;
+        }
+    }
 }
 
 #endif /* SHMEMG_DEVICE_CUH */

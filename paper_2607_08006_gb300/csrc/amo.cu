@@ -191,6 +191,62 @@ __global__ void __launch_bounds__(PP_THREADS, 8) k_pingpong(shmemg_device_ctx_t 
     }
 }
 
+// The same ping-pong between the two CTAs of a pair inside one cluster, through
+// distributed shared memory: the payload is stored straight into the peer's
+// shared-memory window and the signal is a word of that window, raised with a
+// cluster-scope release add; each side acquire-polls its own window.  At the end each
+// PE writes the last payload it received to buf + payload and adds the rounds it
+// received to its heap signal word: the heap ends as after the same put_signals into
+// the heap.
+__global__ void __launch_bounds__(PP_THREADS, 8) k_pingpong_cluster(shmemg_device_ctx_t c, uint64_t buf_off,
+                                                                 uint64_t sig_off, uint64_t payload, int iters,
+                                                                 uint64_t *lat) {
+    extern __shared__ __align__(16) uint8_t s_win[];  // payload bytes, then the signal word
+    __shared__ int s_stop;
+    const int me = blockIdx.x, pair = me >> 1;
+    const uint32_t peer_rank = shmemg_d_cluster_ctarank() ^ 1u;
+    const bool pinger = (me & 1) == 0;
+    uint64_t *my_sig = (uint64_t *)(s_win + ((payload + 15) & ~15ull));
+    if (threadIdx.x == 0) {
+        *my_sig = 0;
+        s_stop = 0;
+    }
+    shmemg_d_cluster_sync();  // both CTAs started, windows initialised
+    const uint8_t *src = shmemg_d_addr(c, me, buf_off);
+    uint64_t t_start = 0;
+    for (int t = 0; t < iters; t++) {
+        if (pinger) {
+            if (threadIdx.x == 0) t_start = shmemg_d_globaltimer();
+            shmemg_d_putmem_signal_cluster_block(s_win, src, payload, my_sig, 1, SHMEMG_SIGNAL_ADD, peer_rank);
+            if (threadIdx.x == 0) {
+                if (shmemg_d_signal_wait_until_cluster(c, my_sig, SHMEMG_CMP_GE, (uint64_t)t + 1, pair) != SHMEMG_SUCCESS)
+                    s_stop = 1;
+                if (lat) lat[(uint64_t)pair * iters + t] = shmemg_d_globaltimer() - t_start;
+            }
+            __syncthreads();
+        } else {
+            if (threadIdx.x == 0 &&
+                shmemg_d_signal_wait_until_cluster(c, my_sig, SHMEMG_CMP_GE, (uint64_t)t + 1, pair) != SHMEMG_SUCCESS)
+                s_stop = 1;
+            __syncthreads();
+            if (s_stop) break;
+            shmemg_d_putmem_signal_cluster_block(s_win, src, payload, my_sig, 1, SHMEMG_SIGNAL_ADD, peer_rank);
+        }
+        if (s_stop) break;
+    }
+    // the peer's last update of this window precedes the last signal this CTA acquired;
+    // the cluster barrier also keeps both windows alive until both are done
+    shmemg_d_cluster_sync();
+    if (*my_sig == 0) return;  // nothing received: the heap keeps its contents
+    // (the window is shared memory: read it with shared-space loads, never ld.global)
+    shmemg_d_copy_from_cluster(shmemg_d_group_block(), shmemg_d_addr(c, me, buf_off + payload), s_win,
+                               shmemg_d_cluster_ctarank(), payload);
+    if (threadIdx.x == 0) {
+        uint64_t *hs = (uint64_t *)shmemg_d_addr(c, me, sig_off);
+        *hs += *my_sig;
+    }
+}
+
 __global__ void k_time(uint64_t *out) { *out = shmemg_d_globaltimer(); }
 
 }  // namespace shmemg
@@ -252,6 +308,46 @@ int shmemg_pingpong(void *buf, uint64_t *sig, uint64_t payload, int npairs, int 
     cfg.attrs = &attr;
     cfg.numAttrs = 1;
     return cuda_rc(cudaLaunchKernelExC(&cfg, (const void *)k_pingpong, args));
+}
+
+int shmemg_pingpong_cluster(void *buf, uint64_t *sig, uint64_t payload, int npairs, int iters, uint64_t *lat_ns,
+                            void *stream) {
+    if (int rc = check_init()) return rc;
+    State &S = st();
+    if (npairs < 1 || iters < 0 || 2 * npairs > S.npes || payload > SHMEMG_PINGPONG_CLUSTER_MAX) return SHMEMG_ERR_INVALID_ARG;
+    if (S.pe_mode != SHMEMG_PE_MODE_CTA || S.cluster_dim < 2 || (2 * npairs) % S.cluster_dim) return SHMEMG_ERR_UNSUPPORTED;
+    uint64_t boff, soff;
+    if (sym_offset(buf, 2 * payload, &boff) || sym_offset(sig, 8, &soff) || (soff & 7)) return SHMEMG_ERR_NOT_SYMMETRIC;
+    shmemg_device_ctx_t c = device_ctx();
+    const size_t smem = ((payload + 15) & ~15ull) + 16;
+    if (smem > 48 * 1024 && cudaFuncSetAttribute((const void *)k_pingpong_cluster,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+        cudaGetLastError();
+        return SHMEMG_ERR_UNSUPPORTED;
+    }
+    void *args[] = {(void *)&c, (void *)&boff, (void *)&soff, (void *)&payload, (void *)&iters, (void *)&lat_ns};
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(2 * npairs);
+    cfg.blockDim = dim3(PP_THREADS);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = to_stream(stream);
+    cudaLaunchAttribute attr[2];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = S.cluster_dim;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int nclusters = 0;  // every pair's two CTAs wait on each other: all must be resident
+    if (cudaOccupancyMaxActiveClusters(&nclusters, (const void *)k_pingpong_cluster, &cfg) != cudaSuccess) {
+        cudaGetLastError();
+        return SHMEMG_ERR_UNSUPPORTED;
+    }
+    if ((int64_t)nclusters * S.cluster_dim < 2 * npairs) return SHMEMG_ERR_UNSUPPORTED;
+    attr[1].id = cudaLaunchAttributeCooperative;
+    attr[1].val.cooperative = 1;
+    cfg.numAttrs = 2;
+    return cuda_rc(cudaLaunchKernelExC(&cfg, (const void *)k_pingpong_cluster, args));
 }
 
 int shmemg_device_time_ns(uint64_t *out) {

@@ -86,6 +86,19 @@ __global__ void __launch_bounds__(INTERP_THREADS) k_interp(shmemg_device_ctx_t c
     // the op list is staged through shared memory OP_BATCH records at a time (one
     // coalesced copy per batch instead of a dependent global load per op and thread)
     __shared__ __align__(16) shmemg_op_t s_ops[OP_BATCH];
+    // shared-team ops of a CTA-mode heap launched in clusters go through DSMEM: the team
+    // barrier on shared-memory flags, small collectives staged in the bulk ring, which
+    // then serves as each CTA's window (free between ops: every bulk copy has drained)
+    __shared__ shmemg_cluster_state_t s_cs;
+    const bool dsm = c.pe_mode == SHMEMG_PE_MODE_CTA && c.cluster_dim > 1;
+    shmemg_cluster_state_t *cs = dsm ? &s_cs : nullptr;
+    const uint64_t win_bytes = use_bulk ? SHMEMG_BULK_SMEM : 0;
+    if (dsm) shmemg_d_cluster_begin(s_cs);
+    auto staged = [&](const shmemg_op_t &o) {
+        if (!dsm || o.team != SHMEMG_TEAM_SHARED) return false;
+        const uint64_t b = shmemg_d_cluster_stage_bytes(o.kind, o.n, o.dtype, c.cluster_dim);
+        return b > 0 && b <= win_bytes;
+    };
     bool failed = false;
     for (int64_t base = 0; base < nops && !failed; base += OP_BATCH) {
     const int cnt = (int)(nops - base < OP_BATCH ? nops - base : OP_BATCH);
@@ -172,20 +185,25 @@ __global__ void __launch_bounds__(INTERP_THREADS) k_interp(shmemg_device_ctx_t c
             break;
         case SHMEMG_OP_TEAM_SYNC: {
             int grp;
-            if (shmemg_d_team_rank(*shmemg_d_team(c, o.team), me, &grp) >= 0) rc = shmemg_d_team_sync_pe(c, o.team, i);
+            if (shmemg_d_team_rank(*shmemg_d_team(c, o.team), me, &grp) >= 0)
+                rc = shmemg_d_team_sync_pe(c, o.team, i, cs);
             break;
         }
         case SHMEMG_OP_BROADCAST:
-            rc = shmemg_d_broadcastmem_pe(c, o.team, o.dst, o.src, o.n, o.pe, i);
+            if (staged(o)) rc = shmemg_d_cluster_broadcastmem_pe(c, s_cs, s_ring, o.dst, o.src, o.n, o.pe, i);
+            else rc = shmemg_d_broadcastmem_pe(c, o.team, o.dst, o.src, o.n, o.pe, i, cs);
             break;
         case SHMEMG_OP_FCOLLECT:
-            rc = shmemg_d_fcollectmem_pe(c, o.team, o.dst, o.src, o.n, i);
+            if (staged(o)) rc = shmemg_d_cluster_fcollectmem_pe(c, s_cs, s_ring, o.dst, o.src, o.n, i);
+            else rc = shmemg_d_fcollectmem_pe(c, o.team, o.dst, o.src, o.n, i, cs);
             break;
         case SHMEMG_OP_ALLTOALL:
-            rc = shmemg_d_alltoallmem_pe(c, o.team, o.dst, o.src, o.n, i);
+            if (staged(o)) rc = shmemg_d_cluster_alltoallmem_pe(c, s_cs, s_ring, o.dst, o.src, o.n, i);
+            else rc = shmemg_d_alltoallmem_pe(c, o.team, o.dst, o.src, o.n, i, cs);
             break;
         case SHMEMG_OP_REDUCE:
-            rc = shmemg_d_reduce_pe(c, o.team, o.dst, o.src, o.n, o.dtype, o.sub, i);
+            if (staged(o)) rc = shmemg_d_cluster_reduce_pe(c, s_cs, s_ring, o.dst, o.src, o.n, o.dtype, o.sub, i);
+            else rc = shmemg_d_reduce_pe(c, o.team, o.dst, o.src, o.n, o.dtype, o.sub, i, cs);
             break;
         default:
             if (leader) shmemg_d_set_status(c, SHMEMG_ERR_INVALID_ARG, i);
@@ -198,6 +216,7 @@ __global__ void __launch_bounds__(INTERP_THREADS) k_interp(shmemg_device_ctx_t c
     }
     }
     shmemg_d_quiet_pe(c);
+    if (dsm) shmemg_d_cluster_end();  // no CTA leaves while a peer may still touch its shared memory
 }
 
 int interp_threads() {

@@ -387,6 +387,9 @@ int shmemg_query_capabilities(shmemg_team_t team, shmemg_caps_t *out) {
                  SHMEMG_CAP_PERSISTENT_SERVER | SHMEMG_CAP_BATCHED_COLL | SHMEMG_CAP_QUANTIZED_REDUCE;
     out->default_heap = SHMEMG_HEAP_GPU;
     out->path = SHMEMG_PATH_DIRECT_LOCAL_HBM;
+    // the shared team of a CTA-mode heap is a thread-block cluster: its device-initiated
+    // barrier and small collectives go through distributed shared memory
+    if (team == SHMEMG_TEAM_SHARED && s.pe_mode == SHMEMG_PE_MODE_CTA && s.cluster_dim > 1) out->path |= SHMEMG_PATH_DSMEM;
     out->rma_scopes = SHMEMG_SCOPE_THREAD | SHMEMG_SCOPE_WARP | SHMEMG_SCOPE_BLOCK | SHMEMG_SCOPE_CLUSTER;
     out->coll_scopes = SHMEMG_SCOPE_BLOCK | SHMEMG_SCOPE_CLUSTER | SHMEMG_SCOPE_GRID;
     out->device_ordinal = s.device;

@@ -145,6 +145,7 @@ _SIGS = {
     "shmemg_run_script_host": [P, I64, P, P],
     "shmemg_amo_stream": [P, U64, P, U64, U64, U64, P, U32, P],
     "shmemg_pingpong": [P, P, U64, I, I, P, P],
+    "shmemg_pingpong_cluster": [P, P, U64, I, I, P, P],
     "shmemg_batch_create": [P, I, P, P],
     "shmemg_batch_launch": [P, P],
     "shmemg_batch_autotune": [P, P, P],
@@ -451,6 +452,10 @@ def amo_stream(table, words_per_pe, ops_dev, nops, op_seed, table_seed, fetched_
 
 def pingpong(buf, sig, payload, npairs, iters, lat_dev, stream=None):
     _call("shmemg_pingpong", _ptr(buf), _ptr(sig), payload, npairs, iters, _ptr(lat_dev), _stream(stream))
+
+
+def pingpong_cluster(buf, sig, payload, npairs, iters, lat_dev, stream=None):
+    _call("shmemg_pingpong_cluster", _ptr(buf), _ptr(sig), payload, npairs, iters, _ptr(lat_dev), _stream(stream))
 
 
 # batched collectives -----------------------------------------------------------------

@@ -488,12 +488,106 @@ def run_script_leg(torch, sg, reps=5):
     return out
 
 
+# ----------------------------------------------------------------------------- cluster (DSMEM) team
+def run_cluster_leg(torch, sg, rounds=200, reps=3, iters=10000):
+    """The device shared team as a thread-block cluster.  (1) The 512 put_signal /
+    wait_until ping-pong pairs (1024 CTAs, each pair inside one 2-CTA cluster) through
+    distributed shared memory vs the same pairs through L2/HBM, half round trip per
+    payload, final heaps checked.  (2) One cluster of 8 CTA PEs: `rounds` collectives in
+    one device-initiated script on the shared team (DSMEM barrier, windows staged in
+    shared memory) vs the same 8 PEs as the world team (L2 barrier, loads and stores in
+    HBM/L2), time per collective, results compared."""
+    out = {}
+    npes, H = 1024, 16384
+    heap = sg.Heap(npes, H, pe_mode=sg.PE_MODE_CTA, cluster_dim=2)
+    try:
+        parts = heap.partitions()
+        parts.random_(0, 255)
+        sig_off = 3 * 4096
+        lat = torch.zeros(512 * iters, dtype=torch.int64, device="cuda")
+        pp = {}
+        for payload in (8, 64, 512, 4096):
+            row = {}
+            for mode, fn in (("l2", sg.pingpong), ("dsmem", sg.pingpong_cluster)):
+                parts[:, payload:2 * payload].zero_()
+                parts[:, sig_off:sig_off + 8].zero_()
+                torch.cuda.synchronize()
+                fn(heap.base, heap.base + sig_off, payload, 512, iters, lat)
+                torch.cuda.synchronize()
+                half = lat.cpu().numpy().astype(np.float64) / 2 / 1e3
+                peer = parts.view(512, 2, H).flip(1).reshape(npes, H)
+                ok = bool(torch.equal(parts[:, payload:2 * payload], peer[:, :payload])) and \
+                    bool((parts[:, sig_off:sig_off + 8].contiguous().view(torch.int64) == iters).all())
+                row[mode] = {"half_rtt_us_p50": round(float(np.percentile(half, 50)), 3),
+                             "half_rtt_us_p99": round(float(np.percentile(half, 99)), 3), "final_heap_ok": ok}
+            row["speedup_p50"] = round(row["l2"]["half_rtt_us_p50"] / row["dsmem"]["half_rtt_us_p50"], 2)
+            pp[str(payload)] = row
+        out["pingpong_512_pairs"] = pp
+        del lat
+    finally:
+        heap.close()
+
+    P, Hc = 8, 1 << 20
+    heap = sg.Heap(P, Hc, pe_mode=sg.PE_MODE_CTA, cluster_dim=P)
+    try:
+        parts = heap.partitions()
+        parts.random_(0, 255)
+        parts[:, :65536].view(torch.float32).normal_()
+        stream = torch.cuda.current_stream()
+        dst = 512 * 1024
+        cases = [("team_sync", W.OP_TEAM_SYNC, 0, 0, 0), ("reduce_int64_256B", W.OP_REDUCE, W.DT_INT64, 0, 32),
+                 ("reduce_int64_4KiB", W.OP_REDUCE, W.DT_INT64, 0, 512),
+                 ("reduce_int64_64KiB", W.OP_REDUCE, W.DT_INT64, 0, 8192),
+                 ("reduce_fp32_4KiB", W.OP_REDUCE, W.DT_FLOAT, 0, 1024), ("broadcast_4KiB", W.OP_BCAST, 0, 3, 4096),
+                 ("fcollect_4KiB", W.OP_FCOLLECT, 0, 0, 4096), ("alltoall_512B", W.OP_ALLTOALL, 0, 0, 512)]
+        coll = {}
+        for name, kind, dt, root, n in cases:
+            row = {}
+            res = {}
+            for mode, team in (("global", 0), ("dsmem", 1)):
+                ops = np.zeros(rounds, W.OP_DTYPE)
+                for k in range(rounds):
+                    ops[k] = (kind, dt, W.RED_SUM, team, root, -1, dst, 4096 if kind != W.OP_REDUCE else 0, n, 0, 0, 0)
+                dev = torch.from_numpy(ops.view(np.uint8).copy()).cuda()
+                parts[:, dst:].zero_()
+                times = []
+                for _ in range(reps + 1):
+                    e0, e1 = _events(torch)
+                    e0.record(stream)
+                    sg.run_script(dev, rounds, None, stream)
+                    e1.record(stream)
+                    torch.cuda.synchronize()
+                    times.append(e0.elapsed_time(e1))
+                res[mode] = parts[:, dst:dst + 65536].clone()
+                row[mode + "_us_per_op"] = round(float(np.median(times[1:])) * 1e3 / rounds, 3)
+            row["speedup"] = round(row["global_us_per_op"] / row["dsmem_us_per_op"], 2)
+            row["results_equal"] = bool(torch.equal(res["global"], res["dsmem"]))
+            coll[name] = row
+        out["one_cluster_8_pes"] = coll
+        out["status"] = sg.get_status()[0]
+    finally:
+        heap.close()
+    return out
+
+
 # ----------------------------------------------------------------------------- AMO / signal stress
 def _events(torch):
     return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
 
 
-def run_amo(torch, sg, nops_log2=26, reps=3):
+def _amo_ops(pool, seed, nops, bits, dist, ch=1 << 24):
+    """W.amo_stream_np over [0, nops) in chunks of `ch` ops on a process pool (the
+    stream does not depend on the chunking)."""
+    out = np.empty(nops, np.uint32)
+    futs = {pool.submit(W.amo_stream_np, seed, min(ch, nops - c), bits, dist=dist, offset=c): c
+            for c in range(0, nops, ch)}
+    for f in futs:
+        c = futs[f]
+        out[c:c + ch] = f.result()
+    return out
+
+
+def run_amo(torch, sg, nops_log2=30, reps=3):
     """1024 PEs (one CTA each) over a 2^27-word int64 table; uniform and Zipf(1.1)
     streams of 2^nops_log2 fetch_add/compare_swap/fetch_xor; GUPS with and without warp
     aggregation, against an L2-resident table and the HBM-sector ceiling; then 512
@@ -510,14 +604,20 @@ def run_amo(torch, sg, nops_log2=26, reps=3):
             parts[p0:p0 + 128, :wpp * 8].view(torch.int64).copy_(W.cb64_torch(tseed, idx).view(128, wpp))
         nops = 1 << nops_log2
         s = torch.cuda.current_stream()
+        # the op streams are drawn on the host by a spawned process pool (no CUDA state in
+        # the workers), chunk by chunk
+        import concurrent.futures as cf
+        import multiprocessing as mp
+
+        workers = max(1, min(16, os.cpu_count() or 1))
+        pool = cf.ProcessPoolExecutor(workers, mp_context=mp.get_context("spawn"))
+        out["generator_processes"] = workers
         for dist in ("uniform", "zipf"):
             t0 = time.perf_counter()
-            ops = np.empty(nops, np.uint32)
-            ch = 1 << 24
-            for c in range(0, nops, ch):
-                ops[c:c + ch] = W.amo_stream_np(W.derive_seed("amo-" + dist), min(ch, nops - c), 27, dist=dist, offset=c)
+            ops = _amo_ops(pool, W.derive_seed("amo-" + dist), nops, 27, dist)
             gen_s = time.perf_counter() - t0
             dops = torch.from_numpy(ops.view(np.int32)).cuda()
+            del ops
             fetched = torch.empty(nops, dtype=torch.int64, device="cuda")
             for agg in (0, 1):
                 sg.amo_stream(heap.base, wpp, dops, nops, oseed, tseed, fetched, flags=agg)
@@ -532,10 +632,11 @@ def run_amo(torch, sg, nops_log2=26, reps=3):
                                                               "ms": round(ms, 3)}
             out[f"{dist}_generation_s"] = round(gen_s, 2)
             del dops, fetched
-        # L2-resident reference: the same kernel on a table of 2^21 words (16 MiB)
+        # L2-resident reference: the same kernel on a table of 2^21 words (16 MiB), 2^26 ops
         small_wpp = (1 << 21) // npes
-        ops = W.amo_stream_np(5, nops, 21, dist="uniform")
-        dops = torch.from_numpy(ops.view(np.int32)).cuda()
+        nops = 1 << min(nops_log2, 26)
+        dops = torch.from_numpy(_amo_ops(pool, 5, nops, 21, "uniform").view(np.int32)).cuda()
+        pool.shutdown()
         sg.amo_stream(heap.base, small_wpp, dops, nops, oseed, tseed, None, flags=0)
         e0, e1 = _events(torch)
         e0.record(s)
@@ -953,9 +1054,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="shmemg", choices=["shmemg", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--secondary", default="script,amo,batch,serve",
-                    help="extra workloads measured after the sweep (comma list of script,amo,batch,serve or 'none')")
-    ap.add_argument("--amo-ops-log2", type=int, default=26)
+    ap.add_argument("--secondary", default="script,amo,cluster,batch,serve",
+                    help="extra workloads measured after the sweep (comma list of script,amo,cluster,batch,serve "
+                         "or 'none')")
+    ap.add_argument("--amo-ops-log2", type=int, default=30)
     ap.add_argument("--serve-requests", type=int, default=4096)
     ap.add_argument("--profile", choices=PROFILE_CASES, help="run one small single-kernel case (for ncu) and exit")
     args = ap.parse_args()
@@ -984,6 +1086,8 @@ def main():
                     r = run_script_leg(torch, sg)
                 elif name == "amo":
                     r = run_amo(torch, sg, args.amo_ops_log2)
+                elif name == "cluster":
+                    r = run_cluster_leg(torch, sg)
                 elif name == "batch":
                     r = run_batch(torch, sg)
                 elif name == "serve":

@@ -501,12 +501,13 @@ static __device__ __forceinline__ int shmemg_d_team_barrier_leader(const shmemg_
  * A kernel using this path keeps one shmemg_cluster_state_t in shared memory and calls
  * shmemg_d_cluster_begin first and shmemg_d_cluster_end last, with every thread of
  * every CTA: a CTA may touch a peer's shared memory only after the peer has started and
- * before it exits, and both calls are hardware cluster barriers.  Every wait in between
- * is bounded, so every CTA reaches the final barrier. */
+ * before it exits, and both calls are hardware cluster barriers.  The shared team's
+ * barrier is the hardware cluster barrier too, which has no timeout: such a kernel
+ * keeps every CTA of a cluster on the same sequence of cluster barriers, also after an
+ * error (a CTA that has failed still passes the barriers of the operations it skips),
+ * and every other wait in it is bounded, so every CTA reaches every barrier. */
 typedef struct {
-    uint32_t flag[8];  /* flag[j]: last barrier generation cluster rank j has reached */
-    uint32_t gen;      /* cluster barriers this CTA has entered (thread 0) */
-    int rc;            /* last barrier result, for the CTA's other threads */
+    int rc;  /* reserved: the state is what marks a kernel as running the cluster path */
 } shmemg_cluster_state_t;
 
 /* Every DSMEM access below names its state space: a peer's copy of a shared-memory
@@ -517,19 +518,11 @@ static __device__ __forceinline__ uint32_t shmemg_d_cluster_addr(const void *loc
     asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(shmemg_smem_u32(local)), "r"(rank));
     return r;
 }
-static __device__ __forceinline__ void shmemg_d_st_release_cluster_u32(uint32_t dsm, uint32_t v) {
-    asm volatile("st.release.cluster.shared::cluster.u32 [%0], %1;" ::"r"(dsm), "r"(v) : "memory");
-}
 static __device__ __forceinline__ void shmemg_d_st_release_cluster_u64(uint32_t dsm, uint64_t v) {
     asm volatile("st.release.cluster.shared::cluster.u64 [%0], %1;" ::"r"(dsm), "l"(v) : "memory");
 }
 static __device__ __forceinline__ void shmemg_d_red_release_cluster_add_u64(uint32_t dsm, uint64_t v) {
     asm volatile("red.release.cluster.shared::cluster.add.u64 [%0], %1;" ::"r"(dsm), "l"(v) : "memory");
-}
-static __device__ __forceinline__ uint32_t shmemg_d_ld_acquire_cluster_u32(const uint32_t *own) {
-    uint32_t v;
-    asm volatile("ld.acquire.cluster.shared::cta.u32 %0, [%1];" : "=r"(v) : "r"(shmemg_smem_u32(own)) : "memory");
-    return v;
 }
 static __device__ __forceinline__ uint64_t shmemg_d_ld_acquire_cluster_u64(const uint64_t *own) {
     uint64_t v;
@@ -610,8 +603,7 @@ static __device__ __forceinline__ void shmemg_d_st_cluster(uint32_t a, V v) {
 }
 
 static __device__ __forceinline__ void shmemg_d_cluster_begin(shmemg_cluster_state_t &cs) {
-    if (threadIdx.x < 8) cs.flag[threadIdx.x] = 0;
-    if (threadIdx.x == 0) cs.gen = 0;
+    if (threadIdx.x == 0) cs.rc = 0;
     shmemg_d_cluster_sync();
 }
 static __device__ __forceinline__ void shmemg_d_cluster_end() { shmemg_d_cluster_sync(); }
@@ -624,47 +616,28 @@ static __device__ __forceinline__ bool shmemg_d_team_is_cluster(const shmemg_dev
     return cs && team == SHMEMG_TEAM_SHARED && c.pe_mode == SHMEMG_PE_MODE_CTA && c.cluster_dim > 1;
 }
 
-/* Barrier of the cluster's CTAs, entered by thread 0 of each: it stores its new
- * generation into every member's flag[own rank] (release, cluster scope) and polls its
- * own flags (acquire) until every member has reached the generation: no atomics, and
- * each CTA spins only on its own shared memory.  Bounded like every wait here. */
-static __device__ __forceinline__ int shmemg_d_cluster_barrier_leader(const shmemg_device_ctx_t &c,
-                                                                      shmemg_cluster_state_t &cs, int64_t detail) {
-    const uint32_t n = shmemg_d_cluster_nctarank(), me = shmemg_d_cluster_ctarank();
-    const uint32_t gen = ++cs.gen;
-    for (uint32_t j = 0; j < n; j++) shmemg_d_st_release_cluster_u32(shmemg_d_cluster_addr(&cs.flag[me], j), gen);
-    uint64_t t0 = 0;
-    for (uint32_t j = 0; j < n; j++) {
-        for (uint32_t it = 0; (int32_t)(shmemg_d_ld_acquire_cluster_u32(&cs.flag[j]) - gen) < 0; it++) {
-            if ((it & 255) == 255) {
-                const uint64_t now = shmemg_d_globaltimer();
-                if (t0 == 0) t0 = now;
-                else if (now - t0 > c.timeout_ns) {
-                    shmemg_d_set_status(c, SHMEMG_ERR_TIMEOUT, detail);
-                    return SHMEMG_ERR_TIMEOUT;
-                }
-                if (shmemg_d_get_status(c) != 0) return SHMEMG_ERR_DEVICE;
-            }
-        }
-    }
-    return SHMEMG_SUCCESS;
-}
-/* Cluster barrier at CTA scope (every thread calls); `quiet` first makes the CTA's
- * earlier writes visible GPU-wide, as a team barrier does. */
-static __device__ __noinline__ int shmemg_d_cluster_sync_pe(const shmemg_device_ctx_t &c,
+/* Barrier of the cluster's CTAs at CTA scope (every thread of every CTA calls it): the
+ * hardware cluster barrier, release/acquire at cluster scope, so that each member sees
+ * every write the others made before it.  `quiet` first makes the CTA's earlier writes
+ * visible GPU-wide, as a team barrier does.  It cannot fail; the int result keeps the
+ * interface of the team barriers. */
+static __device__ __forceinline__ int shmemg_d_cluster_sync_pe(const shmemg_device_ctx_t &c,
                                                                shmemg_cluster_state_t &cs, bool quiet, int64_t detail) {
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        if (quiet) shmemg_d_fence_gpu();
-        cs.rc = shmemg_d_cluster_barrier_leader(c, cs, detail);
+    (void)c;
+    (void)cs;
+    (void)detail;
+    if (quiet) {
+        __syncthreads();
+        if (threadIdx.x == 0) shmemg_d_fence_gpu();
+        __syncwarp();
     }
-    __syncthreads();
-    return cs.rc;
+    shmemg_d_cluster_sync();
+    return SHMEMG_SUCCESS;
 }
 
 /* Team barrier at PE scope (all threads of the calling PE call it): quiet, then the
  * leader runs the team barrier; the result is broadcast to the PE's threads.  With a
- * cluster state and the cluster's own team, the barrier goes through DSMEM. */
+ * cluster state and the cluster's own team, it is the hardware cluster barrier. */
 static __device__ __forceinline__ int shmemg_d_team_sync_pe(const shmemg_device_ctx_t &c, int team, int64_t detail,
                                                             shmemg_cluster_state_t *cs = nullptr) {
     if (shmemg_d_team_is_cluster(c, cs, team)) return shmemg_d_cluster_sync_pe(c, *cs, true, detail);
@@ -679,12 +652,13 @@ static __device__ __forceinline__ int shmemg_d_team_sync_pe(const shmemg_device_
         shmemg_sync_rc = rc;
     }
     shmemg_d_pe_sync(c);
-    int rc = shmemg_sync_rc;
-    if (c.pe_mode == SHMEMG_PE_MODE_CLUSTER) {
-        /* the leader CTA's result reaches the other CTAs through the status word */
-        if (rc == SHMEMG_SUCCESS && shmemg_d_get_status(c) != 0) rc = SHMEMG_ERR_DEVICE;
-    }
-    return rc;
+    /* in pe_mode CLUSTER every CTA takes the leader CTA's result, read through DSMEM, so
+     * the CTAs of a PE decide as one (their hardware PE barriers stay in step); the
+     * leader writes the slot again only after the next PE barrier, which every CTA
+     * reaches after this read */
+    if (c.pe_mode == SHMEMG_PE_MODE_CLUSTER && c.cluster_dim > 1)
+        return shmemg_d_ld_cluster<int>(shmemg_d_cluster_addr(&shmemg_sync_rc, 0));
+    return shmemg_sync_rc;
 }
 static __device__ __forceinline__ int shmemg_d_barrier_all_pe(const shmemg_device_ctx_t &c, int64_t detail) {
     return shmemg_d_team_sync_pe(c, SHMEMG_TEAM_WORLD, detail);
@@ -1046,42 +1020,98 @@ static __device__ __forceinline__ V shmemg_tree_sum8(const Ld &ld, int P) {
     return acc;
 }
 
-/* dst[v] = combination over the P members' windows of vector v (team-rank order) */
+/* Slice-owner combination from the windows: this member owns vectors [v0, v1); each is
+ * read from the P members' windows through DSMEM (team-rank order; the fixed tree for
+ * float sums), combined, and stored to the P members' destinations. */
 template <typename T, typename V, int OP>
-static __device__ __forceinline__ void shmemg_d_cluster_reduce_vecs(const uint8_t *win, int P, V *dst, uint64_t nvec) {
+static __device__ __forceinline__ void shmemg_d_cluster_reduce_vecs(const uint8_t *win, int P, uint8_t *heap,
+                                                                   uint64_t H, int pe0, uint64_t dst_off, uint64_t v0,
+                                                                   uint64_t v1) {
     constexpr int NL = sizeof(V) / sizeof(T);
-    for (uint64_t vi = threadIdx.x; vi < nvec; vi += blockDim.x) {
-        auto ld = [&](int r) { return shmemg_d_ld_cluster<V>(shmemg_d_cluster_addr(win, (uint32_t)r) + (uint32_t)(vi * sizeof(V))); };
+    const uint32_t w0 = shmemg_d_cluster_addr(win, 0);
+    const uint32_t wstride = shmemg_d_cluster_addr(win, 1) - w0;  /* windows of consecutive ranks */
+    for (uint64_t vi = v0 + threadIdx.x; vi < v1; vi += blockDim.x) {
+        auto ld = [&](int r) { return shmemg_d_ld_cluster<V>(w0 + (uint32_t)r * wstride + (uint32_t)(vi * sizeof(V))); };
         V acc;
         if constexpr (OP == SHMEMG_SUM && std::is_floating_point<T>::value) {
             acc = shmemg_tree_sum8<V>(ld, P);
         } else {
-            acc = ld(0);
-            for (int r = 1; r < P; r++) {
-                V x = ld(r);
+            auto comb = [&](const V &x) {
 #pragma unroll
                 for (int l = 0; l < NL; l++) {
                     T &s = reinterpret_cast<T *>(&acc)[l];
-                    s = shmemg_comb<T>(s, reinterpret_cast<T *>(&x)[l], OP);
+                    s = shmemg_comb<T>(s, reinterpret_cast<const T *>(&x)[l], OP);
                 }
+            };
+            acc = ld(0);
+            int r = 1;
+            for (; r + 3 < P; r += 4) {  /* four members' loads in flight */
+                const V a = ld(r), b = ld(r + 1), d = ld(r + 2), e = ld(r + 3);
+                comb(a);
+                comb(b);
+                comb(d);
+                comb(e);
             }
+            for (; r < P; r++) comb(ld(r));
         }
-        dst[vi] = acc;
+        for (int r = 0; r < P; r++) *(V *)(heap + (uint64_t)(pe0 + r) * H + dst_off + vi * sizeof(V)) = acc;
     }
 }
 template <typename T, typename V16>
-static __device__ __forceinline__ void shmemg_d_cluster_reduce_t(const uint8_t *win, int P, uint8_t *dst,
-                                                                uint64_t nelems, int op) {
-    const bool v16 = (((uint64_t)dst | (nelems * sizeof(T))) & 15) == 0;
+static __device__ __forceinline__ void shmemg_d_cluster_reduce_t(const uint8_t *win, int P, int r, uint8_t *heap,
+                                                                uint64_t H, int pe0, uint64_t dst_off, uint64_t nelems,
+                                                                int op) {
+    const bool v16 = ((dst_off | (nelems * sizeof(T)) | H) & 15) == 0;
+    const uint64_t nv = v16 ? nelems * sizeof(T) / 16 : nelems;
+    uint64_t lo, hi;
+    shmemg_d_slice(nv, r, P, 1, &lo, &hi);
     if (v16) {
-        const uint64_t nv = nelems * sizeof(T) / 16;
-        if (op == SHMEMG_SUM) shmemg_d_cluster_reduce_vecs<T, V16, SHMEMG_SUM>(win, P, (V16 *)dst, nv);
-        else if (op == SHMEMG_MAX) shmemg_d_cluster_reduce_vecs<T, V16, SHMEMG_MAX>(win, P, (V16 *)dst, nv);
-        else shmemg_d_cluster_reduce_vecs<T, V16, SHMEMG_MIN>(win, P, (V16 *)dst, nv);
+        if (op == SHMEMG_SUM) shmemg_d_cluster_reduce_vecs<T, V16, SHMEMG_SUM>(win, P, heap, H, pe0, dst_off, lo, hi);
+        else if (op == SHMEMG_MAX) shmemg_d_cluster_reduce_vecs<T, V16, SHMEMG_MAX>(win, P, heap, H, pe0, dst_off, lo, hi);
+        else shmemg_d_cluster_reduce_vecs<T, V16, SHMEMG_MIN>(win, P, heap, H, pe0, dst_off, lo, hi);
     } else {
-        if (op == SHMEMG_SUM) shmemg_d_cluster_reduce_vecs<T, T, SHMEMG_SUM>(win, P, (T *)dst, nelems);
-        else if (op == SHMEMG_MAX) shmemg_d_cluster_reduce_vecs<T, T, SHMEMG_MAX>(win, P, (T *)dst, nelems);
-        else shmemg_d_cluster_reduce_vecs<T, T, SHMEMG_MIN>(win, P, (T *)dst, nelems);
+        if (op == SHMEMG_SUM) shmemg_d_cluster_reduce_vecs<T, T, SHMEMG_SUM>(win, P, heap, H, pe0, dst_off, lo, hi);
+        else if (op == SHMEMG_MAX) shmemg_d_cluster_reduce_vecs<T, T, SHMEMG_MAX>(win, P, heap, H, pe0, dst_off, lo, hi);
+        else shmemg_d_cluster_reduce_vecs<T, T, SHMEMG_MIN>(win, P, heap, H, pe0, dst_off, lo, hi);
+    }
+}
+
+/* Gather of nj blocks of nv vectors: block b (rank j0 + b) of the members' windows at
+ * byte offset woff -> dst + b * blk.  Four blocks' loads are in flight per thread. */
+template <typename V>
+static __device__ __forceinline__ void shmemg_d_cluster_gather_vec(uint8_t *dst, uint64_t blk, const uint8_t *win,
+                                                                  uint64_t woff, int j0, int nj, uint64_t nv) {
+    const uint32_t w0 = shmemg_d_cluster_addr(win, 0);
+    const uint32_t wstride = shmemg_d_cluster_addr(win, 1) - w0;
+    const uint64_t total = nv * (uint64_t)nj, step = blockDim.x;
+    auto src = [&](uint64_t k, uint64_t *b, uint64_t *i) {
+        *b = k / nv;
+        *i = k - *b * nv;
+        return w0 + (uint32_t)(j0 + *b) * wstride + (uint32_t)(woff + *i * sizeof(V));
+    };
+    uint64_t k = threadIdx.x;
+    for (; k + 3 * step < total; k += 4 * step) {
+        uint64_t b[4], i[4];
+        V x[4];
+#pragma unroll
+        for (int u = 0; u < 4; u++) x[u] = shmemg_d_ld_cluster<V>(src(k + u * step, &b[u], &i[u]));
+#pragma unroll
+        for (int u = 0; u < 4; u++) *(V *)(dst + b[u] * blk + i[u] * sizeof(V)) = x[u];
+    }
+    for (; k < total; k += step) {
+        uint64_t b, i;
+        const V x = shmemg_d_ld_cluster<V>(src(k, &b, &i));
+        *(V *)(dst + b * blk + i * sizeof(V)) = x;
+    }
+}
+static __device__ __forceinline__ void shmemg_d_cluster_gather(uint8_t *dst, uint64_t n, const uint8_t *win,
+                                                              uint64_t woff, int j0, int nj) {
+    switch (shmemg_d_vec_width(dst, win + woff, n)) {
+    case 16: shmemg_d_cluster_gather_vec<uint4>(dst, n, win, woff, j0, nj, n / 16); break;
+    case 8: shmemg_d_cluster_gather_vec<uint2>(dst, n, win, woff, j0, nj, n / 8); break;
+    case 4: shmemg_d_cluster_gather_vec<uint32_t>(dst, n, win, woff, j0, nj, n / 4); break;
+    case 2: shmemg_d_cluster_gather_vec<uint16_t>(dst, n, win, woff, j0, nj, n / 2); break;
+    default: shmemg_d_cluster_gather_vec<uint8_t>(dst, n, win, woff, j0, nj, n); break;
     }
 }
 
@@ -1096,62 +1126,58 @@ static __device__ __forceinline__ uint64_t shmemg_d_cluster_stage_bytes(int kind
 }
 
 static __device__ __noinline__ int shmemg_d_cluster_reduce_pe(const shmemg_device_ctx_t &c, shmemg_cluster_state_t &cs,
-                                                                 uint8_t *win, uint64_t dst_off, uint64_t src_off,
-                                                                 uint64_t nelems, int dtype, int op, int64_t detail) {
-    const int me = shmemg_d_my_pe(c), P = (int)shmemg_d_cluster_nctarank();
+                                                              uint8_t *win, uint64_t dst_off, uint64_t src_off,
+                                                              uint64_t nelems, int dtype, int op, int64_t detail) {
+    const int me = shmemg_d_my_pe(c), P = (int)shmemg_d_cluster_nctarank(), r = (int)shmemg_d_cluster_ctarank();
     int rc = shmemg_d_cluster_sync_pe(c, cs, true, detail);
     if (rc) return rc;
     shmemg_d_copy_group(shmemg_d_group_block(), win, shmemg_d_addr(c, me, src_off),
                         shmemg_d_cluster_stage_bytes(SHMEMG_OP_REDUCE, nelems, dtype, P));
     if ((rc = shmemg_d_cluster_sync_pe(c, cs, false, detail))) return rc;
-    uint8_t *dst = shmemg_d_addr(c, me, dst_off);
-    if (dtype == SHMEMG_INT32) shmemg_d_cluster_reduce_t<int32_t, int4>(win, P, dst, nelems, op);
-    else if (dtype == SHMEMG_INT64) shmemg_d_cluster_reduce_t<int64_t, longlong2>(win, P, dst, nelems, op);
-    else shmemg_d_cluster_reduce_t<float, float4>(win, P, dst, nelems, op);
+    const int pe0 = me - r;
+    if (dtype == SHMEMG_INT32) shmemg_d_cluster_reduce_t<int32_t, int4>(win, P, r, c.heap, c.pe_stride, pe0, dst_off, nelems, op);
+    else if (dtype == SHMEMG_INT64) shmemg_d_cluster_reduce_t<int64_t, longlong2>(win, P, r, c.heap, c.pe_stride, pe0, dst_off, nelems, op);
+    else shmemg_d_cluster_reduce_t<float, float4>(win, P, r, c.heap, c.pe_stride, pe0, dst_off, nelems, op);
     return shmemg_d_cluster_sync_pe(c, cs, false, detail);
 }
 /* root (team rank) stages n bytes; every member copies the root's window */
 static __device__ __noinline__ int shmemg_d_cluster_broadcastmem_pe(const shmemg_device_ctx_t &c,
-                                                                       shmemg_cluster_state_t &cs, uint8_t *win,
-                                                                       uint64_t dst_off, uint64_t src_off, uint64_t n,
-                                                                       int root, int64_t detail) {
+                                                                    shmemg_cluster_state_t &cs, uint8_t *win,
+                                                                    uint64_t dst_off, uint64_t src_off, uint64_t n,
+                                                                    int root, int64_t detail) {
     const int me = shmemg_d_my_pe(c);
     int rc = shmemg_d_cluster_sync_pe(c, cs, true, detail);
     if (rc) return rc;
     if ((int)shmemg_d_cluster_ctarank() == root)
         shmemg_d_copy_group(shmemg_d_group_block(), win, shmemg_d_addr(c, me, src_off), n);
     if ((rc = shmemg_d_cluster_sync_pe(c, cs, false, detail))) return rc;
-    shmemg_d_copy_from_cluster(shmemg_d_group_block(), shmemg_d_addr(c, me, dst_off), win, (uint32_t)root, n);
+    shmemg_d_cluster_gather(shmemg_d_addr(c, me, dst_off), n, win, 0, root, 1);
     return shmemg_d_cluster_sync_pe(c, cs, false, detail);
 }
 /* each member stages its n bytes; member r's dst block j = member j's window */
 static __device__ __noinline__ int shmemg_d_cluster_fcollectmem_pe(const shmemg_device_ctx_t &c,
-                                                                      shmemg_cluster_state_t &cs, uint8_t *win,
-                                                                      uint64_t dst_off, uint64_t src_off, uint64_t n,
-                                                                      int64_t detail) {
+                                                                   shmemg_cluster_state_t &cs, uint8_t *win,
+                                                                   uint64_t dst_off, uint64_t src_off, uint64_t n,
+                                                                   int64_t detail) {
     const int me = shmemg_d_my_pe(c), P = (int)shmemg_d_cluster_nctarank();
     int rc = shmemg_d_cluster_sync_pe(c, cs, true, detail);
     if (rc) return rc;
     shmemg_d_copy_group(shmemg_d_group_block(), win, shmemg_d_addr(c, me, src_off), n);
     if ((rc = shmemg_d_cluster_sync_pe(c, cs, false, detail))) return rc;
-    for (int j = 0; j < P; j++)
-        shmemg_d_copy_from_cluster(shmemg_d_group_block(), shmemg_d_addr(c, me, dst_off + (uint64_t)j * n), win,
-                                   (uint32_t)j, n);
+    shmemg_d_cluster_gather(shmemg_d_addr(c, me, dst_off), n, win, 0, 0, P);
     return shmemg_d_cluster_sync_pe(c, cs, false, detail);
 }
 /* each member stages its P blocks; member r's dst block j = block r of member j's window */
 static __device__ __noinline__ int shmemg_d_cluster_alltoallmem_pe(const shmemg_device_ctx_t &c,
-                                                                      shmemg_cluster_state_t &cs, uint8_t *win,
-                                                                      uint64_t dst_off, uint64_t src_off, uint64_t n,
-                                                                      int64_t detail) {
+                                                                   shmemg_cluster_state_t &cs, uint8_t *win,
+                                                                   uint64_t dst_off, uint64_t src_off, uint64_t n,
+                                                                   int64_t detail) {
     const int me = shmemg_d_my_pe(c), P = (int)shmemg_d_cluster_nctarank(), r = (int)shmemg_d_cluster_ctarank();
     int rc = shmemg_d_cluster_sync_pe(c, cs, true, detail);
     if (rc) return rc;
     shmemg_d_copy_group(shmemg_d_group_block(), win, shmemg_d_addr(c, me, src_off), n * (uint64_t)P);
     if ((rc = shmemg_d_cluster_sync_pe(c, cs, false, detail))) return rc;
-    for (int j = 0; j < P; j++)
-        shmemg_d_copy_from_cluster(shmemg_d_group_block(), shmemg_d_addr(c, me, dst_off + (uint64_t)j * n),
-                                   win + (uint64_t)r * n, (uint32_t)j, n);
+    shmemg_d_cluster_gather(shmemg_d_addr(c, me, dst_off), n, win, (uint64_t)r * n, 0, P);
     return shmemg_d_cluster_sync_pe(c, cs, false, detail);
 }
 

@@ -80,15 +80,17 @@ __global__ void __launch_bounds__(INTERP_THREADS) k_interp(shmemg_device_ctx_t c
     const int me = shmemg_d_my_pe(c);
     const shmemg_group g = shmemg_d_group_pe(c);
     const bool leader = shmemg_d_pe_leader(c);
-    __shared__ int s_rc;
+    __shared__ int s_wrc[2];
+    int n_waits = 0;
     extern __shared__ __align__(128) uint8_t s_ring[];
     __shared__ __align__(8) uint64_t s_bars[SHMEMG_BULK_STAGES];
     // the op list is staged through shared memory OP_BATCH records at a time (one
     // coalesced copy per batch instead of a dependent global load per op and thread)
     __shared__ __align__(16) shmemg_op_t s_ops[OP_BATCH];
-    // shared-team ops of a CTA-mode heap launched in clusters go through DSMEM: the team
-    // barrier on shared-memory flags, small collectives staged in the bulk ring, which
-    // then serves as each CTA's window (free between ops: every bulk copy has drained)
+    // shared-team ops of a CTA-mode heap launched in clusters run inside the cluster: the
+    // team barrier is the hardware cluster barrier, small collectives are staged in the
+    // bulk ring, which then serves as each CTA's DSMEM window (free between ops: every
+    // bulk copy has drained)
     __shared__ shmemg_cluster_state_t s_cs;
     const bool dsm = c.pe_mode == SHMEMG_PE_MODE_CTA && c.cluster_dim > 1;
     shmemg_cluster_state_t *cs = dsm ? &s_cs : nullptr;
@@ -99,8 +101,20 @@ __global__ void __launch_bounds__(INTERP_THREADS) k_interp(shmemg_device_ctx_t c
         const uint64_t b = shmemg_d_cluster_stage_bytes(o.kind, o.n, o.dtype, c.cluster_dim);
         return b > 0 && b <= win_bytes;
     };
+    // Hardware cluster barriers an op runs on the shared team (a fixed count per op
+    // record): a CTA that has failed still passes them for every op it skips, so the
+    // CTAs of a cluster always meet at the same barriers (they have no timeout).
+    auto cluster_barriers = [&](const shmemg_op_t &o) {
+        if (!dsm || o.team != SHMEMG_TEAM_SHARED) return 0;
+        switch (o.kind) {
+        case SHMEMG_OP_TEAM_SYNC: return 1;
+        case SHMEMG_OP_BROADCAST: case SHMEMG_OP_FCOLLECT: case SHMEMG_OP_ALLTOALL: case SHMEMG_OP_REDUCE:
+            return staged(o) ? 3 : 2;
+        default: return 0;
+        }
+    };
     bool failed = false;
-    for (int64_t base = 0; base < nops && !failed; base += OP_BATCH) {
+    for (int64_t base = 0; base < nops && (!failed || dsm); base += OP_BATCH) {
     const int cnt = (int)(nops - base < OP_BATCH ? nops - base : OP_BATCH);
     __syncthreads();
     for (int q = threadIdx.x; q < cnt * 4; q += blockDim.x)
@@ -110,9 +124,14 @@ __global__ void __launch_bounds__(INTERP_THREADS) k_interp(shmemg_device_ctx_t c
         const int64_t i = base + k;
         const shmemg_op_t o = s_ops[k];
         int rc = SHMEMG_SUCCESS;
+        if (failed) {  // only in a clustered CTA-mode launch: walk on, through the barriers
+            for (int b = cluster_barriers(o); b > 0; b--) shmemg_d_cluster_sync();
+            continue;
+        }
         if (!op_valid(c, o)) {  // an invalid op ends the script there, recorded with its index
             if (leader) shmemg_d_set_status(c, SHMEMG_ERR_INVALID_ARG, i);
             failed = true;
+            if (dsm) continue;
             break;
         }
         switch (o.kind) {
@@ -165,15 +184,20 @@ __global__ void __launch_bounds__(INTERP_THREADS) k_interp(shmemg_device_ctx_t c
             break;
         case SHMEMG_OP_WAIT_UNTIL:
             if (o.issuer == me) {
+                // the leader's result decides for the whole PE (in pe_mode CLUSTER the other
+                // CTAs read it through DSMEM); two slots, so the leader rewrites one only
+                // after the PE barrier of the next wait, which every CTA passes after reading
+                const int slot = n_waits++ & 1;
                 if (threadIdx.x == 0) {
                     int w = SHMEMG_SUCCESS;
                     if (leader) w = shmemg_d_signal_wait_until(c, (const uint64_t *)shmemg_d_addr(c, me, o.dst), o.sub,
                                                                (uint64_t)o.operand, i);
-                    s_rc = w;
+                    s_wrc[slot] = w;
                 }
                 shmemg_d_pe_sync(c);
-                rc = s_rc;
-                if (c.pe_mode == SHMEMG_PE_MODE_CLUSTER && shmemg_d_get_status(c) != 0) rc = SHMEMG_ERR_DEVICE;
+                rc = c.pe_mode == SHMEMG_PE_MODE_CLUSTER && c.cluster_dim > 1
+                         ? shmemg_d_ld_cluster<int>(shmemg_d_cluster_addr(&s_wrc[slot], 0))
+                         : s_wrc[slot];
             }
             break;
         case SHMEMG_OP_QUIET:
@@ -211,7 +235,7 @@ __global__ void __launch_bounds__(INTERP_THREADS) k_interp(shmemg_device_ctx_t c
         }
         if (rc != SHMEMG_SUCCESS) {
             failed = true;  // uniform across the PE: every thread leaves both loops
-            break;
+            if (!dsm) break;
         }
     }
     }

@@ -177,8 +177,9 @@ def test_pingpong_cluster_needs_cluster_heap(sg, heapf):
 
 
 def test_cluster_barrier_timeout_is_bounded(sg, heapf):
-    """PE 1 waits on a signal nobody raises and times out; PE 0, waiting for it in the
-    DSMEM team barrier, sees the recorded error and leaves; the context survives."""
+    """PE 1 waits on a signal nobody raises and times out; having failed, it still
+    passes the shared-team (cluster) barrier of the next op, where PE 0 waits for it, so
+    the launch ends; the status names the timeout and the context survives."""
     npes, H = 2, 4096
     h = heapf(npes, H, pe_mode=sg.PE_MODE_CTA, cluster_dim=2, timeout_ns=3_000_000)
     h.partitions().zero_()
@@ -194,3 +195,31 @@ def test_cluster_barrier_timeout_is_bounded(sg, heapf):
     sg.clear_status()
     x = torch.ones(4, device="cuda")
     assert float(x.sum()) == 4.0
+
+
+def test_cluster_failed_pe_keeps_barrier_sequence(sg, heapf):
+    """After PE 1 fails (a timed-out wait), the ops that follow -- shared-team syncs,
+    staged and unstaged shared-team collectives, a world barrier -- still end: the failed
+    PE walks the rest of the script through each op's cluster barriers, the others learn
+    of the failure at the world barrier, and the launch returns with the timeout
+    recorded."""
+    npes, H, cd = 8, 1 << 20, 4
+    h = heapf(npes, H, pe_mode=sg.PE_MODE_CTA, cluster_dim=cd, timeout_ns=3_000_000)
+    h.partitions().zero_()
+    ops = [_rec(kind=W.OP_WAIT_UNTIL, sub=W.CMP_EQ, issuer=1, dst=0, operand=12345),
+           _rec(kind=W.OP_TEAM_SYNC, team=SHARED),
+           _rec(kind=W.OP_REDUCE, dtype=W.DT_INT64, sub=W.RED_SUM, team=SHARED, dst=65536, src=4096, n=1000),
+           _rec(kind=W.OP_REDUCE, dtype=W.DT_INT32, sub=W.RED_MAX, team=SHARED, dst=131072, src=4096, n=60000),
+           _rec(kind=W.OP_BCAST, team=SHARED, pe=2, dst=524288, src=4096, n=3000),
+           _rec(kind=W.OP_BARRIER_ALL),
+           _rec(kind=W.OP_ALLTOALL, team=SHARED, dst=600000, src=4096, n=64),
+           _rec(kind=W.OP_TEAM_SYNC, team=SHARED)]
+    ops = np.array(ops, dtype=W.OP_DTYPE)
+    sg.clear_status()
+    dev = torch.from_numpy(ops.view(np.uint8).copy()).cuda()
+    sg.run_script(dev, len(ops), None)
+    torch.cuda.synchronize()
+    code, detail = sg.get_status()
+    assert code == sg.ERR_TIMEOUT and detail == 0
+    sg.clear_status()
+    assert float(torch.ones(4, device="cuda").sum()) == 4.0

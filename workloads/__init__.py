@@ -52,10 +52,18 @@ def cb64(seed: int, i: int) -> int:
 def cb64_np(seed: int, idx: np.ndarray) -> np.ndarray:
     """Vectorised ``cb64`` over a numpy integer array; returns uint64."""
     with np.errstate(over="ignore"):
-        z = (np.asarray(idx).astype(np.uint64) ^ np.uint64(seed & MASK64)) + np.uint64(GAMMA)
-        z = (z ^ (z >> np.uint64(30))) * np.uint64(_M1)
-        z = (z ^ (z >> np.uint64(27))) * np.uint64(_M2)
-        return z ^ (z >> np.uint64(31))
+        z = np.array(idx, dtype=np.uint64, copy=True)   # in place from here: one temporary
+        z ^= np.uint64(seed & MASK64)
+        z += np.uint64(GAMMA)
+        t = z >> np.uint64(30)
+        z ^= t
+        z *= np.uint64(_M1)
+        np.right_shift(z, np.uint64(27), out=t)
+        z ^= t
+        z *= np.uint64(_M2)
+        np.right_shift(z, np.uint64(31), out=t)
+        z ^= t
+        return z
 
 
 def _s64(c: int) -> int:

@@ -939,7 +939,8 @@ def run_serve(torch, sg, nreq=4096, rates=None, npes=512, Hs=32 << 20):
 
 
 # ----------------------------------------------------------------------------- profiling cases
-PROFILE_CASES = ("interp_ring", "reduce", "reduce_f32", "broadcast", "alltoall", "amo", "batch_bf16", "qsum")
+PROFILE_CASES = ("interp_ring", "reduce", "reduce_f32", "broadcast", "alltoall", "amo", "batch_bf16", "qsum",
+                 "pingpong_cluster", "cluster_coll")
 
 
 def run_profile_case(name, launches=4):
@@ -1007,6 +1008,21 @@ def run_profile_case(name, launches=4):
                 b.launch(s)
             torch.cuda.synchronize()
             b.destroy()
+    elif name == "pingpong_cluster":  # 64 pairs, each inside one 2-CTA cluster, 4 KiB, 2000 round trips
+        heap = sg.Heap(128, 16384, pe_mode=sg.PE_MODE_CTA, cluster_dim=2)
+        heap.partitions().zero_()
+        for _ in range(launches):
+            sg.pingpong_cluster(heap.base, heap.base + 12288, 4096, 64, 2000, None, s)
+    elif name == "cluster_coll":      # 8 clusters of 8 CTA PEs: shared-team reduce 64 KiB + fcollect 4 KiB
+        heap = sg.Heap(64, 1 << 20, pe_mode=sg.PE_MODE_CTA, cluster_dim=8)
+        heap.partitions().random_(0, 255)
+        ops = np.zeros(200, W.OP_DTYPE)
+        for k in range(100):
+            ops[2 * k] = (W.OP_REDUCE, W.DT_INT64, W.RED_SUM, 1, 0, -1, 512 * KiB, 0, 8192, 0, 0, 0)
+            ops[2 * k + 1] = (W.OP_FCOLLECT, 0, 0, 1, 0, -1, 768 * KiB, 65536, 4096, 0, 0, 0)
+        dev = torch.from_numpy(ops.view(np.uint8).copy()).cuda()
+        for _ in range(launches):
+            sg.run_script(dev, len(ops), None, s)
     else:
         raise SystemExit(f"unknown profile case {name}")
     torch.cuda.synchronize()

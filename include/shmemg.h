@@ -370,9 +370,12 @@ int shmemg_pingpong(void *buf, uint64_t *sig, uint64_t payload, int npairs, int 
  * and the signal is a word of that window (cluster-scope release add, acquire poll).
  * At the end PE p writes the last payload it received to its buf + payload and adds
  * the rounds it received to its `sig`: the heap ends exactly as after shmemg_pingpong.
- * Needs pe_mode CTA with cluster_dim >= 2 (each pair inside one device shared team),
- * 2*npairs a multiple of cluster_dim, payload <= SHMEMG_PINGPONG_CLUSTER_MAX, and every
- * CTA co-resident (else SHMEMG_ERR_UNSUPPORTED); other arguments as shmemg_pingpong. */
+ * Needs pe_mode CTA with cluster_dim >= 2 (each pair inside one device shared team) and
+ * 2*npairs a multiple of cluster_dim (else SHMEMG_ERR_UNSUPPORTED), payload <=
+ * SHMEMG_PINGPONG_CLUSTER_MAX; other arguments as shmemg_pingpong.  A pair's CTAs share
+ * a cluster, which the hardware schedules at once, so no cooperative launch is needed.
+ * Launched without its clusters (by a profiler's replay, say) the kernel records
+ * SHMEMG_ERR_UNSUPPORTED in the status word and touches nothing. */
 #define SHMEMG_PINGPONG_CLUSTER_MAX (64u << 10)
 int shmemg_pingpong_cluster(void *buf, uint64_t *sig, uint64_t payload, int npairs, int iters,
                             uint64_t *lat_ns, void *stream);

@@ -204,6 +204,10 @@ __global__ void __launch_bounds__(PP_THREADS, 8) k_pingpong_cluster(shmemg_devic
     extern __shared__ __align__(16) uint8_t s_win[];  // payload bytes, then the signal word
     __shared__ int s_stop;
     const int me = blockIdx.x, pair = me >> 1;
+    if (shmemg_d_cluster_nctarank() < 2) {  // launched without clusters: no peer to map
+        if (threadIdx.x == 0 && me == 0) shmemg_d_set_status(c, SHMEMG_ERR_UNSUPPORTED, -1);
+        return;
+    }
     const uint32_t peer_rank = shmemg_d_cluster_ctarank() ^ 1u;
     const bool pinger = (me & 1) == 0;
     uint64_t *my_sig = (uint64_t *)(s_win + ((payload + 15) & ~15ull));
@@ -331,22 +335,15 @@ int shmemg_pingpong_cluster(void *buf, uint64_t *sig, uint64_t payload, int npai
     cfg.blockDim = dim3(PP_THREADS);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = to_stream(stream);
-    cudaLaunchAttribute attr[2];
+    cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
     attr[0].val.clusterDim.x = S.cluster_dim;
     attr[0].val.clusterDim.y = 1;
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    int nclusters = 0;  // every pair's two CTAs wait on each other: all must be resident
-    if (cudaOccupancyMaxActiveClusters(&nclusters, (const void *)k_pingpong_cluster, &cfg) != cudaSuccess) {
-        cudaGetLastError();
-        return SHMEMG_ERR_UNSUPPORTED;
-    }
-    if ((int64_t)nclusters * S.cluster_dim < 2 * npairs) return SHMEMG_ERR_UNSUPPORTED;
-    attr[1].id = cudaLaunchAttributeCooperative;
-    attr[1].val.cooperative = 1;
-    cfg.numAttrs = 2;
+    // no cooperative launch needed: the two CTAs of a pair are in one cluster, which the
+    // hardware always schedules at once, and pairs never wait on each other
     return cuda_rc(cudaLaunchKernelExC(&cfg, (const void *)k_pingpong_cluster, args));
 }
 

@@ -92,7 +92,11 @@ __global__ void __launch_bounds__(INTERP_THREADS) k_interp(shmemg_device_ctx_t c
     // bulk ring, which then serves as each CTA's DSMEM window (free between ops: every
     // bulk copy has drained)
     __shared__ shmemg_cluster_state_t s_cs;
-    const bool dsm = c.pe_mode == SHMEMG_PE_MODE_CTA && c.cluster_dim > 1;
+    // (only when the launch really has clusters of cluster_dim CTAs: a launch without
+    // them -- a profiler replaying it, say -- runs the shared team on the L2/HBM path and
+    // never maps a peer CTA that does not exist)
+    const bool dsm = c.pe_mode == SHMEMG_PE_MODE_CTA && c.cluster_dim > 1 &&
+                     shmemg_d_cluster_nctarank() == (uint32_t)c.cluster_dim;
     shmemg_cluster_state_t *cs = dsm ? &s_cs : nullptr;
     const uint64_t win_bytes = use_bulk ? SHMEMG_BULK_SMEM : 0;
     if (dsm) shmemg_d_cluster_begin(s_cs);

@@ -365,7 +365,7 @@ int shmemg_pingpong(void *buf, uint64_t *sig, uint64_t payload, int npairs, int 
                     uint64_t *lat_ns, void *stream);
 
 /* The ping-pong of shmemg_pingpong between the two CTAs of each pair inside one
- * thread-block cluster, through distributed shared memory (Sec. 5.3 direct pointers,
+ * thread-block cluster, through distributed shared memory (Sec. 4.2 direct pointers,
  * Sec. 6.3 device shared team): the payload goes into the peer's shared-memory window
  * and the signal is a word of that window (cluster-scope release add, acquire poll).
  * At the end PE p writes the last payload it received to its buf + payload and adds

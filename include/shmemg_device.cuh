@@ -496,7 +496,7 @@ static __device__ __forceinline__ int shmemg_d_team_barrier_leader(const shmemg_
  * of a CTA-mode heap with cluster_dim > 1 is one hardware thread-block cluster when a
  * kernel is launched with clusters of cluster_dim CTAs: its members can load and store
  * each other's shared memory (distributed shared memory, DSMEM) directly, the direct
- * pointer idea of shmem_ptr (Sec. 5.3) applied to on-chip memory.
+ * pointer idea of shmem_ptr (Sec. 4.2) applied to on-chip memory.
  *
  * A kernel using this path keeps one shmemg_cluster_state_t in shared memory and calls
  * shmemg_d_cluster_begin first and shmemg_d_cluster_end last, with every thread of

@@ -305,8 +305,14 @@ enum {
     SHMEMG_OP_BROADCAST = 13, SHMEMG_OP_FCOLLECT = 14, SHMEMG_OP_ALLTOALL = 15,
     SHMEMG_OP_REDUCE = 16, SHMEMG_OP_TEAM_SYNC = 17
 };
+/* Bits 8-15 of `kind` are flags.  SHMEMG_OP_WARP issues the op at warp scope (Sec. 6.3
+ * participation scopes): one warp of the issuing PE (put, get, their _nbi forms,
+ * put_signal) or of every member PE (collectives, team_sync, barrier_all) performs it,
+ * with the same result as the PE-scope form; on other kinds it is invalid. */
+#define SHMEMG_OP_KIND_MASK 0xFFu
+#define SHMEMG_OP_WARP 0x100u
 typedef struct {
-    uint32_t kind;
+    uint32_t kind;     /* SHMEMG_OP_* | flags */
     uint8_t dtype;     /* AMO / reduce element type */
     uint8_t sub;       /* reduce op, signal op, or wait comparison */
     uint16_t team;     /* collectives */

@@ -349,6 +349,18 @@ static __device__ __forceinline__ void shmemg_d_getmem_block(const shmemg_device
     shmemg_d_getmem_group(c, shmemg_d_group_block(), dst, src, n, pe, shmemg_d_my_pe(c));
     __syncthreads();
 }
+/* warp-scope forms: the 32 lanes of the calling warp share the copy; the warp's local
+ * completion (its lanes have read the source) on return */
+static __device__ __forceinline__ void shmemg_d_putmem_warp(const shmemg_device_ctx_t &c, void *dst,
+                                                            const void *src, uint64_t n, int pe) {
+    shmemg_d_putmem_group(c, shmemg_d_group_warp(), dst, src, n, pe, shmemg_d_my_pe(c));
+    __syncwarp();
+}
+static __device__ __forceinline__ void shmemg_d_getmem_warp(const shmemg_device_ctx_t &c, void *dst,
+                                                            const void *src, uint64_t n, int pe) {
+    shmemg_d_getmem_group(c, shmemg_d_group_warp(), dst, src, n, pe, shmemg_d_my_pe(c));
+    __syncwarp();
+}
 /* thread-scope forms */
 static __device__ __forceinline__ void shmemg_d_putmem(const shmemg_device_ctx_t &c, void *dst, const void *src,
                                                        uint64_t n, int pe) {
@@ -432,6 +444,19 @@ static __device__ __forceinline__ void shmemg_d_putmem_signal_block(const shmemg
         shmemg_d_signal_op((uint64_t *)shmemg_d_ptr(c, sig, pe), v, sig_op);
     }
     __syncthreads();
+}
+/* put-with-signal at warp scope: the warp's lanes share the put, lane 0 fences and
+ * updates the signal once the warp has written. */
+static __device__ __forceinline__ void shmemg_d_putmem_signal_warp(const shmemg_device_ctx_t &c, void *dst,
+                                                                   const void *src, uint64_t n, uint64_t *sig,
+                                                                   uint64_t v, int sig_op, int pe) {
+    shmemg_d_putmem_group(c, shmemg_d_group_warp(), dst, src, n, pe, shmemg_d_my_pe(c));
+    __syncwarp();
+    if ((threadIdx.x & 31u) == 0) {
+        shmemg_d_fence_gpu();
+        shmemg_d_signal_op((uint64_t *)shmemg_d_ptr(c, sig, pe), v, sig_op);
+    }
+    __syncwarp();
 }
 /* wait_until on the caller's own signal word (thread scope, Sec. 6.4 single unscoped
  * contract), bounded: SHMEMG_SUCCESS or SHMEMG_ERR_TIMEOUT (recorded in the status
@@ -861,69 +886,142 @@ static __device__ __forceinline__ void shmemg_d_slice(uint64_t total, int r, int
 }
 
 /* ------------------------------------------------------------------ device collectives */
-/* PE-scope team collectives (every thread of every member PE calls with identical
- * arguments: Sec. 6.3 uniform participation).  Each quiets and synchronises the team
- * on entry and exit; in between, member r does its share: a slice of the elements or
- * bytes (reduce, broadcast) or its own blocks (fcollect, alltoall).  Offsets are
- * symmetric byte offsets.  Return SHMEMG_SUCCESS or a timeout / device error. */
-static __device__ __forceinline__ int shmemg_d_reduce_pe(const shmemg_device_ctx_t &c, int team, uint64_t dst_off,
-                                                         uint64_t src_off, uint64_t nelems, int dtype, int op,
-                                                         int64_t detail,
-                                                         shmemg_cluster_state_t *cs = nullptr) {
+/* Warp-scope team barrier (Sec. 6.3 participation scopes: one warp of the PE calls it,
+ * all 32 lanes with identical arguments): lane 0 quiets the warp's writes and runs the
+ * team barrier for the PE; the result is broadcast to the warp. */
+static __device__ __forceinline__ int shmemg_d_team_sync_warp(const shmemg_device_ctx_t &c, int team, int64_t detail) {
+    const shmemg_dteam_t *t = shmemg_d_team(c, team);
+    int grp = 0;
+    const int r = shmemg_d_team_rank(*t, shmemg_d_my_pe(c), &grp);
+    __syncwarp();
+    int rc = SHMEMG_SUCCESS;
+    if ((threadIdx.x & 31u) == 0 && r >= 0)
+        rc = shmemg_d_team_barrier_leader(c, t->bar_base + grp, (uint32_t)t->size, detail);
+    rc = __shfl_sync(0xffffffffu, rc, 0);
+    __syncwarp();
+    return rc;
+}
+
+/* Participation scope of a device collective: the threads that cooperate and the team
+ * synchronisation they use.  PE scope: every thread of the PE (its block, or its
+ * cluster in pe_mode CLUSTER); warp scope: one warp of the PE.  A runtime choice, so
+ * both scopes share one copy of the data-movement code. */
+static __device__ __forceinline__ shmemg_group shmemg_d_scope_group(const shmemg_device_ctx_t &c, bool warp) {
+    return warp ? shmemg_d_group_warp() : shmemg_d_group_pe(c);
+}
+static __device__ __forceinline__ int shmemg_d_scope_sync(const shmemg_device_ctx_t &c, int team, int64_t detail,
+                                                          shmemg_cluster_state_t *cs, bool warp) {
+    return warp ? shmemg_d_team_sync_warp(c, team, detail) : shmemg_d_team_sync_pe(c, team, detail, cs);
+}
+
+/* Team collectives at PE or warp scope (every participating thread of every member PE
+ * calls with identical arguments: Sec. 6.3 uniform participation).  Each quiets and
+ * synchronises the team on entry and exit; in between, member r does its share: a
+ * slice of the elements or bytes (reduce, broadcast) or its own blocks (fcollect,
+ * alltoall).  Offsets are symmetric byte offsets.  Return SHMEMG_SUCCESS or a timeout /
+ * device error. */
+static __device__ __forceinline__ int shmemg_d_reduce_scoped(const shmemg_device_ctx_t &c, int team, uint64_t dst_off,
+                                                             uint64_t src_off, uint64_t nelems, int dtype, int op,
+                                                             int64_t detail, shmemg_cluster_state_t *cs, bool warp) {
     const shmemg_dteam_t t = *shmemg_d_team(c, team);
     int grp = 0, r = shmemg_d_team_rank(t, shmemg_d_my_pe(c), &grp);
     if (r < 0) return SHMEMG_SUCCESS;
-    int rc = shmemg_d_team_sync_pe(c, team, detail, cs);
+    int rc = shmemg_d_scope_sync(c, team, detail, cs, warp);
     if (rc) return rc;
     uint64_t es = dtype == SHMEMG_INT64 ? 8 : 4, lo, hi;
     shmemg_d_slice(nelems, r, t.size, 16 / es, &lo, &hi);
-    shmemg_d_reduce_elems(shmemg_d_group_pe(c), c.heap, c.pe_stride, shmemg_d_team_member(t, grp, 0), t.stride,
-                          t.size, dst_off, src_off, lo, hi, dtype, op);
-    return shmemg_d_team_sync_pe(c, team, detail, cs);
+    shmemg_d_reduce_elems(shmemg_d_scope_group(c, warp), c.heap, c.pe_stride, shmemg_d_team_member(t, grp, 0),
+                          t.stride, t.size, dst_off, src_off, lo, hi, dtype, op);
+    return shmemg_d_scope_sync(c, team, detail, cs, warp);
 }
-static __device__ __forceinline__ int shmemg_d_broadcastmem_pe(const shmemg_device_ctx_t &c, int team, uint64_t dst_off,
-                                                               uint64_t src_off, uint64_t n, int root, int64_t detail,
-                                                               shmemg_cluster_state_t *cs = nullptr) {
+static __device__ __forceinline__ int shmemg_d_broadcastmem_scoped(const shmemg_device_ctx_t &c, int team,
+                                                                   uint64_t dst_off, uint64_t src_off, uint64_t n,
+                                                                   int root, int64_t detail, shmemg_cluster_state_t *cs,
+                                                                   bool warp) {
     const shmemg_dteam_t t = *shmemg_d_team(c, team);
     int grp = 0, r = shmemg_d_team_rank(t, shmemg_d_my_pe(c), &grp);
     if (r < 0) return SHMEMG_SUCCESS;
-    int rc = shmemg_d_team_sync_pe(c, team, detail, cs);
+    int rc = shmemg_d_scope_sync(c, team, detail, cs, warp);
     if (rc) return rc;
     uint64_t lo, hi;
     shmemg_d_slice(n, r, t.size, 16, &lo, &hi);
     const uint8_t *src = shmemg_d_addr(c, shmemg_d_team_member(t, grp, root), src_off);
-    shmemg_d_replicate_bytes(shmemg_d_group_pe(c), c.heap, c.pe_stride, shmemg_d_team_member(t, grp, 0), t.stride,
-                             t.size, dst_off, src, lo, hi);
-    return shmemg_d_team_sync_pe(c, team, detail, cs);
+    shmemg_d_replicate_bytes(shmemg_d_scope_group(c, warp), c.heap, c.pe_stride, shmemg_d_team_member(t, grp, 0),
+                             t.stride, t.size, dst_off, src, lo, hi);
+    return shmemg_d_scope_sync(c, team, detail, cs, warp);
 }
-static __device__ __forceinline__ int shmemg_d_fcollectmem_pe(const shmemg_device_ctx_t &c, int team, uint64_t dst_off,
-                                                              uint64_t src_off, uint64_t n, int64_t detail,
-                                                              shmemg_cluster_state_t *cs = nullptr) {
+static __device__ __forceinline__ int shmemg_d_fcollectmem_scoped(const shmemg_device_ctx_t &c, int team,
+                                                                  uint64_t dst_off, uint64_t src_off, uint64_t n,
+                                                                  int64_t detail, shmemg_cluster_state_t *cs, bool warp) {
     const shmemg_dteam_t t = *shmemg_d_team(c, team);
     int grp = 0, r = shmemg_d_team_rank(t, shmemg_d_my_pe(c), &grp);
     if (r < 0) return SHMEMG_SUCCESS;
-    int rc = shmemg_d_team_sync_pe(c, team, detail, cs);
+    int rc = shmemg_d_scope_sync(c, team, detail, cs, warp);
     if (rc) return rc;
     const uint8_t *src = shmemg_d_addr(c, shmemg_d_team_member(t, grp, r), src_off);
-    shmemg_d_replicate_bytes(shmemg_d_group_pe(c), c.heap, c.pe_stride, shmemg_d_team_member(t, grp, 0), t.stride,
-                             t.size, dst_off + (uint64_t)r * n, src, 0, n);
-    return shmemg_d_team_sync_pe(c, team, detail, cs);
+    shmemg_d_replicate_bytes(shmemg_d_scope_group(c, warp), c.heap, c.pe_stride, shmemg_d_team_member(t, grp, 0),
+                             t.stride, t.size, dst_off + (uint64_t)r * n, src, 0, n);
+    return shmemg_d_scope_sync(c, team, detail, cs, warp);
 }
-static __device__ __forceinline__ int shmemg_d_alltoallmem_pe(const shmemg_device_ctx_t &c, int team, uint64_t dst_off,
-                                                              uint64_t src_off, uint64_t n, int64_t detail,
-                                                              shmemg_cluster_state_t *cs = nullptr) {
+static __device__ __forceinline__ int shmemg_d_alltoallmem_scoped(const shmemg_device_ctx_t &c, int team,
+                                                                  uint64_t dst_off, uint64_t src_off, uint64_t n,
+                                                                  int64_t detail, shmemg_cluster_state_t *cs, bool warp) {
     const shmemg_dteam_t t = *shmemg_d_team(c, team);
     int grp = 0, r = shmemg_d_team_rank(t, shmemg_d_my_pe(c), &grp);
     if (r < 0) return SHMEMG_SUCCESS;
-    int rc = shmemg_d_team_sync_pe(c, team, detail, cs);
+    int rc = shmemg_d_scope_sync(c, team, detail, cs, warp);
     if (rc) return rc;
     const int me = shmemg_d_team_member(t, grp, r);
     for (int j = 0; j < t.size; j++) {
         int pj = shmemg_d_team_member(t, grp, j);
-        shmemg_d_copy_group(shmemg_d_group_pe(c), shmemg_d_addr(c, pj, dst_off + (uint64_t)r * n),
+        shmemg_d_copy_group(shmemg_d_scope_group(c, warp), shmemg_d_addr(c, pj, dst_off + (uint64_t)r * n),
                             shmemg_d_addr(c, me, src_off + (uint64_t)j * n), n);
     }
-    return shmemg_d_team_sync_pe(c, team, detail, cs);
+    return shmemg_d_scope_sync(c, team, detail, cs, warp);
+}
+
+/* PE scope: every thread of the PE; with a cluster state, the shared team's barrier is
+ * the hardware cluster barrier */
+static __device__ __forceinline__ int shmemg_d_reduce_pe(const shmemg_device_ctx_t &c, int team, uint64_t dst_off,
+                                                         uint64_t src_off, uint64_t nelems, int dtype, int op,
+                                                         int64_t detail, shmemg_cluster_state_t *cs = nullptr) {
+    return shmemg_d_reduce_scoped(c, team, dst_off, src_off, nelems, dtype, op, detail, cs, false);
+}
+static __device__ __forceinline__ int shmemg_d_broadcastmem_pe(const shmemg_device_ctx_t &c, int team, uint64_t dst_off,
+                                                               uint64_t src_off, uint64_t n, int root, int64_t detail,
+                                                               shmemg_cluster_state_t *cs = nullptr) {
+    return shmemg_d_broadcastmem_scoped(c, team, dst_off, src_off, n, root, detail, cs, false);
+}
+static __device__ __forceinline__ int shmemg_d_fcollectmem_pe(const shmemg_device_ctx_t &c, int team, uint64_t dst_off,
+                                                              uint64_t src_off, uint64_t n, int64_t detail,
+                                                              shmemg_cluster_state_t *cs = nullptr) {
+    return shmemg_d_fcollectmem_scoped(c, team, dst_off, src_off, n, detail, cs, false);
+}
+static __device__ __forceinline__ int shmemg_d_alltoallmem_pe(const shmemg_device_ctx_t &c, int team, uint64_t dst_off,
+                                                              uint64_t src_off, uint64_t n, int64_t detail,
+                                                              shmemg_cluster_state_t *cs = nullptr) {
+    return shmemg_d_alltoallmem_scoped(c, team, dst_off, src_off, n, detail, cs, false);
+}
+/* warp scope: one warp of each member PE (all 32 lanes) */
+static __device__ __forceinline__ int shmemg_d_reduce_warp(const shmemg_device_ctx_t &c, int team, uint64_t dst_off,
+                                                           uint64_t src_off, uint64_t nelems, int dtype, int op,
+                                                           int64_t detail) {
+    return shmemg_d_reduce_scoped(c, team, dst_off, src_off, nelems, dtype, op, detail, nullptr, true);
+}
+static __device__ __forceinline__ int shmemg_d_broadcastmem_warp(const shmemg_device_ctx_t &c, int team,
+                                                                 uint64_t dst_off, uint64_t src_off, uint64_t n,
+                                                                 int root, int64_t detail) {
+    return shmemg_d_broadcastmem_scoped(c, team, dst_off, src_off, n, root, detail, nullptr, true);
+}
+static __device__ __forceinline__ int shmemg_d_fcollectmem_warp(const shmemg_device_ctx_t &c, int team,
+                                                                uint64_t dst_off, uint64_t src_off, uint64_t n,
+                                                                int64_t detail) {
+    return shmemg_d_fcollectmem_scoped(c, team, dst_off, src_off, n, detail, nullptr, true);
+}
+static __device__ __forceinline__ int shmemg_d_alltoallmem_warp(const shmemg_device_ctx_t &c, int team,
+                                                                uint64_t dst_off, uint64_t src_off, uint64_t n,
+                                                                int64_t detail) {
+    return shmemg_d_alltoallmem_scoped(c, team, dst_off, src_off, n, detail, nullptr, true);
 }
 
 /* ------------------------------------------------------------------ cluster collectives */

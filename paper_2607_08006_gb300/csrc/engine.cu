@@ -556,7 +556,9 @@ int shmemg_run_script_host(const shmemg_op_t *ops, int64_t nops, int64_t *fetche
         const shmemg_op_t &o = ops[i];
         uint8_t *dst = S.heap + o.dst, *src = S.heap + o.src;
         int rc = SHMEMG_SUCCESS;
-        switch (o.kind) {
+        // a host-issued op has no thread scope: the warp-scope flag selects the same op
+        if ((o.kind & ~SHMEMG_OP_KIND_MASK) & ~SHMEMG_OP_WARP) return SHMEMG_ERR_INVALID_ARG;
+        switch (o.kind & SHMEMG_OP_KIND_MASK) {
         case SHMEMG_OP_PUT: rc = shmemg_putmem(dst, src, o.n, o.pe, o.issuer, stream); break;
         case SHMEMG_OP_PUT_NBI: rc = shmemg_putmem_nbi(dst, src, o.n, o.pe, o.issuer, stream); break;
         case SHMEMG_OP_GET: rc = shmemg_getmem(dst, src, o.n, o.pe, o.issuer, stream); break;

@@ -41,7 +41,19 @@ __device__ __forceinline__ bool op_valid(const shmemg_device_ctx_t &c, const shm
     const uint64_t H = c.pe_stride;
     auto in = [&](uint64_t off, uint64_t n) { return off <= H && n <= H - off; };
     auto pe_ok = [&](int p) { return p >= 0 && p < c.npes; };
-    switch (o.kind) {
+    const uint32_t kind = o.kind & SHMEMG_OP_KIND_MASK, flags = o.kind & ~SHMEMG_OP_KIND_MASK;
+    if (flags & ~SHMEMG_OP_WARP) return false;
+    if (flags) {  // warp scope: RMA, put_signal, barriers and collectives only
+        switch (kind) {
+        case SHMEMG_OP_PUT: case SHMEMG_OP_GET: case SHMEMG_OP_PUT_NBI: case SHMEMG_OP_GET_NBI:
+        case SHMEMG_OP_PUT_SIGNAL: case SHMEMG_OP_BARRIER_ALL: case SHMEMG_OP_TEAM_SYNC: case SHMEMG_OP_BROADCAST:
+        case SHMEMG_OP_FCOLLECT: case SHMEMG_OP_ALLTOALL: case SHMEMG_OP_REDUCE:
+            break;
+        default:
+            return false;
+        }
+    }
+    switch (kind) {
     case SHMEMG_OP_PUT: case SHMEMG_OP_PUT_NBI: case SHMEMG_OP_GET: case SHMEMG_OP_GET_NBI:
         return pe_ok(o.pe) && pe_ok(o.issuer) && in(o.dst, o.n) && in(o.src, o.n);
     case SHMEMG_OP_FETCH_ADD: case SHMEMG_OP_COMPARE_SWAP: case SHMEMG_OP_FETCH_XOR: {
@@ -61,7 +73,7 @@ __device__ __forceinline__ bool op_valid(const shmemg_device_ctx_t &c, const shm
     if (o.team >= SHMEMG_MAX_TEAMS) return false;
     const shmemg_dteam_t t = *shmemg_d_team(c, o.team);
     if (!t.valid) return false;
-    switch (o.kind) {
+    switch (kind) {
     case SHMEMG_OP_TEAM_SYNC: return true;
     case SHMEMG_OP_BROADCAST: return o.pe >= 0 && o.pe < t.size && in(o.dst, o.n) && in(o.src, o.n);
     case SHMEMG_OP_FCOLLECT: return in(o.dst, o.n * (uint64_t)t.size) && in(o.src, o.n);
@@ -101,7 +113,7 @@ __global__ void __launch_bounds__(INTERP_THREADS) k_interp(shmemg_device_ctx_t c
     const uint64_t win_bytes = use_bulk ? SHMEMG_BULK_SMEM : 0;
     if (dsm) shmemg_d_cluster_begin(s_cs);
     auto staged = [&](const shmemg_op_t &o) {
-        if (!dsm || o.team != SHMEMG_TEAM_SHARED) return false;
+        if (!dsm || o.team != SHMEMG_TEAM_SHARED || (o.kind & SHMEMG_OP_WARP)) return false;
         const uint64_t b = shmemg_d_cluster_stage_bytes(o.kind, o.n, o.dtype, c.cluster_dim);
         return b > 0 && b <= win_bytes;
     };
@@ -109,7 +121,7 @@ __global__ void __launch_bounds__(INTERP_THREADS) k_interp(shmemg_device_ctx_t c
     // record): a CTA that has failed still passes them for every op it skips, so the
     // CTAs of a cluster always meet at the same barriers (they have no timeout).
     auto cluster_barriers = [&](const shmemg_op_t &o) {
-        if (!dsm || o.team != SHMEMG_TEAM_SHARED) return 0;
+        if (!dsm || o.team != SHMEMG_TEAM_SHARED || (o.kind & SHMEMG_OP_WARP)) return 0;
         switch (o.kind) {
         case SHMEMG_OP_TEAM_SYNC: return 1;
         case SHMEMG_OP_BROADCAST: case SHMEMG_OP_FCOLLECT: case SHMEMG_OP_ALLTOALL: case SHMEMG_OP_REDUCE:
@@ -138,19 +150,35 @@ __global__ void __launch_bounds__(INTERP_THREADS) k_interp(shmemg_device_ctx_t c
             if (dsm) continue;
             break;
         }
-        switch (o.kind) {
+        // warp scope (SHMEMG_OP_WARP): warp 0 of the PE's leader CTA performs the op with
+        // the warp-scope forms; the rest of the PE takes its result afterwards
+        const bool warp = (o.kind & SHMEMG_OP_WARP) != 0;
+        const bool active =
+            !warp || (threadIdx.x < 32 && (c.pe_mode != SHMEMG_PE_MODE_CLUSTER || shmemg_d_cluster_ctarank() == 0));
+        const shmemg_group gw = warp ? shmemg_d_group_warp() : g;
+        switch (o.kind & SHMEMG_OP_KIND_MASK) {
         case SHMEMG_OP_PUT:
         case SHMEMG_OP_PUT_NBI:
             if (o.issuer == me) {
-                pe_copy(c, g, shmemg_d_addr(c, o.pe, o.dst), shmemg_d_addr(c, me, o.src), o.n, use_bulk, s_ring, s_bars);
-                if (o.kind == SHMEMG_OP_PUT) shmemg_d_pe_sync(c);
+                if (warp) {
+                    if (active) shmemg_d_copy_group(gw, shmemg_d_addr(c, o.pe, o.dst), shmemg_d_addr(c, me, o.src), o.n);
+                } else {
+                    pe_copy(c, g, shmemg_d_addr(c, o.pe, o.dst), shmemg_d_addr(c, me, o.src), o.n, use_bulk, s_ring,
+                            s_bars);
+                    if (o.kind == SHMEMG_OP_PUT) shmemg_d_pe_sync(c);
+                }
             }
             break;
         case SHMEMG_OP_GET:
         case SHMEMG_OP_GET_NBI:
             if (o.issuer == me) {
-                pe_copy(c, g, shmemg_d_addr(c, me, o.dst), shmemg_d_addr(c, o.pe, o.src), o.n, use_bulk, s_ring, s_bars);
-                if (o.kind == SHMEMG_OP_GET) shmemg_d_pe_sync(c);
+                if (warp) {
+                    if (active) shmemg_d_copy_group(gw, shmemg_d_addr(c, me, o.dst), shmemg_d_addr(c, o.pe, o.src), o.n);
+                } else {
+                    pe_copy(c, g, shmemg_d_addr(c, me, o.dst), shmemg_d_addr(c, o.pe, o.src), o.n, use_bulk, s_ring,
+                            s_bars);
+                    if (o.kind == SHMEMG_OP_GET) shmemg_d_pe_sync(c);
+                }
             }
             break;
         case SHMEMG_OP_FETCH_ADD:
@@ -178,11 +206,18 @@ __global__ void __launch_bounds__(INTERP_THREADS) k_interp(shmemg_device_ctx_t c
             break;
         case SHMEMG_OP_PUT_SIGNAL:
             if (o.issuer == me) {
-                shmemg_d_copy_group(g, shmemg_d_addr(c, o.pe, o.dst), shmemg_d_addr(c, me, o.src), o.n);
-                shmemg_d_pe_sync(c);
-                if (leader) {
-                    shmemg_d_fence_gpu();
-                    shmemg_d_signal_op((uint64_t *)shmemg_d_addr(c, o.pe, o.aux), (uint64_t)o.operand, o.sub);
+                if (warp) {
+                    if (active)
+                        shmemg_d_putmem_signal_warp(c, shmemg_d_addr(c, 0, o.dst), shmemg_d_addr(c, 0, o.src), o.n,
+                                                    (uint64_t *)shmemg_d_addr(c, 0, o.aux), (uint64_t)o.operand, o.sub,
+                                                    o.pe);
+                } else {
+                    shmemg_d_copy_group(g, shmemg_d_addr(c, o.pe, o.dst), shmemg_d_addr(c, me, o.src), o.n);
+                    shmemg_d_pe_sync(c);
+                    if (leader) {
+                        shmemg_d_fence_gpu();
+                        shmemg_d_signal_op((uint64_t *)shmemg_d_addr(c, o.pe, o.aux), (uint64_t)o.operand, o.sub);
+                    }
                 }
             }
             break;
@@ -209,33 +244,43 @@ __global__ void __launch_bounds__(INTERP_THREADS) k_interp(shmemg_device_ctx_t c
             if (o.issuer == me || o.issuer < 0) shmemg_d_quiet_pe(c);
             break;
         case SHMEMG_OP_BARRIER_ALL:
-            rc = shmemg_d_barrier_all_pe(c, i);
+            if (active) rc = shmemg_d_scope_sync(c, SHMEMG_TEAM_WORLD, i, nullptr, warp);
             break;
         case SHMEMG_OP_TEAM_SYNC: {
             int grp;
-            if (shmemg_d_team_rank(*shmemg_d_team(c, o.team), me, &grp) >= 0)
-                rc = shmemg_d_team_sync_pe(c, o.team, i, cs);
+            if (active && shmemg_d_team_rank(*shmemg_d_team(c, o.team), me, &grp) >= 0)
+                rc = shmemg_d_scope_sync(c, o.team, i, cs, warp);
             break;
         }
         case SHMEMG_OP_BROADCAST:
             if (staged(o)) rc = shmemg_d_cluster_broadcastmem_pe(c, s_cs, s_ring, o.dst, o.src, o.n, o.pe, i);
-            else rc = shmemg_d_broadcastmem_pe(c, o.team, o.dst, o.src, o.n, o.pe, i, cs);
+            else if (active) rc = shmemg_d_broadcastmem_scoped(c, o.team, o.dst, o.src, o.n, o.pe, i, cs, warp);
             break;
         case SHMEMG_OP_FCOLLECT:
             if (staged(o)) rc = shmemg_d_cluster_fcollectmem_pe(c, s_cs, s_ring, o.dst, o.src, o.n, i);
-            else rc = shmemg_d_fcollectmem_pe(c, o.team, o.dst, o.src, o.n, i, cs);
+            else if (active) rc = shmemg_d_fcollectmem_scoped(c, o.team, o.dst, o.src, o.n, i, cs, warp);
             break;
         case SHMEMG_OP_ALLTOALL:
             if (staged(o)) rc = shmemg_d_cluster_alltoallmem_pe(c, s_cs, s_ring, o.dst, o.src, o.n, i);
-            else rc = shmemg_d_alltoallmem_pe(c, o.team, o.dst, o.src, o.n, i, cs);
+            else if (active) rc = shmemg_d_alltoallmem_scoped(c, o.team, o.dst, o.src, o.n, i, cs, warp);
             break;
         case SHMEMG_OP_REDUCE:
             if (staged(o)) rc = shmemg_d_cluster_reduce_pe(c, s_cs, s_ring, o.dst, o.src, o.n, o.dtype, o.sub, i);
-            else rc = shmemg_d_reduce_pe(c, o.team, o.dst, o.src, o.n, o.dtype, o.sub, i, cs);
+            else if (active) rc = shmemg_d_reduce_scoped(c, o.team, o.dst, o.src, o.n, o.dtype, o.sub, i, cs, warp);
             break;
         default:
             if (leader) shmemg_d_set_status(c, SHMEMG_ERR_INVALID_ARG, i);
             rc = SHMEMG_ERR_INVALID_ARG;
+        }
+        if (warp) {
+            // the active warp's result decides for the PE (the same two-slot hand-over as a
+            // wait's; in pe_mode CLUSTER the other CTAs read the leader's slot via DSMEM)
+            const int slot = n_waits++ & 1;
+            if (threadIdx.x == 0) s_wrc[slot] = rc;
+            shmemg_d_pe_sync(c);
+            rc = c.pe_mode == SHMEMG_PE_MODE_CLUSTER && c.cluster_dim > 1
+                     ? shmemg_d_ld_cluster<int>(shmemg_d_cluster_addr(&s_wrc[slot], 0))
+                     : s_wrc[slot];
         }
         if (rc != SHMEMG_SUCCESS) {
             failed = true;  // uniform across the PE: every thread leaves both loops

@@ -391,7 +391,7 @@ int shmemg_query_capabilities(shmemg_team_t team, shmemg_caps_t *out) {
     // barrier and small collectives go through distributed shared memory
     if (team == SHMEMG_TEAM_SHARED && s.pe_mode == SHMEMG_PE_MODE_CTA && s.cluster_dim > 1) out->path |= SHMEMG_PATH_DSMEM;
     out->rma_scopes = SHMEMG_SCOPE_THREAD | SHMEMG_SCOPE_WARP | SHMEMG_SCOPE_BLOCK | SHMEMG_SCOPE_CLUSTER;
-    out->coll_scopes = SHMEMG_SCOPE_BLOCK | SHMEMG_SCOPE_CLUSTER | SHMEMG_SCOPE_GRID;
+    out->coll_scopes = SHMEMG_SCOPE_WARP | SHMEMG_SCOPE_BLOCK | SHMEMG_SCOPE_CLUSTER | SHMEMG_SCOPE_GRID;
     out->device_ordinal = s.device;
     out->pe_mode = s.pe_mode;
     out->cluster_dim = s.cluster_dim;

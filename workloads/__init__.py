@@ -190,6 +190,7 @@ OP_FADD, OP_CSWAP, OP_FXOR = 5, 6, 7
 OP_PUT_SIGNAL, OP_WAIT_UNTIL = 8, 9
 OP_BARRIER_ALL, OP_QUIET, OP_FENCE = 10, 11, 12
 OP_BCAST, OP_FCOLLECT, OP_ALLTOALL, OP_REDUCE, OP_TEAM_SYNC = 13, 14, 15, 16, 17
+OP_WARP = 0x100   # flag bit of `kind`: the op is issued at warp scope (same result)
 COLLECTIVE_KINDS = (OP_BARRIER_ALL, OP_BCAST, OP_FCOLLECT, OP_ALLTOALL, OP_REDUCE, OP_TEAM_SYNC)
 AMO_KINDS = (OP_FADD, OP_CSWAP, OP_FXOR)
 

@@ -494,9 +494,9 @@ def run_cluster_leg(torch, sg, rounds=200, reps=3, iters=10000):
     wait_until ping-pong pairs (1024 CTAs, each pair inside one 2-CTA cluster) through
     distributed shared memory vs the same pairs through L2/HBM, half round trip per
     payload, final heaps checked.  (2) One cluster of 8 CTA PEs: `rounds` collectives in
-    one device-initiated script on the shared team (DSMEM barrier, windows staged in
+    one device-initiated script on the shared team (cluster barrier, windows staged in
     shared memory) vs the same 8 PEs as the world team (L2 barrier, loads and stores in
-    HBM/L2), time per collective, results compared."""
+    HBM/L2) at PE scope and at warp scope, time per collective, results compared."""
     out = {}
     npes, H = 1024, 16384
     heap = sg.Heap(npes, H, pe_mode=sg.PE_MODE_CTA, cluster_dim=2)
@@ -544,10 +544,11 @@ def run_cluster_leg(torch, sg, rounds=200, reps=3, iters=10000):
         for name, kind, dt, root, n in cases:
             row = {}
             res = {}
-            for mode, team in (("global", 0), ("dsmem", 1)):
+            for mode, team, flag in (("global", 0, 0), ("global_warp", 0, W.OP_WARP), ("dsmem", 1, 0)):
                 ops = np.zeros(rounds, W.OP_DTYPE)
                 for k in range(rounds):
-                    ops[k] = (kind, dt, W.RED_SUM, team, root, -1, dst, 4096 if kind != W.OP_REDUCE else 0, n, 0, 0, 0)
+                    ops[k] = (kind | flag, dt, W.RED_SUM, team, root, -1, dst, 4096 if kind != W.OP_REDUCE else 0, n,
+                              0, 0, 0)
                 dev = torch.from_numpy(ops.view(np.uint8).copy()).cuda()
                 parts[:, dst:].zero_()
                 times = []
@@ -561,12 +562,76 @@ def run_cluster_leg(torch, sg, rounds=200, reps=3, iters=10000):
                 res[mode] = parts[:, dst:dst + 65536].clone()
                 row[mode + "_us_per_op"] = round(float(np.median(times[1:])) * 1e3 / rounds, 3)
             row["speedup"] = round(row["global_us_per_op"] / row["dsmem_us_per_op"], 2)
-            row["results_equal"] = bool(torch.equal(res["global"], res["dsmem"]))
+            row["results_equal"] = bool(torch.equal(res["global"], res["dsmem"])) and \
+                bool(torch.equal(res["global"], res["global_warp"]))
             coll[name] = row
         out["one_cluster_8_pes"] = coll
         out["status"] = sg.get_status()[0]
     finally:
         heap.close()
+    return out
+
+
+# ----------------------------------------------------------------------------- halo exchange
+def run_halo(torch, sg, iters=100, reps=3):
+    """The halo-exchange stencil (case study 1): 128 PEs as 16 x 8 tiles of 1024 x 1024
+    binary32 (a 8192 x 16384 periodic grid, 512 MiB per buffer), `iters` Jacobi sweeps
+    with the boundary stores fused into each sweep and one signal per neighbour (one
+    launch), vs one launch per sweep; PE = one CTA and PE = a 2-CTA cluster.  GB/s of
+    algorithmic bytes (every sweep reads and writes the grid, plus the halos); results of
+    both forms compared bitwise; the oracle timed on one sweep of a 2048 x 4096 sample."""
+    import oracle as orc
+
+    px, py, nx, ny = 16, 8, 1024, 1024
+    npes = px * py
+    hs = sg.halo_stride(nx, ny)
+    tile_b, halo_b = 2 * nx * ny * 4, 2 * hs * 4
+    H = (tile_b + halo_b + 64 + 4095) // 4096 * 4096
+    sweep_bytes = npes * (2 * nx * ny * 4 + 2 * (2 * nx + 2 * ny) * 4)
+    out = {"pes": f"{px}x{py}", "tile": f"{nx}x{ny}", "grid": f"{py * ny}x{px * nx}", "iters": iters,
+           "bytes_per_sweep": sweep_bytes}
+    stream = torch.cuda.current_stream()
+    for name, mode, cd in (("cta", sg.PE_MODE_CTA, 1), ("cluster2", sg.PE_MODE_CLUSTER, 2)):
+        heap = sg.Heap(npes, H, pe_mode=mode, cluster_dim=cd)
+        try:
+            parts = heap.partitions()
+            parts.zero_()
+            gen = torch.Generator(device="cuda")
+            gen.manual_seed(W.derive_seed("halo") & 0x7FFFFFFF)
+            init = torch.randn(npes, nx * ny, device="cuda", generator=gen)
+            tiles, halos, sigs = heap.sym(0, tile_b), heap.sym(tile_b, halo_b), heap.sym(tile_b + halo_b, 32)
+            row = {}
+            res = {}
+            for variant in ("persistent", "plain"):
+                times = []
+                for _ in range(reps + 1):
+                    parts[:, :nx * ny * 4].view(torch.float32).copy_(init)
+                    e0, e1 = _events(torch)
+                    e0.record(stream)
+                    sg.halo_jacobi(tiles, halos, sigs, px, py, nx, ny, iters, stream, plain=variant == "plain")
+                    e1.record(stream)
+                    torch.cuda.synchronize()
+                    times.append(e0.elapsed_time(e1))
+                ms = float(np.median(times[1:]))
+                r0 = (iters & 1) * nx * ny * 4
+                res[variant] = parts[:, r0:r0 + nx * ny * 4].clone()
+                row[variant] = {"ms": round(ms, 3), "us_per_sweep": round(ms * 1e3 / iters, 2),
+                                "GBps": round(iters * sweep_bytes / (ms * 1e-3) / 1e9, 1)}
+            row["speedup_vs_plain"] = round(row["plain"]["ms"] / row["persistent"]["ms"], 2)
+            row["results_equal"] = bool(torch.equal(res["persistent"], res["plain"]))
+            row["status"] = sg.get_status()[0]
+            out[name] = row
+        finally:
+            heap.close()
+    hbm, _ = measured_peaks()
+    best = max(out["cta"]["persistent"]["GBps"], out["cluster2"]["persistent"]["GBps"])
+    out["frac_of_hbm"] = round(best / hbm, 4)
+    g = W.normals_np(11, 2048 * 4096).astype(np.float32).reshape(2048, 4096)
+    t0 = time.perf_counter()
+    orc.halo_jacobi(g, 1)
+    dt = time.perf_counter() - t0
+    out["oracle"] = {"GBps": round(2 * g.nbytes / dt / 1e9, 3), "sample": "one sweep of a 2048 x 4096 grid",
+                     "cores": 1, "seconds": round(dt, 3)}
     return out
 
 
@@ -1070,9 +1135,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="shmemg", choices=["shmemg", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--secondary", default="script,amo,cluster,batch,serve",
-                    help="extra workloads measured after the sweep (comma list of script,amo,cluster,batch,serve "
-                         "or 'none')")
+    ap.add_argument("--secondary", default="script,amo,cluster,halo,batch,serve",
+                    help="extra workloads measured after the sweep (comma list of script,amo,cluster,halo,batch,"
+                         "serve or 'none')")
     ap.add_argument("--amo-ops-log2", type=int, default=30)
     ap.add_argument("--serve-requests", type=int, default=4096)
     ap.add_argument("--profile", choices=PROFILE_CASES, help="run one small single-kernel case (for ncu) and exit")
@@ -1104,6 +1169,8 @@ def main():
                     r = run_amo(torch, sg, args.amo_ops_log2)
                 elif name == "cluster":
                     r = run_cluster_leg(torch, sg)
+                elif name == "halo":
+                    r = run_halo(torch, sg)
                 elif name == "batch":
                     r = run_batch(torch, sg)
                 elif name == "serve":

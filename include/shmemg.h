@@ -386,6 +386,27 @@ int shmemg_pingpong(void *buf, uint64_t *sig, uint64_t payload, int npairs, int 
 int shmemg_pingpong_cluster(void *buf, uint64_t *sig, uint64_t payload, int npairs, int iters,
                             uint64_t *lat_ns, void *stream);
 
+/* ----------------------------------------------------------------- halo exchange */
+/* A GPU-resident halo exchange in a stencil code (Sec. 4.4, case study 1): the npes PEs
+ * form a px x py grid (PE = y*px + x) over a periodic 2-D grid of binary32 values; PE p
+ * owns an nx x ny tile (row-major, nx a multiple of 4) and runs `iters` Jacobi sweeps
+ * out = 0.25 * ((up + down) + (left + right)) (RNE, in this order).  Symmetric objects:
+ *   tiles  2*nx*ny floats: tile 0 holds the input; after the call the result is in tile
+ *          (iters & 1);
+ *   halos  2*hs floats, hs = 2*nx + 2*ny rounded up to a multiple of 4 (work space);
+ *   sigs   4 uint64, zero before the call (left zero after a successful call).
+ * shmemg_halo_jacobi: one cooperative launch; after each sweep a PE stores its new
+ * boundary rows and columns straight into its four neighbours' halo buffers (device-
+ * initiated puts fused into the sweep), then signals each neighbour (put-with-signal,
+ * Sec. 7); before each sweep it waits for its four signals (bounded wait_until).
+ * shmemg_halo_jacobi_plain: the same sweeps, one stream-ordered launch per sweep (the
+ * plain launch-per-op path: kernel boundaries replace the signals).  tiles and halos
+ * 16-byte aligned, px*py == npes, else SHMEMG_ERR_INVALID_ARG. */
+int shmemg_halo_jacobi(float *tiles, float *halos, uint64_t *sigs, int px, int py, int nx, int ny,
+                       int iters, void *stream);
+int shmemg_halo_jacobi_plain(float *tiles, float *halos, uint64_t *sigs, int px, int py, int nx,
+                             int ny, int iters, void *stream);
+
 /* ----------------------------------------------------------------- batched collectives */
 /* Many teams' uneven collectives in one persistent launch captured in a CUDA graph. */
 typedef struct {

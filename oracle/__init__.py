@@ -288,3 +288,18 @@ def check_serialisation(group, kind, operand, cond, fetched, w0, final=None,
     r = lib().or_check_serialisation(n, _p(group), _p(kind), _p(operand), _p(cond), _p(fetched),
                                      _p(w0), _p(fin), int(has_final), budget_per_group, C.byref(bad))
     return int(r)
+
+
+def halo_jacobi(grid, iters: int) -> np.ndarray:
+    """Jacobi sweeps on a periodic 2-D binary32 grid: every point becomes
+    0.25 * ((up + down) + (left + right)), each operation rounded to binary32 -- the
+    stencil of the halo-exchange workload (paper Sec. 4.4, case study 1), written on the
+    whole grid, with no decomposition into tiles and no halos."""
+    g = np.ascontiguousarray(grid, dtype=np.float32)
+    q = np.float32(0.25)
+    for _ in range(iters):
+        up, dn = np.roll(g, 1, axis=0), np.roll(g, -1, axis=0)
+        lf, rt = np.roll(g, 1, axis=1), np.roll(g, -1, axis=1)
+        g = q * ((up + dn) + (lf + rt))
+    return g
+

@@ -288,7 +288,6 @@ int shmemg_amo_stream(int64_t *table, uint64_t words_per_pe, const uint32_t *ops
     return cuda_rc(cudaGetLastError());
 }
 
-int launch_pe_grid(const void *kernel, void **args, size_t smem, cudaStream_t s);
 
 int shmemg_pingpong(void *buf, uint64_t *sig, uint64_t payload, int npairs, int iters, uint64_t *lat_ns, void *stream) {
     if (int rc = check_init()) return rc;

@@ -49,6 +49,11 @@ int cuda_rc(cudaError_t e);  // maps a CUDA error to SHMEMG_ERR_CUDA (records th
 // max co-resident CTAs of a kernel (occupancy), cached per kernel
 int ctas_for(const void *kernel, int threads, size_t smem);
 
+// cooperative launch with one CTA per PE (pe_mode CTA) or one cluster of cluster_dim CTAs
+// per PE, `threads` per CTA (0: the interpreter's count); SHMEMG_ERR_UNSUPPORTED if the
+// GPU cannot hold every PE at once
+int launch_pe_grid(const void *kernel, void **args, size_t smem, cudaStream_t s, int threads = 0);
+
 // scratch words in the reserved prefix: [SHMEMG_SCRATCH_OFF, +2 MiB)
 enum : uint64_t {
     SCR_SIGNAL_DONE = 0,            // 4096 uint32 counters for multi-CTA put_signal

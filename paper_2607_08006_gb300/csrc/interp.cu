@@ -302,10 +302,11 @@ int interp_threads() {
     return t;
 }
 
-// Cooperative launch of `kernel` with one CTA (or cluster) per PE.
-int launch_pe_grid(const void *kernel, void **args, size_t smem, cudaStream_t s) {
+// Cooperative launch of `kernel` with one CTA (or cluster) per PE; `threads` per CTA
+// (0: the interpreter's count).
+int launch_pe_grid(const void *kernel, void **args, size_t smem, cudaStream_t s, int threads) {
     State &S = st();
-    const int threads = interp_threads();
+    if (threads <= 0) threads = interp_threads();
     const int cd = S.cluster_dim;
     const unsigned grid = S.pe_mode == SHMEMG_PE_MODE_CLUSTER ? (unsigned)(S.npes * cd) : (unsigned)S.npes;
     cudaLaunchConfig_t cfg = {};

@@ -146,6 +146,8 @@ _SIGS = {
     "shmemg_amo_stream": [P, U64, P, U64, U64, U64, P, U32, P],
     "shmemg_pingpong": [P, P, U64, I, I, P, P],
     "shmemg_pingpong_cluster": [P, P, U64, I, I, P, P],
+    "shmemg_halo_jacobi": [P, P, P, I, I, I, I, I, P],
+    "shmemg_halo_jacobi_plain": [P, P, P, I, I, I, I, I, P],
     "shmemg_batch_create": [P, I, P, P],
     "shmemg_batch_launch": [P, P],
     "shmemg_batch_autotune": [P, P, P],
@@ -456,6 +458,16 @@ def pingpong(buf, sig, payload, npairs, iters, lat_dev, stream=None):
 
 def pingpong_cluster(buf, sig, payload, npairs, iters, lat_dev, stream=None):
     _call("shmemg_pingpong_cluster", _ptr(buf), _ptr(sig), payload, npairs, iters, _ptr(lat_dev), _stream(stream))
+
+
+def halo_stride(nx, ny):
+    """Floats per halo buffer of the halo exchange (2nx + 2ny rounded up to 4)."""
+    return (2 * nx + 2 * ny + 3) // 4 * 4
+
+
+def halo_jacobi(tiles, halos, sigs, px, py, nx, ny, iters, stream=None, plain=False):
+    _call("shmemg_halo_jacobi_plain" if plain else "shmemg_halo_jacobi", _ptr(tiles), _ptr(halos), _ptr(sigs),
+          px, py, nx, ny, iters, _stream(stream))
 
 
 # batched collectives -----------------------------------------------------------------

@@ -522,3 +522,56 @@ def test_plain_script_race_free_invariants(orc):
     cs = idx[s.ops["kind"][idx] == W.OP_CSWAP]
     succ = fetched[cs] == s.ops["cond"][cs]
     assert succ.any() and (~succ).any()
+
+
+# ----------------------------------------------------------------- halo-exchange stencil
+def _jacobi_fixtures():
+    grids, cur = [], None
+    for line in open(os.path.join(GOLD, "jacobi_order.txt")):
+        f = line.split()
+        if not f or f[0].startswith("#"):
+            continue
+        if f[0] == "grid":
+            cur = {"name": f[1], "g": np.zeros((int(f[2]), int(f[3])), np.float32), "expect": []}
+            grids.append(cur)
+        elif f[0] == "set":
+            cur["g"][int(f[1]), int(f[2])] = np.float32(float.fromhex(f[3]))
+        elif f[0] == "expect":
+            cur["expect"].append((int(f[1]), int(f[2]), float.fromhex(f[3])))
+    return grids
+
+
+def test_halo_jacobi_operation_order_golden(orc):
+    """The pairing (up + down) + (left + right), each add and the multiply rounded to
+    binary32, against hand-derived values where other pairings round differently."""
+    for fx in _jacobi_fixtures():
+        out = orc.halo_jacobi(fx["g"], 1)
+        for i, j, v in fx["expect"]:
+            assert float(out[i, j]) == v, (fx["name"], i, j, float(out[i, j]), v)
+
+
+def test_halo_jacobi_constant_delta_and_sum(orc):
+    """A constant grid is a fixed point; a unit delta spreads 1/4 to exactly its four
+    periodic neighbours (the corner wraps); the grid sum is conserved."""
+    c = np.full((6, 10), 3.25, np.float32)
+    assert np.array_equal(orc.halo_jacobi(c, 7), c)
+    d = np.zeros((5, 7), np.float32)
+    d[0, 0] = 1.0
+    want = np.zeros_like(d)
+    for i, j in ((1, 0), (4, 0), (0, 1), (0, 6)):
+        want[i, j] = 0.25
+    assert np.array_equal(orc.halo_jacobi(d, 1), want)
+    x = W.normals_np(5, 12 * 9).astype(np.float32).reshape(12, 9)
+    y = orc.halo_jacobi(x, 10)
+    assert abs(float(y.astype(np.float64).sum()) - float(x.astype(np.float64).sum())) < 1e-4
+
+
+def test_halo_jacobi_fourier_mode_decay(orc):
+    """A separable Fourier mode cos(2 pi k x / Nx) cos(2 pi l y / Ny) is an eigenvector:
+    each sweep scales it by (cos(2 pi k / Nx) + cos(2 pi l / Ny)) / 2."""
+    ny, nx, k, l, T = 16, 24, 3, 2, 6
+    yy, xx = np.meshgrid(np.arange(ny), np.arange(nx), indexing="ij")
+    g0 = np.cos(2 * np.pi * k * xx / nx) * np.cos(2 * np.pi * l * yy / ny)
+    lam = (np.cos(2 * np.pi * k / nx) + np.cos(2 * np.pi * l / ny)) / 2
+    out = orc.halo_jacobi(g0.astype(np.float32), T).astype(np.float64)
+    assert np.max(np.abs(out - lam ** T * g0)) < 2e-6

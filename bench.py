@@ -908,10 +908,15 @@ def serve_latency(recs, t0_host, arrivals, offset_ns):
     return (done_host - (t0_host + arrivals[recs["ticket"].astype(np.int64)].astype(np.int64))) / 1e3
 
 
-def run_serve(torch, sg, nreq=4096, rates=None, npes=512, Hs=32 << 20):
+SERVE_RATES = (1e6, 2e6, 5e6, 1e7, 2e7, 5e7)          # the configuration's arrival rates (req/s)
+SERVE_SAT_FRACTIONS = (0.1, 0.25, 0.5, 0.75, 1.0, 1.25)  # and fractions of the measured saturation rate
+
+
+def run_serve(torch, sg, nreq=1 << 16, rates=None, npes=512, Hs=32 << 20):
     """512 PEs x 32 MiB (16 GiB).  Mixed Poisson arrivals: 60 % put/get 8 B-4 MiB, 25 %
     int64 AMOs, 10 % fp32/bf16 team reductions, 5 % alltoall; served by the persistent
-    engine and by one launch per request, same arrivals; throughput and p50/p99 latency."""
+    engine and by one launch per request, same arrivals; throughput and p50/p99 latency
+    at 1-50 M req/s and at 0.1-1.25 x the saturation rate, `nreq` requests per point."""
     lay = W.serve_layout(H=Hs, amo_words=8192)
     heap = sg.Heap(npes, Hs)
     out = {"npes": npes, "heap_bytes": npes * Hs, "requests_per_point": nreq}
@@ -927,6 +932,7 @@ def run_serve(torch, sg, nreq=4096, rates=None, npes=512, Hs=32 << 20):
         cfg.arena_offset, cfg.arena_bytes = lay.arena_offset, lay.arena_bytes
         cfg.amo_offset, cfg.amo_words = lay.amo_offset, lay.amo_words
         cfg.max_ns = 300 * 10**9
+        cfg.ring_slots = 1 << 17     # room for a whole point's requests and completions
         reqs = W.gen_serve_requests(W.derive_seed("serve-reqs"), nreq, npes, lay)
         mb = float(np.mean(reqs["n"][np.isin(reqs["kind"], (1, 2))])) / 1e6
         out["mix_counts"] = {k: int(v) for k, v in zip(("rma", "amo", "reduce", "alltoall"), (
@@ -936,7 +942,7 @@ def run_serve(torch, sg, nreq=4096, rates=None, npes=512, Hs=32 << 20):
         offset, err = sg.clock_offset(50)
         out["clock_offset_err_us"] = round(err / 1e3, 2)
         sstream = torch.cuda.Stream()
-        comp_buf = np.zeros(8192, sg.COMPLETION_DTYPE)
+        comp_buf = np.zeros(16384, sg.COMPLETION_DTYPE)
 
         def serve_once(arr):
             srv = sg.Server(cfg, sstream)
@@ -990,7 +996,8 @@ def run_serve(torch, sg, nreq=4096, rates=None, npes=512, Hs=32 << 20):
         r_p, t_p = plain_once(zero)
         out["burst_plain"] = summarise(r_p, t_p, zero)
         lam_sat = sat["req_per_s"]
-        pts = rates or [0.5 * lam_sat, 0.9 * lam_sat, 1e6, 1e7]
+        out["saturation_req_per_s"] = lam_sat
+        pts = rates or [f * lam_sat for f in SERVE_SAT_FRACTIONS] + list(SERVE_RATES)
         out["points"] = []
         for lam in pts:
             arr = W.poisson_arrivals_ns(W.derive_seed("serve-arrivals"), nreq, lam)
@@ -1139,7 +1146,7 @@ def main():
                     help="extra workloads measured after the sweep (comma list of script,amo,cluster,halo,batch,"
                          "serve or 'none')")
     ap.add_argument("--amo-ops-log2", type=int, default=30)
-    ap.add_argument("--serve-requests", type=int, default=4096)
+    ap.add_argument("--serve-requests", type=int, default=1 << 16)
     ap.add_argument("--profile", choices=PROFILE_CASES, help="run one small single-kernel case (for ncu) and exit")
     args = ap.parse_args()
     if args.profile:

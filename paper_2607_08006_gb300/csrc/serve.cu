@@ -26,7 +26,8 @@
 
 namespace shmemg {
 
-constexpr int SV_THREADS = 256;
+constexpr int SV_THREADS = 256;   // CTAs of the plain path and of the server (two per SM)
+constexpr int SRV_THREADS = SV_THREADS;
 constexpr uint64_t RMA_TILE = 64ull << 10;    // bytes per put/get tile
 constexpr uint64_t RED_TILE = 8192;           // elements per reduce tile
 constexpr uint64_t A2A_TILE = 32ull << 10;    // bytes per alltoall block chunk
@@ -44,6 +45,9 @@ struct SvHost {                      // mapped host memory
     uint8_t p3[120];
 };
 
+constexpr uint32_t SV_MAX_SMID = 1024;
+constexpr uint64_t SECONDARY_DELAY_NS = 1000;  // head start of each SM's first worker on a new request
+
 struct SvCtl {                       // device memory
     unsigned long long fifo_head;
     uint8_t p0[120];
@@ -57,21 +61,30 @@ struct SvCtl {                       // device memory
     uint8_t p4[120];
     unsigned long long consumed_cache;  // last host `consumed` value seen by the device
     uint8_t p5[120];
+    unsigned int sm_workers[SV_MAX_SMID];  // worker CTAs per SM id (each worker's rank on its SM)
 };
 
-struct SvSlot {
+// One admitted request.  The claim word, which every worker that looks at the request
+// touches, has a cache line of its own; the completion count and checksum (one update
+// per published chunk) share another; the request fields are read-mostly.
+struct __align__(128) SvSlot {
     shmemg_req_t req;
     uint64_t dst_off;
     uint32_t page0, npages;
     uint32_t ntiles, gen;
-    unsigned long long claim;        // (gen << 32) | next tile
-    unsigned int done;
-    unsigned int busy;
-    unsigned long long checksum;
     uint64_t t_admit;
+    uint64_t t_pub;                  // when the admitter queued it
     int32_t status;
-    int32_t pad;
+    unsigned int busy;
+    uint8_t pad0[128 - 112];
+    unsigned long long claim;        // (gen << 32) | next tile
+    uint8_t pad1[120];
+    unsigned int done;
+    unsigned int pad2;
+    unsigned long long checksum;
+    uint8_t pad3[112];
 };
+static_assert(sizeof(SvSlot) == 384, "slot layout");
 
 struct SvArgs {
     uint8_t *heap;
@@ -239,11 +252,22 @@ __device__ uint64_t run_tile(const SvArgs &a, const shmemg_req_t &r, uint64_t ds
             for (uint64_t v = e0 / 2 + threadIdx.x; v < e1 / 2; v += blockDim.x) {
                 const uint64_t off = r.src + 16 * v;
                 longlong2 s = __ldcg((const longlong2 *)(heap + (uint64_t)pe0 * H + off));
-                for (int m = 1; m < P; m++) {
-                    longlong2 x = __ldcg((const longlong2 *)(heap + (uint64_t)(pe0 + m) * H + off));
+                auto add = [&](const longlong2 &x) {
                     s.x = (long long)((unsigned long long)s.x + (unsigned long long)x.x);
                     s.y = (long long)((unsigned long long)s.y + (unsigned long long)x.y);
+                };
+                int m = 1;
+                for (; m + 3 < P; m += 4) {  // four members' loads in flight
+                    const longlong2 x0 = __ldcg((const longlong2 *)(heap + (uint64_t)(pe0 + m) * H + off));
+                    const longlong2 x1 = __ldcg((const longlong2 *)(heap + (uint64_t)(pe0 + m + 1) * H + off));
+                    const longlong2 x2 = __ldcg((const longlong2 *)(heap + (uint64_t)(pe0 + m + 2) * H + off));
+                    const longlong2 x3 = __ldcg((const longlong2 *)(heap + (uint64_t)(pe0 + m + 3) * H + off));
+                    add(x0);
+                    add(x1);
+                    add(x2);
+                    add(x3);
                 }
+                for (; m < P; m++) add(__ldcg((const longlong2 *)(heap + (uint64_t)(pe0 + m) * H + off)));
                 for (int m = 0; m < P; m++) *(longlong2 *)(heap + (uint64_t)(pe0 + m) * H + dst_off + 16 * v) = s;
                 uint4 w;
                 memcpy(&w, &s, 16);
@@ -258,7 +282,24 @@ __device__ uint64_t run_tile(const SvArgs &a, const shmemg_req_t &r, uint64_t ds
                 acc += ck4(w, 4 * v);
             }
         } else {
-            for (uint64_t q = e0 / 4 + threadIdx.x; q < e1 / 4; q += blockDim.x) {
+            // bf16: eight elements per thread with 16-byte code loads, eight members'
+            // codes and scales loaded ahead (sources and scales are 16-byte aligned); a
+            // trailing group of four the 4-wide way
+            const uint64_t v1 = e1 / 8;
+            for (uint64_t v = e0 / 8 + threadIdx.x; v < v1; v += blockDim.x) {
+                float4 o[2];
+                qsum_wide_acc<SHMEMG_FMT_BF16>(heap, H, pe0, 1, P, r.src, (uint64_t)r.cond, 8 * v, o);
+                for (int m = 0; m < P; m++) {
+                    float4 *d = (float4 *)(heap + (uint64_t)(pe0 + m) * H + dst_off + 32 * v);
+                    d[0] = o[0];
+                    d[1] = o[1];
+                }
+                uint4 w0, w1;
+                memcpy(&w0, &o[0], 16);
+                memcpy(&w1, &o[1], 16);
+                acc += ck4(w0, 8 * v) + ck4(w1, 8 * v + 4);
+            }
+            for (uint64_t q = 2 * v1 + threadIdx.x; q < e1 / 4; q += blockDim.x) {
                 qsum4<SHMEMG_FMT_BF16>(heap, H, pe0, 1, P, dst_off, r.src, (uint64_t)r.cond, 4 * q, r.n, true);
                 uint4 w = __ldcg((const uint4 *)(heap + (uint64_t)pe0 * H + dst_off + 16 * q));
                 acc += ck4(w, 4 * q);
@@ -321,14 +362,19 @@ __device__ void write_completion(const SvArgs &a, uint64_t ticket, uint64_t t_ad
 }
 
 // ------------------------------------------------------------------ admitter
-__device__ bool find_pages(const SvArgs &a, const Geo &g, uint32_t need, uint32_t *first) {
+// Page bitmaps, warp-collective (all 32 lanes call with the same arguments): lane m
+// handles members m, m + 32, ... of the request's PEs, so a request spread over P PEs
+// costs about P/32 dependent loads or atomics per bitmap word, not P.
+__device__ bool find_pages(const SvArgs &a, const Geo &g, uint32_t need, uint32_t *first, int lane) {
     if (need == 0) { *first = 0; return true; }
     if (need > a.pages_per_pe) return false;
     uint32_t run = 0;
     for (uint32_t w = 0; w < a.bm_words; w++) {
-        unsigned long long occ = 0;
-        for (int m = 0; m < g.count; m++)
-            occ |= *(volatile unsigned long long *)&a.bitmaps[(uint64_t)(g.first + m) * a.bm_words + w];
+        unsigned long long mine = 0;
+        for (int m = lane; m < g.count; m += 32)
+            mine |= *(volatile unsigned long long *)&a.bitmaps[(uint64_t)(g.first + m) * a.bm_words + w];
+        const unsigned long long occ = (unsigned long long)__reduce_or_sync(0xffffffffu, (unsigned)mine) |
+                                       ((unsigned long long)__reduce_or_sync(0xffffffffu, (unsigned)(mine >> 32)) << 32);
         for (int b = 0; b < 64; b++) {
             const uint32_t page = w * 64 + b;
             if (page >= a.pages_per_pe) return false;
@@ -343,8 +389,8 @@ __device__ bool find_pages(const SvArgs &a, const Geo &g, uint32_t need, uint32_
     return false;
 }
 
-__device__ void mark_pages(const SvArgs &a, int first_pe, int count, uint32_t p0, uint32_t np, bool set) {
-    for (int m = 0; m < count; m++) {
+__device__ void mark_pages(const SvArgs &a, int first_pe, int count, uint32_t p0, uint32_t np, bool set, int lane) {
+    for (int m = lane; m < count; m += 32) {
         unsigned long long *bm = a.bitmaps + (uint64_t)(first_pe + m) * a.bm_words;
         for (uint32_t p = p0; p < p0 + np;) {
             const uint32_t w = p / 64, b = p % 64;
@@ -355,6 +401,7 @@ __device__ void mark_pages(const SvArgs &a, int first_pe, int count, uint32_t p0
             p += nb;
         }
     }
+    __syncwarp();
 }
 
 // Admission state of the admitter (lane 0 of CTA 0's first warp).
@@ -374,46 +421,57 @@ __device__ __forceinline__ void adm_flush(const SvArgs &a, AdmState &st) {
 }
 
 // Tries to admit one request: 1 = admitted (or completed with an error), 0 = no slot,
-// queue room or pages yet (retry later).
-__device__ int adm_try(const SvArgs &a, AdmState &st, const shmemg_req_t &r, uint64_t now) {
+// queue room or pages yet (retry later).  Warp-collective: every lane computes the same
+// verdict (lane 0's reads are broadcast); lane 0 writes the slot and the queue.
+__device__ int adm_try(const SvArgs &a, AdmState &st, const shmemg_req_t &r, uint64_t now, int lane) {
     const Geo g = geometry(r, a.npes, a.H, a.cfg.amo_words);
     if (!g.valid) {
-        write_completion(a, r.ticket, now, 0, SHMEMG_ERR_INVALID_ARG);
+        if (lane == 0) write_completion(a, r.ticket, now, 0, SHMEMG_ERR_INVALID_ARG);
+        __syncwarp();
         return 1;
     }
     const uint32_t need = (uint32_t)((g.bytes + a.cfg.page_bytes - 1) / a.cfg.page_bytes);
     if (need > a.pages_per_pe) {
-        write_completion(a, r.ticket, now, 0, SHMEMG_ERR_OUT_OF_HEAP);
+        if (lane == 0) write_completion(a, r.ticket, now, 0, SHMEMG_ERR_OUT_OF_HEAP);
+        __syncwarp();
         return 1;
     }
-    if (st.fifo_tail - *(volatile unsigned long long *)&a.ctl->fifo_head >= a.fifo_cap) return 0;
     int slot = -1;
-    for (uint32_t i = 0; i < a.nslots; i++) {
-        const uint32_t s = (st.rot + i) % a.nslots;
-        if (*(volatile unsigned int *)&a.slots[s].busy == 0) { slot = (int)s; break; }
+    if (lane == 0 && st.fifo_tail - *(volatile unsigned long long *)&a.ctl->fifo_head < a.fifo_cap) {
+        for (uint32_t i = 0; i < a.nslots; i++) {
+            const uint32_t k = (st.rot + i) % a.nslots;
+            if (*(volatile unsigned int *)&a.slots[k].busy == 0) { slot = (int)k; break; }
+        }
     }
+    slot = __shfl_sync(0xffffffffu, slot, 0);
     if (slot < 0) return 0;
     uint32_t p0 = 0;
-    if (!find_pages(a, g, need, &p0)) return 0;
+    if (!find_pages(a, g, need, &p0, lane)) return 0;
     shmemg_d_fence_gpu();  // page frees and slot releases seen above happen before reuse
-    mark_pages(a, g.first, g.count, p0, need, true);
+    mark_pages(a, g.first, g.count, p0, need, true, lane);
     SvSlot &s = a.slots[slot];
-    const uint32_t gen = s.gen + 1;
-    s.req = r;
-    s.dst_off = a.cfg.arena_offset + (uint64_t)p0 * a.cfg.page_bytes;
-    s.page0 = p0;
-    s.npages = need;
-    s.ntiles = g.ntiles;
-    s.gen = gen;
-    s.done = 0;
-    s.checksum = 0;
-    s.t_admit = now;
-    s.status = 0;
-    s.busy = 1;
-    // release: a worker whose fetch-and-add sees this generation also sees the fields above
-    asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(&s.claim), "l"((unsigned long long)gen << 32) : "memory");
-    atomicAdd(&a.ctl->inflight, 1ull);
-    a.fifo[st.fifo_tail % a.fifo_cap] = ((unsigned long long)gen << 32) | (unsigned)slot;
+    if (lane == 0) {
+        const uint32_t gen = s.gen + 1;
+        s.req = r;
+        s.dst_off = a.cfg.arena_offset + (uint64_t)p0 * a.cfg.page_bytes;
+        s.page0 = p0;
+        s.npages = need;
+        s.ntiles = g.ntiles;
+        s.gen = gen;
+        s.done = 0;
+        s.checksum = 0;
+        s.t_admit = now;
+        s.status = 0;
+        s.busy = 1;
+        // release: a worker whose fetch-and-add sees this generation also sees the fields
+        // above (and the page marks, ordered before it by the warp barrier)
+        asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(&s.claim), "l"((unsigned long long)gen << 32)
+                     : "memory");
+        atomicAdd(&a.ctl->inflight, 1ull);
+        a.fifo[st.fifo_tail % a.fifo_cap] = ((unsigned long long)gen << 32) | (unsigned)slot;
+        s.t_pub = now_dev();
+    }
+    __syncwarp();
     st.fifo_tail++;
     st.rot = (uint32_t)slot + 1;
     return 1;
@@ -476,25 +534,32 @@ __device__ void admitter_warp(const SvArgs &a) {
         }
         __syncwarp();
         int admitted = 0;
-        if (lane == 0) {
-            const uint64_t now = now_dev();
-            for (int i = s_npend; i < s_npend + nnew; i++) s_since[i] = now;
-            int n = s_npend + nnew;
+        {
+            const uint64_t now = __shfl_sync(0xffffffffu, now_dev(), 0);
+            if (lane == 0)
+                for (int i = s_npend; i < s_npend + nnew; i++) s_since[i] = now;
+            __syncwarp();
+            const int n = s_npend + nnew;
             const bool aged = n > 0 && now - s_since[0] > AGE_NS;
             int k = 0;
-            for (int i = 0; i < n; i++) {
+            for (int i = 0; i < n; i++) {  // the whole warp admits, in order
                 const bool try_it = !aged || i == 0;
-                if (try_it && adm_try(a, st, s_pend[i], now)) {
+                if (try_it && adm_try(a, st, s_pend[i], now, lane)) {
                     admitted++;
                     continue;
                 }
-                if (k != i) {
+                if (k != i && lane == 0) {
                     s_pend[k] = s_pend[i];
                     s_since[k] = s_since[i];
                 }
+                __syncwarp();
                 k++;
             }
-            s_npend = k;
+            if (lane == 0) s_npend = k;
+            __syncwarp();
+        }
+        if (lane == 0) {
+            const uint64_t now = now_dev();
             adm_flush(a, st);
             if (nnew > 0)
                 asm volatile("st.release.sys.global.u64 [%0], %1;" ::"l"((const uint64_t *)&a.host->head), "l"(head)
@@ -515,54 +580,119 @@ __device__ void admitter_warp(const SvArgs &a) {
 }
 
 // ------------------------------------------------------------------ workers
-__device__ void finalize(const SvArgs &a, SvSlot &s) {
-    shmemg_d_fence_gpu();
+// Run by warp 0 of the worker whose publish completed the slot's tile count (every other
+// publisher's tiles and checksum terms happen before that acq_rel add): frees the pages
+// (lanes split the members), writes the completion record and releases the slot.
+__device__ void finalize(const SvArgs &a, SvSlot &s, int lane) {
     const shmemg_req_t r = s.req;
     const Geo g = geometry(r, a.npes, a.H, a.cfg.amo_words);
-    if (s.npages) mark_pages(a, g.first, g.count, s.page0, s.npages, false);
-    write_completion(a, r.ticket, s.t_admit, s.checksum, s.status);
-    atomicAdd(&a.ctl->inflight, ~0ull);  // -1
-    shmemg_d_fence_gpu();
-    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(&s.busy), "r"(0u) : "memory");
+    if (s.npages) mark_pages(a, g.first, g.count, s.page0, s.npages, false, lane);
+    if (lane == 0) {
+        write_completion(a, r.ticket, s.t_admit, s.checksum, s.status);
+        atomicAdd(&a.ctl->inflight, ~0ull);  // -1
+        // the release orders the page frees (warp barrier above) and the count before the
+        // slot's reuse
+        asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(&s.busy), "r"(0u) : "memory");
+    }
+    __syncwarp();
 }
 
-// Claims tile k of whatever request slot s holds now: fetch-and-add on the slot's
-// (generation, next tile) word, then an acquire fence (the admitter published the slot
-// with a release store of that word).  A claimed k < ntiles is always executed, even by
-// a worker that came from an older queue entry of the same slot, so no index is lost.
-__device__ __forceinline__ bool claim_tile(const SvArgs &a, uint32_t slot, uint32_t *tile) {
+// Publishes `cnt` finished tiles of slot s with their checksum terms (AMO: the fetched
+// value): one acq_rel add on the tile count -- release for this CTA's tile writes
+// (ordered before it by a CTA barrier) and the checksum, acquire for the other
+// publishers'.  True for the publisher that completes the count (it finalizes).
+__device__ __forceinline__ bool publish(const SvArgs &a, uint32_t slot, uint64_t sum, unsigned long long amo,
+                                        uint32_t cnt) {
     SvSlot &s = a.slots[slot];
-    const unsigned long long c = atomicAdd(&s.claim, 1ull);
-    shmemg_d_fence_gpu();
-    if ((uint32_t)c < *(volatile uint32_t *)&s.ntiles) {
-        *tile = (uint32_t)c;
+    const uint32_t kind = s.req.kind;
+    if (kind == SHMEMG_OP_FETCH_ADD || kind == SHMEMG_OP_COMPARE_SWAP || kind == SHMEMG_OP_FETCH_XOR) s.checksum = amo;
+    else atomicAdd(&s.checksum, (unsigned long long)sum);
+    unsigned int old;
+    asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(&s.done), "r"(cnt) : "memory");
+    return old + cnt == s.ntiles;
+}
+
+// Claims tiles [k, k + cnt) of whatever request slot s holds now: fetch-and-add of the
+// chunk size on the slot's (generation, next tile) word with acquire semantics (the
+// admitter published the slot with a release store of that word).  Big requests are
+// claimed in chunks (about half of an even share per worker), so the claim word and
+// the completion counter see few atomics; a claimed index below ntiles is always
+// executed, even by a worker that came from an older queue entry of the same slot, so
+// no index is lost.
+__device__ __forceinline__ bool claim_tiles(const SvArgs &a, uint32_t slot, uint32_t *tile, uint32_t *cnt) {
+    SvSlot &s = a.slots[slot];
+    const uint32_t nt = *(volatile uint32_t *)&s.ntiles;
+    // a plain look first: an exhausted request costs no atomic on its busy claim line
+    if ((uint32_t)*(volatile unsigned long long *)&s.claim >= nt) return false;
+    const uint32_t nworkers = gridDim.x - 1;
+    uint32_t chunk = nt / (2 * nworkers);
+    chunk = chunk < 1 ? 1 : chunk > 64 ? 64 : chunk;
+    unsigned long long c;
+    asm volatile("atom.acquire.gpu.global.add.u64 %0, [%1], %2;" : "=l"(c) : "l"(&s.claim), "l"((unsigned long long)chunk)
+                 : "memory");
+    const uint32_t k = (uint32_t)c, n = *(volatile uint32_t *)&s.ntiles;
+    if (k < n) {
+        *tile = k;
+        *cnt = k + chunk <= n ? chunk : n - k;
         return true;
     }
     return false;
 }
 
+// A worker CTA.  Thread 0 claims chunks of tiles, the CTA runs them; the finished tiles
+// of a slot are published together when the worker leaves the slot (its next claim there
+// fails) or at once when the chunk held the slot's last tile (nobody will claim after
+// it), so a worker that keeps claiming one request pays one publish for all its tiles.
+// Two workers share an SM; the first on each SM (its primary) gets a head start on a newly
+// queued request, so a request with fewer tiles than SMs spreads over distinct SMs
+// instead of doubling up on some while others idle.  Idle workers watch only the queue
+// tail (one relaxed load) until it moves.
 __device__ void worker(const SvArgs &a) {
     __shared__ int s_cmd;
-    __shared__ uint32_t s_slot, s_tile;
+    __shared__ int s_fin;  // slot whose count this CTA's publish completed (warp 0 finalizes), -1 none
+    __shared__ uint32_t s_slot, s_tile, s_cnt;
     __shared__ unsigned long long s_amo;
     const uint32_t me = blockIdx.x - 1;
+    bool primary = true;
+    if (threadIdx.x == 0) s_fin = -1;
+    if (threadIdx.x == 0) {
+        uint32_t smid;
+        asm volatile("mov.u32 %0, %%smid;" : "=r"(smid));
+        primary = atomicAdd(&a.ctl->sm_workers[smid % SV_MAX_SMID], 1u) == 0;
+    }
+    const uint32_t max_sleep = primary ? 256 : 1024;
+    unsigned long long idle_tail = ~0ull;  // thread 0: queue tail of the last scan that found it empty
     uint32_t sleep_ns = 32;
-    int sticky = -1;  // slot of the last claim: try it again first
+    int sticky = -1;                    // slot of the last claim: try it again first
+    uint32_t pend_cnt = 0;              // thread 0: finished, unpublished tiles of `sticky`
+    uint64_t pend_sum = 0;
+    unsigned long long pend_amo = 0;
     for (;;) {
         if (threadIdx.x == 0) {
             int cmd = 0;
-            uint32_t tile;
-            if (sticky >= 0 && claim_tile(a, (uint32_t)sticky, &tile)) {
+            uint32_t tile, cnt;
+            if (sticky >= 0 && claim_tiles(a, (uint32_t)sticky, &tile, &cnt)) {
                 s_slot = (uint32_t)sticky;
                 s_tile = tile;
+                s_cnt = cnt;
                 cmd = 1;
+            } else {
+                if (pend_cnt && publish(a, (uint32_t)sticky, pend_sum, pend_amo, pend_cnt))  // leaving the slot
+                    s_fin = sticky;
+                pend_cnt = 0;
+                pend_sum = 0;
+                sticky = -1;
             }
-            sticky = -1;
             for (int tries = 0; tries < 64 && cmd == 0; tries++) {
                 if (*(volatile unsigned int *)&a.ctl->exit_flag) { cmd = -1; break; }
+                if (idle_tail != ~0ull && *(volatile unsigned long long *)&a.ctl->fifo_tail == idle_tail) break;
                 const unsigned long long h = shmemg_d_ld_acquire_u64((const uint64_t *)&a.ctl->fifo_head);
                 const unsigned long long t = shmemg_d_ld_acquire_u64((const uint64_t *)&a.ctl->fifo_tail);
-                if (h >= t) break;
+                if (h >= t) {
+                    idle_tail = t;  // nothing queued: nothing new until the tail moves
+                    break;
+                }
+                idle_tail = ~0ull;
                 const uint32_t live = (uint32_t)((t - h) < WINDOW ? (t - h) : WINDOW);
                 const uint32_t start = me % live;
                 for (uint32_t j = 0; j < live && cmd == 0; j++) {
@@ -575,44 +705,65 @@ __device__ void worker(const SvArgs &a) {
                         if (pos == h) atomicCAS(&a.ctl->fifo_head, h, h + 1);  // exhausted or stale head
                         continue;
                     }
-                    if (claim_tile(a, slot, &tile)) {
+                    if (!primary && now_dev() - *(volatile uint64_t *)&s.t_pub < SECONDARY_DELAY_NS) continue;
+                    if (claim_tiles(a, slot, &tile, &cnt)) {
                         s_slot = slot;
                         s_tile = tile;
+                        s_cnt = cnt;
                         sticky = (int)slot;
                         cmd = 1;
                     }
                 }
             }
-            if (cmd == 1) sticky = (int)s_slot;
             s_cmd = cmd;
         }
         __syncthreads();
+        if (s_fin >= 0) {  // warp 0 finalizes the request this CTA completed
+            if (threadIdx.x < 32) finalize(a, a.slots[s_fin], threadIdx.x);
+            __syncthreads();
+            if (threadIdx.x == 0) s_fin = -1;
+        }
         const int cmd = s_cmd;
         if (cmd < 0) break;
         if (cmd == 0) {
             __syncthreads();
             __nanosleep(sleep_ns);
-            if (sleep_ns < 1024) sleep_ns <<= 1;
+            if (sleep_ns < max_sleep) sleep_ns <<= 1;
             continue;
         }
         sleep_ns = 32;
         SvSlot &s = a.slots[s_slot];
         const shmemg_req_t r = s.req;
-        const uint64_t part = run_tile(a, r, s.dst_off, s_tile, &s_amo);
-        const uint64_t sum = block_sum_u64(part);
+        const uint32_t t0 = s_tile, cnt = s_cnt;
+        uint64_t part = 0;
+        for (uint32_t k = 0; k < cnt; k++) {
+            part += run_tile(a, r, s.dst_off, t0 + k, &s_amo);
+            __syncthreads();  // (an AMO's fetched value is in s_amo)
+        }
+        const uint64_t sum = block_sum_u64(part);  // ends with a CTA barrier: the tiles are written
         if (threadIdx.x == 0) {
-            if (r.kind == SHMEMG_OP_FETCH_ADD || r.kind == SHMEMG_OP_COMPARE_SWAP || r.kind == SHMEMG_OP_FETCH_XOR)
-                s.checksum = s_amo;
-            else
-                atomicAdd(&s.checksum, (unsigned long long)sum);
-            shmemg_d_fence_gpu();
-            if (atomicAdd(&s.done, 1u) == s.ntiles - 1) finalize(a, s);
+            pend_sum += sum;
+            pend_amo = s_amo;
+            pend_cnt += cnt;
+            if (t0 + cnt >= s.ntiles) {  // the slot's last tile: nobody claims after this chunk
+                if (publish(a, s_slot, pend_sum, pend_amo, pend_cnt)) s_fin = (int)s_slot;
+                pend_cnt = 0;
+                pend_sum = 0;
+                sticky = -1;
+            }
         }
         __syncthreads();
+        if (s_fin >= 0) {
+            if (threadIdx.x < 32) finalize(a, a.slots[s_fin], threadIdx.x);
+            __syncthreads();
+            if (threadIdx.x == 0) s_fin = -1;
+            __syncthreads();
+        }
     }
+    // (no unpublished tiles can remain here: the kernel exits only once nothing is in flight)
 }
 
-__global__ void __launch_bounds__(SV_THREADS, 2) k_server(SvArgs a) {
+__global__ void __launch_bounds__(SRV_THREADS, 2) k_server(SvArgs a) {
     if (blockIdx.x == 0) {
         if (threadIdx.x < 32) admitter_warp(a);
         return;
@@ -759,14 +910,14 @@ int shmemg_server_start(const shmemg_server_cfg_t *cfg_in, void *stream, shmemg_
     if ((rc = cuda_rc(cudaHostGetDevicePointer(&p, s->comp, 0)))) { server_free(s); return rc; }
     a.comp = (shmemg_completion_t *)p;
     int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_server, SV_THREADS, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_server, SRV_THREADS, 0);
     int cap = per_sm * S.sm_count;
     int workers = cfg.workers > 0 ? cfg.workers : cap - 1;
     if (workers < 1 || workers + 1 > cap) { server_free(s); return SHMEMG_ERR_UNSUPPORTED; }
     s->stream = to_stream(stream);
     cudaLaunchConfig_t lc = {};
     lc.gridDim = dim3(workers + 1);
-    lc.blockDim = dim3(SV_THREADS);
+    lc.blockDim = dim3(SRV_THREADS);
     lc.stream = s->stream;
     cudaLaunchAttribute at;
     at.id = cudaLaunchAttributeCooperative;

@@ -166,7 +166,7 @@ int shmemg_team_translate_pe(shmemg_team_t src_team, int src_pe, shmemg_team_t d
 #define SHMEMG_CAP_DEVICE_COLL (1ull << 4)
 #define SHMEMG_CAP_STREAM_ORDERED (1ull << 5)      /* host ops take a stream */
 #define SHMEMG_CAP_DEVICE_CTX_DEFAULT (1ull << 6)
-#define SHMEMG_CAP_EXPLICIT_DEVICE_CTX (1ull << 7) /* not provided */
+#define SHMEMG_CAP_EXPLICIT_DEVICE_CTX (1ull << 7) /* explicit device contexts (script ops) */
 #define SHMEMG_CAP_DEVICE_TEAMS (1ull << 8)
 #define SHMEMG_CAP_PTR_DEVICE (1ull << 9)          /* shmemg_ptr valid in device code */
 #define SHMEMG_CAP_PTR_HOST (1ull << 10)           /* not provided */
@@ -193,7 +193,7 @@ typedef struct {
     int32_t cluster_dim;
     int32_t team_n_pes;
     int32_t shared_team_size;   /* PEs in the caller's device shared team (locality) */
-    int32_t reserved0;
+    int32_t device_ctx_count;   /* device contexts per PE: the default + explicit ones */
     uint64_t heap_bytes_per_pe;
     uint64_t heap_free_bytes;   /* largest free symmetric range */
     uint64_t wait_timeout_ns;
@@ -311,10 +311,21 @@ enum {
  * with the same result as the PE-scope form; on other kinds it is invalid. */
 #define SHMEMG_OP_KIND_MASK 0xFFu
 #define SHMEMG_OP_WARP 0x100u
+/* Device contexts (Sec. 6.2): `sub` of put_nbi / get_nbi picks the context, 0 = the
+ * default device context, 1..SHMEMG_DEVICE_CTX_COUNT-1 explicit contexts; `sub` of
+ * quiet / fence picks the context it completes, or SHMEMG_CTX_ALL.  Each explicit
+ * context is an independent completion domain: its non-blocking transfers move in the
+ * background (TMA bulk copies advanced at every later op of the PE) and only quiet or
+ * fence on that context -- or on all -- waits for them; barriers and collectives quiet
+ * the default context only.  Every context is complete when the script ends.
+ * Transfers whose addresses or length are not 16-byte multiples (or with the bulk
+ * engine off) complete at once, as on the default context. */
+#define SHMEMG_DEVICE_CTX_COUNT 4
+#define SHMEMG_CTX_ALL 0xFF
 typedef struct {
     uint32_t kind;     /* SHMEMG_OP_* | flags */
     uint8_t dtype;     /* AMO / reduce element type */
-    uint8_t sub;       /* reduce op, signal op, or wait comparison */
+    uint8_t sub;       /* reduce op, signal op, wait comparison, or context (nbi, quiet, fence) */
     uint16_t team;     /* collectives */
     int32_t pe;        /* target PE (RMA, AMO, signal); root team rank (broadcast) */
     int32_t issuer;    /* issuing PE (RMA, AMO, signal, wait); -1 for collectives */

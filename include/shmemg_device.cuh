@@ -156,6 +156,10 @@ static __device__ __forceinline__ void shmemg_d_pe_sync(const shmemg_device_ctx_
     if (c.pe_mode == SHMEMG_PE_MODE_CLUSTER) shmemg_d_cluster_sync();
     else __syncthreads();
 }
+/* the PE's first CTA (its only CTA in pe_mode CTA) */
+static __device__ __forceinline__ bool shmemg_d_pe_leader_cta(const shmemg_device_ctx_t &c) {
+    return c.pe_mode != SHMEMG_PE_MODE_CLUSTER || shmemg_d_cluster_ctarank() == 0;
+}
 static __device__ __forceinline__ bool shmemg_d_pe_leader(const shmemg_device_ctx_t &c) {
     return threadIdx.x == 0 && (c.pe_mode != SHMEMG_PE_MODE_CLUSTER || shmemg_d_cluster_ctarank() == 0);
 }

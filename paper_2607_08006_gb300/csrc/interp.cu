@@ -34,6 +34,110 @@ __device__ __forceinline__ void pe_copy(const shmemg_device_ctx_t &c, shmemg_gro
     }
 }
 
+// ---------------------------------------------------------------- explicit contexts
+// Explicit device contexts (Sec. 6.2: contexts as independent ordering and completion
+// domains, an optional resource-limited feature beside the default device context).
+// Context k (1..SHMEMG_DEVICE_CTX_COUNT-1) of a PE is served by one thread of the PE's
+// leader CTA, thread 32*k, with a ring of CTX_STAGES shared-memory stages, one mbarrier
+// per stage and the thread's own bulk-group queue: its put_nbi / get_nbi are queued and
+// moved chunk by chunk with TMA bulk copies (global -> shared -> global) that run while
+// the PE goes on with later ops -- the thread advances them without blocking at every op
+// boundary -- and only quiet / fence on that context (or on all of them) waits for them.
+// Context 0, the default context, completes its non-blocking ops as it issues them.
+constexpr int CTX_STAGES = 2;
+constexpr uint32_t CTX_CHUNK = 12u << 10;
+constexpr int CTX_QCAP = 8;
+constexpr size_t CTX_SMEM = (size_t)(SHMEMG_DEVICE_CTX_COUNT - 1) * CTX_STAGES * CTX_CHUNK;
+
+struct CtxXfer {
+    uint64_t dst, src, n;  // generic global addresses, 16-byte multiples
+};
+// Chunks are numbered across the context's transfers; chunk k uses stage k % CTX_STAGES,
+// its load completes phase (k / CTX_STAGES) & 1 of that stage's mbarrier.
+struct CtxState {
+    CtxXfer q[CTX_QCAP];
+    uint32_t head, tail;              // queued transfers; q[head] is being loaded
+    uint64_t off;                     // bytes of q[head] whose loads are issued
+    uint64_t ld, st;                  // chunks whose loads / stores are issued
+    uint64_t st_dst[CTX_STAGES];      // where each stage's chunk goes, and its length
+    uint32_t st_len[CTX_STAGES];
+    uint64_t bar[CTX_STAGES];
+};
+
+__device__ __forceinline__ bool ctx_mbar_test(uint64_t *bar, uint32_t parity) {
+    uint32_t done;
+    asm volatile("{\n\t.reg .pred p;\n\tmbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+                 : "=r"(done)
+                 : "r"(shmemg_smem_u32(bar)), "r"(parity)
+                 : "memory");
+    return done != 0;
+}
+
+// Issues what can be issued now without waiting: stores of chunks whose loads have
+// landed, then loads into stages whose previous chunk's store has read them.
+__device__ __forceinline__ void ctx_progress(CtxState &x, uint8_t *ring) {
+    while (x.st < x.ld) {
+        const uint32_t s = (uint32_t)(x.st % CTX_STAGES);
+        if (!ctx_mbar_test(&x.bar[s], (uint32_t)((x.st / CTX_STAGES) & 1))) break;
+        shmemg_bulk_store((void *)x.st_dst[s], ring + (size_t)s * CTX_CHUNK, x.st_len[s]);
+        x.st++;
+    }
+    while (x.head != x.tail && x.ld < x.st + CTX_STAGES) {
+        if (x.ld >= CTX_STAGES) {  // the stage's previous chunk: its store must have read it
+            const uint32_t newer = (uint32_t)(x.st - (x.ld - CTX_STAGES) - 1);
+            if (newer == 0) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+            else asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");  // CTX_STAGES == 2: newer <= 1
+        }
+        const CtxXfer &t = x.q[x.head % CTX_QCAP];
+        const uint32_t len = (uint32_t)(t.n - x.off < CTX_CHUNK ? t.n - x.off : CTX_CHUNK);
+        const uint32_t s = (uint32_t)(x.ld % CTX_STAGES);
+        x.st_dst[s] = t.dst + x.off;
+        x.st_len[s] = len;
+        shmemg_bulk_load(ring + (size_t)s * CTX_CHUNK, (const void *)(t.src + x.off), len, &x.bar[s]);
+        x.ld++;
+        x.off += len;
+        if (x.off == t.n) {
+            x.head++;
+            x.off = 0;
+        }
+    }
+}
+
+// Completes every transfer of the context (bounded waits; a load that never lands is
+// recorded as a timeout) and makes its writes visible to generic loads.
+__device__ __forceinline__ void ctx_drain(const shmemg_device_ctx_t &c, CtxState &x, uint8_t *ring) {
+    for (;;) {
+        ctx_progress(x, ring);
+        if (x.head == x.tail && x.st == x.ld) break;
+        if (x.st < x.ld) {
+            const uint32_t s = (uint32_t)(x.st % CTX_STAGES);
+            if (!shmemg_mbar_wait(&x.bar[s], (uint32_t)((x.st / CTX_STAGES) & 1), c.timeout_ns)) {
+                shmemg_d_set_status(c, SHMEMG_ERR_TIMEOUT, -3);
+                break;
+            }
+        }
+    }
+    asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+}
+
+__device__ __forceinline__ void ctx_enqueue(const shmemg_device_ctx_t &c, CtxState &x, uint8_t *ring, uint64_t dst,
+                                            uint64_t src, uint64_t n) {
+    if (x.tail - x.head == CTX_QCAP) ctx_drain(c, x, ring);  // queue full: finish what is queued
+    asm volatile("fence.proxy.async.global;" ::: "memory");    // earlier generic writes -> async proxy
+    x.q[x.tail % CTX_QCAP] = {dst, src, n};
+    x.tail++;
+    ctx_progress(x, ring);
+}
+
+// A context moves a transfer in the background when the bulk engine is on and the bulk
+// copy's 16-byte rule holds; otherwise the op completes at once like the default
+// context's (completing earlier than quiet is always allowed).
+__device__ __forceinline__ bool ctx_aligned(const shmemg_device_ctx_t &, const void *d, const void *s, uint64_t n,
+                                            int use_bulk) {
+    return use_bulk && n > 0 && (((uint64_t)d | (uint64_t)s | n) & 15) == 0;
+}
+
 // Device-side check of one op (the same rules as the host's argument checks): PEs in
 // range, byte ranges inside a partition, AMO alignment, live teams.  Every thread of
 // every PE evaluates it on the same record, so the verdict is uniform.
@@ -54,8 +158,11 @@ __device__ __forceinline__ bool op_valid(const shmemg_device_ctx_t &c, const shm
         }
     }
     switch (kind) {
-    case SHMEMG_OP_PUT: case SHMEMG_OP_PUT_NBI: case SHMEMG_OP_GET: case SHMEMG_OP_GET_NBI:
+    case SHMEMG_OP_PUT: case SHMEMG_OP_GET:
         return pe_ok(o.pe) && pe_ok(o.issuer) && in(o.dst, o.n) && in(o.src, o.n);
+    case SHMEMG_OP_PUT_NBI: case SHMEMG_OP_GET_NBI:  // sub: the context
+        return pe_ok(o.pe) && pe_ok(o.issuer) && in(o.dst, o.n) && in(o.src, o.n) &&
+               o.sub < SHMEMG_DEVICE_CTX_COUNT && (o.sub == 0 || !flags);
     case SHMEMG_OP_FETCH_ADD: case SHMEMG_OP_COMPARE_SWAP: case SHMEMG_OP_FETCH_XOR: {
         const uint64_t es = o.dtype == SHMEMG_INT64 ? 8 : o.dtype == SHMEMG_INT32 ? 4 : 0;
         return es && pe_ok(o.pe) && pe_ok(o.issuer) && in(o.dst, es) && o.dst % es == 0;
@@ -65,7 +172,9 @@ __device__ __forceinline__ bool op_valid(const shmemg_device_ctx_t &c, const shm
                o.sub <= SHMEMG_SIGNAL_ADD;
     case SHMEMG_OP_WAIT_UNTIL:
         return pe_ok(o.issuer) && in(o.dst, 8) && o.dst % 8 == 0 && o.sub <= SHMEMG_CMP_LE;
-    case SHMEMG_OP_QUIET: case SHMEMG_OP_FENCE: case SHMEMG_OP_BARRIER_ALL:
+    case SHMEMG_OP_QUIET: case SHMEMG_OP_FENCE:  // sub: the context, or SHMEMG_CTX_ALL
+        return o.sub < SHMEMG_DEVICE_CTX_COUNT || o.sub == SHMEMG_CTX_ALL;
+    case SHMEMG_OP_BARRIER_ALL:
         return true;
     default:
         break;
@@ -104,6 +213,21 @@ __global__ void __launch_bounds__(INTERP_THREADS) k_interp(shmemg_device_ctx_t c
     // bulk ring, which then serves as each CTA's DSMEM window (free between ops: every
     // bulk copy has drained)
     __shared__ shmemg_cluster_state_t s_cs;
+    // explicit contexts: served by thread 32*k of the leader CTA (with the bulk ring only)
+    __shared__ __align__(16) CtxState s_ctx[SHMEMG_DEVICE_CTX_COUNT - 1];
+    const int my_ctx = (use_bulk && shmemg_d_pe_leader_cta(c) && (threadIdx.x & 31) == 0 && threadIdx.x >= 32 &&
+                        threadIdx.x < 32 * SHMEMG_DEVICE_CTX_COUNT)
+                           ? (int)(threadIdx.x >> 5)
+                           : 0;
+    uint8_t *ctx_ring = my_ctx ? s_ring + SHMEMG_BULK_SMEM + (size_t)(my_ctx - 1) * CTX_STAGES * CTX_CHUNK : nullptr;
+    if (my_ctx) {
+        CtxState &x = s_ctx[my_ctx - 1];
+        x.head = x.tail = 0;
+        x.off = x.ld = x.st = 0;
+        for (int k = 0; k < CTX_STAGES; k++)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(shmemg_smem_u32(&x.bar[k])) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
     // (only when the launch really has clusters of cluster_dim CTAs: a launch without
     // them -- a profiler replaying it, say -- runs the shared team on the L2/HBM path and
     // never maps a peer CTA that does not exist)
@@ -140,6 +264,7 @@ __global__ void __launch_bounds__(INTERP_THREADS) k_interp(shmemg_device_ctx_t c
         const int64_t i = base + k;
         const shmemg_op_t o = s_ops[k];
         int rc = SHMEMG_SUCCESS;
+        if (my_ctx) ctx_progress(s_ctx[my_ctx - 1], ctx_ring);  // background transfers advance
         if (failed) {  // only in a clustered CTA-mode launch: walk on, through the barriers
             for (int b = cluster_barriers(o); b > 0; b--) shmemg_d_cluster_sync();
             continue;
@@ -159,7 +284,12 @@ __global__ void __launch_bounds__(INTERP_THREADS) k_interp(shmemg_device_ctx_t c
         switch (o.kind & SHMEMG_OP_KIND_MASK) {
         case SHMEMG_OP_PUT:
         case SHMEMG_OP_PUT_NBI:
-            if (o.issuer == me) {
+            if (o.issuer == me && o.kind == SHMEMG_OP_PUT_NBI && o.sub != 0 &&
+                ctx_aligned(c, shmemg_d_addr(c, o.pe, o.dst), shmemg_d_addr(c, me, o.src), o.n, use_bulk)) {
+                if (my_ctx == o.sub)  // queued on its context, moved in the background
+                    ctx_enqueue(c, s_ctx[my_ctx - 1], ctx_ring, (uint64_t)shmemg_d_addr(c, o.pe, o.dst),
+                                (uint64_t)shmemg_d_addr(c, me, o.src), o.n);
+            } else if (o.issuer == me) {
                 if (warp) {
                     if (active) shmemg_d_copy_group(gw, shmemg_d_addr(c, o.pe, o.dst), shmemg_d_addr(c, me, o.src), o.n);
                 } else {
@@ -171,7 +301,12 @@ __global__ void __launch_bounds__(INTERP_THREADS) k_interp(shmemg_device_ctx_t c
             break;
         case SHMEMG_OP_GET:
         case SHMEMG_OP_GET_NBI:
-            if (o.issuer == me) {
+            if (o.issuer == me && o.kind == SHMEMG_OP_GET_NBI && o.sub != 0 &&
+                ctx_aligned(c, shmemg_d_addr(c, me, o.dst), shmemg_d_addr(c, o.pe, o.src), o.n, use_bulk)) {
+                if (my_ctx == o.sub)
+                    ctx_enqueue(c, s_ctx[my_ctx - 1], ctx_ring, (uint64_t)shmemg_d_addr(c, me, o.dst),
+                                (uint64_t)shmemg_d_addr(c, o.pe, o.src), o.n);
+            } else if (o.issuer == me) {
                 if (warp) {
                     if (active) shmemg_d_copy_group(gw, shmemg_d_addr(c, me, o.dst), shmemg_d_addr(c, o.pe, o.src), o.n);
                 } else {
@@ -240,8 +375,11 @@ __global__ void __launch_bounds__(INTERP_THREADS) k_interp(shmemg_device_ctx_t c
             }
             break;
         case SHMEMG_OP_QUIET:
-        case SHMEMG_OP_FENCE:
-            if (o.issuer == me || o.issuer < 0) shmemg_d_quiet_pe(c);
+        case SHMEMG_OP_FENCE:  // fence on a context completes it too (ordering by completion)
+            if (o.issuer == me || o.issuer < 0) {
+                if (my_ctx && (o.sub == SHMEMG_CTX_ALL || o.sub == my_ctx)) ctx_drain(c, s_ctx[my_ctx - 1], ctx_ring);
+                shmemg_d_quiet_pe(c);
+            }
             break;
         case SHMEMG_OP_BARRIER_ALL:
             if (active) rc = shmemg_d_scope_sync(c, SHMEMG_TEAM_WORLD, i, nullptr, warp);
@@ -288,6 +426,9 @@ __global__ void __launch_bounds__(INTERP_THREADS) k_interp(shmemg_device_ctx_t c
         }
     }
     }
+    // every context's transfers complete before the PE ends (none may still read this
+    // CTA's shared memory when it exits)
+    if (my_ctx) ctx_drain(c, s_ctx[my_ctx - 1], ctx_ring);
     shmemg_d_quiet_pe(c);
     if (dsm) shmemg_d_cluster_end();  // no CTA leaves while a peer may still touch its shared memory
 }
@@ -364,12 +505,12 @@ extern "C" int shmemg_run_script(const shmemg_op_t *ops, int64_t nops, int64_t *
         const char *e = getenv("SHMEMG_BULK");
         bulk = (e && *e == '0') ? 0 : 1;
         if (bulk && cudaFuncSetAttribute((const void *)k_interp, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         SHMEMG_BULK_SMEM) != cudaSuccess) {
+                                         (int)(SHMEMG_BULK_SMEM + CTX_SMEM)) != cudaSuccess) {
             cudaGetLastError();
             bulk = 0;
         }
     }
     int use_bulk = bulk;
     void *args[] = {(void *)&c, (void *)&ops, (void *)&nops, (void *)&fetched, (void *)&use_bulk};
-    return launch_pe_grid((const void *)k_interp, args, use_bulk ? SHMEMG_BULK_SMEM : 0, to_stream(stream));
+    return launch_pe_grid((const void *)k_interp, args, use_bulk ? SHMEMG_BULK_SMEM + CTX_SMEM : 0, to_stream(stream));
 }

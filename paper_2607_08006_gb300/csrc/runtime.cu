@@ -383,7 +383,7 @@ int shmemg_query_capabilities(shmemg_team_t team, shmemg_caps_t *out) {
     memset(out, 0, sizeof(*out));
     out->flags = SHMEMG_CAP_GPU_AWARE_HOST | SHMEMG_CAP_DEVICE_RMA | SHMEMG_CAP_DEVICE_AMO | SHMEMG_CAP_DEVICE_SIGNAL |
                  SHMEMG_CAP_DEVICE_COLL | SHMEMG_CAP_STREAM_ORDERED | SHMEMG_CAP_DEVICE_CTX_DEFAULT |
-                 SHMEMG_CAP_DEVICE_TEAMS | SHMEMG_CAP_PTR_DEVICE | SHMEMG_CAP_PROGRESS_GPU |
+                 SHMEMG_CAP_DEVICE_TEAMS | SHMEMG_CAP_PTR_DEVICE | SHMEMG_CAP_PROGRESS_GPU | SHMEMG_CAP_EXPLICIT_DEVICE_CTX |
                  SHMEMG_CAP_PERSISTENT_SERVER | SHMEMG_CAP_BATCHED_COLL | SHMEMG_CAP_QUANTIZED_REDUCE;
     out->default_heap = SHMEMG_HEAP_GPU;
     out->path = SHMEMG_PATH_DIRECT_LOCAL_HBM;
@@ -397,6 +397,7 @@ int shmemg_query_capabilities(shmemg_team_t team, shmemg_caps_t *out) {
     out->cluster_dim = s.cluster_dim;
     out->team_n_pes = t.size;
     out->shared_team_size = s.teams[SHMEMG_TEAM_SHARED].size;
+    out->device_ctx_count = SHMEMG_DEVICE_CTX_COUNT;
     out->heap_bytes_per_pe = s.H;
     uint64_t best = 0;
     for (auto &f : s.free_ranges) best = f.second > best ? f.second : best;

@@ -60,7 +60,7 @@ class Caps(C.Structure):
     _fields_ = [("flags", C.c_uint64), ("default_heap", C.c_int32), ("path", C.c_int32), ("rma_scopes", C.c_uint32),
                 ("coll_scopes", C.c_uint32), ("device_ordinal", C.c_int32), ("pe_mode", C.c_int32),
                 ("cluster_dim", C.c_int32), ("team_n_pes", C.c_int32), ("shared_team_size", C.c_int32),
-                ("reserved0", C.c_int32), ("heap_bytes_per_pe", C.c_uint64), ("heap_free_bytes", C.c_uint64),
+                ("device_ctx_count", C.c_int32), ("heap_bytes_per_pe", C.c_uint64), ("heap_free_bytes", C.c_uint64),
                 ("wait_timeout_ns", C.c_uint64)]
 
 

@@ -29,18 +29,22 @@ def _dev(ops):
 
 
 def test_context_visibility(sg, heapf, orc):
-    """A default device context is reported and usable from device code; explicit
-    device contexts are not offered, and the capability says so (Sec. 6.2)."""
+    """A default device context is reported and usable from device code, and so are the
+    explicit contexts the capability reports (Sec. 6.2)."""
     npes, H = 4, 1 << 16
     h = heapf(npes, H)
     caps = sg.query_capabilities(sg.TEAM_WORLD)
-    assert "DEVICE_CTX_DEFAULT" in caps["flag_names"] and "EXPLICIT_DEVICE_CTX" not in caps["flag_names"]
+    assert "DEVICE_CTX_DEFAULT" in caps["flag_names"] and "EXPLICIT_DEVICE_CTX" in caps["flag_names"]
+    assert caps["device_ctx_count"] > 1
     ctx = sg.device_ctx()
     assert ctx.npes == npes and ctx.pe_stride == H
     init = random_heap(npes, H, 1)
     upload(h, init)
-    ops, dev = _dev([_rec(kind=W.OP_PUT, pe=3, issuer=0, dst=8192, src=0, n=1000)])
-    sg.run_script(dev, 1, None)          # device code on the default context
+    ops, dev = _dev([_rec(kind=W.OP_PUT, pe=3, issuer=0, dst=8192, src=0, n=1000),     # default context
+                     _rec(kind=W.OP_PUT_NBI, sub=caps["device_ctx_count"] - 1, pe=2, issuer=1, dst=16384, src=0,
+                          n=4096),                                                   # the last explicit one
+                     _rec(kind=W.OP_QUIET, sub=caps["device_ctx_count"] - 1, issuer=1)])
+    sg.run_script(dev, len(ops), None)
     ref = orc.Heap(npes, H, init)
     ref.run_script(ops)
     assert sg.get_status()[0] == 0 and first_diff(download(h), ref.mem) is None

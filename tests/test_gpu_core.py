@@ -16,7 +16,8 @@ def test_init_caps_malloc_ptr(sg, heapf, orc):
     for f in ("GPU_AWARE_HOST", "DEVICE_RMA", "DEVICE_AMO", "DEVICE_COLL", "DEVICE_CTX_DEFAULT", "DEVICE_TEAMS",
               "PTR_DEVICE", "STREAM_ORDERED", "PROGRESS_GPU"):
         assert f in caps["flag_names"]
-    assert "PTR_HOST" not in caps["flag_names"] and "EXPLICIT_DEVICE_CTX" not in caps["flag_names"]
+    assert "PTR_HOST" not in caps["flag_names"] and "EXPLICIT_DEVICE_CTX" in caps["flag_names"]
+    assert caps["device_ctx_count"] == 4
     assert caps["team_n_pes"] == 6 and caps["shared_team_size"] == 2 and caps["default_heap"] == 1
     assert sg.query_capabilities(sg.TEAM_SHARED)["team_n_pes"] == 2
     a = h.malloc(100)

@@ -1,0 +1,105 @@
+"""Explicit device contexts (Sec. 6.2): non-blocking puts and gets on contexts 1..3 move
+in the background and complete at quiet on their context (or on all); the final heap
+equals the oracle's (which applies every op at once) whenever the script quiets before it
+reads, in every PE mode; the queue, the kernel's end and invalid contexts are covered."""
+import numpy as np
+import pytest
+import torch
+
+import workloads as W
+from gpu_util import download, first_diff, random_heap, upload
+
+pytestmark = pytest.mark.gpu
+KiB, MiB = 1 << 10, 1 << 20
+ALL = 0xFF
+
+
+def _rec(**kw):
+    r = np.zeros((), dtype=W.OP_DTYPE)
+    r["issuer"] = -1
+    for k, v in kw.items():
+        r[k] = v
+    return r
+
+
+def _run(sg, h, orc, init, ops):
+    ops = np.array(ops, dtype=W.OP_DTYPE)
+    dev = torch.from_numpy(ops.view(np.uint8).copy()).cuda()
+    sg.clear_status()
+    sg.run_script(dev, len(ops), None)
+    torch.cuda.synchronize()
+    assert sg.get_status()[0] == 0
+    ref = orc.Heap(h.npes, h.H, init)
+    ref.run_script(ops)
+    return first_diff(download(h), ref.mem)
+
+
+@pytest.mark.parametrize("mode,cd", [(0, 1), (0, 2), (1, 2)])
+def test_context_transfers_bitexact(sg, heapf, orc, mode, cd):
+    npes, H = 8, 8 * MiB
+    h = heapf(npes, H, pe_mode=mode, cluster_dim=cd)
+    init = random_heap(npes, H, 30 + mode)
+    upload(h, init)
+    ops = []
+    for p in range(npes):
+        ops += [_rec(kind=W.OP_PUT_NBI, sub=1, pe=(p + 1) % npes, issuer=p, dst=2 * MiB, src=0, n=MiB + 48),
+                _rec(kind=W.OP_GET_NBI, sub=2, pe=(p + 2) % npes, issuer=p, dst=4 * MiB, src=MiB + 512, n=300 * KiB),
+                _rec(kind=W.OP_PUT_NBI, sub=3, pe=(p + 3) % npes, issuer=p, dst=5 * MiB + 8, src=8, n=1000),  # unaligned
+                _rec(kind=W.OP_PUT, pe=(p + 5) % npes, issuer=p, dst=6 * MiB + 4096 * p, src=64, n=4096)]
+    for p in range(npes):
+        ops += [_rec(kind=W.OP_QUIET, sub=1, issuer=p), _rec(kind=W.OP_QUIET, sub=2, issuer=p),
+                _rec(kind=W.OP_QUIET, sub=ALL, issuer=p)]
+    ops += [_rec(kind=W.OP_BARRIER_ALL)]
+    for p in range(npes):   # read what the contexts delivered
+        ops += [_rec(kind=W.OP_GET, pe=(p + 1) % npes, issuer=p, dst=7 * MiB, src=2 * MiB + 4096, n=64 * KiB)]
+    assert _run(sg, h, orc, init, ops) is None
+
+
+def test_context_queue_overflow_and_end_of_script(sg, heapf, orc):
+    """More transfers than a context queues (its queue drains to make room), and
+    transfers never quieted (the script's end completes them)."""
+    npes, H = 4, 4 * MiB
+    h = heapf(npes, H)
+    init = random_heap(npes, H, 41)
+    upload(h, init)
+    ops = []
+    for k in range(20):   # PE 0 queues 14 transfers on context 1 (8 fit), the rest on context 2
+        ops.append(_rec(kind=W.OP_PUT_NBI, sub=1 if k < 14 else 2, pe=1 + k % 3, issuer=0,
+                        dst=2 * MiB + 32 * KiB * k, src=16 * KiB * k, n=32 * KiB))
+    assert _run(sg, h, orc, init, ops) is None
+
+
+def test_context_overlaps_default_context_work(sg, heapf, orc):
+    """A large transfer on context 1 while the same PEs run blocking puts and
+    put_signal / wait pairs on the default context; only then quiet context 1."""
+    npes, H = 4, 32 * MiB
+    h = heapf(npes, H)
+    init = random_heap(npes, H, 52)
+    init.reshape(npes, H)[:, 31 * MiB:31 * MiB + 64] = 0
+    upload(h, init)
+    ops = [_rec(kind=W.OP_PUT_NBI, sub=1, pe=(p + 1) % npes, issuer=p, dst=16 * MiB, src=0, n=12 * MiB)
+           for p in range(npes)]
+    for k in range(50):
+        p = k % npes
+        ops.append(_rec(kind=W.OP_PUT, pe=(p + 2) % npes, issuer=p, dst=30 * MiB + 4096 * k, src=13 * MiB, n=4096))
+    ops.append(_rec(kind=W.OP_PUT_SIGNAL, sub=W.SIG_ADD, pe=1, issuer=0, dst=29 * MiB, src=14 * MiB, n=8192,
+                    operand=1, aux=31 * MiB))
+    ops.append(_rec(kind=W.OP_WAIT_UNTIL, sub=W.CMP_GE, issuer=1, dst=31 * MiB, operand=1))
+    ops += [_rec(kind=W.OP_QUIET, sub=1, issuer=p) for p in range(npes)]
+    ops.append(_rec(kind=W.OP_BARRIER_ALL))
+    assert _run(sg, h, orc, init, ops) is None
+
+
+@pytest.mark.parametrize("bad", [
+    dict(kind=W.OP_PUT_NBI, sub=4, pe=1, issuer=0, dst=0, src=4096, n=64),     # no context 4
+    dict(kind=W.OP_QUIET, sub=7, issuer=0),                                     # no context 7
+    dict(kind=W.OP_PUT_NBI | W.OP_WARP, sub=1, pe=1, issuer=0, dst=0, src=4096, n=64)])  # warp scope on a context
+def test_invalid_contexts_rejected(sg, heapf, bad):
+    h = heapf(2, 1 << 16)
+    ops = np.array([_rec(kind=W.OP_BARRIER_ALL), _rec(**bad)], dtype=W.OP_DTYPE)
+    sg.clear_status()
+    sg.run_script(torch.from_numpy(ops.view(np.uint8).copy()).cuda(), 2, None)
+    torch.cuda.synchronize()
+    code, detail = sg.get_status()
+    assert code == sg.ERR_INVALID_ARG and detail == 1
+    sg.clear_status()

@@ -572,6 +572,84 @@ def run_cluster_leg(torch, sg, rounds=200, reps=3, iters=10000):
     return out
 
 
+# ----------------------------------------------------------------------------- device contexts
+def run_ctx_leg(torch, sg, reps=3, big=32 * MiB, nsmall=100, small=8 * KiB):
+    """Explicit device contexts: 64 PEs (one CTA each) each move `big` bytes to a
+    neighbour and run `nsmall` blocking puts of `small` bytes to another, in one script:
+    the big transfer blocking on the default context, vs put_nbi on context 1 quieted at
+    the end (moving in the background while the small puts run), vs each part alone.
+    Also `nsmall` small puts each followed by a quiet on context 2 (independent of the big
+    transfer on context 1) vs by a quiet on all contexts.  Heaps compared."""
+    npes = 64
+    Hc = 2 * big + 2 * nsmall * small + MiB
+    heap = sg.Heap(npes, Hc)
+    out = {"npes": npes, "big_bytes": big, "small_ops": nsmall, "small_bytes": small}
+    try:
+        parts = heap.partitions()
+        parts.random_(0, 255)
+        init = parts.clone()
+        stream = torch.cuda.current_stream()
+        B0, S0 = big, 2 * big
+
+        def big_op(p, kind, ctx):
+            return (kind, 0, ctx, 0, (p + 1) % npes, p, B0, 0, big, 0, 0, 0)
+
+        def small_ops(p, k, quiet_ctx=None):
+            # (sources in the big transfer's source range: read-only, no race with it)
+            o = [(W.OP_PUT, 0, 0, 0, (p + 2) % npes, p, S0 + small * k, small * (k % 16), small, 0, 0, 0)]
+            if quiet_ctx is not None:
+                o.append((W.OP_QUIET, 0, quiet_ctx, 0, 0, p, 0, 0, 0, 0, 0, 0))
+            return o
+
+        def script(with_big, kind=W.OP_PUT, ctx=0, quiet_ctx=None, with_small=True):
+            ops = []
+            for p in range(npes):
+                if with_big:
+                    ops.append(big_op(p, kind, ctx))
+            if with_small:
+                for k in range(nsmall):
+                    for p in range(npes):
+                        ops += small_ops(p, k, quiet_ctx)
+            for p in range(npes):
+                ops.append((W.OP_QUIET, 0, 0xFF, 0, 0, p, 0, 0, 0, 0, 0, 0))
+            ops.append((W.OP_BARRIER_ALL, 0, 0, 0, 0, -1, 0, 0, 0, 0, 0, 0))
+            return np.array(ops, dtype=W.OP_DTYPE)
+
+        cases = {"blocking_big_then_small": script(True),
+                 "ctx1_big_with_small": script(True, W.OP_PUT_NBI, 1),
+                 "small_only": script(False),
+                 "blocking_big_only": script(True, with_small=False),
+                 "ctx1_big_only": script(True, W.OP_PUT_NBI, 1, with_small=False),
+                 "ctx1_big_small_quiet_ctx2": script(True, W.OP_PUT_NBI, 1, quiet_ctx=2),
+                 "ctx1_big_small_quiet_all": script(True, W.OP_PUT_NBI, 1, quiet_ctx=0xFF)}
+        res = {}
+        heaps = {}
+        for name, ops in cases.items():
+            dev = torch.from_numpy(ops.view(np.uint8).copy()).cuda()
+            times = []
+            for _ in range(reps + 1):
+                parts.copy_(init)
+                e0, e1 = _events(torch)
+                e0.record(stream)
+                sg.run_script(dev, len(ops), None, stream)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                times.append(e0.elapsed_time(e1))
+            res[name] = {"ms": round(float(np.median(times[1:])), 3), "ops": int(len(ops))}
+            heaps[name] = parts.clone()
+        out["cases"] = res
+        out["heaps_equal"] = bool(torch.equal(heaps["blocking_big_then_small"], heaps["ctx1_big_with_small"])) and \
+            bool(torch.equal(heaps["ctx1_big_with_small"], heaps["ctx1_big_small_quiet_ctx2"]))
+        out["overlap_saving_ms"] = round(res["blocking_big_then_small"]["ms"] - res["ctx1_big_with_small"]["ms"], 3)
+        out["quiet_ctx2_saving_ms"] = round(res["ctx1_big_small_quiet_all"]["ms"] - res["ctx1_big_small_quiet_ctx2"]["ms"], 3)
+        out["ctx1_GBps"] = round(npes * 2 * big / (res["ctx1_big_only"]["ms"] * 1e-3) / 1e9, 1)
+        out["blocking_GBps"] = round(npes * 2 * big / (res["blocking_big_only"]["ms"] * 1e-3) / 1e9, 1)
+        out["status"] = sg.get_status()[0]
+    finally:
+        heap.close()
+    return out
+
+
 # ----------------------------------------------------------------------------- halo exchange
 def run_halo(torch, sg, iters=100, reps=3):
     """The halo-exchange stencil (case study 1): 128 PEs as 16 x 8 tiles of 1024 x 1024
@@ -1142,9 +1220,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="shmemg", choices=["shmemg", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--secondary", default="script,amo,cluster,halo,batch,serve",
-                    help="extra workloads measured after the sweep (comma list of script,amo,cluster,halo,batch,"
-                         "serve or 'none')")
+    ap.add_argument("--secondary", default="script,amo,cluster,ctx,halo,batch,serve",
+                    help="extra workloads measured after the sweep (comma list of script,amo,cluster,ctx,halo,"
+                         "batch,serve or 'none')")
     ap.add_argument("--amo-ops-log2", type=int, default=30)
     ap.add_argument("--serve-requests", type=int, default=1 << 16)
     ap.add_argument("--profile", choices=PROFILE_CASES, help="run one small single-kernel case (for ncu) and exit")
@@ -1178,6 +1256,8 @@ def main():
                     r = run_cluster_leg(torch, sg)
                 elif name == "halo":
                     r = run_halo(torch, sg)
+                elif name == "ctx":
+                    r = run_ctx_leg(torch, sg)
                 elif name == "batch":
                     r = run_batch(torch, sg)
                 elif name == "serve":

@@ -652,15 +652,15 @@ def run_ctx_leg(torch, sg, reps=3, big=32 * MiB, nsmall=100, small=8 * KiB):
 
 # ----------------------------------------------------------------------------- halo exchange
 def run_halo(torch, sg, iters=100, reps=3):
-    """The halo-exchange stencil (case study 1): 128 PEs as 16 x 8 tiles of 1024 x 1024
-    binary32 (a 8192 x 16384 periodic grid, 512 MiB per buffer), `iters` Jacobi sweeps
+    """The halo-exchange stencil (case study 1): 152 PEs (one per SM) as 19 x 8 tiles of
+    1024 x 1024 binary32 (a 8192 x 19456 periodic grid, 608 MiB per buffer), `iters` Jacobi sweeps
     with the boundary stores fused into each sweep and one signal per neighbour (one
     launch), vs one launch per sweep; PE = one CTA and PE = a 2-CTA cluster.  GB/s of
     algorithmic bytes (every sweep reads and writes the grid, plus the halos); results of
     both forms compared bitwise; the oracle timed on one sweep of a 2048 x 4096 sample."""
     import oracle as orc
 
-    px, py, nx, ny = 16, 8, 1024, 1024
+    px, py, nx, ny = 19, 8, 1024, 1024
     npes = px * py
     hs = sg.halo_stride(nx, ny)
     tile_b, halo_b = 2 * nx * ny * 4, 2 * hs * 4

@@ -1136,7 +1136,7 @@ def run_serve(torch, sg, nreq=1 << 16, rates=None, npes=512, Hs=32 << 20):
 
 # ----------------------------------------------------------------------------- profiling cases
 PROFILE_CASES = ("interp_ring", "reduce", "reduce_f32", "broadcast", "alltoall", "amo", "batch_bf16", "qsum",
-                 "pingpong_cluster", "cluster_coll")
+                 "pingpong_cluster", "cluster_coll", "halo")
 
 
 def run_profile_case(name, launches=4):
@@ -1219,6 +1219,15 @@ def run_profile_case(name, launches=4):
         dev = torch.from_numpy(ops.view(np.uint8).copy()).cuda()
         for _ in range(launches):
             sg.run_script(dev, len(ops), None, s)
+    elif name == "halo":              # 8 x 8 PEs of 1024 x 1024 binary32 (256 MiB per buffer), 4 sweeps
+        px, py, nx, ny = 8, 8, 1024, 1024
+        tile_b, halo_b = 2 * nx * ny * 4, 2 * sg.halo_stride(nx, ny) * 4
+        heap = sg.Heap(px * py, (tile_b + halo_b + 64 + 4095) // 4096 * 4096)
+        heap.partitions().zero_()
+        heap.partitions()[:, :nx * ny * 4].view(torch.float32).normal_()
+        for _ in range(launches):
+            sg.halo_jacobi(heap.sym(0, tile_b), heap.sym(tile_b, halo_b), heap.sym(tile_b + halo_b, 32), px, py, nx,
+                           ny, 4, s)
     else:
         raise SystemExit(f"unknown profile case {name}")
     torch.cuda.synchronize()

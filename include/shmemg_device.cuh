@@ -488,25 +488,30 @@ static __device__ __forceinline__ int shmemg_d_signal_wait_until(const shmemg_de
 
 /* ------------------------------------------------------------------ barriers */
 /* Barrier of one team group, entered by the leader thread of each member PE after the
- * PE's own quiet.  Generation counting: read the generation, arrive; the last arrival
- * resets the count and releases the next generation; the others acquire-spin on it
- * (bounded).  Needs every member PE resident on the GPU at once. */
+ * PE's own quiet.  The slot's count (low half) and generation (high half) form one
+ * 64-bit word: a PE arrives with one acq_rel add of 1 (release for the PE's writes,
+ * ordered before it by the PE barrier; the old value gives the generation); the last
+ * arrival adds 2^32 - size, which resets the count and opens the next generation in one
+ * release; the others acquire-poll the word until the generation moves -- spinning at
+ * first, then backing off -- bounded.  Needs every member PE resident on the GPU at once. */
 static __device__ __forceinline__ int shmemg_d_team_barrier_leader(const shmemg_device_ctx_t &c, int bar_slot,
                                                                    uint32_t size, int64_t detail) {
     shmemg_dbar_t *b = (shmemg_dbar_t *)(c.state + SHMEMG_BARRIERS_OFF) + bar_slot;
-    shmemg_d_fence_gpu();
-    uint32_t gen = shmemg_d_ld_acquire_u32(&b->gen);
-    uint32_t arrived = atomicAdd(&b->count, 1u);
-    if (arrived == size - 1) {
-        b->count = 0;
-        shmemg_d_st_release_u32(&b->gen, gen + 1);
+    unsigned long long *w = (unsigned long long *)&b->count;  /* count | gen << 32 */
+    unsigned long long old;
+    asm volatile("atom.acq_rel.gpu.global.add.u64 %0, [%1], %2;" : "=l"(old) : "l"(w), "l"(1ull) : "memory");
+    const uint32_t gen = (uint32_t)(old >> 32);
+    if ((uint32_t)old == size - 1) {
+        asm volatile("red.release.gpu.global.add.u64 [%0], %1;" ::"l"(w), "l"((1ull << 32) - size) : "memory");
         return SHMEMG_SUCCESS;
     }
     uint64_t t0 = 0;
     uint32_t ns = 32;
     for (uint32_t it = 0;; it++) {
-        if (shmemg_d_ld_acquire_u32(&b->gen) != gen) return SHMEMG_SUCCESS;
-        if ((it & 63) == 0) {
+        unsigned long long v;
+        asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(w) : "memory");
+        if ((uint32_t)(v >> 32) != gen) return SHMEMG_SUCCESS;
+        if ((it & 63) == 63) {
             uint64_t now = shmemg_d_globaltimer();
             if (t0 == 0) t0 = now;
             else if (now - t0 > c.timeout_ns) {
@@ -515,8 +520,10 @@ static __device__ __forceinline__ int shmemg_d_team_barrier_leader(const shmemg_
             }
             if (shmemg_d_get_status(c) != 0) return SHMEMG_ERR_DEVICE;
         }
-        __nanosleep(ns);
-        if (ns < 512) ns <<= 1;
+        if (it >= 256) {  /* a long wait: stop hammering the line */
+            __nanosleep(ns);
+            if (ns < 512) ns <<= 1;
+        }
     }
 }
 

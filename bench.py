@@ -778,8 +778,8 @@ def _amo_ops(pool, seed, nops, bits, dist, ch=1 << 24):
 
 def run_amo(torch, sg, nops_log2=30, reps=3):
     """1024 PEs (one CTA each) over a 2^27-word int64 table; uniform and Zipf(1.1)
-    streams of 2^nops_log2 fetch_add/compare_swap/fetch_xor; GUPS with and without warp
-    aggregation, against an L2-resident table and the HBM-sector ceiling; then 512
+    streams of 2^nops_log2 fetch_add/compare_swap/fetch_xor; GUPS plain, warp-aggregated
+    and block-combined, against an L2-resident table and the HBM-sector ceiling; then 512
     put_signal/wait_until ping-pong pairs."""
     npes, wpp = 1024, 1 << 17
     Hh = wpp * 8 + 16384
@@ -808,7 +808,7 @@ def run_amo(torch, sg, nops_log2=30, reps=3):
             dops = torch.from_numpy(ops.view(np.int32)).cuda()
             del ops
             fetched = torch.empty(nops, dtype=torch.int64, device="cuda")
-            for agg in (0, 1):
+            for agg, name in ((0, "plain"), (1, "agg"), (2, "combine")):
                 sg.amo_stream(heap.base, wpp, dops, nops, oseed, tseed, fetched, flags=agg)
                 e0, e1 = _events(torch)
                 e0.record(s)
@@ -817,8 +817,7 @@ def run_amo(torch, sg, nops_log2=30, reps=3):
                 e1.record(s)
                 torch.cuda.synchronize()
                 ms = e0.elapsed_time(e1) / reps
-                out[f"{dist}_{'agg' if agg else 'plain'}"] = {"GUPS": round(nops / (ms * 1e-3) / 1e9, 3),
-                                                              "ms": round(ms, 3)}
+                out[f"{dist}_{name}"] = {"GUPS": round(nops / (ms * 1e-3) / 1e9, 3), "ms": round(ms, 3)}
             out[f"{dist}_generation_s"] = round(gen_s, 2)
             del dops, fetched
         # L2-resident reference: the same kernel on a table of 2^21 words (16 MiB), 2^26 ops
@@ -1135,7 +1134,7 @@ def run_serve(torch, sg, nreq=1 << 16, rates=None, npes=512, Hs=32 << 20):
 
 
 # ----------------------------------------------------------------------------- profiling cases
-PROFILE_CASES = ("interp_ring", "reduce", "reduce_f32", "broadcast", "alltoall", "amo", "batch_bf16", "qsum",
+PROFILE_CASES = ("interp_ring", "reduce", "reduce_f32", "broadcast", "alltoall", "amo", "amo_plain", "amo_combine", "amo_combine_zipf", "batch_bf16", "qsum",
                  "pingpong_cluster", "cluster_coll", "halo")
 
 
@@ -1188,6 +1187,15 @@ def run_profile_case(name, launches=4):
         f = torch.empty(nops, dtype=torch.int64, device="cuda")
         for _ in range(launches):
             sg.amo_stream(heap.base, wpp, ops, nops, 1, 2, f, 0, s)
+    elif name in ("amo_plain", "amo_combine", "amo_combine_zipf"):  # as "amo", 2^24 ops
+        wpp = 1 << 17
+        heap = sg.Heap(1024, wpp * 8)
+        nops = 1 << 24
+        dist = "zipf" if name.endswith("zipf") else "uniform"
+        ops = torch.from_numpy(W.amo_stream_np(1, nops, 27, dist=dist).view(np.int32)).cuda()
+        f = torch.empty(nops, dtype=torch.int64, device="cuda")
+        for _ in range(launches):
+            sg.amo_stream(heap.base, wpp, ops, nops, 1, 2, f, 0 if name == "amo_plain" else 2, s)
     elif name in ("batch_bf16", "qsum"):   # 64 PEs, bf16 payloads of 1 Mi elements
         n = 1 << 20
         heap = sg.Heap(64, 12 * n)

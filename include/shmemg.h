@@ -363,10 +363,15 @@ int shmemg_run_script_host(const shmemg_op_t *ops, int64_t nops, int64_t *fetche
  * (r mod 2^20) + 1, compare_swap swaps in r if the word equals its initial value
  * splitmix64(table_seed ^ w), fetch_xor xors r (1 if r is 0).  fetched[i] (device, may
  * be NULL) gets the old value.  flags bit 0: warp-aggregate fetch_add/fetch_xor on
- * equal targets (the aggregated ops are consecutive in the serial order).  An op whose
+ * equal targets (the aggregated ops are consecutive in the serial order).  flags bit 1
+ * (takes precedence): combine the ops of each CTA tile of 1024 that have the same word
+ * and code -- fetch_add, fetch_xor and compare_swap -- into one atomic per group (again
+ * consecutive in the serial order; a compare_swap whose swap value equals the compare
+ * value is applied on its own).  An op whose
  * word is >= npes*words_per_pe (or whose code is 3) is skipped and recorded in the
  * status word (SHMEMG_ERR_INVALID_ARG, detail = op index). */
 #define SHMEMG_AMO_AGGREGATE 1u
+#define SHMEMG_AMO_COMBINE_BLOCK 2u
 int shmemg_amo_stream(int64_t *table, uint64_t words_per_pe, const uint32_t *ops, uint64_t nops,
                       uint64_t op_seed, uint64_t table_seed, int64_t *fetched, uint32_t flags,
                       void *stream);

@@ -3,6 +3,8 @@
 // study 2 of Sec. 4.4: fine-grained atomics and polling flags in graph analytics).
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "internal.h"
 
 namespace shmemg {
@@ -147,6 +149,161 @@ __global__ void __launch_bounds__(AMO_THREADS) k_amo_stream(AmoArgs a) {
     }
 }
 
+// Block-combined stream.  PE p's range [p*nops/npes, (p+1)*nops/npes) is cut into tiles
+// of CB_TILE consecutive ops; a persistent grid (as many CTAs as are resident at once)
+// walks the tiles of all PEs, a CTA acting as the tile's PE (op j of a tile at thread
+// j % blockDim.x, CB_U per thread).  Ops of one tile with the same target word and
+// op code form a group through an open-addressing table in shared memory; the group is
+// applied to the word by ONE global atomic, and its ops take consecutive places in the
+// serial order (the order of their shared-memory atomics):
+//   fetch_add / fetch_xor -- each op's shared atomic on the group's accumulator returns
+//     the combined operand of the ops before it (its prefix); the op that inserted the
+//     key applies the total and every op fetches old + prefix (old ^ prefix);
+//   compare_swap -- all ops on word w compare against the same initial value c, so after
+//     the first op of a group the word holds either its old value (old != c) or the first
+//     op's swap value r0; provided no swap value equals c, the later ops all fail and
+//     fetch that value.  The first op (shared counter 0) issues CAS(c, r0); an op whose
+//     swap value equals c is applied on its own.
+// With Zipf-distributed targets this turns the serialised atomics on the hottest words
+// (about 11% of all ops land on one word at s = 1.1 over 2^27 words) into one atomic per
+// tile and group.
+constexpr int CB_THREADS = 256;
+constexpr int CB_U = 4;
+constexpr int CB_TILE = CB_THREADS * CB_U;
+constexpr int CB_SLOTS_LOG2 = CB_TILE == 1024 ? 11 : CB_TILE == 2048 ? 12 : CB_TILE == 512 ? 10 : 13;
+constexpr int CB_SLOTS = 1 << CB_SLOTS_LOG2;   // load factor <= 1/2
+static_assert(CB_SLOTS >= 2 * CB_TILE, "table load factor");
+constexpr int CB_MIN_BLOCKS = 4;
+constexpr size_t CB_SMEM = (size_t)CB_SLOTS * (8 + 4);
+
+__device__ __forceinline__ unsigned long long *amo_addr(const AmoArgs &a, uint32_t w) {
+    const uint64_t pe = a.wpp_log2 >= 0 ? (uint64_t)w >> a.wpp_log2 : w / a.wpp;
+    return (unsigned long long *)(a.heap + pe * a.H + a.table_off + (w - pe * a.wpp) * 8);
+}
+
+__global__ void __launch_bounds__(CB_THREADS, CB_MIN_BLOCKS) k_amo_combine(AmoArgs a) {
+    extern __shared__ __align__(16) unsigned char cb_smem[];
+    unsigned long long *s_acc = (unsigned long long *)cb_smem;   // accumulator / counter, then the fetched base
+    uint32_t *s_key = (uint32_t *)(s_acc + CB_SLOTS);            // (word << 2 | code) + 1, 0 = empty
+    __shared__ uint64_t s_tile[2];                    // [base, hi) of the CTA's current tile
+    const uint64_t tiles_per_pe = (a.nops / (uint64_t)a.npes + 1 + CB_TILE - 1) / CB_TILE;
+    const uint64_t ntiles = tiles_per_pe * (uint64_t)a.npes;
+    auto tile = [&](uint64_t t) {   // thread 0: tile t covers ops [base, hi) of its PE's range
+        const uint64_t p = t / tiles_per_pe;
+        s_tile[0] = a.nops * p / (uint64_t)a.npes + (t - p * tiles_per_pe) * CB_TILE;
+        s_tile[1] = a.nops * (p + 1) / (uint64_t)a.npes;
+    };
+    for (int j = threadIdx.x; j < CB_SLOTS; j += blockDim.x) {
+        s_key[j] = 0u;
+        s_acc[j] = 0ull;
+    }
+    if (threadIdx.x == 0 && blockIdx.x < ntiles) tile(blockIdx.x);
+    __syncthreads();
+    // per op: word, then slot (bits 0..CB_SLOTS_LOG2-1), role (next 2 bits: 0 inactive,
+    // 1 group member, 2 group issuer, 3 applied on its own) and code (2 bits); the prefix
+    constexpr int ROLE = CB_SLOTS_LOG2, CODE = CB_SLOTS_LOG2 + 2;
+    for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const uint64_t base = s_tile[0], hi = s_tile[1];
+        if (base >= hi) {            // uniform across the CTA
+            __syncthreads();
+            if (threadIdx.x == 0 && t + gridDim.x < ntiles) tile(t + gridDim.x);
+            __syncthreads();
+            continue;
+        }
+        uint32_t w[CB_U], sr[CB_U];
+        unsigned long long pre[CB_U];
+#pragma unroll
+        for (int k = 0; k < CB_U; k++) {
+            const uint64_t i = base + (uint64_t)k * blockDim.x + threadIdx.x;
+            sr[k] = 0u;
+            w[k] = 0u;
+            pre[k] = 0ull;
+            if (i >= hi) continue;
+            const uint32_t op = __ldcs(a.ops + i);
+            w[k] = op & ((1u << 27) - 1u);
+            const uint32_t code = (op >> 27) & 3u;
+            if (w[k] >= a.nwords || code == 3u) {
+                int *stw = (int *)(a.state + SHMEMG_STATUS_OFF);
+                if (atomicCAS(stw, 0, SHMEMG_ERR_INVALID_ARG) == 0) *(volatile int64_t *)(a.state + SHMEMG_STATUS_OFF + 8) = (int64_t)i;
+                continue;
+            }
+            const uint64_t r = cb64(a.op_seed, i);
+            unsigned long long opnd;
+            if (code == 1u) {
+                const uint64_t c = cb64(a.table_seed, w[k]);
+                if (r == c) {
+                    sr[k] = 3u << ROLE | code << CODE;
+                    const unsigned long long old = atomicCAS(amo_addr(a, w[k]), c, r);
+                    if (a.fetched) __stcs((unsigned long long *)a.fetched + i, old);
+                    continue;
+                }
+                opnd = 1ull;
+            } else {
+                opnd = code == 0u ? (r & ((1u << 20) - 1u)) + 1u : (r ? r : 1ull);
+            }
+            const uint32_t key = (w[k] << 2 | code) + 1u;
+            uint32_t h = (key * 0x9E3779B1u) >> (32 - CB_SLOTS_LOG2);
+            uint32_t prev = 0;
+            for (int q = 0; q < CB_SLOTS; q++) {   // an empty or matching slot always exists
+                prev = atomicCAS(&s_key[h], 0u, key);
+                if (prev == 0u || prev == key) break;
+                h = (h + 1) & (CB_SLOTS - 1);
+            }
+            pre[k] = code == 2u ? atomicXor(&s_acc[h], opnd) : atomicAdd(&s_acc[h], opnd);
+            const uint32_t role = (code == 1u ? pre[k] == 0ull : prev == 0u) ? 2u : 1u;
+            sr[k] = h | role << ROLE | code << CODE;
+        }
+        __syncthreads();
+        // issuers apply their group (all atomics issued before any result is used)
+        unsigned long long old[CB_U];
+#pragma unroll
+        for (int k = 0; k < CB_U; k++) {
+            old[k] = 0ull;
+            if ((sr[k] >> ROLE & 3u) != 2u) continue;
+            const uint32_t code = sr[k] >> CODE & 3u;
+            unsigned long long *p = amo_addr(a, w[k]);
+            if (code == 1u) {
+                old[k] = atomicCAS(p, cb64(a.table_seed, w[k]), cb64(a.op_seed, base + (uint64_t)k * blockDim.x + threadIdx.x));
+            } else {
+                const unsigned long long tot = s_acc[sr[k] & (CB_SLOTS - 1)];
+                old[k] = code == 0u ? atomicAdd(p, tot) : atomicXor(p, tot);
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < CB_U; k++) {
+            if ((sr[k] >> ROLE & 3u) != 2u) continue;
+            const uint32_t code = sr[k] >> CODE & 3u;
+            unsigned long long b = old[k];
+            if (code == 1u) {   // what the later ops of the group fetch
+                const uint64_t c = cb64(a.table_seed, w[k]);
+                b = old[k] == c ? cb64(a.op_seed, base + (uint64_t)k * blockDim.x + threadIdx.x) : old[k];
+            }
+            s_acc[sr[k] & (CB_SLOTS - 1)] = b;
+            if (a.fetched)
+                __stcs((unsigned long long *)a.fetched + base + (uint64_t)k * blockDim.x + threadIdx.x,
+                       code == 0u ? old[k] + pre[k] : code == 2u ? (old[k] ^ pre[k]) : old[k]);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < CB_U; k++) {
+            if ((sr[k] >> ROLE & 3u) != 1u || !a.fetched) continue;
+            const uint32_t code = sr[k] >> CODE & 3u;
+            const unsigned long long b = s_acc[sr[k] & (CB_SLOTS - 1)];
+            __stcs((unsigned long long *)a.fetched + base + (uint64_t)k * blockDim.x + threadIdx.x,
+                   code == 0u ? b + pre[k] : code == 2u ? (b ^ pre[k]) : b);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < CB_U; k++)
+            if ((sr[k] >> ROLE & 3u) == 2u) {
+                s_key[sr[k] & (CB_SLOTS - 1)] = 0u;
+                s_acc[sr[k] & (CB_SLOTS - 1)] = 0ull;
+            }
+        if (threadIdx.x == 0 && t + gridDim.x < ntiles) tile(t + gridDim.x);
+        __syncthreads();
+    }
+}
+
 // Ping-pong between PEs 2k and 2k+1 (one CTA each): put the payload into the peer's
 // buf + payload, release-add 1 to the peer's signal, acquire-wait for the own signal.
 // (at most 64 registers: 1024 ping-pong CTAs must be co-resident)
@@ -267,7 +424,7 @@ int shmemg_amo_stream(int64_t *table, uint64_t words_per_pe, const uint32_t *ops
     if ((uint64_t)S.npes * words_per_pe > (1ull << 27)) return SHMEMG_ERR_INVALID_ARG;  // 27-bit word index
     uint64_t off;
     if (sym_offset(table, words_per_pe * 8, &off) || (off & 7)) return SHMEMG_ERR_NOT_SYMMETRIC;
-    if (flags & ~SHMEMG_AMO_AGGREGATE) return SHMEMG_ERR_INVALID_ARG;
+    if (flags & ~(SHMEMG_AMO_AGGREGATE | SHMEMG_AMO_COMBINE_BLOCK)) return SHMEMG_ERR_INVALID_ARG;
     if (nops == 0) return SHMEMG_SUCCESS;
     AmoArgs a;
     a.heap = S.heap;
@@ -284,7 +441,17 @@ int shmemg_amo_stream(int64_t *table, uint64_t words_per_pe, const uint32_t *ops
     a.flags = flags;
     a.nwords = (uint64_t)S.npes * words_per_pe;
     a.state = S.base;
-    k_amo_stream<<<S.npes, AMO_THREADS, 0, to_stream(stream)>>>(a);
+    if (flags & SHMEMG_AMO_COMBINE_BLOCK) {
+        static int per_sm = 0;
+        if (!per_sm) {
+            if (cudaFuncSetAttribute((const void *)k_amo_combine, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CB_SMEM) != cudaSuccess ||
+                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_amo_combine, CB_THREADS, CB_SMEM) != cudaSuccess || per_sm < 1)
+                per_sm = 1;
+        }
+        const uint64_t tiles = ((nops / S.npes + 1 + CB_TILE - 1) / CB_TILE) * S.npes;
+        const int grid = (int)std::min<uint64_t>(tiles, (uint64_t)per_sm * S.sm_count);
+        k_amo_combine<<<grid, CB_THREADS, CB_SMEM, to_stream(stream)>>>(a);
+    } else k_amo_stream<<<S.npes, AMO_THREADS, 0, to_stream(stream)>>>(a);
     return cuda_rc(cudaGetLastError());
 }
 

@@ -30,6 +30,7 @@ FMT_BF16, FMT_E4M3 = 0, 1
 TEAM_WORLD, TEAM_SHARED = 0, 1
 RESERVED_BYTES = 4 << 20
 AMO_AGGREGATE = 1
+AMO_COMBINE_BLOCK = 2
 
 CAP_NAMES = ["GPU_AWARE_HOST", "DEVICE_RMA", "DEVICE_AMO", "DEVICE_SIGNAL", "DEVICE_COLL", "STREAM_ORDERED",
              "DEVICE_CTX_DEFAULT", "EXPLICIT_DEVICE_CTX", "DEVICE_TEAMS", "PTR_DEVICE", "PTR_HOST",

@@ -11,7 +11,7 @@ pytestmark = pytest.mark.gpu
 
 
 def _table_heap(heapf, npes, wpp, tseed):
-    H = wpp * 8 + 65536
+    H = (wpp * 8 + 255) // 256 * 256 + 65536
     h = heapf(npes, H)
     init = W.cb64_np(tseed, np.arange(npes * wpp, dtype=np.uint64)).view(np.int64)
     parts = h.partitions()
@@ -19,15 +19,9 @@ def _table_heap(heapf, npes, wpp, tseed):
     return h, init
 
 
-@pytest.mark.parametrize("agg", [0, 1])
-@pytest.mark.parametrize("dist", ["uniform", "zipf"])
-def test_amo_stream_serialisation(sg, heapf, orc, agg, dist):
-    npes, wpp = 64, 1024
-    nlog = 16
-    tseed, oseed = 0x1234, 0x9876
-    h, init = _table_heap(heapf, npes, wpp, tseed)
-    nops = 1 << 18
-    ops = W.amo_stream_np(77, nops, nlog, dist=dist)
+def _check_stream(sg, orc, h, init, ops, wpp, oseed, tseed, agg):
+    npes = h.npes
+    nops = len(ops)
     dops = torch.from_numpy(ops.view(np.int32)).cuda()
     fetched = torch.zeros(nops, dtype=torch.int64, device="cuda")
     sg.amo_stream(h.base, wpp, dops, nops, oseed, tseed, fetched, flags=agg)
@@ -48,7 +42,33 @@ def test_amo_stream_serialisation(sg, heapf, orc, agg, dist):
     assert np.array_equal(final[untouched], init[untouched])
 
 
-def test_amo_stream_single_kind_exact(sg, heapf, orc):
+@pytest.mark.parametrize("agg", [0, 1, 2])
+@pytest.mark.parametrize("dist", ["uniform", "zipf"])
+def test_amo_stream_serialisation(sg, heapf, orc, agg, dist):
+    npes, wpp = 64, 1024
+    tseed, oseed = 0x1234, 0x9876
+    h, init = _table_heap(heapf, npes, wpp, tseed)
+    _check_stream(sg, orc, h, init, W.amo_stream_np(77, 1 << 18, 16, dist=dist), wpp, oseed, tseed, agg)
+
+
+@pytest.mark.parametrize("agg", [1, 2])
+def test_amo_stream_hot_words_ragged(sg, heapf, orc, agg):
+    """A few hot words (Zipf over 64 words), a stream whose length divides neither the
+    PE count nor the 1024-op combining tile, and op seed == table seed so that the
+    compare_swap ops i that target word i swap in exactly their compare value (applied
+    outside any group by the combining kernel)."""
+    npes, wpp = 8, 8
+    seed = 0x5EED
+    h, init = _table_heap(heapf, npes, wpp, seed)
+    nops = 3 * 8 * 1024 + 777
+    ops = W.amo_stream_np(91, nops, 6, dist="zipf")
+    solo = np.arange(0, npes * wpp, dtype=np.uint32)
+    ops[solo] = solo | np.uint32(W.AMO_CODE_CSWAP << W.AMO_WORD_BITS)
+    _check_stream(sg, orc, h, init, ops, wpp, seed, seed, agg)
+
+
+@pytest.mark.parametrize("agg", [1, 2])
+def test_amo_stream_single_kind_exact(sg, heapf, orc, agg):
     npes, wpp = 16, 4096
     tseed, oseed = 5, 6
     for only in (W.AMO_CODE_FADD, W.AMO_CODE_FXOR):
@@ -56,7 +76,7 @@ def test_amo_stream_single_kind_exact(sg, heapf, orc):
         nops = 300001
         ops = W.amo_stream_np(3, nops, 16, only=only)
         dops = torch.from_numpy(ops.view(np.int32)).cuda()
-        sg.amo_stream(h.base, wpp, dops, nops, oseed, tseed, None, flags=1)
+        sg.amo_stream(h.base, wpp, dops, nops, oseed, tseed, None, flags=agg)
         torch.cuda.synchronize()
         table = init.copy()
         orc.amo_stream(table, ops, oseed, tseed, want_fetched=False)
@@ -65,12 +85,13 @@ def test_amo_stream_single_kind_exact(sg, heapf, orc):
         h.close()
 
 
-def test_amo_stream_bounds_error(sg, heapf):
+@pytest.mark.parametrize("agg", [0, 2])
+def test_amo_stream_bounds_error(sg, heapf, agg):
     npes, wpp = 4, 256
     h, _ = _table_heap(heapf, npes, wpp, 1)
     ops = np.array([5, 1023 | (1 << 27), 2000, 7 | (3 << 27)], dtype=np.uint32)
     sg.clear_status()
-    sg.amo_stream(h.base, wpp, torch.from_numpy(ops.view(np.int32)).cuda(), 4, 1, 1, None)
+    sg.amo_stream(h.base, wpp, torch.from_numpy(ops.view(np.int32)).cuda(), 4, 1, 1, None, flags=agg)
     torch.cuda.synchronize()
     code, detail = sg.get_status()
     assert code == sg.ERR_INVALID_ARG and detail in (2, 3)

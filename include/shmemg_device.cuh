@@ -730,30 +730,34 @@ static __device__ __forceinline__ V shmemg_tree_block(const uint8_t *heap, uint6
 /* Fixed float reduction order: the rank-pairwise tree over P members (level by level,
  * pairs (2i, 2i+1), an odd last value carried up).  It equals the sum of the aligned
  * power-of-two rank blocks of P's binary expansion, combined from the right, which is
- * how it is evaluated here (bitwise identical, order fixed for every P). */
-template <typename V>
+ * how it is evaluated here (bitwise identical, order fixed for every P).  Blocks of up to
+ * 2^MAXB ranks are unrolled (2^MAXB loads in flight per thread); a larger block is the
+ * pairwise tree over its 2^MAXB-rank sub-blocks, combined with a carry stack (a binary
+ * counter), which is the same pairing. */
+template <typename V, int MAXB = 5>
 static __device__ __forceinline__ V shmemg_tree_sum(const uint8_t *heap, uint64_t H, int pe0, int pstride, int P,
                                                     uint64_t off) {
+    static_assert(MAXB >= 1 && MAXB <= 5, "unrolled block size");
     V acc{};
     bool have = false;
-#define SHMEMG_TB(b)                                                                     \
-    if (P & (1 << b)) {                                                                  \
-        V t = shmemg_tree_block<b, V>(heap, H, pe0, pstride, P & ~((2 << b) - 1), off);  \
-        acc = have ? shmemg_vadd<V>::add(t, acc) : t;                                    \
-        have = true;                                                                     \
+#define SHMEMG_TB(b)                                                                         \
+    if constexpr (b <= MAXB) {                                                               \
+        if (P & (1 << b)) {                                                                  \
+            V t = shmemg_tree_block<b, V>(heap, H, pe0, pstride, P & ~((2 << b) - 1), off);  \
+            acc = have ? shmemg_vadd<V>::add(t, acc) : t;                                    \
+            have = true;                                                                     \
+        }                                                                                    \
     }
     SHMEMG_TB(0) SHMEMG_TB(1) SHMEMG_TB(2) SHMEMG_TB(3) SHMEMG_TB(4) SHMEMG_TB(5)
 #undef SHMEMG_TB
-    for (int b = 6; b < 31; b++) {
+    for (int b = MAXB + 1; b < 31; b++) {
         if (!(P & (1 << b))) continue;
-        /* aligned block of 2^b ranks = pairwise tree over its 2^(b-5) blocks of 32,
-         * combined with a carry stack (binary counter): the same pairing */
         int s0 = P & ~((2 << b) - 1);
-        int nsub = 1 << (b - 5);
-        V stack[26];
+        int nsub = 1 << (b - MAXB);
+        V stack[31 - MAXB];
         V v{};
         for (int q = 0; q < nsub; q++) {
-            v = shmemg_tree_block<5, V>(heap, H, pe0, pstride, s0 + q * 32, off);
+            v = shmemg_tree_block<MAXB, V>(heap, H, pe0, pstride, s0 + (q << MAXB), off);
             int cnt = q, j = 0;
             while (cnt & 1) {
                 v = shmemg_vadd<V>::add(stack[j], v);
@@ -783,7 +787,7 @@ template <> __device__ __forceinline__ float shmemg_comb<float>(float a, float b
  * of g owns vectors, reads them from the P members pe0 + r*pstride, combines (integer
  * sums wrap; float sums by the rank-pairwise tree; max/min exact) and writes the result
  * to every member's dst. */
-template <typename T, typename V, int OP>
+template <typename T, typename V, int OP, int TREE_MAXB = 5>
 static __device__ __forceinline__ void shmemg_d_reduce_vecs(shmemg_group g, uint8_t *heap, uint64_t H, int pe0,
                                                            int pstride, int P, uint64_t dst_off, uint64_t src_off,
                                                            uint64_t v0, uint64_t v1) {
@@ -792,7 +796,7 @@ static __device__ __forceinline__ void shmemg_d_reduce_vecs(shmemg_group g, uint
         const uint64_t off = src_off + vi * sizeof(V);
         V acc;
         if constexpr (OP == SHMEMG_SUM && std::is_floating_point<T>::value) {
-            acc = shmemg_tree_sum<V>(heap, H, pe0, pstride, P, off);
+            acc = shmemg_tree_sum<V, TREE_MAXB>(heap, H, pe0, pstride, P, off);
         } else {
             acc = shmemg_ld_cg((const V *)(heap + (uint64_t)pe0 * H + off));
             int r = 1;
@@ -837,19 +841,19 @@ static __device__ __forceinline__ void shmemg_d_reduce_vecs(shmemg_group g, uint
 }
 
 /* dispatch on element type, op and vector width (16-byte vectors when every address
- * and the element range allow it) */
-template <typename T, typename V16>
+ * and the element range allow it); TREE_MAXB bounds the float tree's unrolled blocks */
+template <typename T, typename V16, int TREE_MAXB = 5>
 static __device__ __forceinline__ void shmemg_d_reduce_elems_t(shmemg_group g, uint8_t *heap, uint64_t H, int pe0,
                                                               int pstride, int P, uint64_t dst_off, uint64_t src_off,
                                                               uint64_t e0, uint64_t e1, int op) {
     constexpr uint64_t L = sizeof(V16) / sizeof(T);
     const bool v16 = ((dst_off | src_off | (e0 * sizeof(T)) | (e1 * sizeof(T)) | H) & 15) == 0;
     if (v16) {
-        if (op == SHMEMG_SUM) shmemg_d_reduce_vecs<T, V16, SHMEMG_SUM>(g, heap, H, pe0, pstride, P, dst_off, src_off, e0 / L, e1 / L);
+        if (op == SHMEMG_SUM) shmemg_d_reduce_vecs<T, V16, SHMEMG_SUM, TREE_MAXB>(g, heap, H, pe0, pstride, P, dst_off, src_off, e0 / L, e1 / L);
         else if (op == SHMEMG_MAX) shmemg_d_reduce_vecs<T, V16, SHMEMG_MAX>(g, heap, H, pe0, pstride, P, dst_off, src_off, e0 / L, e1 / L);
         else shmemg_d_reduce_vecs<T, V16, SHMEMG_MIN>(g, heap, H, pe0, pstride, P, dst_off, src_off, e0 / L, e1 / L);
     } else {
-        if (op == SHMEMG_SUM) shmemg_d_reduce_vecs<T, T, SHMEMG_SUM>(g, heap, H, pe0, pstride, P, dst_off, src_off, e0, e1);
+        if (op == SHMEMG_SUM) shmemg_d_reduce_vecs<T, T, SHMEMG_SUM, TREE_MAXB>(g, heap, H, pe0, pstride, P, dst_off, src_off, e0, e1);
         else if (op == SHMEMG_MAX) shmemg_d_reduce_vecs<T, T, SHMEMG_MAX>(g, heap, H, pe0, pstride, P, dst_off, src_off, e0, e1);
         else shmemg_d_reduce_vecs<T, T, SHMEMG_MIN>(g, heap, H, pe0, pstride, P, dst_off, src_off, e0, e1);
     }

@@ -22,6 +22,9 @@
 namespace shmemg {
 
 constexpr int B_THREADS = 256;
+constexpr int B_TREE_MAXB = 3;   // fp32 tree: 8 members' loads in flight per thread
+constexpr int B_QM_BF16 = 8, B_QM_E4M3 = 4;   // quantised: members loaded ahead
+constexpr int B_MIN_BLOCKS = 4;
 enum BKind { BK_F32 = 0, BK_I64 = 1, BK_BF16 = 2, BK_E4M3 = 3 };
 
 struct BTeam {
@@ -45,19 +48,18 @@ struct BArgs {
 template <int FMT>
 __device__ __forceinline__ void batch_qsum(const BArgs &a, const BTeam &t, uint64_t e0, uint64_t e1, float *s_out) {
     constexpr int E = QWide<FMT>::E;
+    constexpr int M = FMT == SHMEMG_FMT_E4M3 ? B_QM_E4M3 : B_QM_BF16;
     const uint64_t CH = (uint64_t)blockDim.x * E;
     uint64_t f0 = e0;
     if (t.vec & 2) {
         for (; f0 + CH <= e1; f0 += CH) {
-            if (threadIdx.x == 0) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");  // s_out free
-            __syncthreads();
-            qsum_chunk_tma<FMT>(a.heap, a.H, t.start, 1, t.size, t.d_off, t.s_off, t.sc_off, f0, s_out);
+            qsum_chunk_tma<FMT, M>(a.heap, a.H, t.start, 1, t.size, t.d_off, t.s_off, t.sc_off, f0, s_out);
         }
     }
     for (uint64_t q = f0 / E + threadIdx.x; q * E < e1; q += blockDim.x) {
         const uint64_t f = q * E;
         if ((t.vec & 2) && f + E <= e1) {
-            qsum_wide<FMT>(a.heap, a.H, t.start, 1, t.size, t.d_off, t.s_off, t.sc_off, f);
+            qsum_wide<FMT, M>(a.heap, a.H, t.start, 1, t.size, t.d_off, t.s_off, t.sc_off, f);
         } else {
             for (int k = 0; k < E / 4 && f + 4 * k < e1; k++)
                 qsum4<FMT>(a.heap, a.H, t.start, 1, t.size, t.d_off, t.s_off, t.sc_off, f + 4 * k, t.n,
@@ -69,7 +71,8 @@ __device__ __forceinline__ void batch_qsum(const BArgs &a, const BTeam &t, uint6
 __device__ __forceinline__ void batch_item(const BArgs &a, const BTeam &t, uint64_t e0, uint64_t e1, float *s_out) {
     const shmemg_group g = {threadIdx.x, blockDim.x};
     if (t.kind == BK_F32) {
-        shmemg_d_reduce_elems_t<float, float4>(g, a.heap, a.H, t.start, 1, t.size, t.d_off, t.s_off, e0, e1, SHMEMG_SUM);
+        shmemg_d_reduce_elems_t<float, float4, B_TREE_MAXB>(g, a.heap, a.H, t.start, 1, t.size, t.d_off, t.s_off, e0, e1,
+                                                         SHMEMG_SUM);
     } else if (t.kind == BK_I64) {
         shmemg_d_reduce_elems_t<int64_t, longlong2>(g, a.heap, a.H, t.start, 1, t.size, t.d_off, t.s_off, e0, e1,
                                                     SHMEMG_SUM);
@@ -79,7 +82,7 @@ __device__ __forceinline__ void batch_item(const BArgs &a, const BTeam &t, uint6
     }
 }
 
-__global__ void __launch_bounds__(B_THREADS) k_batch(BArgs a) {
+__global__ void __launch_bounds__(B_THREADS, B_MIN_BLOCKS) k_batch(BArgs a) {
     __shared__ uint32_t s_item;
     __shared__ __align__(128) float s_out[B_THREADS * 16];  // one quantised chunk (E <= 16)
     for (;;) {

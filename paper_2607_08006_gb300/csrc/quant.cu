@@ -100,8 +100,6 @@ __global__ void __launch_bounds__(Q_THREADS) k_qsum(QSumArgs a) {
     const uint64_t CH = (uint64_t)blockDim.x * E;
     const uint64_t nfull = a.wide ? a.n / CH : 0;
     for (uint64_t ch = blockIdx.x; ch < nfull; ch += gridDim.x) {
-        if (threadIdx.x == 0) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");  // s_out free again
-        __syncthreads();
         qsum_chunk_tma<FMT>(a.heap, a.H, pe0, a.stride, a.size, a.d_off, a.q_off, a.s_off, ch * CH, s_out);
     }
     if (threadIdx.x == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");

@@ -73,18 +73,18 @@ __device__ __forceinline__ void qdecode16(uint4 w, float s, float *d) {
 }
 
 // Wide form of qsum4: elements [e0, e0+E) with E = QWide<FMT>::E, e0 a multiple of E,
-// q_off and d_off 16-byte aligned, e0 + E <= n.  Eight members' codes and scales are
+// q_off and d_off 16-byte aligned, e0 + E <= n.  M members' codes and scales are
 // loaded ahead of their accumulation, which stays in team-rank order.
-template <int FMT>
+template <int FMT, int M = 8>
 __device__ __forceinline__ void qsum_wide_acc(const uint8_t *heap, uint64_t H, int pe0, int pstride, int P,
                                               uint64_t q_off, uint64_t s_off, uint64_t e0, float4 *o);
 
-template <int FMT>
+template <int FMT, int M = 8>
 __device__ __forceinline__ void qsum_wide(uint8_t *heap, uint64_t H, int pe0, int pstride, int P, uint64_t d_off,
                                           uint64_t q_off, uint64_t s_off, uint64_t e0) {
     constexpr int E = QWide<FMT>::E;
     float4 o[E / 4];
-    qsum_wide_acc<FMT>(heap, H, pe0, pstride, P, q_off, s_off, e0, o);
+    qsum_wide_acc<FMT, M>(heap, H, pe0, pstride, P, q_off, s_off, e0, o);
     for (int m = 0; m < P; m++) {
         float4 *dst = (float4 *)(heap + (uint64_t)(pe0 + m * pstride) * H + d_off + 4 * e0);
 #pragma unroll
@@ -92,8 +92,9 @@ __device__ __forceinline__ void qsum_wide(uint8_t *heap, uint64_t H, int pe0, in
     }
 }
 
-// The accumulation of qsum_wide: the E compensated sums of elements [e0, e0+E) into o.
-template <int FMT>
+// The accumulation of qsum_wide: the E compensated sums of elements [e0, e0+E) into o;
+// M members' codes and scales are loaded ahead.
+template <int FMT, int M>
 __device__ __forceinline__ void qsum_wide_acc(const uint8_t *heap, uint64_t H, int pe0, int pstride, int P,
                                               uint64_t q_off, uint64_t s_off, uint64_t e0, float4 *o) {
     constexpr int E = QWide<FMT>::E;
@@ -102,7 +103,6 @@ __device__ __forceinline__ void qsum_wide_acc(const uint8_t *heap, uint64_t H, i
 #pragma unroll
     for (int j = 0; j < E; j++) acc[j] = {0.0f, 0.0f};
     float d[E];
-    constexpr int M = 8;  // members whose codes and scales are loaded ahead
     int r = 0;
     for (; r + M <= P; r += M) {
         uint4 w[M];
@@ -134,14 +134,18 @@ __device__ __forceinline__ void qsum_wide_acc(const uint8_t *heap, uint64_t H, i
 // One CTA's chunk of blockDim.x * E elements starting at c0 (full, aligned): every thread
 // accumulates its E elements into shared memory, then thread 0 bulk-stores the chunk to
 // every member (one TMA store per member instead of P x E/4 vector stores per thread).
-// `out` holds blockDim.x * E floats (128-byte aligned).  Returns with the stores issued;
-// the caller waits (bulk wait_group.read) before it reuses `out`.
-template <int FMT>
+// `out` holds blockDim.x * E floats (128-byte aligned).  The bulk stores of the previous
+// chunk drain from `out` while this chunk is loaded and accumulated; thread 0 waits for
+// them (bulk wait_group.read) only before `out` is overwritten.  Returns with the stores
+// issued.
+template <int FMT, int M = 8>
 __device__ __forceinline__ void qsum_chunk_tma(uint8_t *heap, uint64_t H, int pe0, int pstride, int P, uint64_t d_off,
                                                uint64_t q_off, uint64_t s_off, uint64_t c0, float *out) {
     constexpr int E = QWide<FMT>::E;
     float4 o[E / 4];
-    qsum_wide_acc<FMT>(heap, H, pe0, pstride, P, q_off, s_off, c0 + (uint64_t)threadIdx.x * E, o);
+    qsum_wide_acc<FMT, M>(heap, H, pe0, pstride, P, q_off, s_off, c0 + (uint64_t)threadIdx.x * E, o);
+    if (threadIdx.x == 0) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");  // `out` free again
+    __syncthreads();
 #pragma unroll
     for (int k = 0; k < E / 4; k++) reinterpret_cast<float4 *>(out)[threadIdx.x * (E / 4) + k] = o[k];
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // generic smem writes -> bulk copy engine

@@ -1135,7 +1135,7 @@ def run_serve(torch, sg, nreq=1 << 16, rates=None, npes=512, Hs=32 << 20):
 
 # ----------------------------------------------------------------------------- profiling cases
 PROFILE_CASES = ("interp_ring", "reduce", "reduce_f32", "broadcast", "alltoall", "amo", "amo_plain", "amo_combine", "amo_combine_zipf", "batch_bf16", "qsum",
-                 "pingpong_cluster", "cluster_coll", "halo")
+                 "pingpong_cluster", "cluster_coll", "halo", "halo_plain")
 
 
 def run_profile_case(name, launches=4):
@@ -1227,7 +1227,7 @@ def run_profile_case(name, launches=4):
         dev = torch.from_numpy(ops.view(np.uint8).copy()).cuda()
         for _ in range(launches):
             sg.run_script(dev, len(ops), None, s)
-    elif name == "halo":              # 8 x 8 PEs of 1024 x 1024 binary32 (256 MiB per buffer), 4 sweeps
+    elif name in ("halo", "halo_plain"):  # 8 x 8 PEs of 1024 x 1024 binary32 (256 MiB per buffer), 4 sweeps
         px, py, nx, ny = 8, 8, 1024, 1024
         tile_b, halo_b = 2 * nx * ny * 4, 2 * sg.halo_stride(nx, ny) * 4
         heap = sg.Heap(px * py, (tile_b + halo_b + 64 + 4095) // 4096 * 4096)
@@ -1235,7 +1235,7 @@ def run_profile_case(name, launches=4):
         heap.partitions()[:, :nx * ny * 4].view(torch.float32).normal_()
         for _ in range(launches):
             sg.halo_jacobi(heap.sym(0, tile_b), heap.sym(tile_b, halo_b), heap.sym(tile_b + halo_b, 32), px, py, nx,
-                           ny, 4, s)
+                           ny, 4, s, plain=name == "halo_plain")
     else:
         raise SystemExit(f"unknown profile case {name}")
     torch.cuda.synchronize()

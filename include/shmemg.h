@@ -409,7 +409,9 @@ int shmemg_pingpong_cluster(void *buf, uint64_t *sig, uint64_t payload, int npai
  * out = 0.25 * ((up + down) + (left + right)) (RNE, in this order).  Symmetric objects:
  *   tiles  2*nx*ny floats: tile 0 holds the input; after the call the result is in tile
  *          (iters & 1);
- *   halos  2*hs floats, hs = 2*nx + 2*ny rounded up to a multiple of 4 (work space);
+ *   halos  2*hs floats, hs = shmemg_halo_stride(nx, ny) = 2*nx + 2*ny4 with ny4 = ny
+ *          rounded up to a multiple of 4 (work space: north and south rows, west and
+ *          east columns, each part 16-byte aligned);
  *   sigs   4 uint64, zero before the call (left zero after a successful call).
  * shmemg_halo_jacobi: one cooperative launch; after each sweep a PE stores its new
  * boundary rows and columns straight into its four neighbours' halo buffers (device-
@@ -418,6 +420,7 @@ int shmemg_pingpong_cluster(void *buf, uint64_t *sig, uint64_t payload, int npai
  * shmemg_halo_jacobi_plain: the same sweeps, one stream-ordered launch per sweep (the
  * plain launch-per-op path: kernel boundaries replace the signals).  tiles and halos
  * 16-byte aligned, px*py == npes, else SHMEMG_ERR_INVALID_ARG. */
+uint64_t shmemg_halo_stride(int nx, int ny);
 int shmemg_halo_jacobi(float *tiles, float *halos, uint64_t *sigs, int px, int py, int nx, int ny,
                        int iters, void *stream);
 int shmemg_halo_jacobi_plain(float *tiles, float *halos, uint64_t *sigs, int px, int py, int nx,

@@ -189,6 +189,8 @@ def lib():
             f.restype = C.c_int
         L.shmemg_strerror.argtypes = [I]
         L.shmemg_strerror.restype = C.c_char_p
+        L.shmemg_halo_stride.argtypes = [I, I]
+        L.shmemg_halo_stride.restype = C.c_uint64
         _lib = L
     return _lib
 
@@ -462,8 +464,8 @@ def pingpong_cluster(buf, sig, payload, npairs, iters, lat_dev, stream=None):
 
 
 def halo_stride(nx, ny):
-    """Floats per halo buffer of the halo exchange (2nx + 2ny rounded up to 4)."""
-    return (2 * nx + 2 * ny + 3) // 4 * 4
+    """Floats per halo buffer of the halo exchange (2nx + 2 * ny rounded up to 4)."""
+    return int(lib().shmemg_halo_stride(nx, ny))
 
 
 def halo_jacobi(tiles, halos, sigs, px, py, nx, ny, iters, stream=None, plain=False):

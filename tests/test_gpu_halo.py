@@ -43,7 +43,8 @@ def _run(sg, heapf, orc, px, py, nx, ny, iters, mode=0, cd=1, plain=False, seed=
 
 @pytest.mark.parametrize("plain", [False, True])
 @pytest.mark.parametrize("px,py,nx,ny,iters", [(4, 2, 64, 48, 7), (1, 1, 16, 8, 5), (2, 1, 32, 5, 4),
-                                                (3, 2, 40, 7, 9), (2, 3, 4, 1, 3), (4, 4, 2048, 16, 2)])
+                                                (3, 2, 40, 7, 9), (2, 3, 4, 1, 3), (4, 4, 2048, 16, 2),
+                                                (2, 2, 2208, 9, 3), (3, 1, 384, 37, 5)])
 def test_halo_jacobi_matches_whole_grid(sg, heapf, orc, px, py, nx, ny, iters, plain):
     got, want, sig = _run(sg, heapf, orc, px, py, nx, ny, iters, plain=plain)
     assert np.array_equal(got.view(np.uint32), want.view(np.uint32))

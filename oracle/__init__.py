@@ -271,6 +271,35 @@ def amo_stream(table: np.ndarray, ops: np.ndarray, op_seed: int, table_seed: int
     return fetched
 
 
+def _splitmix64_np(seed: int, i: np.ndarray) -> np.ndarray:
+    """splitmix64 (Steele, Lea, Flood, OOPSLA 2014): first output of the stream seeded
+    with seed ^ i, vectorised (uint64 arithmetic wraps mod 2^64)."""
+    with np.errstate(over="ignore"):
+        z = (np.uint64(seed) ^ i.astype(np.uint64)) + np.uint64(0x9E3779B97F4A7C15)
+        z = (z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)
+        z = (z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)
+        return z ^ (z >> np.uint64(31))
+
+
+def amo_add_word_sums(ops: np.ndarray, first_op: int, op_seed: int, words: np.ndarray) -> np.ndarray:
+    """For each word of the sorted array ``words``: the sum of the fetch_add operands
+    ((r mod 2^20) + 1, r = splitmix64(op_seed ^ i)) of the ops among ``ops`` (packed, op i
+    = first_op + position) that target it.  Fetch_adds commute (Sec. 2.1 atomics), so a
+    word that only fetch_adds touch ends at its initial value plus this sum in any
+    serial order.  Sums of up to 2^32 operands stay below 2^53, exact in binary64."""
+    if len(words) == 0:
+        return np.zeros(0, np.int64)
+    w = (ops & np.uint32((1 << 27) - 1)).astype(np.int64)
+    code = ops >> np.uint32(27)
+    pos = np.searchsorted(words, w)
+    pos[pos == len(words)] = 0
+    hit = (words[pos] == w) & (code == 0)
+    i = np.nonzero(hit)[0]
+    r = _splitmix64_np(op_seed, i.astype(np.uint64) + np.uint64(first_op))
+    v = (r & np.uint64((1 << 20) - 1)) + np.uint64(1)
+    return np.bincount(pos[i], weights=v.astype(np.float64), minlength=len(words)).astype(np.int64)
+
+
 def check_serialisation(group, kind, operand, cond, fetched, w0, final=None,
                         budget_per_group: int = 1 << 26):
     """Number of word groups whose fetched values admit no valid serial order (0 = all

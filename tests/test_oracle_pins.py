@@ -575,3 +575,29 @@ def test_halo_jacobi_fourier_mode_decay(orc):
     lam = (np.cos(2 * np.pi * k / nx) + np.cos(2 * np.pi * l / ny)) / 2
     out = orc.halo_jacobi(g0.astype(np.float32), T).astype(np.float64)
     assert np.max(np.abs(out - lam ** T * g0)) < 2e-6
+
+
+def test_amo_add_word_sums_matches_sequential_application(orc):
+    """The per-word operand sums (vectorised) against the sequential C oracle: on an
+    add-only stream over 2^10 words, init + sums is the final table for every word; on a
+    mixed stream, the sums count only the fetch_add ops (a word no other op touches still
+    ends at init + sum), with a first-op offset."""
+    nlog, nw, oseed, tseed = 10, 1 << 10, 0x77, 0x99
+    init = W.cb64_np(tseed, np.arange(nw, dtype=np.uint64)).view(np.int64)
+    ops = W.amo_stream_np(8, 30000, nlog, only=W.AMO_CODE_FADD, offset=1000)
+    t = init.copy()
+    orc.amo_stream(t, ops, oseed, tseed, first_op=1000, want_fetched=False)
+    words = np.arange(nw, dtype=np.int64)
+    assert np.array_equal(init + orc.amo_add_word_sums(ops, 1000, oseed, words), t)
+    sub = words[::7]
+    assert np.array_equal(orc.amo_add_word_sums(ops, 1000, oseed, sub), (t - init)[::7])
+    nw = 1 << 16
+    init = W.cb64_np(tseed, np.arange(nw, dtype=np.uint64)).view(np.int64)
+    mixed = W.amo_stream_np(9, 30000, 16)
+    t = init.copy()
+    orc.amo_stream(t, mixed, oseed, tseed, want_fetched=False)
+    w = (mixed & ((1 << 27) - 1)).astype(np.int64)
+    code = mixed >> 27
+    only_add = np.setdiff1d(np.unique(w), w[code != 0])
+    s = orc.amo_add_word_sums(mixed, 0, oseed, only_add)
+    assert len(only_add) > 0 and np.array_equal(init[only_add] + s, t[only_add])

@@ -866,62 +866,98 @@ def run_amo(torch, sg, nops_log2=30, reps=3):
 
 
 # ----------------------------------------------------------------------------- batched teams
+class BatchWorkload:
+    """The batched-collective workload on a 128-PE heap: 256 teams of log-uniform 2-128
+    contiguous PEs, n log-uniform 256-4 Mi, 25 % int64 teams (values U[-2^20, 2^20]),
+    the rest fp32 N(0,1) with room for bf16 / E4M3 codes and per-128 scales.  `lay[t]` =
+    (kind, src, dst, codes, scales) symmetric offsets of team t."""
+
+    def __init__(self, torch, sg):
+        self.torch, self.sg = torch, sg
+        bt = self.bt = W.gen_batch_teams()
+        self.world = world = 128
+        P, n = self.P, self.n = bt.size.astype(np.int64), bt.n.astype(np.int64)
+        need = np.where(bt.is_int, 16 * n, 10 * n + 4 * ((n + 127) // 128) + 1024)
+        order = np.argsort(-need, kind="stable")
+        hw = np.zeros(world, np.int64)
+        off = np.zeros(len(P), np.int64)
+        for t in order:
+            s0, e = bt.start[t], bt.start[t] + P[t]
+            o = (int(hw[s0:e].max()) + 255) // 256 * 256
+            off[t] = o
+            hw[s0:e] = o + need[t]
+        self.Hb = int((hw.max() + (1 << 20)) // (1 << 20) * (1 << 20))
+        heap = self.heap = sg.Heap(world, self.Hb)
+        self.base = heap.base
+        self.teams_h = {}
+        try:
+            gen = torch.Generator(device="cuda")
+            gen.manual_seed(W.derive_seed("batch-values") & 0x7FFFFFFF)
+            lay = self.lay = []
+            for t in range(len(P)):
+                o = int(off[t])
+                nt = int(n[t])
+                if bt.is_int[t]:
+                    src, dst = o, o + 8 * nt
+                    for p in range(bt.start[t], bt.start[t] + P[t]):
+                        v = torch.randint(-(1 << 20), (1 << 20) + 1, (nt,), dtype=torch.int64, device="cuda", generator=gen)
+                        heap.view(src, p, torch.int64, nt).copy_(v)
+                    lay.append(("i64", src, dst, None, None))
+                else:
+                    src = o
+                    codes = (o + 4 * nt + 255) // 256 * 256      # 16-byte aligned codes: the wide path
+                    dst = (codes + 2 * nt + 255) // 256 * 256
+                    sc = (dst + 4 * nt + 255) // 256 * 256
+                    for p in range(bt.start[t], bt.start[t] + P[t]):
+                        heap.view(src, p, torch.float32, nt).normal_(generator=gen)
+                    lay.append(("f", src, dst, codes, sc))
+            torch.cuda.synchronize()
+        except BaseException:
+            heap.close()
+            raise
+
+    def team(self, t):
+        key = (int(self.bt.start[t]), int(self.P[t]))
+        if key not in self.teams_h:
+            self.teams_h[key] = self.sg.team_split_strided(self.sg.TEAM_WORLD, key[0], 1, key[1])
+        return self.teams_h[key]
+
+    def descs(self, fmt):
+        sg, d = self.sg, []
+        for t, (k, src, dst, codes, sc) in enumerate(self.lay):
+            st0, sz, nt = int(self.bt.start[t]), int(self.P[t]), int(self.n[t])
+            if k == "i64":
+                d.append(sg.CollDesc(st0, sz, sg.INT64, -1, nt, self.base + dst, self.base + src, None))
+            elif fmt < 0:
+                d.append(sg.CollDesc(st0, sz, sg.FLOAT, -1, nt, self.base + dst, self.base + src, None))
+            else:
+                d.append(sg.CollDesc(st0, sz, sg.FLOAT, fmt, nt, self.base + dst, self.base + codes, self.base + sc))
+        return d
+
+    def quantize(self, fmt):
+        """every float team's fp32 input into its codes + scales (the library's quantiser)"""
+        for t, (k, src, dst, codes, sc) in enumerate(self.lay):
+            if k != "i64":
+                self.sg.quantize(self.team(t), self.base + codes, self.base + sc, self.base + src, fmt, int(self.n[t]))
+        self.torch.cuda.synchronize()
+
+    def close(self):
+        for tm in self.teams_h.values():
+            self.sg.team_destroy(tm)
+        self.teams_h = {}
+        self.heap.close()
+
+
 def run_batch(torch, sg, reps=5, check_teams=32, check_elems=4096):
     """256 teams of log-uniform 2-128 PEs (128-PE world), n log-uniform 256-4 Mi, 25 %
     int64; fp32 N(0,1) payloads vs bf16 / E4M3 payloads with per-128 scales.  One
     graph-captured persistent launch per format, autotuned; compared with one launch per
     team and with the untuned plan; error against binary64 on sampled elements."""
-    bt = W.gen_batch_teams()
-    world = 128
-    P, n = bt.size.astype(np.int64), bt.n.astype(np.int64)
-    need = np.where(bt.is_int, 16 * n, 10 * n + 4 * ((n + 127) // 128) + 1024)
-    order = np.argsort(-need, kind="stable")
-    hw = np.zeros(world, np.int64)
-    off = np.zeros(len(P), np.int64)
-    for t in order:
-        s0, e = bt.start[t], bt.start[t] + P[t]
-        o = (int(hw[s0:e].max()) + 255) // 256 * 256
-        off[t] = o
-        hw[s0:e] = o + need[t]
-    Hb = int((hw.max() + (1 << 20)) // (1 << 20) * (1 << 20))
-    heap = sg.Heap(world, Hb)
-    out = {"teams": len(P), "world": world, "heap_bytes_per_pe": Hb}
+    wl = BatchWorkload(torch, sg)
+    bt, P, n, lay, heap, base = wl.bt, wl.P, wl.n, wl.lay, wl.heap, wl.base
+    out = {"teams": len(P), "world": wl.world, "heap_bytes_per_pe": wl.Hb}
     try:
-        base = heap.base
-        gen = torch.Generator(device="cuda")
-        gen.manual_seed(W.derive_seed("batch-values") & 0x7FFFFFFF)
-        lay = []
-        for t in range(len(P)):
-            o = int(off[t])
-            nt = int(n[t])
-            if bt.is_int[t]:
-                src, dst = o, o + 8 * nt
-                for p in range(bt.start[t], bt.start[t] + P[t]):
-                    v = torch.randint(-(1 << 20), (1 << 20) + 1, (nt,), dtype=torch.int64, device="cuda", generator=gen)
-                    heap.view(src, p, torch.int64, nt).copy_(v)
-                lay.append(("i64", src, dst, None, None))
-            else:
-                src = o
-                codes = (o + 4 * nt + 255) // 256 * 256      # 16-byte aligned codes: the wide path
-                dst = (codes + 2 * nt + 255) // 256 * 256
-                sc = (dst + 4 * nt + 255) // 256 * 256
-                for p in range(bt.start[t], bt.start[t] + P[t]):
-                    heap.view(src, p, torch.float32, nt).normal_(generator=gen)
-                lay.append(("f", src, dst, codes, sc))
-        torch.cuda.synchronize()
-        teams_h = {}
-
-        def descs(fmt):
-            d = []
-            for t, (k, src, dst, codes, sc) in enumerate(lay):
-                st0, sz, nt = int(bt.start[t]), int(P[t]), int(n[t])
-                if k == "i64":
-                    d.append(sg.CollDesc(st0, sz, sg.INT64, -1, nt, base + dst, base + src, None))
-                elif fmt < 0:
-                    d.append(sg.CollDesc(st0, sz, sg.FLOAT, -1, nt, base + dst, base + src, None))
-                else:
-                    d.append(sg.CollDesc(st0, sz, sg.FLOAT, fmt, nt, base + dst, base + codes, base + sc))
-            return d
+        descs = wl.descs
 
         def algo_bytes(fmt):
             tot = 0
@@ -946,29 +982,21 @@ def run_batch(torch, sg, reps=5, check_teams=32, check_elems=4096):
 
         hbm, src_kind = measured_peaks()
         for fmt, name in ((-1, "fp32"), (0, "bf16"), (1, "e4m3")):
-            if fmt >= 0:   # quantise every float team's fp32 input into its codes + scales
-                for t, (k, src, dst, codes, sc) in enumerate(lay):
-                    if k == "i64":
-                        continue
-                    key = (int(bt.start[t]), int(P[t]))
-                    if key not in teams_h:
-                        teams_h[key] = sg.team_split_strided(sg.TEAM_WORLD, key[0], 1, key[1])
-                    sg.quantize(teams_h[key], base + codes, base + sc, base + src, fmt, int(n[t]))
-                torch.cuda.synchronize()
+            if fmt >= 0:
+                wl.quantize(fmt)
             ab = algo_bytes(fmt)
             b = sg.Batch(descs(fmt), sg.Tune(16384, 0, 0, 0))
             untuned = time_graph(b)
             tune = b.autotune()
             tuned = time_graph(b)
             # one launch per team (plain path)
-            for key in {(int(bt.start[t]), int(P[t])) for t in range(len(P))}:
-                if key not in teams_h:
-                    teams_h[key] = sg.team_split_strided(sg.TEAM_WORLD, key[0], 1, key[1])
+            for t in range(len(P)):
+                wl.team(t)
             e0, e1 = _events(torch)
             e0.record(s)
             for _ in range(reps):
                 for t, (k, src, dst, codes, sc) in enumerate(lay):
-                    tm = teams_h[(int(bt.start[t]), int(P[t]))]
+                    tm = wl.team(t)
                     if k == "i64":
                         sg.reduce(tm, base + dst, base + src, int(n[t]), sg.INT64, sg.SUM, s)
                     elif fmt < 0:
@@ -988,10 +1016,8 @@ def run_batch(torch, sg, reps=5, check_teams=32, check_elems=4096):
                          "tune": {"tile_elems": tune.tile_elems, "ctas_per_sm": tune.ctas_per_sm},
                          "algorithmic_bytes": ab, "error_vs_fp64": err}
             b.destroy()
-        for tm in teams_h.values():
-            sg.team_destroy(tm)
     finally:
-        heap.close()
+        wl.close()
     return out
 
 

@@ -1075,6 +1075,9 @@ def run_serve(torch, sg, nreq=1 << 16, rates=None, npes=512, Hs=32 << 20):
         for p in range(npes):
             parts[p, lay.ro_offset:lay.ro_offset + lay.ro_bytes].view(torch.float32).copy_(
                 W.serve_source_words_torch(seed, p, lay.ro_bytes // 4))
+        parts[:, lay.amo_offset:lay.amo_offset + 8 * lay.amo_words].view(torch.int64).copy_(
+            W.cb64_torch(W.derive_seed("serve-amo"), torch.arange(npes * lay.amo_words, device="cuda")).view(
+                npes, lay.amo_words))
         torch.cuda.synchronize()
         cfg = sg.ServerCfg()
         cfg.page_bytes = lay.page_bytes

@@ -1163,7 +1163,7 @@ def run_serve(torch, sg, nreq=1 << 16, rates=None, npes=512, Hs=32 << 20):
 
 
 # ----------------------------------------------------------------------------- profiling cases
-PROFILE_CASES = ("interp_ring", "reduce", "reduce_f32", "broadcast", "alltoall", "amo", "amo_plain", "amo_combine", "amo_combine_zipf", "batch_bf16", "qsum",
+PROFILE_CASES = ("interp_ring", "reduce", "reduce_f32", "broadcast", "alltoall", "amo", "amo_plain", "amo_combine", "amo_combine_zipf", "batch_bf16", "batch_e4m3", "qsum",
                  "pingpong_cluster", "cluster_coll", "halo", "halo_plain")
 
 
@@ -1225,17 +1225,18 @@ def run_profile_case(name, launches=4):
         f = torch.empty(nops, dtype=torch.int64, device="cuda")
         for _ in range(launches):
             sg.amo_stream(heap.base, wpp, ops, nops, 1, 2, f, 0 if name == "amo_plain" else 2, s)
-    elif name in ("batch_bf16", "qsum"):   # 64 PEs, bf16 payloads of 1 Mi elements
+    elif name in ("batch_bf16", "batch_e4m3", "qsum"):   # 64 PEs, bf16 / E4M3 payloads of 1 Mi elements
         n = 1 << 20
         heap = sg.Heap(64, 12 * n)
         x = heap.partitions()[:, :4 * n].view(torch.float32)
         x.normal_()
-        sg.quantize(sg.TEAM_WORLD, heap.base + 4 * n, heap.base + 6 * n, heap.base, sg.FMT_BF16, n, s)
+        fmt = sg.FMT_E4M3 if name == "batch_e4m3" else sg.FMT_BF16
+        sg.quantize(sg.TEAM_WORLD, heap.base + 4 * n, heap.base + 6 * n, heap.base, fmt, n, s)
         if name == "qsum":
             for _ in range(launches):
                 sg.qsum_reduce(sg.TEAM_WORLD, heap.base + 7 * n, heap.base + 4 * n, heap.base + 6 * n, sg.FMT_BF16, n, s)
         else:
-            d = [sg.CollDesc(0, 64, sg.FLOAT, sg.FMT_BF16, n, heap.base + 7 * n, heap.base + 4 * n, heap.base + 6 * n)]
+            d = [sg.CollDesc(0, 64, sg.FLOAT, fmt, n, heap.base + 7 * n, heap.base + 4 * n, heap.base + 6 * n)]
             b = sg.Batch(d, sg.Tune(8192, 0, 0, 0))
             for _ in range(launches):
                 b.launch(s)

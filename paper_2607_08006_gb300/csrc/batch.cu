@@ -42,18 +42,20 @@ struct BArgs {
     uint32_t *counter;    // [0] next item, [1] CTAs done
 };
 
-// quantised tile: full chunks of blockDim x E elements accumulate into shared memory and
-// are bulk-stored to every member (bit 1 of t.vec: 16-byte aligned codes and outputs);
-// the rest runs E (or 4) elements per thread
+// quantised tile: full chunks of blockDim x E elements accumulate into shared memory (two
+// buffers, alternated across the CTA's chunks) and are bulk-stored to every member (bit 1
+// of t.vec: 16-byte aligned codes and outputs); the rest runs E (or 4) elements per thread
 template <int FMT>
-__device__ __forceinline__ void batch_qsum(const BArgs &a, const BTeam &t, uint64_t e0, uint64_t e1, float *s_out) {
+__device__ __forceinline__ void batch_qsum(const BArgs &a, const BTeam &t, uint64_t e0, uint64_t e1, float (*s_out)[B_THREADS * 16],
+                                           int &buf) {
     constexpr int E = QWide<FMT>::E;
     constexpr int M = FMT == SHMEMG_FMT_E4M3 ? B_QM_E4M3 : B_QM_BF16;
     const uint64_t CH = (uint64_t)blockDim.x * E;
     uint64_t f0 = e0;
     if (t.vec & 2) {
         for (; f0 + CH <= e1; f0 += CH) {
-            qsum_chunk_tma<FMT, M>(a.heap, a.H, t.start, 1, t.size, t.d_off, t.s_off, t.sc_off, f0, s_out);
+            qsum_chunk_tma<FMT, M>(a.heap, a.H, t.start, 1, t.size, t.d_off, t.s_off, t.sc_off, f0, s_out[buf]);
+            buf ^= 1;
         }
     }
     for (uint64_t q = f0 / E + threadIdx.x; q * E < e1; q += blockDim.x) {
@@ -68,7 +70,8 @@ __device__ __forceinline__ void batch_qsum(const BArgs &a, const BTeam &t, uint6
     }
 }
 
-__device__ __forceinline__ void batch_item(const BArgs &a, const BTeam &t, uint64_t e0, uint64_t e1, float *s_out) {
+__device__ __forceinline__ void batch_item(const BArgs &a, const BTeam &t, uint64_t e0, uint64_t e1, float (*s_out)[B_THREADS * 16],
+                                           int &buf) {
     const shmemg_group g = {threadIdx.x, blockDim.x};
     if (t.kind == BK_F32) {
         shmemg_d_reduce_elems_t<float, float4, B_TREE_MAXB>(g, a.heap, a.H, t.start, 1, t.size, t.d_off, t.s_off, e0, e1,
@@ -77,14 +80,15 @@ __device__ __forceinline__ void batch_item(const BArgs &a, const BTeam &t, uint6
         shmemg_d_reduce_elems_t<int64_t, longlong2>(g, a.heap, a.H, t.start, 1, t.size, t.d_off, t.s_off, e0, e1,
                                                     SHMEMG_SUM);
     } else {
-        if (t.kind == BK_E4M3) batch_qsum<SHMEMG_FMT_E4M3>(a, t, e0, e1, s_out);
-        else batch_qsum<SHMEMG_FMT_BF16>(a, t, e0, e1, s_out);
+        if (t.kind == BK_E4M3) batch_qsum<SHMEMG_FMT_E4M3>(a, t, e0, e1, s_out, buf);
+        else batch_qsum<SHMEMG_FMT_BF16>(a, t, e0, e1, s_out, buf);
     }
 }
 
 __global__ void __launch_bounds__(B_THREADS, B_MIN_BLOCKS) k_batch(BArgs a) {
     __shared__ uint32_t s_item;
-    __shared__ __align__(128) float s_out[B_THREADS * 16];  // one quantised chunk (E <= 16)
+    __shared__ __align__(128) float s_out[2][B_THREADS * 16];  // two quantised chunks (E <= 16), alternated
+    int buf = 0;
     for (;;) {
         if (threadIdx.x == 0) s_item = atomicAdd(&a.counter[0], 1u);
         __syncthreads();
@@ -95,7 +99,7 @@ __global__ void __launch_bounds__(B_THREADS, B_MIN_BLOCKS) k_batch(BArgs a) {
         const BTeam t = a.teams[item.x];
         const uint64_t e0 = (uint64_t)item.y * a.tile;
         const uint64_t e1 = e0 + a.tile < t.n ? e0 + a.tile : t.n;
-        batch_item(a, t, e0, e1, s_out);
+        batch_item(a, t, e0, e1, s_out, buf);
     }
     if (threadIdx.x == 0) {
         asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");  // this CTA's bulk stores are done

@@ -91,16 +91,19 @@ struct QSumArgs {
 
 // Full, aligned chunks of blockDim x E elements: each thread accumulates E elements
 // (one 16-byte code load per member) into shared memory and thread 0 bulk-stores the
-// chunk to every member.  The ragged tail runs in 4-element steps.
+// chunk to every member (two chunk buffers, so one chunk's stores drain while the next
+// is accumulated).  The ragged tail runs in 4-element steps.
 template <int FMT>
 __global__ void __launch_bounds__(Q_THREADS) k_qsum(QSumArgs a) {
     constexpr int E = QWide<FMT>::E;
-    __shared__ __align__(128) float s_out[Q_THREADS * E];
+    __shared__ __align__(128) float s_out[2][Q_THREADS * E];   // alternate chunk buffers
     const int pe0 = a.start + blockIdx.y * a.gstride;
     const uint64_t CH = (uint64_t)blockDim.x * E;
     const uint64_t nfull = a.wide ? a.n / CH : 0;
+    int buf = 0;
     for (uint64_t ch = blockIdx.x; ch < nfull; ch += gridDim.x) {
-        qsum_chunk_tma<FMT>(a.heap, a.H, pe0, a.stride, a.size, a.d_off, a.q_off, a.s_off, ch * CH, s_out);
+        qsum_chunk_tma<FMT>(a.heap, a.H, pe0, a.stride, a.size, a.d_off, a.q_off, a.s_off, ch * CH, s_out[buf]);
+        buf ^= 1;
     }
     if (threadIdx.x == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
     const uint64_t t0 = nfull * CH;

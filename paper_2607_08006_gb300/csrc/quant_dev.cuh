@@ -134,17 +134,18 @@ __device__ __forceinline__ void qsum_wide_acc(const uint8_t *heap, uint64_t H, i
 // One CTA's chunk of blockDim.x * E elements starting at c0 (full, aligned): every thread
 // accumulates its E elements into shared memory, then thread 0 bulk-stores the chunk to
 // every member (one TMA store per member instead of P x E/4 vector stores per thread).
-// `out` holds blockDim.x * E floats (128-byte aligned).  The bulk stores of the previous
-// chunk drain from `out` while this chunk is loaded and accumulated; thread 0 waits for
-// them (bulk wait_group.read) only before `out` is overwritten.  Returns with the stores
-// issued.
+// `out` holds blockDim.x * E floats (128-byte aligned); callers alternate two such
+// buffers.  The bulk stores of the previous chunks drain while this chunk is loaded and
+// accumulated; before `out` is overwritten thread 0 waits only until every bulk group but
+// the most recent one (the previous chunk's, from the other buffer) has read its source
+// (bulk wait_group.read 1).  Returns with the stores issued as one bulk group.
 template <int FMT, int M = 8>
 __device__ __forceinline__ void qsum_chunk_tma(uint8_t *heap, uint64_t H, int pe0, int pstride, int P, uint64_t d_off,
                                                uint64_t q_off, uint64_t s_off, uint64_t c0, float *out) {
     constexpr int E = QWide<FMT>::E;
     float4 o[E / 4];
     qsum_wide_acc<FMT, M>(heap, H, pe0, pstride, P, q_off, s_off, c0 + (uint64_t)threadIdx.x * E, o);
-    if (threadIdx.x == 0) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");  // `out` free again
+    if (threadIdx.x == 0) asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");  // `out` free again
     __syncthreads();
 #pragma unroll
     for (int k = 0; k < E / 4; k++) reinterpret_cast<float4 *>(out)[threadIdx.x * (E / 4) + k] = o[k];

@@ -252,9 +252,7 @@ static int launch_xfer_v(Xfer x, int ngroups, cudaStream_t s, uint64_t *sig, uin
     x.nitems = x.seg_vec ? nseg * x.chunks_per_seg : 0;
     if (x.nitems == 0 && !sig) return SHMEMG_SUCCESS;
     const void *kfn = sig ? (const void *)k_put_signal<V> : (const void *)k_xfer<V>;
-    uint64_t cap = (uint64_t)ctas_for(kfn, XFER_THREADS, 0);
-    uint64_t gx = x.nitems < cap ? x.nitems : cap;
-    if (gx == 0) gx = 1;
+    const uint64_t gx = balanced_grid(x.nitems, (uint64_t)ctas_for(kfn, XFER_THREADS, 0), ngroups);
     dim3 grid((unsigned)gx, (unsigned)ngroups);
     if (sig) k_put_signal<V><<<grid, XFER_THREADS, 0, s>>>(x, sig, val, op, done);
     else k_xfer<V><<<grid, XFER_THREADS, 0, s>>>(x);
@@ -280,8 +278,8 @@ static int launch_xfer_bulk(Xfer x, int ngroups, cudaStream_t s) {
     x.chunks_per_seg = (x.seg_vec + XB_CHUNK - 1) / XB_CHUNK;
     const uint64_t nseg = x.kind == X_A2A ? (uint64_t)x.size * x.size : x.kind == X_FCOLLECT ? (uint64_t)x.size : 1;
     x.nitems = nseg * x.chunks_per_seg;
-    uint64_t cap = (uint64_t)ctas_for((const void *)k_xfer_bulk, 32, XB_SMEM);
-    dim3 grid((unsigned)(x.nitems < cap ? x.nitems : cap), (unsigned)ngroups);
+    dim3 grid((unsigned)balanced_grid(x.nitems, (uint64_t)ctas_for((const void *)k_xfer_bulk, 32, XB_SMEM), ngroups),
+              (unsigned)ngroups);
     k_xfer_bulk<<<grid, 32, XB_SMEM, s>>>(x, st().base, st().timeout_ns);
     return cuda_rc(cudaGetLastError());
 }
@@ -334,8 +332,7 @@ static int launch_red_v(Red r, int ngroups, cudaStream_t s) {
     r.nitems = (r.nvec + r.chunk_vec - 1) / r.chunk_vec;
     if (r.nitems == 0) return SHMEMG_SUCCESS;
     const void *kfn = (const void *)k_reduce<T, V, OP>;
-    uint64_t cap = (uint64_t)ctas_for(kfn, RED_THREADS, 0);
-    dim3 grid((unsigned)(r.nitems < cap ? r.nitems : cap), (unsigned)ngroups);
+    dim3 grid((unsigned)balanced_grid(r.nitems, (uint64_t)ctas_for(kfn, RED_THREADS, 0), ngroups), (unsigned)ngroups);
     k_reduce<T, V, OP><<<grid, RED_THREADS, 0, s>>>(r);
     return cuda_rc(cudaGetLastError());
 }

@@ -48,6 +48,10 @@ int cuda_rc(cudaError_t e);  // maps a CUDA error to SHMEMG_ERR_CUDA (records th
 
 // max co-resident CTAs of a kernel (occupancy), cached per kernel
 int ctas_for(const void *kernel, int threads, size_t smem);
+// Grid for `nitems` equal work items taken grid-stride by at most `cap` resident CTAs
+// (split over `ngroups` grid rows): as many rounds as the items need, and the fewest CTAs
+// that finish them in that many rounds, so no partial last wave runs on an idle GPU.
+uint64_t balanced_grid(uint64_t nitems, uint64_t cap, int ngroups = 1);
 
 // cooperative launch with one CTA per PE (pe_mode CTA) or one cluster of cluster_dim CTAs
 // per PE, `threads` per CTA (0: the interpreter's count); SHMEMG_ERR_UNSUPPORTED if the

@@ -179,10 +179,9 @@ int shmemg_qsum_reduce(shmemg_team_t team, float *dst, const void *q, const floa
     a.vec = (d & 15) == 0 && (qo & (fmt == SHMEMG_FMT_E4M3 ? 3 : 7)) == 0;
     a.wide = (d & 15) == 0 && (qo & 15) == 0;
     const void *kfn = fmt == SHMEMG_FMT_E4M3 ? (const void *)k_qsum<SHMEMG_FMT_E4M3> : (const void *)k_qsum<SHMEMG_FMT_BF16>;
-    uint64_t cap = (uint64_t)ctas_for(kfn, Q_THREADS, 0);
     const uint64_t E = fmt == SHMEMG_FMT_E4M3 ? 16 : 8;
-    uint64_t need = (n + Q_THREADS * E - 1) / (Q_THREADS * E);
-    dim3 grid((unsigned)(need < cap ? need : cap), (unsigned)t.ngroups);
+    const uint64_t need = (n + Q_THREADS * E - 1) / (Q_THREADS * E);
+    dim3 grid((unsigned)balanced_grid(need, (uint64_t)ctas_for(kfn, Q_THREADS, 0), t.ngroups), (unsigned)t.ngroups);
     if (fmt == SHMEMG_FMT_E4M3) k_qsum<SHMEMG_FMT_E4M3><<<grid, Q_THREADS, 0, to_stream(stream)>>>(a);
     else k_qsum<SHMEMG_FMT_BF16><<<grid, Q_THREADS, 0, to_stream(stream)>>>(a);
     return cuda_rc(cudaGetLastError());

@@ -57,6 +57,13 @@ int team_get(shmemg_team_t t, HostTeam *out) {
     return SHMEMG_SUCCESS;
 }
 
+uint64_t balanced_grid(uint64_t nitems, uint64_t cap, int ngroups) {
+    if (ngroups > 1) cap = cap / (uint64_t)ngroups > 0 ? cap / (uint64_t)ngroups : 1;
+    if (nitems <= cap) return nitems > 0 ? nitems : 1;
+    const uint64_t rounds = (nitems + cap - 1) / cap;
+    return (nitems + rounds - 1) / rounds;
+}
+
 int ctas_for(const void *kernel, int threads, size_t smem) {
     static std::mutex mu;
     static std::unordered_map<std::string, int> cache;

@@ -570,7 +570,7 @@ __device__ void admitter_warp(const SvArgs &a) {
         __syncwarp();
         if (nnew == 0 && s_adm == 0) {
             __nanosleep(sleep_ns);
-            if (sleep_ns < 1024) sleep_ns <<= 1;
+            if (sleep_ns < 256) sleep_ns <<= 1;
         } else {
             sleep_ns = 64;
         }
@@ -619,11 +619,13 @@ __device__ __forceinline__ bool publish(const SvArgs &a, uint32_t slot, uint64_t
 // the completion counter see few atomics; a claimed index below ntiles is always
 // executed, even by a worker that came from an older queue entry of the same slot, so
 // no index is lost.
-__device__ __forceinline__ bool claim_tiles(const SvArgs &a, uint32_t slot, uint32_t *tile, uint32_t *cnt) {
+__device__ __forceinline__ bool claim_tiles(const SvArgs &a, uint32_t slot, uint32_t *tile, uint32_t *cnt,
+                                            bool look = true) {
     SvSlot &s = a.slots[slot];
     const uint32_t nt = *(volatile uint32_t *)&s.ntiles;
-    // a plain look first: an exhausted request costs no atomic on its busy claim line
-    if ((uint32_t)*(volatile unsigned long long *)&s.claim >= nt) return false;
+    // a plain look first (unless the caller has just looked): an exhausted request costs
+    // no atomic on its busy claim line
+    if (look && (uint32_t)*(volatile unsigned long long *)&s.claim >= nt) return false;
     const uint32_t nworkers = gridDim.x - 1;
     uint32_t chunk = nt / (2 * nworkers);
     chunk = chunk < 1 ? 1 : chunk > 64 ? 64 : chunk;
@@ -706,7 +708,7 @@ __device__ void worker(const SvArgs &a) {
                         continue;
                     }
                     if (!primary && now_dev() - *(volatile uint64_t *)&s.t_pub < SECONDARY_DELAY_NS) continue;
-                    if (claim_tiles(a, slot, &tile, &cnt)) {
+                    if (claim_tiles(a, slot, &tile, &cnt, false)) {   // the claim word was read just above
                         s_slot = slot;
                         s_tile = tile;
                         s_cnt = cnt;
@@ -746,7 +748,19 @@ __device__ void worker(const SvArgs &a) {
             pend_amo = s_amo;
             pend_cnt += cnt;
             if (t0 + cnt >= s.ntiles) {  // the slot's last tile: nobody claims after this chunk
-                if (publish(a, s_slot, pend_sum, pend_amo, pend_cnt)) s_fin = (int)s_slot;
+                if (pend_cnt == s.ntiles) {
+                    // this worker ran every tile of the request: nobody else publishes,
+                    // so its result goes straight to the slot (read by warp 0 of this CTA
+                    // after the barrier below) without the completion counter's atomic
+                    const uint32_t kind = s.req.kind;
+                    s.checksum = kind == SHMEMG_OP_FETCH_ADD || kind == SHMEMG_OP_COMPARE_SWAP ||
+                                         kind == SHMEMG_OP_FETCH_XOR
+                                     ? pend_amo
+                                     : pend_sum;
+                    s_fin = (int)s_slot;
+                } else if (publish(a, s_slot, pend_sum, pend_amo, pend_cnt)) {
+                    s_fin = (int)s_slot;
+                }
                 pend_cnt = 0;
                 pend_sum = 0;
                 sticky = -1;

@@ -437,17 +437,25 @@ __device__ int adm_try(const SvArgs &a, AdmState &st, const shmemg_req_t &r, uin
         return 1;
     }
     int slot = -1;
-    if (lane == 0 && st.fifo_tail - *(volatile unsigned long long *)&a.ctl->fifo_head < a.fifo_cap) {
-        for (uint32_t i = 0; i < a.nslots; i++) {
-            const uint32_t k = (st.rot + i) % a.nslots;
-            if (*(volatile unsigned int *)&a.slots[k].busy == 0) { slot = (int)k; break; }
+    if (lane == 0) {
+        // the queue head and the first candidate slot are read together; a slot is taken
+        // only through an acquire load of its busy word (its finalizer released it)
+        const uint32_t k0 = st.rot % a.nslots;
+        const unsigned long long head = *(volatile unsigned long long *)&a.ctl->fifo_head;
+        const uint32_t b0 = shmemg_d_ld_acquire_u32(&a.slots[k0].busy);
+        if (st.fifo_tail - head < a.fifo_cap) {
+            if (b0 == 0) slot = (int)k0;
+            for (uint32_t i = 1; i < a.nslots && slot < 0; i++) {
+                const uint32_t k = (st.rot + i) % a.nslots;
+                if (shmemg_d_ld_acquire_u32(&a.slots[k].busy) == 0) slot = (int)k;
+            }
         }
     }
     slot = __shfl_sync(0xffffffffu, slot, 0);
     if (slot < 0) return 0;
     uint32_t p0 = 0;
     if (!find_pages(a, g, need, &p0, lane)) return 0;
-    shmemg_d_fence_gpu();  // page frees and slot releases seen above happen before reuse
+    if (need) shmemg_d_fence_gpu();  // page frees seen above happen before the pages' reuse
     mark_pages(a, g.first, g.count, p0, need, true, lane);
     SvSlot &s = a.slots[slot];
     if (lane == 0) {
@@ -620,12 +628,12 @@ __device__ __forceinline__ bool publish(const SvArgs &a, uint32_t slot, uint64_t
 // executed, even by a worker that came from an older queue entry of the same slot, so
 // no index is lost.
 __device__ __forceinline__ bool claim_tiles(const SvArgs &a, uint32_t slot, uint32_t *tile, uint32_t *cnt,
-                                            bool look = true) {
+                                            uint32_t nt_seen = 0) {
     SvSlot &s = a.slots[slot];
-    const uint32_t nt = *(volatile uint32_t *)&s.ntiles;
-    // a plain look first (unless the caller has just looked): an exhausted request costs
-    // no atomic on its busy claim line
-    if (look && (uint32_t)*(volatile unsigned long long *)&s.claim >= nt) return false;
+    // a plain look first (unless the caller has just looked, and passes the tile count it
+    // saw): an exhausted request costs no atomic on its busy claim line
+    const uint32_t nt = nt_seen ? nt_seen : *(volatile uint32_t *)&s.ntiles;
+    if (!nt_seen && (uint32_t)*(volatile unsigned long long *)&s.claim >= nt) return false;
     const uint32_t nworkers = gridDim.x - 1;
     uint32_t chunk = nt / (2 * nworkers);
     chunk = chunk < 1 ? 1 : chunk > 64 ? 64 : chunk;
@@ -703,12 +711,13 @@ __device__ void worker(const SvArgs &a) {
                     const uint32_t slot = (uint32_t)e, gen = (uint32_t)(e >> 32);
                     SvSlot &s = a.slots[slot];
                     const unsigned long long c = *(volatile unsigned long long *)&s.claim;
-                    if ((uint32_t)(c >> 32) != gen || (uint32_t)c >= *(volatile uint32_t *)&s.ntiles) {
+                    const uint32_t nt = *(volatile uint32_t *)&s.ntiles;
+                    if ((uint32_t)(c >> 32) != gen || (uint32_t)c >= nt) {
                         if (pos == h) atomicCAS(&a.ctl->fifo_head, h, h + 1);  // exhausted or stale head
                         continue;
                     }
                     if (!primary && now_dev() - *(volatile uint64_t *)&s.t_pub < SECONDARY_DELAY_NS) continue;
-                    if (claim_tiles(a, slot, &tile, &cnt, false)) {   // the claim word was read just above
+                    if (claim_tiles(a, slot, &tile, &cnt, nt)) {   // claim word and tile count read just above
                         s_slot = slot;
                         s_tile = tile;
                         s_cnt = cnt;

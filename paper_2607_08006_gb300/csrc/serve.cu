@@ -628,7 +628,7 @@ __device__ __forceinline__ bool publish(const SvArgs &a, uint32_t slot, uint64_t
 // executed, even by a worker that came from an older queue entry of the same slot, so
 // no index is lost.
 __device__ __forceinline__ bool claim_tiles(const SvArgs &a, uint32_t slot, uint32_t *tile, uint32_t *cnt,
-                                            uint32_t nt_seen = 0) {
+                                            shmemg_req_t *req, uint64_t *dst_off, uint32_t nt_seen = 0) {
     SvSlot &s = a.slots[slot];
     // a plain look first (unless the caller has just looked, and passes the tile count it
     // saw): an exhausted request costs no atomic on its busy claim line
@@ -640,10 +640,16 @@ __device__ __forceinline__ bool claim_tiles(const SvArgs &a, uint32_t slot, uint
     unsigned long long c;
     asm volatile("atom.acquire.gpu.global.add.u64 %0, [%1], %2;" : "=l"(c) : "l"(&s.claim), "l"((unsigned long long)chunk)
                  : "memory");
+    // the request and its destination are read together with the tile count (all ordered
+    // after the acquire above), so the claim costs one round trip more, not three
     const uint32_t k = (uint32_t)c, n = *(volatile uint32_t *)&s.ntiles;
+    const shmemg_req_t rq = s.req;
+    const uint64_t d = s.dst_off;
     if (k < n) {
         *tile = k;
         *cnt = k + chunk <= n ? chunk : n - k;
+        *req = rq;
+        *dst_off = d;
         return true;
     }
     return false;
@@ -662,6 +668,8 @@ __device__ void worker(const SvArgs &a) {
     __shared__ int s_fin;  // slot whose count this CTA's publish completed (warp 0 finalizes), -1 none
     __shared__ uint32_t s_slot, s_tile, s_cnt;
     __shared__ unsigned long long s_amo;
+    __shared__ __align__(16) shmemg_req_t s_req;   // the claimed slot's request and destination
+    __shared__ uint64_t s_dst;
     const uint32_t me = blockIdx.x - 1;
     bool primary = true;
     if (threadIdx.x == 0) s_fin = -1;
@@ -681,7 +689,7 @@ __device__ void worker(const SvArgs &a) {
         if (threadIdx.x == 0) {
             int cmd = 0;
             uint32_t tile, cnt;
-            if (sticky >= 0 && claim_tiles(a, (uint32_t)sticky, &tile, &cnt)) {
+            if (sticky >= 0 && claim_tiles(a, (uint32_t)sticky, &tile, &cnt, &s_req, &s_dst)) {
                 s_slot = (uint32_t)sticky;
                 s_tile = tile;
                 s_cnt = cnt;
@@ -717,7 +725,7 @@ __device__ void worker(const SvArgs &a) {
                         continue;
                     }
                     if (!primary && now_dev() - *(volatile uint64_t *)&s.t_pub < SECONDARY_DELAY_NS) continue;
-                    if (claim_tiles(a, slot, &tile, &cnt, nt)) {   // claim word and tile count read just above
+                    if (claim_tiles(a, slot, &tile, &cnt, &s_req, &s_dst, nt)) {   // claim word and tile count read just above
                         s_slot = slot;
                         s_tile = tile;
                         s_cnt = cnt;
@@ -744,11 +752,12 @@ __device__ void worker(const SvArgs &a) {
         }
         sleep_ns = 32;
         SvSlot &s = a.slots[s_slot];
-        const shmemg_req_t r = s.req;
+        const shmemg_req_t r = s_req;
+        const uint64_t dst_off = s_dst;
         const uint32_t t0 = s_tile, cnt = s_cnt;
         uint64_t part = 0;
         for (uint32_t k = 0; k < cnt; k++) {
-            part += run_tile(a, r, s.dst_off, t0 + k, &s_amo);
+            part += run_tile(a, r, dst_off, t0 + k, &s_amo);
             __syncthreads();  // (an AMO's fetched value is in s_amo)
         }
         const uint64_t sum = block_sum_u64(part);  // ends with a CTA barrier: the tiles are written
@@ -761,7 +770,7 @@ __device__ void worker(const SvArgs &a) {
                     // this worker ran every tile of the request: nobody else publishes,
                     // so its result goes straight to the slot (read by warp 0 of this CTA
                     // after the barrier below) without the completion counter's atomic
-                    const uint32_t kind = s.req.kind;
+                    const uint32_t kind = s_req.kind;
                     s.checksum = kind == SHMEMG_OP_FETCH_ADD || kind == SHMEMG_OP_COMPARE_SWAP ||
                                          kind == SHMEMG_OP_FETCH_XOR
                                      ? pend_amo

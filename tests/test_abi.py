@@ -64,3 +64,18 @@ def test_record_layouts_agree():
     for name in ("kind", "dtype", "sub", "team", "pe", "issuer", "dst", "src", "n", "operand", "cond", "aux"):
         assert name in W.OP_DTYPE.names and re.search(r"\b%s;" % name, hdr)
     assert np.dtype(W.OP_DTYPE).fields["aux"][1] == 56
+
+
+def test_halo_stride_pads_the_side_columns(libpath):
+    """Host-only: the halo buffer holds the north and south rows (nx floats each) and the
+    west and east columns (ny floats each) padded to a multiple of 4, so each of the four
+    parts, and the second buffer of the pair, starts on a 16-byte boundary."""
+    import paper_2607_08006_gb300 as sg
+
+    for nx, ny in ((4, 1), (8, 5), (1024, 1024), (2208, 9), (384, 37), (40, 7)):
+        hs = sg.halo_stride(nx, ny)
+        ny4 = (ny + 3) // 4 * 4
+        assert hs == 2 * nx + 2 * ny4
+        for part in (0, nx, 2 * nx, 2 * nx + ny4, hs):
+            assert part % 4 == 0
+        assert 2 * nx + ny4 + ny <= hs   # the east column fits inside the buffer

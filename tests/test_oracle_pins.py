@@ -579,9 +579,9 @@ def test_halo_jacobi_fourier_mode_decay(orc):
 
 def test_amo_add_word_sums_matches_sequential_application(orc):
     """The per-word operand sums (vectorised) against the sequential C oracle: on an
-    add-only stream over 2^10 words, init + sums is the final table for every word; on a
-    mixed stream, the sums count only the fetch_add ops (a word no other op touches still
-    ends at init + sum), with a first-op offset."""
+    add-only stream over 2^10 words, init + sums is the final table for every word, with
+    a first-op offset; on a mixed stream the sums count only the fetch_add ops, also on
+    words that other kinds of op touch."""
     nlog, nw, oseed, tseed = 10, 1 << 10, 0x77, 0x99
     init = W.cb64_np(tseed, np.arange(nw, dtype=np.uint64)).view(np.int64)
     ops = W.amo_stream_np(8, 30000, nlog, only=W.AMO_CODE_FADD, offset=1000)
@@ -591,13 +591,89 @@ def test_amo_add_word_sums_matches_sequential_application(orc):
     assert np.array_equal(init + orc.amo_add_word_sums(ops, 1000, oseed, words), t)
     sub = words[::7]
     assert np.array_equal(orc.amo_add_word_sums(ops, 1000, oseed, sub), (t - init)[::7])
-    nw = 1 << 16
+    # mixed stream over 2^12 words (most words see several kinds): the sequential oracle
+    # runs the same stream with every non-add op moved to a sentinel word (same position,
+    # so the same draw), which leaves each other word at init + the sum of its fetch_adds
+    nw = 1 << 12
     init = W.cb64_np(tseed, np.arange(nw, dtype=np.uint64)).view(np.int64)
-    mixed = W.amo_stream_np(9, 30000, 16)
-    t = init.copy()
-    orc.amo_stream(t, mixed, oseed, tseed, want_fetched=False)
-    w = (mixed & ((1 << 27) - 1)).astype(np.int64)
+    mixed = W.amo_stream_np(9, 30000, 12)
     code = mixed >> 27
-    only_add = np.setdiff1d(np.unique(w), w[code != 0])
-    s = orc.amo_add_word_sums(mixed, 0, oseed, only_add)
-    assert len(only_add) > 0 and np.array_equal(init[only_add] + s, t[only_add])
+    sentinel = np.uint32(nw - 1)
+    moved = np.where(code == 0, mixed, (mixed & ~np.uint32((1 << 27) - 1)) | sentinel).astype(np.uint32)
+    t = init.copy()
+    orc.amo_stream(t, moved, oseed, tseed, want_fetched=False)
+    w = (mixed & ((1 << 27) - 1)).astype(np.int64)
+    checked = np.arange(nw - 1, dtype=np.int64)
+    mixed_words = np.intersect1d(w[code == 0], w[code != 0])
+    assert len(mixed_words) > 100          # words that see fetch_adds and other kinds
+    s = orc.amo_add_word_sums(mixed, 0, oseed, checked)
+    assert np.array_equal(init[checked] + s, t[checked])
+
+
+# --------------------------------------------------------------------------- planted mistakes
+# Each pin must catch a plausible mistake in the function it pins: the oracle function is
+# replaced (on the CPU, in a stand-in module) by a variant with one such mistake, and at
+# least one of its pins has to fail.
+def _jacobi_with(mistake):
+    def sweep(grid, iters):
+        g = np.ascontiguousarray(grid, dtype=np.float32)
+        q = np.float32(0.25)
+        for _ in range(iters):
+            up, dn = np.roll(g, 1, axis=0), np.roll(g, -1, axis=0)
+            lf, rt = np.roll(g, 1, axis=1), np.roll(g, -1, axis=1)
+            if mistake == "pairing":        # (up + left) + (down + right)
+                g = q * ((up + lf) + (dn + rt))
+            elif mistake == "weight":       # 1/5 instead of 1/4
+                g = np.float32(0.2) * ((up + dn) + (lf + rt))
+            elif mistake == "no_wrap":      # zero boundary instead of periodic
+                up[0, :] = 0
+                dn[-1, :] = 0
+                lf[:, 0] = 0
+                rt[:, -1] = 0
+                g = q * ((up + dn) + (lf + rt))
+            elif mistake == "axis":         # left/right taken along the rows' axis
+                g = q * ((up + dn) + (np.roll(g, 1, axis=0) + rt))
+            elif mistake == "fma":          # one rounding fewer (sum formed in binary64)
+                g = (0.25 * ((up.astype(np.float64) + dn) + (lf.astype(np.float64) + rt))).astype(np.float32)
+        return g
+    return sweep
+
+
+@pytest.mark.parametrize("mistake", ["pairing", "weight", "no_wrap", "axis", "fma"])
+def test_halo_pins_catch_a_planted_mistake(mistake):
+    import types
+
+    fake = types.SimpleNamespace(halo_jacobi=_jacobi_with(mistake))
+    caught = 0
+    for pin in (test_halo_jacobi_operation_order_golden, test_halo_jacobi_constant_delta_and_sum,
+                test_halo_jacobi_fourier_mode_decay):
+        try:
+            pin(fake)
+        except AssertionError:
+            caught += 1
+    assert caught >= 1, mistake
+
+
+def _word_sums_with(orc, mistake):
+    def sums(ops, first_op, op_seed, words):
+        w = (ops & np.uint32((1 << 27) - 1)).astype(np.int64)
+        code = ops >> np.uint32(27)
+        pos = np.searchsorted(words, w)
+        pos[pos == len(words)] = 0
+        hit = (words[pos] == w) & ((code == 0) if mistake != "all_codes" else True)
+        i = np.nonzero(hit)[0]
+        idx = i.astype(np.uint64) + (np.uint64(first_op) if mistake != "no_offset" else np.uint64(0))
+        r = W.cb64_np(op_seed, idx)
+        mask = np.uint64((1 << 20) - 1) if mistake != "mask" else np.uint64((1 << 21) - 1)
+        v = (r & mask) + (np.uint64(1) if mistake != "no_plus_one" else np.uint64(0))
+        return np.bincount(pos[i], weights=v.astype(np.float64), minlength=len(words)).astype(np.int64)
+    return sums
+
+
+@pytest.mark.parametrize("mistake", ["all_codes", "no_offset", "mask", "no_plus_one"])
+def test_amo_sum_pin_catches_a_planted_mistake(orc, mistake):
+    import types
+
+    fake = types.SimpleNamespace(amo_stream=orc.amo_stream, amo_add_word_sums=_word_sums_with(orc, mistake))
+    with pytest.raises(AssertionError):
+        test_amo_add_word_sums_matches_sequential_application(fake)

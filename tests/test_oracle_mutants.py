@@ -1,0 +1,63 @@
+"""Planted mistakes in the C oracle fail its pins.  Each case copies the oracle package
+to a temporary directory, changes one line of its C source to a plausible mistake (the
+kind of slip a careful reader could miss), builds that copy and runs the pins written for
+the function against it: at least one must fail.  The oracle in the tree is untouched."""
+import importlib.util
+import os
+import shutil
+
+import pytest
+
+import test_oracle_pins as pins
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+MUTANTS = {
+    # the odd element of a tree level folded into the first pair instead of carried up
+    "tree_carry": ("if (m & 1) v[k++] = v[m - 1];", "if (m & 1) v[0] = v[0] + v[m - 1];",
+                   [pins.test_fp32_tree_golden]),
+    # bfloat16 ties rounded away from zero instead of to even
+    "bf16_ties_away": ("return (lo & 1) ? hi : lo;", "return hi;", [pins.test_bf16_golden_and_round_trip]),
+    # E4M3 ties to the odd code
+    "e4m3_ties_odd": ("(d == bd && (c & 1) == 0)", "(d == bd && (c & 1) == 1)", [pins.test_e4m3_golden_and_exhaustive]),
+    # Neumaier without its compensation term in the result
+    "neumaier_no_comp": ("volatile float y = sum + c;", "volatile float y = sum;",
+                         [pins.test_neumaier_golden_and_exact_rational]),
+    # Neumaier's magnitude test reversed
+    "neumaier_branch": ("if (fabsf(sum) >= fabsf(x[i])) {", "if (fabsf(sum) <= fabsf(x[i])) {",
+                        [pins.test_neumaier_golden_and_exact_rational]),
+    # compare_swap storing when the values differ
+    "cswap_condition": ("else if (kind == K_CSWAP) nw = (old == cond) ? (uint64_t)v : (uint64_t)old;",
+                        "else if (kind == K_CSWAP) nw = (old != cond) ? (uint64_t)v : (uint64_t)old;",
+                        [pins.test_amo_wraparound_cswap_xor]),
+    # alltoall without the transpose (block j of member i stays block j)
+    "alltoall_no_transpose": ("memcpy(tmp + ((uint64_t)j * size + i) * m,", "memcpy(tmp + ((uint64_t)i * size + j) * m,",
+                              [pins.test_alltoall_is_exact_transpose_permutation]),
+}
+
+
+def _mutant_oracle(tmp_path, name, old, new):
+    src = open(os.path.join(ROOT, "oracle", "oracle.c")).read()
+    assert src.count(old) == 1, name
+    d = tmp_path / "oracle"
+    shutil.copytree(os.path.join(ROOT, "oracle"), d, ignore=shutil.ignore_patterns("_build", "__pycache__"))
+    (d / "oracle.c").write_text(src.replace(old, new))
+    spec = importlib.util.spec_from_file_location(f"oracle_mutant_{name}", d / "__init__.py",
+                                                  submodule_search_locations=[str(d)])
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    mod.build(force=True)
+    return mod
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_pins_fail_on_a_planted_mistake(tmp_path, name):
+    old, new, tests = MUTANTS[name]
+    mutant = _mutant_oracle(tmp_path, name, old, new)
+    failed = 0
+    for t in tests:
+        try:
+            t(mutant)
+        except (AssertionError, mutant.OracleError):
+            failed += 1
+    assert failed >= 1, name

@@ -1,0 +1,66 @@
+"""The hand-derived binary32 tree sums of tests/golden/fp32_tree_sum.txt through every GPU
+float sum path: the host-issued reduction (k_reduce, tree unrolled in 32-rank blocks), a
+device script's reduction (the interpreter) and the batched engine (8-rank blocks with a
+carry stack).  Each evaluates the rank-pairwise tree as sums of aligned power-of-two
+blocks, and each must land on the values derived by hand from the level-by-level
+definition."""
+import os
+
+import numpy as np
+import pytest
+import torch
+
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+GOLD = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "fp32_tree_sum.txt")
+
+
+def _cases():
+    out = []
+    for line in open(GOLD):
+        line = line.strip()
+        if line and not line.startswith("#"):
+            vals, tree, _seq = [c.strip() for c in line.split(";")]
+            out.append((np.array([float(x) for x in vals.split(",")], np.float32), np.float32(float(tree))))
+    return out
+
+
+@pytest.mark.parametrize("path", ["host", "script", "batch"])
+def test_fp32_tree_golden_on_every_gpu_path(sg, path):
+    cases = _cases()
+    assert len(cases) >= 6
+    for vals, want in cases:
+        P = len(vals)
+        h = sg.Heap(P, 4096)   # one heap at a time: each case closes its own
+        try:
+            _check(sg, h, P, vals, want, path)
+        finally:
+            h.close()
+
+
+def _check(sg, h, P, vals, want, path):
+    for r in range(P):
+        h.view(0, r, torch.float32, 4).copy_(torch.tensor([vals[r], 0, 0, 0], dtype=torch.float32))
+    torch.cuda.synchronize()
+    sg.clear_status()
+    if path == "host":
+        sg.reduce(sg.TEAM_WORLD, h.base + 1024, h.base, 1, sg.FLOAT, sg.SUM)
+        sg.quiet()
+    elif path == "script":
+        op = np.zeros((), dtype=W.OP_DTYPE)
+        op["kind"], op["dtype"], op["sub"], op["team"] = W.OP_REDUCE, W.DT_FLOAT, W.RED_SUM, 0
+        op["issuer"], op["dst"], op["src"], op["n"] = -1, 1024, 0, 1
+        ops = np.array([op], dtype=W.OP_DTYPE)
+        sg.run_script(torch.from_numpy(ops.view(np.uint8).copy()).cuda(), 1, None)
+    else:
+        b = sg.Batch([sg.CollDesc(0, P, sg.FLOAT, -1, 1, h.base + 1024, h.base, None)], sg.Tune(2048, 0, 0, 0))
+        b.launch()
+        torch.cuda.synchronize()
+        b.destroy()
+    torch.cuda.synchronize()
+    assert sg.get_status()[0] == 0
+    for r in (0, P - 1):
+        got = h.view(1024, r, torch.float32, 1).cpu().numpy()[0]
+        assert np.float32(got).view(np.uint32) == want.view(np.uint32), (path, vals.tolist(), float(got), float(want))

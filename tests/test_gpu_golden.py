@@ -64,3 +64,51 @@ def _check(sg, h, P, vals, want, path):
     for r in (0, P - 1):
         got = h.view(1024, r, torch.float32, 1).cpu().numpy()[0]
         assert np.float32(got).view(np.uint32) == want.view(np.uint32), (path, vals.tolist(), float(got), float(want))
+
+
+def _neumaier_cases():
+    out = []
+    for line in open(os.path.join(os.path.dirname(GOLD), "neumaier.txt")):
+        line = line.strip()
+        if line and not line.startswith("#"):
+            vals, want, _naive = [c.strip() for c in line.split(";")]
+            v = np.array([float(x) for x in vals.split(",")], np.float32)
+            if np.all((v.view(np.uint32) & 0xFFFF) == 0):   # exact in bfloat16
+                out.append((v, np.float32(float(want))))
+    return out
+
+
+@pytest.mark.parametrize("path", ["qsum", "batch"])
+def test_neumaier_golden_on_the_quantised_gpu_paths(sg, path):
+    """The hand-traced Neumaier sums of tests/golden/neumaier.txt whose values are exact
+    in bfloat16, as bf16 codes with scale 1 (the dequantised values are the traced ones):
+    the standalone quantised reduce and the batched engine accumulate them in team-rank
+    order and must give the traced results bitwise."""
+    cases = _neumaier_cases()
+    assert len(cases) >= 3
+    for vals, want in cases:
+        P = len(vals)
+        h = sg.Heap(P, 4096)
+        try:
+            codes = (vals.view(np.uint32) >> 16).astype(np.uint16).view(np.int16)
+            for r in range(P):
+                h.view(0, r, torch.int16, 8).copy_(torch.tensor([codes[r]] + [0] * 7, dtype=torch.int16))
+                h.view(256, r, torch.float32, 4).copy_(torch.tensor([1.0, 0, 0, 0], dtype=torch.float32))
+            torch.cuda.synchronize()
+            sg.clear_status()
+            if path == "qsum":
+                sg.qsum_reduce(sg.TEAM_WORLD, h.base + 1024, h.base, h.base + 256, sg.FMT_BF16, 1)
+                sg.quiet()
+            else:
+                b = sg.Batch([sg.CollDesc(0, P, sg.FLOAT, sg.FMT_BF16, 1, h.base + 1024, h.base, h.base + 256)],
+                             sg.Tune(2048, 0, 0, 0))
+                b.launch()
+                torch.cuda.synchronize()
+                b.destroy()
+            torch.cuda.synchronize()
+            assert sg.get_status()[0] == 0
+            for r in (0, P - 1):
+                got = h.view(1024, r, torch.float32, 1).cpu().numpy()[0]
+                assert np.float32(got).view(np.uint32) == want.view(np.uint32), (path, vals.tolist(), float(got))
+        finally:
+            h.close()

@@ -112,3 +112,83 @@ def test_neumaier_golden_on_the_quantised_gpu_paths(sg, path):
                 assert np.float32(got).view(np.uint32) == want.view(np.uint32), (path, vals.tolist(), float(got))
         finally:
             h.close()
+
+
+def _golden_rows(name):
+    rows = []
+    for line in open(os.path.join(os.path.dirname(GOLD), name)):
+        line = line.strip()
+        if line and not line.startswith("#"):
+            rows.append([c.strip() for c in line.split(";")])
+    return rows
+
+
+def _quantize_codes(sg, vals, fmt, pin):
+    """Codes the GPU quantiser gives `vals` when every 128-element block also holds `pin`
+    as its largest magnitude (so the block's scale is exactly 1 for E4M3 pin 448, or for
+    bf16 pin 1)."""
+    per = 127
+    nb = (len(vals) + per - 1) // per
+    x = np.zeros((nb, 128), np.float32)
+    x[:, 0] = pin
+    flat = np.zeros(nb * per, np.float32)
+    flat[:len(vals)] = vals
+    x[:, 1:] = flat.reshape(nb, per)
+    n = nb * 128
+    h = sg.Heap(1, 1 << 20)
+    try:
+        h.view(0, 0, torch.float32, n).copy_(torch.from_numpy(x.reshape(-1)))
+        qb = 1 if fmt == sg.FMT_E4M3 else 2
+        q_off, s_off = 1 << 18, 1 << 19
+        sg.clear_status()
+        sg.quantize(sg.TEAM_WORLD, h.base + q_off, h.base + s_off, h.base, fmt, n)
+        sg.quiet()
+        assert sg.get_status()[0] == 0
+        scales = h.view(s_off, 0, torch.float32, nb).cpu().numpy()
+        assert np.all(scales == 1.0)
+        dt = torch.uint8 if qb == 1 else torch.int16
+        q = h.view(q_off, 0, dt, n).cpu().numpy().reshape(nb, 128)[:, 1:].reshape(-1)[:len(vals)]
+        return q.astype(np.uint8) if qb == 1 else q.view(np.uint16)
+    finally:
+        h.close()
+
+
+def test_e4m3_encoding_golden_on_the_gpu_quantiser(sg, orc):
+    """The golden encodings up to 448, every finite code's value (round trip) and every
+    midpoint of adjacent codes (ties to the even code), through the GPU quantiser with
+    scale 1."""
+    vals, want = [], []
+    for row in _golden_rows("e4m3.txt"):
+        # (magnitudes above 448 saturate: they would set the block's scale, so they stay
+        # with the oracle's pin and the GPU parity tests)
+        if row[0].startswith("enc") and abs(float(row[0][3:])) <= 448.0:
+            vals.append(float(row[0][3:]))
+            want.append(int(row[1], 16))
+    dec = [orc.e4m3_decode(c) for c in range(0x7F)]
+    for c in range(0x7F):
+        vals += [dec[c], -dec[c]]
+        want += [c, c | 0x80 if c else 0x80]
+    for c in range(0x7E):
+        vals.append((dec[c] + dec[c + 1]) / 2)
+        want.append(c if c % 2 == 0 else c + 1)
+    got = _quantize_codes(sg, np.array(vals, np.float32), sg.FMT_E4M3, 448.0)
+    bad = [(v, int(g), w) for v, g, w in zip(vals, got, want) if int(g) != w]
+    assert not bad, bad[:8]
+
+
+def test_bf16_encoding_golden_on_the_gpu_quantiser(sg, orc):
+    """The golden bf16 encodings of magnitude at most 1 and the midpoints of adjacent bf16
+    values in [1/256, 1) (ties to even), through the GPU quantiser with scale 1."""
+    vals, want = [], []
+    for v, code in _golden_rows("bf16.txt"):
+        if abs(float(v)) <= 1.0:
+            vals.append(float(v))
+            want.append(int(code, 16))
+    for c in range(0x3B80, 0x3F80, 3):   # 2^-8 <= value < 1
+        lo, hi = orc.bf16_decode(c), orc.bf16_decode(c + 1)
+        vals.append((lo + hi) / 2)
+        want.append(c if c % 2 == 0 else c + 1)
+    assert len(vals) > 300
+    got = _quantize_codes(sg, np.array(vals, np.float32), sg.FMT_BF16, 1.0)
+    bad = [(v, int(g), w) for v, g, w in zip(vals, got, want) if int(g) != w]
+    assert not bad, bad[:8]

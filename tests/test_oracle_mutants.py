@@ -30,6 +30,14 @@ MUTANTS = {
     "cswap_condition": ("else if (kind == K_CSWAP) nw = (old == cond) ? (uint64_t)v : (uint64_t)old;",
                         "else if (kind == K_CSWAP) nw = (old != cond) ? (uint64_t)v : (uint64_t)old;",
                         [pins.test_amo_wraparound_cswap_xor]),
+    # the serialisation checker accepting a group whatever the word's final value
+    "checker_ignores_final": ("if (!has_final || cur == final) { result = 1; break; }", "if (1) { result = 1; break; }",
+                              [pins.test_serialisation_checker_vs_brute_force,
+                               pins.test_serialisation_checker_groups_and_long_chain]),
+    # the AMO stream's compare_swap swapping when the word differs from its initial value
+    "stream_cswap_condition": ("else if (code == 1) nw = ((uint64_t)old == or_cb64(table_seed, w)) ? r : (uint64_t)old;",
+                               "else if (code == 1) nw = ((uint64_t)old != or_cb64(table_seed, w)) ? r : (uint64_t)old;",
+                               [pins.test_amo_stream_single_kind_closed_forms]),
     # alltoall without the transpose (block j of member i stays block j)
     "alltoall_no_transpose": ("memcpy(tmp + ((uint64_t)j * size + i) * m,", "memcpy(tmp + ((uint64_t)i * size + j) * m,",
                               [pins.test_alltoall_is_exact_transpose_permutation]),

@@ -2,13 +2,16 @@
 to a temporary directory, changes one line of its C source to a plausible mistake (the
 kind of slip a careful reader could miss), builds that copy and runs the pins written for
 the function against it: at least one must fail.  The oracle in the tree is untouched."""
+import functools
 import importlib.util
 import os
 import shutil
 
+import numpy as np
 import pytest
 
 import test_oracle_pins as pins
+import workloads as W
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
@@ -38,6 +41,18 @@ MUTANTS = {
     "stream_cswap_condition": ("else if (code == 1) nw = ((uint64_t)old == or_cb64(table_seed, w)) ? r : (uint64_t)old;",
                                "else if (code == 1) nw = ((uint64_t)old != or_cb64(table_seed, w)) ? r : (uint64_t)old;",
                                [pins.test_amo_stream_single_kind_closed_forms]),
+    # quantisation by a rounded reciprocal of the scale instead of a division
+    "quantize_reciprocal": ("volatile float y = x[i] / s;", "volatile float y = x[i] * (1.0f / s);",
+                            [pins.test_quantize_scales_and_codes]),
+    # fcollect gathering the members in reverse rank order
+    "fcollect_order": ("memcpy(tmp + (uint64_t)r * nbytes, at(&h, member(start, stride, r), src), nbytes);",
+                       "memcpy(tmp + (uint64_t)r * nbytes, at(&h, member(start, stride, size - 1 - r), src), nbytes);",
+                       [pins.test_fcollect_definition]),
+    # the int64 max reduction keeping the smaller value
+    "i64_max_is_min": ("                else if (op == R_MAX) acc = x > acc ? x : acc;\n                else acc = x < acc ? x : acc;\n            }\n            memcpy(out + k * 8, &acc, 8);",
+                       "                else if (op == R_MAX) acc = x < acc ? x : acc;\n                else acc = x < acc ? x : acc;\n            }\n            memcpy(out + k * 8, &acc, 8);",
+                       [functools.partial(pins.test_int_reduce_brute_force_tiny, dtype=W.DT_INT64, npdt=np.int64, bits=64),
+                        pins.test_reduce_closed_form_and_one_hot]),
     # alltoall without the transpose (block j of member i stays block j)
     "alltoall_no_transpose": ("memcpy(tmp + ((uint64_t)j * size + i) * m,", "memcpy(tmp + ((uint64_t)i * size + j) * m,",
                               [pins.test_alltoall_is_exact_transpose_permutation]),

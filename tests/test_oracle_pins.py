@@ -315,6 +315,11 @@ def test_quantize_scales_and_codes(orc):
     assert s.tolist() == [1.0, 4.0]
     assert [orc.bf16_decode(int(c)) for c in q[128:]] == [0.5, -1.0, 0.25]
     assert np.all(q[:128] == 0)
+    # a tie that only the exact quotient reaches: s = 7, x = 4.716796875, x / s = 345/512 =
+    # 0.673828125 exactly, halfway between bf16 0.671875 (0x3F2C, even) and 0.67578125
+    # (0x3F2D); x times a rounded 1/7 lands above the midpoint instead
+    q, s = orc.quantize(np.array([7.0, 4.716796875], np.float32), W.FMT_BF16)
+    assert s.tolist() == [7.0] and int(q[1]) == 0x3F2C
 
 
 def test_qsum_single_member_is_dequantised_input(orc):

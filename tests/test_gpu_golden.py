@@ -192,3 +192,23 @@ def test_bf16_encoding_golden_on_the_gpu_quantiser(sg, orc):
     got = _quantize_codes(sg, np.array(vals, np.float32), sg.FMT_BF16, 1.0)
     bad = [(v, int(g), w) for v, g, w in zip(vals, got, want) if int(g) != w]
     assert not bad, bad[:8]
+
+
+def test_gpu_quantiser_divides_exactly(sg):
+    """The hand-derived bf16 tie of the oracle's quantiser pin: in a block of largest
+    magnitude 7, x = 4.716796875 gives x / 7 = 345/512 exactly, halfway between 0x3F2C
+    (even) and 0x3F2D; only a correctly rounded quotient (not x times a rounded 1/7)
+    reaches the tie and its even code."""
+    h = sg.Heap(1, 1 << 16)
+    try:
+        x = np.zeros(128, np.float32)
+        x[0], x[1] = 7.0, 4.716796875
+        h.view(0, 0, torch.float32, 128).copy_(torch.from_numpy(x))
+        sg.clear_status()
+        sg.quantize(sg.TEAM_WORLD, h.base + 4096, h.base + 8192, h.base, sg.FMT_BF16, 128)
+        sg.quiet()
+        assert sg.get_status()[0] == 0
+        assert h.view(8192, 0, torch.float32, 1).cpu().numpy()[0] == 7.0
+        assert int(h.view(4096, 0, torch.int16, 2).cpu().numpy().view(np.uint16)[1]) == 0x3F2C
+    finally:
+        h.close()

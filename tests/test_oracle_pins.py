@@ -682,3 +682,88 @@ def test_amo_sum_pin_catches_a_planted_mistake(orc, mistake):
     fake = types.SimpleNamespace(amo_stream=orc.amo_stream, amo_add_word_sums=_word_sums_with(orc, mistake))
     with pytest.raises(AssertionError):
         test_amo_add_word_sums_matches_sequential_application(fake)
+
+
+# --------------------------------------------------------------------------- served results
+def test_checksum32_closed_forms(orc):
+    """Word i (little-endian) weighs 2i + 1, modulo 2^64: an empty buffer is 0; byte 3 of
+    word 0 weighs 2^24; word 1 weighs 3 and word 2 weighs 5; n words of 2^32 - 1 give
+    (2^32 - 1) * n^2 mod 2^64 (the first n odd numbers sum to n^2), which wraps for large n."""
+    assert orc.checksum32(np.zeros(0, np.uint8)) == 0
+    assert orc.checksum32(np.array([0, 0, 0, 1], np.uint8)) == 1 << 24
+    assert orc.checksum32(np.array([7, 0, 0, 0, 1, 0, 0, 0, 2, 0, 0, 0], np.uint8)) == 7 + 3 * 1 + 5 * 2
+    for n in (1, 2, 1000, 1 << 17):
+        buf = np.full(4 * n, 0xFF, np.uint8)
+        assert orc.checksum32(buf) == ((2 ** 32 - 1) * n * n) % 2 ** 64
+    assert ((2 ** 32 - 1) * (1 << 17) ** 2) >= 2 ** 64   # the last case does wrap
+
+
+def test_serve_request_results_by_kind(orc):
+    """Each request kind's result from the operations it is defined by: put / get return
+    the checksum of the source bytes (the copy is exact); alltoall the checksum of the
+    team's blocks transposed (numpy); a reduction that of the heap model's team reduce; an
+    AMO its fetched value, leaving the updated word."""
+    lay = W.serve_layout(H=1 << 20, amo_words=64)
+    npes = 6
+    init = np.zeros((npes, lay.H), np.uint8)
+    rng = np.random.default_rng(3)
+    init[:, lay.ro_offset:lay.ro_offset + lay.ro_bytes] = rng.integers(0, 256, (npes, lay.ro_bytes), dtype=np.uint8)
+    words = rng.integers(-2 ** 40, 2 ** 40, npes * lay.amo_words, dtype=np.int64)
+    init[:, :8 * lay.amo_words] = words.view(np.uint8).reshape(npes, -1)
+    src = lay.ro_offset + 4096
+
+    def req(**kw):
+        r = np.zeros((), W.REQ_DTYPE)
+        for k, v in kw.items():
+            r[k] = v
+        return r
+
+    # put from PE 4 to PE 1 and get by PE 2 from PE 5
+    for kind, pe, iss, srcpe in ((1, 1, 4, 4), (2, 5, 2, 5)):
+        h = orc.Heap(npes, lay.H, init.reshape(-1).copy())
+        got = orc.serve_request(h, req(kind=kind, pe=pe, issuer=iss, n=1000, src=src), lay.amo_offset,
+                                lay.amo_words, lay.arena_offset)
+        assert got == orc.checksum32(init[srcpe, src:src + 1000])
+    # alltoall over PEs 1..4, 64 bytes per pair
+    P, m = 4, 64
+    h = orc.Heap(npes, lay.H, init.reshape(-1).copy())
+    got = orc.serve_request(h, req(kind=15, pe=1, issuer=P, n=m, src=src), lay.amo_offset, lay.amo_words,
+                            lay.arena_offset)
+    blocks = np.stack([init[1 + i, src:src + P * m].reshape(P, m) for i in range(P)])   # [i][j] = member i's block j
+    want = np.concatenate([blocks[:, j, :].reshape(-1) for j in range(P)])               # member j gets blocks [i][j]
+    assert got == orc.checksum32(want)
+    # fp32 sum over PEs 0..2 of 256 elements
+    P, n = 3, 256
+    h = orc.Heap(npes, lay.H, init.reshape(-1).copy())
+    got = orc.serve_request(h, req(kind=16, dtype=W.DT_FLOAT, fmt=W.FMT_F32, pe=0, issuer=P, n=n, src=src),
+                            lay.amo_offset, lay.amo_words, lay.arena_offset)
+    ref = orc.Heap(npes, lay.H, init.reshape(-1).copy())
+    ref.reduce((0, 1, P), lay.arena_offset, src, n, W.DT_FLOAT, W.RED_SUM)
+    assert got == orc.checksum32(ref.pe(0)[lay.arena_offset:lay.arena_offset + 4 * n])
+    # fetch_add on word 70 (PE 1, index 6): returns the old value, stores old + v
+    h = orc.Heap(npes, lay.H, init.reshape(-1).copy())
+    got = orc.serve_request(h, req(kind=5, dtype=W.DT_INT64, word=70, operand=12345), lay.amo_offset,
+                            lay.amo_words, lay.arena_offset)
+    assert got == int(words[70]) & (2 ** 64 - 1) or got == int(words[70])
+    assert int(h.view(1, lay.amo_offset + 8 * 6, 1, np.int64)[0]) == int(words[70]) + 12345
+
+
+def _checksum_with(mistake):
+    def cs(buf):
+        b = np.ascontiguousarray(buf).tobytes()
+        w = np.frombuffer(b, dtype=">u4" if mistake == "big_endian" else "<u4").astype(np.uint64)
+        i = np.arange(len(w), dtype=np.uint64)
+        k = np.uint64(2) * i + (np.uint64(0) if mistake == "even_weights" else np.uint64(1))
+        if mistake == "no_wrap":
+            return int(sum(int(a) * int(c) for a, c in zip(w, k)))
+        with np.errstate(over="ignore"):
+            return int(np.sum(w * k, dtype=np.uint64))
+    return cs
+
+
+@pytest.mark.parametrize("mistake", ["big_endian", "even_weights", "no_wrap"])
+def test_checksum_pin_catches_a_planted_mistake(mistake):
+    import types
+
+    with pytest.raises(AssertionError):
+        test_checksum32_closed_forms(types.SimpleNamespace(checksum32=_checksum_with(mistake)))

@@ -767,3 +767,34 @@ def test_checksum_pin_catches_a_planted_mistake(mistake):
 
     with pytest.raises(AssertionError):
         test_checksum32_closed_forms(types.SimpleNamespace(checksum32=_checksum_with(mistake)))
+
+
+def test_binary64_references_are_exact_sums(orc):
+    """The binary64 references behind the error gates: with few members and inputs whose
+    products and partial sums are exact in binary64 (bf16 codes in [-1, 1] times a
+    power-of-two scale; binary32 values with small integer numerators), the reference sum
+    equals the exact rational sum and the magnitude sum the exact sum of magnitudes."""
+    from fractions import Fraction as F
+
+    P, n = 3, 256
+    rng = np.random.default_rng(9)
+    h = orc.Heap(P, 8192)
+    # exponents 120..126 (magnitudes 2^-7 .. < 1), any mantissa and sign: three such values
+    # times 1/4 sum exactly in binary64
+    exps = rng.integers(120, 127, (P, n)).astype(np.uint16)
+    codes = (exps << 7) | rng.integers(0, 128, (P, n)).astype(np.uint16) | (rng.integers(0, 2, (P, n)).astype(np.uint16) << 15)
+    scale = np.float32(0.25)
+    for r in range(P):
+        h.view(r, 0, n, np.uint16)[:] = codes[r]
+        h.view(r, 4096, 2, np.float32)[:] = scale
+    y, a = h.qsum_ref64((0, 1, P), 0, 4096, W.FMT_BF16, n)
+    for k in range(n):
+        xs = [F(orc.bf16_decode(int(codes[r, k]))) * F(float(scale)) for r in range(P)]
+        assert F(float(y[k])) == sum(xs) and F(float(a[k])) == sum(abs(x) for x in xs)
+    vals = (rng.integers(-1000, 1000, (P, n)) / np.float32(64)).astype(np.float32)
+    for r in range(P):
+        h.view(r, 0, n, np.float32)[:] = vals[r]
+    y, a = h.reduce_f32_ref64((0, 1, P), 0, n)
+    for k in range(n):
+        xs = [F(float(vals[r, k])) for r in range(P)]
+        assert F(float(y[k])) == sum(xs) and F(float(a[k])) == sum(abs(x) for x in xs)

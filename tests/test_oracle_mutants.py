@@ -53,6 +53,12 @@ MUTANTS = {
                        "                else if (op == R_MAX) acc = x < acc ? x : acc;\n                else acc = x < acc ? x : acc;\n            }\n            memcpy(out + k * 8, &acc, 8);",
                        [functools.partial(pins.test_int_reduce_brute_force_tiny, dtype=W.DT_INT64, npdt=np.int64, bits=64),
                         pins.test_reduce_closed_form_and_one_hot]),
+    # broadcast that leaves the root's own destination untouched
+    "broadcast_skips_root": ("    for (int r = 0; r < size; r++) memcpy(at(&h, member(start, stride, r), dst), tmp, nbytes);\n    free(tmp);\n    return OR_OK;\n}\n\n/* fcollect",
+                             "    for (int r = 0; r < size; r++) if (r != root) memcpy(at(&h, member(start, stride, r), dst), tmp, nbytes);\n    free(tmp);\n    return OR_OK;\n}\n\n/* fcollect",
+                             [pins.test_broadcast_definition_root_included]),
+    # put-with-signal adding where it should set
+    "signal_set_adds": ("    if (sig_op == S_SET) s = v;", "    if (sig_op == S_SET) s = s + v;", [pins.test_signal_ops]),
     # alltoall without the transpose (block j of member i stays block j)
     "alltoall_no_transpose": ("memcpy(tmp + ((uint64_t)j * size + i) * m,", "memcpy(tmp + ((uint64_t)i * size + j) * m,",
                               [pins.test_alltoall_is_exact_transpose_permutation]),

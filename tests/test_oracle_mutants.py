@@ -59,6 +59,9 @@ MUTANTS = {
                              [pins.test_broadcast_definition_root_included]),
     # put-with-signal adding where it should set
     "signal_set_adds": ("    if (sig_op == S_SET) s = v;", "    if (sig_op == S_SET) s = s + v;", [pins.test_signal_ops]),
+    # dequantisation dividing by the block scale instead of multiplying
+    "dequant_divides": ("    volatile float r = v * scales[i / 128];", "    volatile float r = v / scales[i / 128];",
+                        [pins.test_qsum_single_member_is_dequantised_input]),
     # alltoall without the transpose (block j of member i stays block j)
     "alltoall_no_transpose": ("memcpy(tmp + ((uint64_t)j * size + i) * m,", "memcpy(tmp + ((uint64_t)i * size + j) * m,",
                               [pins.test_alltoall_is_exact_transpose_permutation]),

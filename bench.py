@@ -11,7 +11,8 @@ with per-op GB/s and the dominant kernel's fraction of the measured HBM copy pea
 
 --impl reference times the CPU oracle on a bounded sample of the same workload.
 Under torchrun every rank runs an independent replica on its own GPU (nothing is
-exchanged between GPUs); rank 0 prints one JSON line.
+exchanged between GPUs).  Rank 0 prints each secondary leg's full record on its own
+JSON line ({"leg": ...}), then the headline as the LAST line, kept under 1400 bytes.
 """
 from __future__ import annotations
 
@@ -37,9 +38,8 @@ H = 512 * MiB               # grown from 64 MiB to hold the largest sweep points
 A_OFF, B_OFF = 0, 256 * MiB  # sources live in region A, destinations in region B
 I32_OFF = 128 * MiB          # int32 sources: A[128 MiB, 192 MiB); int64 sources: A[0, 128 MiB)
 METRIC = "collective & bulk-RMA GB/s vs HBM peak; AMO GUPS; served p50/p99 op latency"
-WORKLOAD = ("collective and RMA bandwidth sweep: 64 virtual PEs x 512 MiB (64 MiB grown to the largest "
-            "point's footprint); int32/int64 sum+max reduce and fcollect 1Ki-16Mi elements; alltoall "
-            "4KiB-1MiB per pair; broadcast 1KiB-256MiB; put_nbi/get_nbi ring + quiet 8B-256MiB")
+WORKLOAD = ("64 virtual PEs x 512 MiB sweep: int32/int64 sum+max reduce and fcollect 1Ki-16Mi elements; "
+            "alltoall 4KiB-1MiB/pair; broadcast 1KiB-256MiB; put_nbi/get_nbi ring + quiet 8B-256MiB")
 
 
 def sweep_points():
@@ -232,6 +232,11 @@ def run_gpu(args, rank, world):
         bytes_step = sum(b for *_, b in pts)
         per_pt = np.array([[ev[k][i][0].elapsed_time(ev[k][i][1]) for i in range(len(pts))]
                            for k in range(args.steps)]).mean(axis=0)
+        # the GPU on the oracle's bounded sample: the same points, their own launch times
+        sample = {(nm, f, m) for nm, f, m, _ in cpu_sample_points()}
+        sel = [i for i, (nm, f, m, _) in enumerate(pts) if (nm, f, m) in sample]
+        same_sample = {"value": round(sum(pts[i][3] for i in sel) / (float(sum(per_pt[i] for i in sel)) * 1e-3) / 1e9, 1),
+                       "unit": "GB/s"}
         # ---- end-to-end: host inputs -> device, the step, result -> host
         e2e = run_e2e(torch, sg, g, stream, args, world)
         summary = summarise(pts, per_pt)
@@ -251,21 +256,26 @@ def run_gpu(args, rank, world):
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "int32/int64 (integer reduce, byte movement)",
-        "data": "synthetic: seeded splitmix64 values U[-2^20, 2^20]",
-        "config": {"workload": WORKLOAD, "npes": NPES, "heap_bytes_per_pe": H, "pe_mode": "cluster(2 CTAs)",
-                   "points_per_step": len(pts), "algorithmic_bytes_per_step": bytes_step,
-                   "l2": "no flush: each step moves ~%d GiB, far above the 129 MB L2; the big points' inputs "
-                         "exceed L2" % (bytes_step // GiB),
-                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "dtype": "int32/int64",
+        "data": "synthetic, seeded",
+        "config": headline_config(world),
         "roofline": rl,
         "gpu_launches": g.launches_per_step() * args.steps,
         "clocks": clk,
         "e2e": e2e,
+        "gpu_on_cpu_sample": same_sample,
         "per_family": summary["families"],
         "largest_points": summary["largest"],
     }
     return out
+
+
+def headline_config(world):
+    """The workload of one step, as both arms name it."""
+    return {"workload": WORKLOAD, "npes": NPES, "pe": "2-CTA cluster",
+            "algorithmic_bytes_per_step": sum(b for *_, b in sweep_points()),
+            "l2": "no flush: %d GiB/step >> L2" % (sum(b for *_, b in sweep_points()) // GiB),
+            "parallelism": "replicas" if world > 1 else "single GPU"}
 
 
 def summarise(pts, per_pt_ms):
@@ -314,7 +324,7 @@ def roofline_for(summary, hbm, src):
     return {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
             "frac": round(achieved / hbm, 4), "traffic": traffic, "kernel": name,
             "families": d["families"], "share_of_step": round(d["ms"] / total_ms, 3),
-            "peak_source": f"{src}: MEASURED_PEAKS.json hbm_gbs" if src == "measured" else "fallback 6.8 TB/s",
+            "peak_source": "measured hbm_gbs" if src == "measured" else "fallback 6.8 TB/s",
             "launches_per_step": d["launches"], "algorithmic_bytes_per_step": d["bytes"],
             "avg_launch_ms": round(d["ms"] / d["launches"], 4),
             "per_kernel": {k: {"ms_per_step": round(v["ms"], 3), "GBps": round(v["bytes"] / (v["ms"] * 1e-3) / 1e9, 1),
@@ -464,8 +474,7 @@ def cpu_baseline(reps=None):
     n = reps or max(1, int(12.0 / max(secs, 1e-3)))
     secs = sum(run_cpu_sample(orc, heap, pts) for _ in range(n))
     return {"value": round(n * b / secs / 1e9, 3), "unit": "GB/s", "cores": 1, "kind": "oracle",
-            "sample": f"{len(pts)} sweep points with <= {CPU_MAX_ELEMS} reduce / fcollect elements and <= "
-                      f"{CPU_MAX_BYTES // KiB} KiB messages, 64 PEs, {n} passes, {secs:.1f} s, single thread",
+            "sample": f"{len(pts)} small sweep points (<= 256 Ki elts, <= 1 MiB msgs), {n} passes, {secs:.1f} s",
             "seconds": round(secs, 2)}
 
 
@@ -480,12 +489,11 @@ def run_reference(args, rank, world):
         run_cpu_sample(orc, heap, pts)
     secs = sum(run_cpu_sample(orc, heap, pts) for _ in range(args.steps))
     value = b * args.steps / secs / 1e9
-    sample = (f"{len(pts)} sweep points with <= {CPU_MAX_ELEMS} reduce/fcollect elements and <= "
-              f"{CPU_MAX_BYTES // KiB} KiB messages per step, 64 PEs, single-threaded oracle")
+    sample = f"{len(pts)} small sweep points (<= 256 Ki elts, <= 1 MiB msgs) per step, single-threaded oracle"
     return {"impl": "reference", "metric": METRIC, "value": round(value, 3), "unit": "GB/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(secs / args.steps * 1e3, 3),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32/int64",
-            "data": "synthetic", "config": {"workload": WORKLOAD + " (bounded CPU sample)", "npes": NPES},
+            "data": "synthetic", "config": headline_config(world),
             "cpu_baseline": {"value": round(value, 3), "unit": "GB/s", "cores": 1, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": round(value, 3), "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -1306,20 +1314,129 @@ def max_over_ranks(x, world):
     return float(t.item())
 
 
-def main():
+# ----------------------------------------------------------------------------- output
+HEADLINE_MAX = 1400  # bytes of the last stdout line
+ROOFLINE_KEYS = ("bound", "achieved", "peak", "unit", "frac", "traffic", "kernel", "share_of_step", "avg_launch_ms",
+                 "peak_source")
+
+
+def _get(d, *path):
+    for k in path:
+        if not isinstance(d, dict) or k not in d:
+            return None
+        d = d[k]
+    return d
+
+
+def leg_summary(name, r):
+    """A few numbers per secondary leg for the headline (the leg's own line has the rest)."""
+    if name == "script":
+        return {"dev_ops_s": _get(r, "device", "ops_per_s"), "plain_ops_s": _get(r, "host", "ops_per_s"),
+                "ok": bool(_get(r, "device", "heap_matches_oracle") and _get(r, "host", "heap_matches_oracle"))}
+    if name == "amo":
+        uni = [_get(r, "uniform_" + k, "GUPS") for k in ("plain", "agg", "combine")]
+        uni = [u for u in uni if u is not None]
+        return {"uni_GUPS": max(uni) if uni else None, "zipf_GUPS": _get(r, "zipf_combine", "GUPS"),
+                "zipf_plain_GUPS": _get(r, "zipf_plain", "GUPS"), "uni_frac": r.get("uniform_frac_of_hbm_sector_ceiling"),
+                "pp8_us": _get(r, "pingpong_512_pairs", "8", "half_rtt_us_p50")}
+    if name == "cluster":
+        return {"pp8_us": [_get(r, "pingpong_512_pairs", "8", m, "half_rtt_us_p50") for m in ("dsmem", "l2")]}
+    if name == "ctx":
+        return {"overlap_ms": r.get("overlap_saving_ms"), "ctx1_GBps": r.get("ctx1_GBps"),
+                "blocking_GBps": r.get("blocking_GBps")}
+    if name == "halo":
+        return {"GBps": _get(r, "cta", "persistent", "GBps"), "frac": r.get("frac_of_hbm"),
+                "x_plain": _get(r, "cta", "speedup_vs_plain")}
+    if name == "batch":
+        return {f: _get(r, f, "GBps") for f in ("fp32", "bf16", "e4m3")}
+    if name == "serve":
+        pts = r.get("points") or []
+        lo = pts[0] if pts else {}
+        return {"req_s": [_get(r, "burst_server", "req_per_s"), _get(r, "burst_plain", "req_per_s")],
+                "GBps": _get(r, "burst_server", "GBps"), "frac": _get(r, "burst_server", "frac_of_hbm"),
+                "low_p50_us": [_get(lo, "server", "p50_us"), _get(lo, "plain", "p50_us")],
+                "low_p99_us": [_get(lo, "server", "p99_us"), _get(lo, "plain", "p99_us")],
+                "p99_lower": "%d/%d" % (sum(1 for q in pts if (_get(q, "server", "p99_us") or 0) <
+                                            (_get(q, "plain", "p99_us") or 0)), len(pts))}
+    return {}
+
+
+def headline_numbers(summary):
+    """A handful of numbers from the secondary legs, flat, for the headline."""
+    g = _get
+    return {k: v for k, v in {
+        "amo_uni_GUPS": g(summary, "amo", "uni_GUPS"), "amo_zipf_GUPS": g(summary, "amo", "zipf_GUPS"),
+        "batch_e4m3_GBps": g(summary, "batch", "e4m3"), "halo_GBps": g(summary, "halo", "GBps"),
+        "serve_req_s": (g(summary, "serve", "req_s") or [None])[0], "serve_GBps": g(summary, "serve", "GBps")}.items()
+        if v is not None}
+
+
+def compose_headline(out, legs):
+    """The headline: the metric, roofline, clocks, e2e, the CPU baseline and a few numbers
+    per secondary leg -- short enough to be one line that a log tail keeps whole."""
+    keys = ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better", "scaling",
+            "vs_baseline", "dtype", "data", "config", "gpu_launches", "clocks", "e2e", "cpu_baseline",
+            "gpu_on_cpu_sample")
+    h = {k: out[k] for k in keys if k in out}
+    h["roofline"] = {k: out["roofline"][k] for k in ROOFLINE_KEYS if k in out.get("roofline", {})}
+    if "e2e" in h:
+        h["e2e"] = {k: v for k, v in h["e2e"].items() if k in ("value", "unit", "h2d_bytes_per_step",
+                                                                "d2h_bytes_per_step", "ms_per_step")}
+    if "cpu_baseline" in h:
+        h["cpu_baseline"] = {k: v for k, v in h["cpu_baseline"].items() if k != "seconds"}
+    if legs:
+        h["secondary"] = headline_numbers({n: leg_summary(n, r) for n, r in legs.items()})
+    while h.get("secondary") and len(headline_line(h)) > HEADLINE_MAX:
+        h["secondary"].popitem()
+    for drop in (("secondary",), ("gpu_on_cpu_sample",), ("config", "l2"), ("roofline", "peak_source")):
+        if len(headline_line(h)) <= HEADLINE_MAX:
+            break
+        d = h
+        for k in drop[:-1]:
+            d = d.get(k, {})
+        d.pop(drop[-1], None)
+    return h
+
+
+def headline_line(h):
+    return json.dumps(h, separators=(",", ":"))
+
+
+LEGS = ("script", "amo", "cluster", "ctx", "halo", "batch", "serve")
+
+
+def run_leg(name, args, torch, sg):
+    if name == "script":
+        return run_script_leg(torch, sg)
+    if name == "amo":
+        return run_amo(torch, sg, args.amo_ops_log2)
+    if name == "cluster":
+        return run_cluster_leg(torch, sg)
+    if name == "halo":
+        return run_halo(torch, sg)
+    if name == "ctx":
+        return run_ctx_leg(torch, sg)
+    if name == "batch":
+        return run_batch(torch, sg)
+    if name == "serve":
+        return run_serve(torch, sg, args.serve_requests)
+    raise SystemExit(f"unknown secondary leg {name}")
+
+
+def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="shmemg", choices=["shmemg", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--secondary", default="script,amo,cluster,ctx,halo,batch,serve",
-                    help="extra workloads measured after the sweep (comma list of script,amo,cluster,ctx,halo,"
-                         "batch,serve or 'none')")
+    ap.add_argument("--secondary", default=",".join(LEGS),
+                    help="extra workloads measured after the sweep (comma list of %s, or 'none'); each prints "
+                         "its own JSON line before the headline" % ",".join(LEGS))
     ap.add_argument("--amo-ops-log2", type=int, default=30)
     ap.add_argument("--serve-requests", type=int, default=1 << 16)
     ap.add_argument("--profile", choices=PROFILE_CASES, help="run one small single-kernel case (for ncu) and exit")
-    args = ap.parse_args()
+    args = ap.parse_args(argv)
     if args.profile:
         run_profile_case(args.profile)
         return
@@ -1329,37 +1446,29 @@ def main():
             print(json.dumps(run_reference(args, rank, world)), flush=True)
         return
     out = run_gpu(args, rank, world)
-    if rank == 0:
-        if not args.no_cpu_baseline and world == 1:
-            out["cpu_baseline"] = cpu_baseline()
-        sec = [s for s in args.secondary.split(",") if s and s != "none"]
-        if sec:
-            import torch
+    if rank != 0:
+        return
+    if not args.no_cpu_baseline and world == 1:
+        out["cpu_baseline"] = cpu_baseline()
+    # detail lines first, the headline last
+    print(json.dumps({"leg": "sweep", "per_family": out.get("per_family"), "largest_points": out.get("largest_points"),
+                      "roofline": out.get("roofline"), "e2e": out.get("e2e")}), flush=True)
+    legs = {}
+    sec = [s for s in args.secondary.split(",") if s and s != "none"]
+    if sec:
+        import torch
 
-            import paper_2607_08006_gb300 as sg
+        import paper_2607_08006_gb300 as sg
 
-            out["secondary"] = {}
-            for name in sec:
-                t0 = time.perf_counter()
-                if name == "script":
-                    r = run_script_leg(torch, sg)
-                elif name == "amo":
-                    r = run_amo(torch, sg, args.amo_ops_log2)
-                elif name == "cluster":
-                    r = run_cluster_leg(torch, sg)
-                elif name == "halo":
-                    r = run_halo(torch, sg)
-                elif name == "ctx":
-                    r = run_ctx_leg(torch, sg)
-                elif name == "batch":
-                    r = run_batch(torch, sg)
-                elif name == "serve":
-                    r = run_serve(torch, sg, args.serve_requests)
-                else:
-                    continue
-                r["wall_s"] = round(time.perf_counter() - t0, 1)
-                out["secondary"][name] = r
-        print(json.dumps(out), flush=True)
+        for name in sec:
+            t0 = time.perf_counter()
+            r = run_leg(name, args, torch, sg)
+            r["wall_s"] = round(time.perf_counter() - t0, 1)
+            legs[name] = r
+            print(json.dumps({"leg": name, **r}), flush=True)
+    if legs:
+        print(json.dumps({"leg": "summary", **{n: leg_summary(n, r) for n, r in legs.items()}}), flush=True)
+    print(headline_line(compose_headline(out, legs)), flush=True)
 
 
 if __name__ == "__main__":

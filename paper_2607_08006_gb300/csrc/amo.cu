@@ -459,7 +459,7 @@ int shmemg_amo_stream(int64_t *table, uint64_t words_per_pe, const uint32_t *ops
 int shmemg_pingpong(void *buf, uint64_t *sig, uint64_t payload, int npairs, int iters, uint64_t *lat_ns, void *stream) {
     if (int rc = check_init()) return rc;
     State &S = st();
-    if (npairs < 1 || iters < 0 || 2 * npairs > S.npes) return SHMEMG_ERR_INVALID_ARG;
+    if (npairs < 1 || iters < 0 || 2 * (int64_t)npairs > S.npes) return SHMEMG_ERR_INVALID_ARG;
     if (S.pe_mode != SHMEMG_PE_MODE_CTA) return SHMEMG_ERR_UNSUPPORTED;
     uint64_t boff, soff;
     if (sym_offset(buf, 2 * payload, &boff) || sym_offset(sig, 8, &soff) || (soff & 7)) return SHMEMG_ERR_NOT_SYMMETRIC;
@@ -484,7 +484,7 @@ int shmemg_pingpong_cluster(void *buf, uint64_t *sig, uint64_t payload, int npai
                             void *stream) {
     if (int rc = check_init()) return rc;
     State &S = st();
-    if (npairs < 1 || iters < 0 || 2 * npairs > S.npes || payload > SHMEMG_PINGPONG_CLUSTER_MAX) return SHMEMG_ERR_INVALID_ARG;
+    if (npairs < 1 || iters < 0 || 2 * (int64_t)npairs > S.npes || payload > SHMEMG_PINGPONG_CLUSTER_MAX) return SHMEMG_ERR_INVALID_ARG;
     if (S.pe_mode != SHMEMG_PE_MODE_CTA || S.cluster_dim < 2 || (2 * npairs) % S.cluster_dim) return SHMEMG_ERR_UNSUPPORTED;
     uint64_t boff, soff;
     if (sym_offset(buf, 2 * payload, &boff) || sym_offset(sig, 8, &soff) || (soff & 7)) return SHMEMG_ERR_NOT_SYMMETRIC;

@@ -198,7 +198,7 @@ int shmemg_batch_create(const shmemg_coll_desc_t *descs, int count, const shmemg
         const shmemg_coll_desc_t &d = descs[i];
         BTeam t;
         memset(&t, 0, sizeof(t));
-        if (d.size < 1 || d.start < 0 || d.start + d.size > S.npes || d.n == 0) { delete b; return SHMEMG_ERR_INVALID_ARG; }
+        if (d.size < 1 || d.start < 0 || (int64_t)d.start + d.size > S.npes || d.n == 0) { delete b; return SHMEMG_ERR_INVALID_ARG; }
         t.start = d.start;
         t.size = d.size;
         t.n = d.n;
@@ -357,7 +357,7 @@ extern "C" int shmemg_batch_reduce_noalloc(const shmemg_coll_desc_t *descs, int 
         const shmemg_coll_desc_t &c = descs[i];
         BTeam &t = g_noalloc_teams_h[i];
         memset(&t, 0, sizeof(t));
-        if (c.size < 1 || c.start < 0 || c.start + c.size > S.npes || c.n == 0) return SHMEMG_ERR_INVALID_ARG;
+        if (c.size < 1 || c.start < 0 || (int64_t)c.start + c.size > S.npes || c.n == 0) return SHMEMG_ERR_INVALID_ARG;
         t.start = c.start;
         t.size = c.size;
         t.n = c.n;

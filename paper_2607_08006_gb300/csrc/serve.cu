@@ -142,7 +142,7 @@ __host__ __device__ inline Geo geometry(const shmemg_req_t &r, int npes, uint64_
         else if (r.dtype == SHMEMG_FLOAT && r.fmt == FMT_F32) { in_es = 4; out_es = 4; }
         else if (r.dtype == SHMEMG_FLOAT && r.fmt == SHMEMG_FMT_BF16) { in_es = 2; out_es = 4; }
         else return g;
-        if (P < 1 || r.pe < 0 || r.pe + P > npes || r.n == 0 || (r.n & 3) || (r.src & 15) || r.src > H ||
+        if (P < 1 || r.pe < 0 || (int64_t)r.pe + P > npes || r.n == 0 || (r.n & 3) || (r.src & 15) || r.src > H ||
             r.n * in_es > H - r.src)
             return g;
         if (r.fmt == SHMEMG_FMT_BF16 && r.dtype == SHMEMG_FLOAT) {
@@ -157,7 +157,7 @@ __host__ __device__ inline Geo geometry(const shmemg_req_t &r, int npes, uint64_
     }
     case SHMEMG_OP_ALLTOALL: {
         int P = r.issuer;
-        if (P < 1 || r.pe < 0 || r.pe + P > npes || r.n == 0 || (r.n & 15) || (r.src & 15) || r.src > H ||
+        if (P < 1 || r.pe < 0 || (int64_t)r.pe + P > npes || r.n == 0 || (r.n & 15) || (r.src & 15) || r.src > H ||
             r.n * (uint64_t)P > H - r.src)
             return g;
         g.first = r.pe;

@@ -117,3 +117,24 @@ def test_last_word_amos_signal_only_and_satisfied_waits(sg, heapf, orc):
     assert first_diff(download(h), ref.mem) is None
     got = fetched.cpu().numpy()
     assert got[0] == want[0] and (got[1] & 0xFFFFFFFF) == (want[1] & 0xFFFFFFFF)
+
+
+def test_team_ranges_past_int32_are_rejected(sg, heapf):
+    """A team whose start + size passes INT32_MAX is refused before anything launches
+    (the range check is done in 64 bits), by the batched engine and its allocation-free
+    form alike; the heap stays as it was."""
+    h = heapf(4, 1 << 16)
+    parts = h.partitions()
+    parts.random_(0, 255)
+    before = parts.clone()
+    big = (1 << 31) - 1
+    for start, size in ((big, 1), (1, big), (big, big)):
+        d = [sg.CollDesc(start, size, sg.INT64, -1, 8, h.base + 4096, h.base, None)]
+        with pytest.raises(sg.ShmemgError) as e:
+            sg.Batch(d, sg.Tune(16384, 0, 0, 0))
+        assert e.value.code == sg.ERR_INVALID_ARG
+        with pytest.raises(sg.ShmemgError) as e:
+            sg.batch_reduce_noalloc(d, 128)
+        assert e.value.code == sg.ERR_INVALID_ARG
+    torch.cuda.synchronize()
+    assert sg.get_status()[0] == 0 and torch.equal(parts, before)

@@ -62,6 +62,14 @@ MUTANTS = {
     # dequantisation dividing by the block scale instead of multiplying
     "dequant_divides": ("    volatile float r = v * scales[i / 128];", "    volatile float r = v / scales[i / 128];",
                         [pins.test_qsum_single_member_is_dequantised_input]),
+    # the quantised all-reduce accumulating the members in reverse rank order
+    "qsum_reverse_order": ("col[r] = deq(at(&h, p, q_off), (const float *)at(&h, p, s_off), k, fmt);",
+                           "col[size - 1 - r] = deq(at(&h, p, q_off), (const float *)at(&h, p, s_off), k, fmt);",
+                           [pins.test_qsum_multi_member_golden]),
+    # the quantised all-reduce dequantising every member with the first member's scales
+    "qsum_scale_of_member0": ("col[r] = deq(at(&h, p, q_off), (const float *)at(&h, p, s_off), k, fmt);",
+                              "col[r] = deq(at(&h, p, q_off), (const float *)at(&h, member(start, stride, 0), s_off), k, fmt);",
+                              [pins.test_qsum_multi_member_golden, pins.test_serve_request_results_by_kind]),
     # alltoall without the transpose (block j of member i stays block j)
     "alltoall_no_transpose": ("memcpy(tmp + ((uint64_t)j * size + i) * m,", "memcpy(tmp + ((uint64_t)i * size + j) * m,",
                               [pins.test_alltoall_is_exact_transpose_permutation]),

@@ -698,6 +698,48 @@ def test_checksum32_closed_forms(orc):
     assert ((2 ** 32 - 1) * (1 << 17) ** 2) >= 2 ** 64   # the last case does wrap
 
 
+def test_qsum_multi_member_golden(orc):
+    """The hand-traced Neumaier rows of tests/golden/neumaier.txt that are exact in
+    bfloat16, through the heap model's quantised all-reduce on a four-member team of
+    stride 2 (PEs 1, 3, 5, 7 of 9): element k carries row k mod rows, member r holds the
+    row's r-th value (rows of three get a trailing 0, which changes no sum) as a bf16 code
+    times a power-of-two scale of its own per member and block (so the dequantised value
+    is the traced one exactly), over two blocks with a ragged tail.  Every member's dst
+    must equal the traced sum bitwise, and the PEs outside the team stay as they were.
+    The order-sensitive rows fix the team-rank order, the distinct scales that each
+    member's own scale is used."""
+    rows = []
+    for vals, want, _naive in _golden("neumaier.txt"):
+        v = np.array([float(x) for x in vals.split(",")], np.float32)
+        if np.all((v.view(np.uint32) & 0xFFFF) == 0):
+            rows.append((np.concatenate([v, np.zeros(4 - len(v), np.float32)]), np.float32(float(want))))
+    assert len(rows) >= 5
+    npes, P, start, stride, n = 9, 4, 1, 2, 200
+    H = 8192
+    q_off, s_off, dst = 0, 1024, 2048
+    rng = np.random.default_rng(17)
+    init = rng.integers(0, 256, (npes, H), dtype=np.uint8)
+    want = np.empty(n, np.float32)
+    for r in range(P):
+        p = start + r * stride
+        scales = np.array([2.0 ** (3 * r - 4), 2.0 ** (5 - 2 * r)], np.float32)   # per block, distinct per member
+        vals = np.array([rows[k % len(rows)][0][r] for k in range(n)], np.float32)
+        codes = ((vals / np.repeat(scales, 128)[:n]).astype(np.float32).view(np.uint32) >> 16).astype(np.uint16)
+        assert np.array_equal(codes.astype(np.uint32) << 16, (vals / np.repeat(scales, 128)[:n]).view(np.uint32))
+        init[p, q_off:q_off + 2 * n] = codes.view(np.uint8)
+        init[p, s_off:s_off + 8] = scales.view(np.uint8)
+    for k in range(n):
+        want[k] = rows[k % len(rows)][1]
+    h = orc.Heap(npes, H, init.reshape(-1).copy())
+    h.qsum_reduce((start, stride, P), dst=dst, q_off=q_off, s_off=s_off, fmt=W.FMT_BF16, n=n)
+    for p in range(npes):
+        if p in range(start, start + P * stride, stride):
+            assert np.array_equal(h.view(p, dst, n, np.float32).view(np.uint32), want.view(np.uint32)), p
+            assert np.array_equal(h.pe(p)[:dst], init[p, :dst]) and np.array_equal(h.pe(p)[dst + 4 * n:], init[p, dst + 4 * n:])
+        else:
+            assert np.array_equal(h.pe(p), init[p]), p
+
+
 def test_serve_request_results_by_kind(orc):
     """Each request kind's result from the operations it is defined by: put / get return
     the checksum of the source bytes (the copy is exact); alltoall the checksum of the
@@ -740,6 +782,24 @@ def test_serve_request_results_by_kind(orc):
     ref = orc.Heap(npes, lay.H, init.reshape(-1).copy())
     ref.reduce((0, 1, P), lay.arena_offset, src, n, W.DT_FLOAT, W.RED_SUM)
     assert got == orc.checksum32(ref.pe(0)[lay.arena_offset:lay.arena_offset + 4 * n])
+    # bf16 payloads with per-128 scales over PEs 1..3, 256 elements (two blocks): codes of
+    # small integers times power-of-two scales, so every partial sum is an exact binary32
+    # integer and the Neumaier result is the plain integer sum; the scales sit at `cond`
+    P, n = 3, 256
+    ints = rng.integers(-200, 201, (P, n))
+    scl = np.array([[2.0, 0.5], [4.0, 1.0], [0.25, 8.0]], np.float32)
+    h = orc.Heap(npes, lay.H, init.reshape(-1).copy())
+    sc_off = src + 4096
+    for r in range(P):
+        x = (ints[r] / np.repeat(scl[r], 128)).astype(np.float32)
+        h.view(1 + r, src, n, np.uint16)[:] = (x.view(np.uint32) >> 16).astype(np.uint16)
+        assert np.array_equal((x.view(np.uint32) & 0xFFFF), np.zeros(n, np.uint32))   # exact in bf16
+        h.view(1 + r, sc_off, 2, np.float32)[:] = scl[r]
+    got = orc.serve_request(h, req(kind=16, dtype=W.DT_FLOAT, fmt=W.FMT_BF16, pe=1, issuer=P, n=n, src=src,
+                                   cond=sc_off), lay.amo_offset, lay.amo_words, lay.arena_offset)
+    assert got == orc.checksum32(ints.sum(0).astype(np.float32).view(np.uint8))
+    for r in range(P):
+        assert np.array_equal(h.view(1 + r, lay.arena_offset, n, np.float32), ints.sum(0).astype(np.float32))
     # fetch_add on word 70 (PE 1, index 6): returns the old value, stores old + v
     h = orc.Heap(npes, lay.H, init.reshape(-1).copy())
     got = orc.serve_request(h, req(kind=5, dtype=W.DT_INT64, word=70, operand=12345), lay.amo_offset,

@@ -203,7 +203,10 @@ int shmemg_query_capabilities(shmemg_team_t team, shmemg_caps_t *out);
 /* ----------------------------------------------------------------- status */
 /* Device status word: first error recorded by device code since the last clear
  * (SHMEMG_SUCCESS if none) and an operation-specific detail (op index, PE ...).
- * Synchronises the device. */
+ * For SHMEMG_ERR_TIMEOUT of a bulk (TMA) ring: -2 a device-initiated copy, -3 a
+ * host-issued bulk transfer or an explicit context's queue, each after the loads still
+ * in flight have landed; -4 a load that did not land even then (the launch's results are
+ * void and the ring was not used again).  Synchronises the device. */
 int shmemg_get_status(int *code, int64_t *detail);
 int shmemg_clear_status(void *stream);
 const char *shmemg_strerror(int code);

@@ -279,10 +279,28 @@ static __device__ __forceinline__ bool shmemg_mbar_wait(uint64_t *bar, uint32_t 
     }
 }
 
+/* The ring invariant on the timeout path.  A ring of `stages` stages whose wait for chunk
+ * j timed out still has the loads of chunks j .. min(j + stages, count) - 1 issued and not
+ * waited for; they write into shared memory asynchronously, and the bulk-group wait does
+ * not cover them (mbarriers track them).  This waits for each (bounded), so that after a
+ * true return no load of the ring is in flight and the ring may be reused or the CTA may
+ * exit.  A false return means a load did not land within another timeout: the caller
+ * records it (status detail -4: the launch's results are void) and issues nothing more
+ * into that ring. */
+static __device__ __forceinline__ bool shmemg_bulk_drain_loads(uint64_t *bars, uint32_t stages, uint64_t j,
+                                                               uint64_t count, uint64_t timeout_ns) {
+    bool ok = true;
+    const uint64_t end = j + stages < count ? j + stages : count;
+    for (uint64_t k = j; k < end; k++)
+        ok = shmemg_mbar_wait(&bars[k % stages], (uint32_t)((k / stages) & 1u), timeout_ns) && ok;
+    return ok;
+}
+
 /* Thread-scope bulk copy of the chunks first, first+stride, ... of (dst <- src, n bytes);
  * dst, src and n multiples of 16.  smem: SHMEMG_BULK_SMEM bytes (128-byte aligned);
  * bars: SHMEMG_BULK_STAGES mbarriers.  Returns once the data is written (blocking put
- * semantics); SHMEMG_ERR_TIMEOUT (recorded in the status word) if a stage never fills. */
+ * semantics); SHMEMG_ERR_TIMEOUT (recorded in the status word) if a stage never fills, after
+ * waiting (bounded) for the loads still in flight (shmemg_bulk_drain_loads). */
 static __device__ int shmemg_d_bulk_copy_thread(const shmemg_device_ctx_t &c, uint8_t *dst, const uint8_t *src,
                                                 uint64_t n, uint32_t first, uint32_t stride, uint8_t *smem,
                                                 uint64_t *bars) {
@@ -307,7 +325,8 @@ static __device__ int shmemg_d_bulk_copy_thread(const shmemg_device_ctx_t &c, ui
     for (uint32_t j = 0; j < count; j++) {
         const uint32_t s = j % SHMEMG_BULK_STAGES;
         if (!shmemg_mbar_wait(&bars[s], (j / SHMEMG_BULK_STAGES) & 1u, c.timeout_ns)) {
-            shmemg_d_set_status(c, SHMEMG_ERR_TIMEOUT, -2);
+            const bool drained = shmemg_bulk_drain_loads(bars, SHMEMG_BULK_STAGES, j, count, c.timeout_ns);
+            shmemg_d_set_status(c, SHMEMG_ERR_TIMEOUT, drained ? -2 : -4);
             rc = SHMEMG_ERR_TIMEOUT;
             break;
         }

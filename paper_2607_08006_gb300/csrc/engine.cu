@@ -155,8 +155,11 @@ __global__ void __launch_bounds__(32) k_xfer_bulk(Xfer x, uint8_t *state, uint64
     for (uint64_t j = 0; j < count; j++) {
         const uint32_t s = (uint32_t)(j % XB_STAGES);
         if (!shmemg_mbar_wait(&bars[s], (uint32_t)((j / XB_STAGES) & 1), timeout_ns)) {
+            // no load of the ring may still be writing shared memory when the CTA exits
+            const bool drained = shmemg_bulk_drain_loads(bars, XB_STAGES, j, count, timeout_ns);
             int *st = (int *)(state + SHMEMG_STATUS_OFF);
-            if (atomicCAS(st, 0, SHMEMG_ERR_TIMEOUT) == 0) *(volatile int64_t *)(state + SHMEMG_STATUS_OFF + 8) = -3;
+            if (atomicCAS(st, 0, SHMEMG_ERR_TIMEOUT) == 0)
+                *(volatile int64_t *)(state + SHMEMG_STATUS_OFF + 8) = drained ? -3 : -4;
             break;
         }
         const XChunk c = xchunk(x, blockIdx.x + j * gridDim.x, base_pe);

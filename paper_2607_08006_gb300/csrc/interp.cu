@@ -112,7 +112,15 @@ __device__ __forceinline__ void ctx_drain(const shmemg_device_ctx_t &c, CtxState
         if (x.st < x.ld) {
             const uint32_t s = (uint32_t)(x.st % CTX_STAGES);
             if (!shmemg_mbar_wait(&x.bar[s], (uint32_t)((x.st / CTX_STAGES) & 1), c.timeout_ns)) {
-                shmemg_d_set_status(c, SHMEMG_ERR_TIMEOUT, -3);
+                // The other loads in flight land (bounded) before giving up.  The state
+                // stays as it is: a stage is reloaded only after its chunk has been
+                // stored, so a load that lands late overwrites nothing in use, and the
+                // script's final drain waits for it again.
+                bool drained = true;
+                for (uint64_t k = x.st + 1; k < x.ld; k++)
+                    drained = shmemg_mbar_wait(&x.bar[k % CTX_STAGES], (uint32_t)((k / CTX_STAGES) & 1), c.timeout_ns) &&
+                              drained;
+                shmemg_d_set_status(c, SHMEMG_ERR_TIMEOUT, drained ? -3 : -4);
                 break;
             }
         }

@@ -266,6 +266,8 @@ def run_gpu(args, rank, world):
         "gpu_on_cpu_sample": same_sample,
         "per_family": summary["families"],
         "largest_points": summary["largest"],
+        "points": [[nm, m, round(float(ms), 4), round(b / (float(ms) * 1e-3) / 1e9, 1)]
+                   for (nm, f, m, b), ms in zip(pts, per_pt)],
     }
     return out
 
@@ -1171,7 +1173,7 @@ def run_serve(torch, sg, nreq=1 << 16, rates=None, npes=512, Hs=32 << 20):
 
 
 # ----------------------------------------------------------------------------- profiling cases
-PROFILE_CASES = ("interp_ring", "reduce", "reduce_f32", "broadcast", "alltoall", "amo", "amo_plain", "amo_combine", "amo_combine_zipf", "batch_bf16", "batch_e4m3", "qsum",
+PROFILE_CASES = ("interp_ring", "reduce", "reduce_f32", "broadcast", "alltoall", "amo", "amo_l2", "amo_plain", "amo_combine", "amo_combine_zipf", "batch_bf16", "batch_e4m3", "qsum",
                  "pingpong_cluster", "cluster_coll", "halo", "halo_plain")
 
 
@@ -1224,6 +1226,13 @@ def run_profile_case(name, launches=4):
         f = torch.empty(nops, dtype=torch.int64, device="cuda")
         for _ in range(launches):
             sg.amo_stream(heap.base, wpp, ops, nops, 1, 2, f, 0, s)
+    elif name == "amo_l2":         # the same kernel on an L2-resident table: 2^21 words (16 MiB), 2^24 ops
+        wpp = (1 << 21) // 1024
+        heap = sg.Heap(1024, 1 << 17)
+        nops = 1 << 24
+        ops = torch.from_numpy(W.amo_stream_np(5, nops, 21).view(np.int32)).cuda()
+        for _ in range(launches):
+            sg.amo_stream(heap.base, wpp, ops, nops, 1, 2, None, 0, s)
     elif name in ("amo_plain", "amo_combine", "amo_combine_zipf"):  # as "amo", 2^24 ops
         wpp = 1 << 17
         heap = sg.Heap(1024, wpp * 8)
@@ -1451,8 +1460,8 @@ def main(argv=None):
     if not args.no_cpu_baseline and world == 1:
         out["cpu_baseline"] = cpu_baseline()
     # detail lines first, the headline last
-    print(json.dumps({"leg": "sweep", "per_family": out.get("per_family"), "largest_points": out.get("largest_points"),
-                      "roofline": out.get("roofline"), "e2e": out.get("e2e")}), flush=True)
+    print(json.dumps({"leg": "sweep", "per_family": out.get("per_family"), "roofline": out.get("roofline"),
+                      "e2e": out.get("e2e"), "points": out.get("points")}), flush=True)
     legs = {}
     sec = [s for s in args.secondary.split(",") if s and s != "none"]
     if sec:

@@ -505,20 +505,40 @@ int shmemg_batch_reduce_noalloc(const shmemg_coll_desc_t *descs, int count, int 
  *   ALLTOALL blocks of n bytes over PEs pe .. pe+issuer-1 from `src` into fresh pages
  * Offsets `src` (and `cond` for bf16 scales) are symmetric byte offsets of caller data
  * the server only reads: 16-byte aligned; n a multiple of 8 (RMA), 4 (REDUCE) or 16
- * (ALLTOALL).  The result is the fetched value (AMO) or a checksum of the output:
+ * (ALLTOALL).
+ *
+ * Staged payloads (flags & SHMEMG_REQ_STAGED; not for AMOs).  The request brings its
+ * input instead of naming caller data: `word` is the payload's seed, `src` and `cond`
+ * are ignored.  Admission takes one page range, the request's region, on every PE the
+ * request touches (PUT/GET: the source and the destination PE; REDUCE/ALLTOALL: every
+ * member), laid out from its start R (16-byte aligned parts):
+ *   PUT/GET    [R, R + a) destination, [R + a, R + 2a) source, a = n rounded up to 16
+ *   REDUCE     fp32 and int64: [R, R + n*e) source and destination (in place);
+ *              bf16: [R, R + c4) fp32 destination, then the source: codes at R + c4
+ *              (2n bytes) and scales at R + c4 + c2 (4*ceil(n/128) bytes), where c4, c2
+ *              are 4n and 2n rounded up to 16
+ *   ALLTOALL   [R, R + P*n) destination blocks, [R + P*n, R + 2*P*n) source blocks
+ * The request first writes its source on every source PE p: 32-bit word j of the source
+ * part (at byte 4j from its start) is w(j) = (b(z >> 56) << 16) | b((z >> 48) & 255),
+ * where z is the first output of Steele, Lea and Flood's SplitMix64 stream started at
+ * state seed ^ ((p << 40) | j), and b(k) the bfloat16 code of (k - 128) / 128; then it
+ * runs the operation on that source like any other request.
+ *
+ * The result is the fetched value (AMO) or a checksum of the output:
  * sum over its little-endian 32-bit words w_i (members' outputs concatenated in team
  * rank order) of w_i * (2i + 1), modulo 2^64.  Invalid requests complete with an error
  * status.  Progress: the kernel needs no host action to progress; it exits on stop,
  * after idle_ns without requests, or after max_ns in total. */
+#define SHMEMG_REQ_STAGED 1u   /* shmemg_req_t.flags: the request stages its own payload */
 typedef struct {
     uint32_t kind;
     uint8_t dtype;
     uint8_t fmt;
-    uint16_t reserved0;
+    uint16_t flags;     /* SHMEMG_REQ_STAGED or 0 */
     int32_t pe;
     int32_t issuer;     /* RMA/AMO issuing PE; REDUCE/ALLTOALL team size */
     uint64_t n;
-    uint64_t word;
+    uint64_t word;      /* AMO: table word; staged payload: its seed */
     int64_t operand;
     int64_t cond;
     uint64_t src;       /* symmetric offset of the request's input */

@@ -227,10 +227,15 @@ def checksum32(buf: np.ndarray) -> int:
         return int(np.sum(w * (np.uint64(2) * i + np.uint64(1)), dtype=np.uint64))
 
 
-def serve_request(heap: "Heap", r, amo_offset: int, amo_words: int, scratch_off: int):
+def serve_request(heap: "Heap", r, amo_offset: int, amo_words: int, scratch_off: int, payload=None):
     """Expected result of one served request applied alone to `heap` (its output is built
-    at scratch_off): the fetched value for an AMO, else the output's checksum32."""
+    at scratch_off): the fetched value for an AMO, else the output's checksum32.  A request
+    that stages its payload (flags bit 0) builds its whole region at scratch_off; the
+    caller's payload(seed, pe, j0, count) gives words [j0, j0 + count) of heap PE pe's
+    source part."""
     kind = int(r["kind"])
+    if int(r["flags"]) & 1:
+        return _serve_staged(heap, r, scratch_off, payload)
     if kind in (5, 6, 7):
         w = int(r["word"])
         return heap.amo64(kind, w // amo_words, amo_offset + 8 * (w % amo_words), int(r["operand"]), int(r["cond"]))
@@ -254,6 +259,51 @@ def serve_request(heap: "Heap", r, amo_offset: int, amo_words: int, scratch_off:
     if kind == 15:
         heap.alltoall(team, scratch_off, src, n)
         return checksum32(np.concatenate([heap.pe(pe + j)[scratch_off:scratch_off + iss * n] for j in range(iss)]))
+    raise ValueError(kind)
+
+
+def _serve_staged(heap: "Heap", r, R: int, payload):
+    """A request with a staged payload, region at offset R of every PE it touches (the
+    request record's layout): the source part is written word by word from the payload
+    function, then the operation runs on it by its definition."""
+    kind, pe, iss, n, seed = int(r["kind"]), int(r["pe"]), int(r["issuer"]), int(r["n"]), int(r["word"])
+
+    def r16(x):
+        return (x + 15) // 16 * 16
+
+    def write(p, part, j0, count):
+        heap.pe(p)[part + 4 * j0:part + 4 * (j0 + count)] = np.asarray(payload(seed, p, j0, count), np.uint32).view(np.uint8)
+
+    if kind in (1, 2):
+        a = r16(n)
+        sp, dp = (iss, pe) if kind == 1 else (pe, iss)
+        write(sp, R + a, 0, n // 4)
+        heap.put(R, R + a, n, dp, sp)                 # destination part on dp <- source part on sp
+        return checksum32(heap.pe(dp)[R:R + n])
+    team = (pe, 1, iss)
+    if kind == 16:
+        dt, fmt = int(r["dtype"]), int(r["fmt"])
+        if dt == 1:                                   # int64, in place
+            for p in range(pe, pe + iss):
+                write(p, R, 0, 2 * n)
+            heap.reduce(team, R, R, n, 1, 0)
+            return checksum32(heap.pe(pe)[R:R + 8 * n])
+        if fmt == 0:                                  # bf16 codes and per-128 scales after the fp32 output
+            c4, c2 = r16(4 * n), r16(2 * n)
+            for p in range(pe, pe + iss):
+                write(p, R + c4, 0, n // 2)
+                write(p, R + c4, c2 // 4, (n + 127) // 128)
+            heap.qsum_reduce(team, R, R + c4, R + c4 + c2, 0, n)
+        else:                                         # fp32, in place
+            for p in range(pe, pe + iss):
+                write(p, R, 0, n)
+            heap.reduce(team, R, R, n, 2, 0)
+        return checksum32(heap.pe(pe)[R:R + 4 * n])
+    if kind == 15:
+        for p in range(pe, pe + iss):
+            write(p, R + iss * n, 0, iss * n // 4)
+        heap.alltoall(team, R, R + iss * n, n)
+        return checksum32(np.concatenate([heap.pe(pe + j)[R:R + iss * n] for j in range(iss)]))
     raise ValueError(kind)
 
 

@@ -12,15 +12,6 @@ namespace shmemg {
 constexpr int AMO_THREADS = 256;
 constexpr int PP_THREADS = 128;
 
-// splitmix64 (Steele, Lea, Flood, OOPSLA 2014): first output of the stream seeded with
-// seed ^ i -- the counter-based draw both the kernel and the host generators use.
-__device__ __forceinline__ uint64_t cb64(uint64_t seed, uint64_t i) {
-    uint64_t z = (seed ^ i) + 0x9E3779B97F4A7C15ull;
-    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-    return z ^ (z >> 31);
-}
-
 struct AmoArgs {
     uint8_t *heap;
     uint64_t H;

@@ -58,6 +58,15 @@ uint64_t balanced_grid(uint64_t nitems, uint64_t cap, int ngroups = 1);
 // GPU cannot hold every PE at once
 int launch_pe_grid(const void *kernel, void **args, size_t smem, cudaStream_t s, int threads = 0);
 
+// splitmix64 (Steele, Lea, Flood, OOPSLA 2014): first output of the stream started at
+// state seed ^ i -- the counter-based draw of the AMO stream and of staged payloads.
+__device__ __forceinline__ uint64_t cb64(uint64_t seed, uint64_t i) {
+    uint64_t z = (seed ^ i) + 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
 // scratch words in the reserved prefix: [SHMEMG_SCRATCH_OFF, +2 MiB)
 enum : uint64_t {
     SCR_SIGNAL_DONE = 0,            // 4096 uint32 counters for multi-CTA put_signal

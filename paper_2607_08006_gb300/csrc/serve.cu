@@ -76,11 +76,12 @@ struct __align__(128) SvSlot {
     uint64_t t_pub;                  // when the admitter queued it
     int32_t status;
     unsigned int busy;
-    uint8_t pad0[128 - 112];
+    uint32_t nstage;                 // staging tiles (the first ones) of a staged request
+    uint8_t pad0[128 - 116];
     unsigned long long claim;        // (gen << 32) | next tile
     uint8_t pad1[120];
     unsigned int done;
-    unsigned int pad2;
+    unsigned int staged;             // finished staging tiles (release adds; op tiles acquire)
     unsigned long long checksum;
     uint8_t pad3[112];
 };
@@ -108,31 +109,67 @@ __device__ __forceinline__ uint64_t now_dev() { return shmemg_d_globaltimer(); }
 
 // ------------------------------------------------------------------ request geometry
 struct Geo {
-    int first, count;       // PEs whose destination pages the request writes
-    uint64_t bytes;         // destination bytes per such PE
-    uint32_t ntiles;
+    int first, count;       // PEs (a contiguous range) whose pages the request takes
+    int first2, count2;     // a second PE (staged put/get: the source PE), count2 = 0 if none
+    uint64_t bytes;         // bytes per such PE: the destination, or a staged request's region
+    uint32_t ntiles;        // all tiles: staging tiles first, then the operation's
+    uint32_t nstage;        // staging tiles (0 unless the request stages its payload)
     int valid;
 };
 
+__host__ __device__ inline uint64_t round16(uint64_t x) { return (x + 15) & ~(uint64_t)15; }
+
+// Offsets, from the region's start, of a staged request's source part (and of a bf16
+// reduction's scales), per the layout of shmemg_req_t's staged payloads.
+struct StagedParts {
+    uint64_t src, scales;
+};
+__host__ __device__ inline StagedParts staged_parts(const shmemg_req_t &r) {
+    StagedParts p = {0, 0};
+    if (r.kind == SHMEMG_OP_PUT || r.kind == SHMEMG_OP_GET) {
+        p.src = round16(r.n);
+    } else if (r.kind == SHMEMG_OP_REDUCE) {
+        if (r.dtype == SHMEMG_FLOAT && r.fmt == SHMEMG_FMT_BF16) {
+            p.src = round16(4 * r.n);
+            p.scales = p.src + round16(2 * r.n);
+        }
+    } else if (r.kind == SHMEMG_OP_ALLTOALL) {
+        p.src = (uint64_t)r.issuer * r.n;
+    }
+    return p;
+}
+
 __host__ __device__ inline Geo geometry(const shmemg_req_t &r, int npes, uint64_t H, uint64_t amo_words) {
-    Geo g = {0, 0, 0, 0, 0};
+    Geo g = {0, 0, 0, 0, 0, 0, 0, 0};
+    const bool staged = (r.flags & SHMEMG_REQ_STAGED) != 0;
+    if (r.flags & ~(uint16_t)SHMEMG_REQ_STAGED) return g;
     switch (r.kind) {
     case SHMEMG_OP_PUT:
     case SHMEMG_OP_GET: {
-        int w = r.kind == SHMEMG_OP_PUT ? r.pe : r.issuer;
-        if (r.pe < 0 || r.pe >= npes || r.issuer < 0 || r.issuer >= npes || r.n == 0 || (r.n & 7) ||
-            (r.src & 15) || r.src > H || r.n > H - r.src)
+        const int w = r.kind == SHMEMG_OP_PUT ? r.pe : r.issuer, sp = r.kind == SHMEMG_OP_PUT ? r.issuer : r.pe;
+        if (r.pe < 0 || r.pe >= npes || r.issuer < 0 || r.issuer >= npes || r.n == 0 || (r.n & 7) || r.n > H)
             return g;
+        if (!staged && ((r.src & 15) || r.src > H || r.n > H - r.src)) return g;
         g.first = w;
         g.count = 1;
-        g.bytes = r.n;
         g.ntiles = (uint32_t)((r.n + RMA_TILE - 1) / RMA_TILE);
+        if (staged) {
+            g.bytes = 2 * round16(r.n);
+            if (sp != w) {
+                g.first2 = sp;
+                g.count2 = 1;
+            }
+            g.nstage = g.ntiles;
+            g.ntiles *= 2;
+        } else {
+            g.bytes = r.n;
+        }
         break;
     }
     case SHMEMG_OP_FETCH_ADD:
     case SHMEMG_OP_COMPARE_SWAP:
     case SHMEMG_OP_FETCH_XOR:
-        if (r.dtype != SHMEMG_INT64 || amo_words == 0 || r.word >= (uint64_t)npes * amo_words) return g;
+        if (staged || r.dtype != SHMEMG_INT64 || amo_words == 0 || r.word >= (uint64_t)npes * amo_words) return g;
         g.ntiles = 1;
         break;
     case SHMEMG_OP_REDUCE: {
@@ -142,28 +179,46 @@ __host__ __device__ inline Geo geometry(const shmemg_req_t &r, int npes, uint64_
         else if (r.dtype == SHMEMG_FLOAT && r.fmt == FMT_F32) { in_es = 4; out_es = 4; }
         else if (r.dtype == SHMEMG_FLOAT && r.fmt == SHMEMG_FMT_BF16) { in_es = 2; out_es = 4; }
         else return g;
-        if (P < 1 || r.pe < 0 || (int64_t)r.pe + P > npes || r.n == 0 || (r.n & 3) || (r.src & 15) || r.src > H ||
-            r.n * in_es > H - r.src)
-            return g;
-        if (r.fmt == SHMEMG_FMT_BF16 && r.dtype == SHMEMG_FLOAT) {
-            uint64_t sb = (r.n + 127) / 128 * 4;
-            if (r.cond < 0 || ((uint64_t)r.cond & 3) || (uint64_t)r.cond > H || sb > H - (uint64_t)r.cond) return g;
+        if (P < 1 || r.pe < 0 || (int64_t)r.pe + P > npes || r.n == 0 || (r.n & 3) || r.n > H) return g;
+        const bool bf = r.fmt == SHMEMG_FMT_BF16 && r.dtype == SHMEMG_FLOAT;
+        if (!staged) {
+            if ((r.src & 15) || r.src > H || r.n * in_es > H - r.src) return g;
+            if (bf) {
+                uint64_t sb = (r.n + 127) / 128 * 4;
+                if (r.cond < 0 || ((uint64_t)r.cond & 3) || (uint64_t)r.cond > H || sb > H - (uint64_t)r.cond) return g;
+            }
         }
         g.first = r.pe;
         g.count = P;
-        g.bytes = r.n * out_es;
         g.ntiles = (uint32_t)((r.n + RED_TILE - 1) / RED_TILE);
+        if (staged) {
+            const StagedParts sp = staged_parts(r);
+            g.bytes = bf ? sp.scales + round16((r.n + 127) / 128 * 4) : r.n * out_es;  // fp32, int64: in place
+            g.nstage = g.ntiles;
+            g.ntiles *= 2;
+        } else {
+            g.bytes = r.n * out_es;
+        }
         break;
     }
     case SHMEMG_OP_ALLTOALL: {
         int P = r.issuer;
-        if (P < 1 || r.pe < 0 || (int64_t)r.pe + P > npes || r.n == 0 || (r.n & 15) || (r.src & 15) || r.src > H ||
-            r.n * (uint64_t)P > H - r.src)
+        if (P < 1 || r.pe < 0 || (int64_t)r.pe + P > npes || r.n == 0 || (r.n & 15) || r.n > H ||
+            r.n * (uint64_t)P > H)
             return g;
+        if (!staged && ((r.src & 15) || r.src > H || r.n * (uint64_t)P > H - r.src)) return g;
+        const uint64_t nt = (uint64_t)P * P * ((r.n + A2A_TILE - 1) / A2A_TILE);
+        if (nt > (1u << 29)) return g;  // tile indices stay far inside 32 bits
         g.first = r.pe;
         g.count = P;
-        g.bytes = r.n * (uint64_t)P;
-        g.ntiles = (uint32_t)((uint64_t)P * P * ((r.n + A2A_TILE - 1) / A2A_TILE));
+        g.ntiles = (uint32_t)nt;
+        if (staged) {
+            g.bytes = 2 * r.n * (uint64_t)P;
+            g.nstage = (uint32_t)((uint64_t)P * ((r.n * (uint64_t)P + A2A_TILE - 1) / A2A_TILE));
+            g.ntiles += g.nstage;
+        } else {
+            g.bytes = r.n * (uint64_t)P;
+        }
         break;
     }
     default:
@@ -172,6 +227,9 @@ __host__ __device__ inline Geo geometry(const shmemg_req_t &r, int npes, uint64_
     g.valid = 1;
     return g;
 }
+
+// PE of member m of the request's page set (the first range, then the second)
+__host__ __device__ inline int geo_pe(const Geo &g, int m) { return m < g.count ? g.first + m : g.first2 + (m - g.count); }
 
 // ------------------------------------------------------------------ tiles
 __device__ __forceinline__ uint64_t ck4(uint4 x, uint64_t i) {
@@ -217,12 +275,95 @@ __device__ __forceinline__ uint64_t copy_ck(uint8_t *dst, const uint8_t *src, ui
     return acc;
 }
 
+// ------------------------------------------------------------------ staged payloads
+// Word j of PE p's staged source: two bfloat16 codes of (k - 128) / 128 from the top two
+// bytes of the counter draw (shmemg_req_t's staged payloads).
+__device__ __forceinline__ uint32_t payload_bf16(uint32_t k) {
+    return __float_as_uint((float)((int)k - 128) * 0.0078125f) >> 16;  // exact: k - 128 has <= 8 bits
+}
+__device__ __forceinline__ uint32_t payload_word(uint64_t seed, int p, uint64_t j) {
+    const uint64_t z = cb64(seed, ((uint64_t)p << 40) | j);
+    return (payload_bf16((uint32_t)(z >> 56)) << 16) | payload_bf16((uint32_t)(z >> 48) & 255u);
+}
+// words [j0, j1) of PE p's source part, which starts at `part` (16-byte aligned): four
+// words per 16-byte store where the range allows, single words at its ends
+__device__ void stage_words(uint8_t *part, uint64_t seed, int p, uint64_t j0, uint64_t j1) {
+    uint32_t *w = (uint32_t *)part;
+    const uint64_t a0 = (j0 + 3) & ~(uint64_t)3, a1 = j1 & ~(uint64_t)3;
+    if (a0 >= a1) {
+        for (uint64_t j = j0 + threadIdx.x; j < j1; j += blockDim.x) w[j] = payload_word(seed, p, j);
+        return;
+    }
+    for (uint64_t j = j0 + threadIdx.x; j < a0; j += blockDim.x) w[j] = payload_word(seed, p, j);
+    for (uint64_t q = a0 / 4 + threadIdx.x; q < a1 / 4; q += blockDim.x) {
+        const uint64_t j = 4 * q;
+        ((uint4 *)part)[q] = make_uint4(payload_word(seed, p, j), payload_word(seed, p, j + 1),
+                                        payload_word(seed, p, j + 2), payload_word(seed, p, j + 3));
+    }
+    for (uint64_t j = a1 + threadIdx.x; j < j1; j += blockDim.x) w[j] = payload_word(seed, p, j);
+}
+
+// Staging tile k of a staged request whose region starts at `reg` on every PE it touches:
+// writes its share of the source part(s).  PUT/GET: bytes of one RMA tile on the source
+// PE; REDUCE: the elements of one reduce tile on every member (bf16: their codes and the
+// scales of their blocks); ALLTOALL: one A2A_TILE chunk of one member's source blocks.
+__device__ void stage_tile(const SvArgs &a, const shmemg_req_t &r, uint64_t reg, uint32_t k) {
+    uint8_t *heap = a.heap;
+    const uint64_t H = a.H, seed = r.word;
+    const StagedParts sp = staged_parts(r);
+    switch (r.kind) {
+    case SHMEMG_OP_PUT:
+    case SHMEMG_OP_GET: {
+        const int p = r.kind == SHMEMG_OP_PUT ? r.issuer : r.pe;
+        const uint64_t b0 = (uint64_t)k * RMA_TILE, b1 = b0 + RMA_TILE < r.n ? b0 + RMA_TILE : r.n;
+        stage_words(heap + (uint64_t)p * H + reg + sp.src, seed, p, b0 / 4, b1 / 4);
+        break;
+    }
+    case SHMEMG_OP_REDUCE: {
+        const uint64_t e0 = (uint64_t)k * RED_TILE, e1 = e0 + RED_TILE < r.n ? e0 + RED_TILE : r.n;
+        const bool bf = r.dtype == SHMEMG_FLOAT && r.fmt == SHMEMG_FMT_BF16;
+        const uint64_t es = r.dtype == SHMEMG_INT64 ? 8 : bf ? 2 : 4;
+        for (int m = 0; m < r.issuer; m++) {
+            const int p = r.pe + m;
+            uint8_t *part = heap + (uint64_t)p * H + reg + sp.src;
+            stage_words(part, seed, p, e0 * es / 4, e1 * es / 4);
+            if (bf)
+                stage_words(part, seed, p, (sp.scales - sp.src) / 4 + e0 / 128, (sp.scales - sp.src) / 4 + (e1 + 127) / 128);
+        }
+        break;
+    }
+    case SHMEMG_OP_ALLTOALL: {
+        const uint64_t span = (uint64_t)r.issuer * r.n, per = (span + A2A_TILE - 1) / A2A_TILE;
+        const int i = (int)(k / per);
+        const uint64_t b0 = (k - (uint64_t)i * per) * A2A_TILE, b1 = b0 + A2A_TILE < span ? b0 + A2A_TILE : span;
+        const int p = r.pe + i;
+        stage_words(heap + (uint64_t)p * H + reg + sp.src, seed, p, b0 / 4, b1 / 4);
+        break;
+    }
+    default:
+        break;
+    }
+}
+
 // one tile of a request (all threads of the CTA); returns this thread's checksum terms
-// (AMO: thread 0 stores the fetched value through *amo_out)
-__device__ uint64_t run_tile(const SvArgs &a, const shmemg_req_t &r, uint64_t dst_off, uint32_t k,
-                             unsigned long long *amo_out) {
+// (AMO: thread 0 stores the fetched value through *amo_out).  Tiles below `nstage` stage
+// a staged request's payload; the operation's tile k runs as tile k - nstage, its source
+// in the request's region.
+__device__ uint64_t run_tile(const SvArgs &a, const shmemg_req_t &r0, uint64_t dst_off, uint32_t k,
+                             unsigned long long *amo_out, uint32_t nstage = 0) {
     uint8_t *heap = a.heap;
     const uint64_t H = a.H;
+    shmemg_req_t r = r0;
+    if (r0.flags & SHMEMG_REQ_STAGED) {
+        if (k < nstage) {
+            stage_tile(a, r0, dst_off, k);
+            return 0;
+        }
+        k -= nstage;
+        const StagedParts sp = staged_parts(r0);
+        r.src = dst_off + sp.src;                 // fp32 / int64 reductions: in place
+        r.cond = (int64_t)(dst_off + sp.scales);
+    }
     switch (r.kind) {
     case SHMEMG_OP_PUT:
     case SHMEMG_OP_GET: {
@@ -371,8 +512,8 @@ __device__ bool find_pages(const SvArgs &a, const Geo &g, uint32_t need, uint32_
     uint32_t run = 0;
     for (uint32_t w = 0; w < a.bm_words; w++) {
         unsigned long long mine = 0;
-        for (int m = lane; m < g.count; m += 32)
-            mine |= *(volatile unsigned long long *)&a.bitmaps[(uint64_t)(g.first + m) * a.bm_words + w];
+        for (int m = lane; m < g.count + g.count2; m += 32)
+            mine |= *(volatile unsigned long long *)&a.bitmaps[(uint64_t)geo_pe(g, m) * a.bm_words + w];
         const unsigned long long occ = (unsigned long long)__reduce_or_sync(0xffffffffu, (unsigned)mine) |
                                        ((unsigned long long)__reduce_or_sync(0xffffffffu, (unsigned)(mine >> 32)) << 32);
         for (int b = 0; b < 64; b++) {
@@ -389,9 +530,9 @@ __device__ bool find_pages(const SvArgs &a, const Geo &g, uint32_t need, uint32_
     return false;
 }
 
-__device__ void mark_pages(const SvArgs &a, int first_pe, int count, uint32_t p0, uint32_t np, bool set, int lane) {
-    for (int m = lane; m < count; m += 32) {
-        unsigned long long *bm = a.bitmaps + (uint64_t)(first_pe + m) * a.bm_words;
+__device__ void mark_pages(const SvArgs &a, const Geo &g, uint32_t p0, uint32_t np, bool set, int lane) {
+    for (int m = lane; m < g.count + g.count2; m += 32) {
+        unsigned long long *bm = a.bitmaps + (uint64_t)geo_pe(g, m) * a.bm_words;
         for (uint32_t p = p0; p < p0 + np;) {
             const uint32_t w = p / 64, b = p % 64;
             const uint32_t nb = (64 - b) < (p0 + np - p) ? (64 - b) : (p0 + np - p);
@@ -456,7 +597,7 @@ __device__ int adm_try(const SvArgs &a, AdmState &st, const shmemg_req_t &r, uin
     uint32_t p0 = 0;
     if (!find_pages(a, g, need, &p0, lane)) return 0;
     if (need) shmemg_d_fence_gpu();  // page frees seen above happen before the pages' reuse
-    mark_pages(a, g.first, g.count, p0, need, true, lane);
+    mark_pages(a, g, p0, need, true, lane);
     SvSlot &s = a.slots[slot];
     if (lane == 0) {
         const uint32_t gen = s.gen + 1;
@@ -465,6 +606,8 @@ __device__ int adm_try(const SvArgs &a, AdmState &st, const shmemg_req_t &r, uin
         s.page0 = p0;
         s.npages = need;
         s.ntiles = g.ntiles;
+        s.nstage = g.nstage;
+        s.staged = 0;
         s.gen = gen;
         s.done = 0;
         s.checksum = 0;
@@ -594,7 +737,7 @@ __device__ void admitter_warp(const SvArgs &a) {
 __device__ void finalize(const SvArgs &a, SvSlot &s, int lane) {
     const shmemg_req_t r = s.req;
     const Geo g = geometry(r, a.npes, a.H, a.cfg.amo_words);
-    if (s.npages) mark_pages(a, g.first, g.count, s.page0, s.npages, false, lane);
+    if (s.npages) mark_pages(a, g, s.page0, s.npages, false, lane);
     if (lane == 0) {
         write_completion(a, r.ticket, s.t_admit, s.checksum, s.status);
         atomicAdd(&a.ctl->inflight, ~0ull);  // -1
@@ -628,7 +771,8 @@ __device__ __forceinline__ bool publish(const SvArgs &a, uint32_t slot, uint64_t
 // executed, even by a worker that came from an older queue entry of the same slot, so
 // no index is lost.
 __device__ __forceinline__ bool claim_tiles(const SvArgs &a, uint32_t slot, uint32_t *tile, uint32_t *cnt,
-                                            shmemg_req_t *req, uint64_t *dst_off, uint32_t nt_seen = 0) {
+                                            shmemg_req_t *req, uint64_t *dst_off, uint32_t *nstage,
+                                            uint32_t nt_seen = 0) {
     SvSlot &s = a.slots[slot];
     // a plain look first (unless the caller has just looked, and passes the tile count it
     // saw): an exhausted request costs no atomic on its busy claim line
@@ -645,14 +789,30 @@ __device__ __forceinline__ bool claim_tiles(const SvArgs &a, uint32_t slot, uint
     const uint32_t k = (uint32_t)c, n = *(volatile uint32_t *)&s.ntiles;
     const shmemg_req_t rq = s.req;
     const uint64_t d = s.dst_off;
+    const uint32_t ns = s.nstage;
     if (k < n) {
         *tile = k;
         *cnt = k + chunk <= n ? chunk : n - k;
         *req = rq;
         *dst_off = d;
+        *nstage = ns;
         return true;
     }
     return false;
+}
+
+// Thread 0 of a worker about to run an operation tile of a staged request: acquire-waits
+// until all `ns` staging tiles are counted (they were claimed before it, by workers that
+// run them without waiting on anything); false after 10 s.
+__device__ bool wait_staged(const SvArgs &a, SvSlot &s, uint32_t ns) {
+    if (shmemg_d_ld_acquire_u32(&s.staged) >= ns) return true;
+    const uint64_t t0 = now_dev();
+    for (uint32_t sl = 32;;) {
+        if (shmemg_d_ld_acquire_u32(&s.staged) >= ns) return true;
+        if (now_dev() - t0 > 10000000000ull) return false;
+        __nanosleep(sl);
+        if (sl < 256) sl <<= 1;
+    }
 }
 
 // A worker CTA.  Thread 0 claims chunks of tiles, the CTA runs them; the finished tiles
@@ -670,6 +830,7 @@ __device__ void worker(const SvArgs &a) {
     __shared__ unsigned long long s_amo;
     __shared__ __align__(16) shmemg_req_t s_req;   // the claimed slot's request and destination
     __shared__ uint64_t s_dst;
+    __shared__ uint32_t s_nstage;
     const uint32_t me = blockIdx.x - 1;
     bool primary = true;
     if (threadIdx.x == 0) s_fin = -1;
@@ -689,7 +850,7 @@ __device__ void worker(const SvArgs &a) {
         if (threadIdx.x == 0) {
             int cmd = 0;
             uint32_t tile, cnt;
-            if (sticky >= 0 && claim_tiles(a, (uint32_t)sticky, &tile, &cnt, &s_req, &s_dst)) {
+            if (sticky >= 0 && claim_tiles(a, (uint32_t)sticky, &tile, &cnt, &s_req, &s_dst, &s_nstage)) {
                 s_slot = (uint32_t)sticky;
                 s_tile = tile;
                 s_cnt = cnt;
@@ -725,7 +886,7 @@ __device__ void worker(const SvArgs &a) {
                         continue;
                     }
                     if (!primary && now_dev() - *(volatile uint64_t *)&s.t_pub < SECONDARY_DELAY_NS) continue;
-                    if (claim_tiles(a, slot, &tile, &cnt, &s_req, &s_dst, nt)) {   // claim word and tile count read just above
+                    if (claim_tiles(a, slot, &tile, &cnt, &s_req, &s_dst, &s_nstage, nt)) {   // claim word and tile count read just above
                         s_slot = slot;
                         s_tile = tile;
                         s_cnt = cnt;
@@ -754,12 +915,29 @@ __device__ void worker(const SvArgs &a) {
         SvSlot &s = a.slots[s_slot];
         const shmemg_req_t r = s_req;
         const uint64_t dst_off = s_dst;
-        const uint32_t t0 = s_tile, cnt = s_cnt;
+        const uint32_t t0 = s_tile, cnt = s_cnt, ns = s_nstage;
         uint64_t part = 0;
+        uint32_t staged_here = 0;  // staging tiles of this chunk not yet counted in s.staged
         for (uint32_t k = 0; k < cnt; k++) {
-            part += run_tile(a, r, dst_off, t0 + k, &s_amo);
+            const uint32_t tk = t0 + k;
+            if (ns && tk >= ns && (k == 0 || tk == ns)) {
+                // the operation's first tile in this chunk: count this chunk's staging
+                // tiles (written before the barrier that ended each), then wait until
+                // every staging tile of the request is written
+                if (threadIdx.x == 0) {
+                    if (staged_here)
+                        asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(&s.staged), "r"(staged_here) : "memory");
+                    if (!wait_staged(a, s, ns)) s.status = SHMEMG_ERR_TIMEOUT;
+                }
+                staged_here = 0;
+                __syncthreads();
+            }
+            part += run_tile(a, r, dst_off, tk, &s_amo, ns);
             __syncthreads();  // (an AMO's fetched value is in s_amo)
+            if (tk < ns) staged_here++;
         }
+        if (staged_here && threadIdx.x == 0)
+            asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(&s.staged), "r"(staged_here) : "memory");
         const uint64_t sum = block_sum_u64(part);  // ends with a CTA barrier: the tiles are written
         if (threadIdx.x == 0) {
             pend_sum += sum;
@@ -810,14 +988,18 @@ struct PlainScratch {
     uint64_t t_start;
 };
 
-__global__ void __launch_bounds__(SV_THREADS, 2) k_plain(SvArgs a, shmemg_req_t r, uint32_t ntiles, int status,
-                                                      PlainScratch *sc, shmemg_completion_t *rec) {
+// Tiles [lo, hi) of request r, grid-stride.  A staged request runs as two launches on one
+// stream: its staging tiles, then its operation tiles (final = 1: that launch's last CTA
+// writes the completion record).
+__global__ void __launch_bounds__(SV_THREADS, 2) k_plain(SvArgs a, shmemg_req_t r, uint32_t lo, uint32_t hi,
+                                                      uint32_t nstage, int final, int status, PlainScratch *sc,
+                                                      shmemg_completion_t *rec) {
     __shared__ unsigned long long s_amo;
-    if (blockIdx.x == 0 && threadIdx.x == 0) sc->t_start = now_dev();
+    if (lo == 0 && blockIdx.x == 0 && threadIdx.x == 0) sc->t_start = now_dev();
     uint64_t part = 0;
     if (status == SHMEMG_SUCCESS)
-        for (uint32_t k = blockIdx.x; k < ntiles; k += gridDim.x) {
-            part += run_tile(a, r, a.cfg.arena_offset, k, &s_amo);
+        for (uint32_t k = lo + blockIdx.x; k < hi; k += gridDim.x) {
+            part += run_tile(a, r, a.cfg.arena_offset, k, &s_amo, nstage);
             __syncthreads();
             if (threadIdx.x == 0 && (r.kind == SHMEMG_OP_FETCH_ADD || r.kind == SHMEMG_OP_COMPARE_SWAP ||
                                      r.kind == SHMEMG_OP_FETCH_XOR))
@@ -827,7 +1009,11 @@ __global__ void __launch_bounds__(SV_THREADS, 2) k_plain(SvArgs a, shmemg_req_t 
     if (threadIdx.x == 0) {
         atomicAdd(&sc->checksum, (unsigned long long)sum);
         shmemg_d_fence_gpu();
-        if (atomicAdd(&sc->done, 1u) == gridDim.x - 1) {
+        const bool last = atomicAdd(&sc->done, 1u) == gridDim.x - 1;
+        if (last && !final) {
+            sc->done = 0;  // the staging launch: the next launch on the stream counts anew
+            shmemg_d_fence_gpu();
+        } else if (last) {
             shmemg_d_fence_gpu();
             const bool amo = r.kind == SHMEMG_OP_FETCH_ADD || r.kind == SHMEMG_OP_COMPARE_SWAP ||
                              r.kind == SHMEMG_OP_FETCH_XOR;
@@ -1044,10 +1230,16 @@ int shmemg_request_run(const shmemg_req_t *req, const shmemg_server_cfg_t *cfg_i
     int status = g.valid ? SHMEMG_SUCCESS : SHMEMG_ERR_INVALID_ARG;
     if (g.valid && g.bytes > cfg.arena_bytes) status = SHMEMG_ERR_OUT_OF_HEAP;
     PlainScratch *sc = (PlainScratch *)(S.base + SHMEMG_SCRATCH_OFF + SCR_WORK) + (S.call_seq++ % 1024);
-    int cap = ctas_for((const void *)k_plain, SV_THREADS, 0);
-    int grid = (int)(g.ntiles < (uint32_t)cap ? (g.ntiles ? g.ntiles : 1) : (uint32_t)cap);
+    const uint32_t cap = (uint32_t)ctas_for((const void *)k_plain, SV_THREADS, 0);
+    auto grid_for = [&](uint32_t tiles) { return (int)(tiles < cap ? (tiles ? tiles : 1) : cap); };
     SvArgs ka = a;
-    k_plain<<<grid, SV_THREADS, 0, to_stream(stream)>>>(ka, *req, g.ntiles, status, sc, rec);
+    const uint32_t ns = status == SHMEMG_SUCCESS ? g.nstage : 0;
+    if (ns) {  // the staged payload first, then the operation
+        k_plain<<<grid_for(ns), SV_THREADS, 0, to_stream(stream)>>>(ka, *req, 0, ns, ns, 0, status, sc, rec);
+        if (int rc = cuda_rc(cudaGetLastError())) return rc;
+    }
+    k_plain<<<grid_for(g.ntiles - ns), SV_THREADS, 0, to_stream(stream)>>>(ka, *req, ns, g.ntiles, ns, 1, status, sc,
+                                                                           rec);
     return cuda_rc(cudaGetLastError());
 }
 

@@ -76,12 +76,12 @@ class Tune(C.Structure):
 
 
 class Req(C.Structure):
-    _fields_ = [("kind", C.c_uint32), ("dtype", C.c_uint8), ("fmt", C.c_uint8), ("reserved0", C.c_uint16),
+    _fields_ = [("kind", C.c_uint32), ("dtype", C.c_uint8), ("fmt", C.c_uint8), ("flags", C.c_uint16),
                 ("pe", C.c_int32), ("issuer", C.c_int32), ("n", C.c_uint64), ("word", C.c_uint64),
                 ("operand", C.c_int64), ("cond", C.c_int64), ("src", C.c_uint64), ("ticket", C.c_uint64)]
 
 
-REQ_DTYPE = np.dtype([("kind", "<u4"), ("dtype", "u1"), ("fmt", "u1"), ("reserved0", "<u2"), ("pe", "<i4"),
+REQ_DTYPE = np.dtype([("kind", "<u4"), ("dtype", "u1"), ("fmt", "u1"), ("flags", "<u2"), ("pe", "<i4"),
                       ("issuer", "<i4"), ("n", "<u8"), ("word", "<u8"), ("operand", "<i8"), ("cond", "<i8"),
                       ("src", "<u8"), ("ticket", "<u8")])
 COMPLETION_DTYPE = np.dtype([("ticket", "<u8"), ("t_admit_ns", "<u8"), ("t_done_ns", "<u8"), ("result", "<u8"),

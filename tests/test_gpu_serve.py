@@ -130,3 +130,98 @@ def test_server_admission_errors_and_idle_exit(sg, heapf):
     time.sleep(0.5)                          # idle bound: the kernel leaves by itself
     assert stream.query()
     srv.stop()
+
+
+def _staged_requests(lay, npes, count=600, seed=5):
+    """The generator's staged mix plus the boundary cases of the staged layout: an fp32
+    reduction in place over the whole arena, the largest bf16 reduction that fits, an
+    alltoall whose source and destination blocks fill the arena, a self put and a put of
+    half the arena, a get whose size is not a multiple of 16, an int64 reduction."""
+    reqs = W.gen_serve_requests(seed, count, npes, lay, rma_max=256 << 10, red_lo=1024, red_hi=1 << 16,
+                                a2a_lo=16, a2a_hi=16 << 10, p_hi=16, distinct_amo_words=True, staged=True)
+    A = lay.arena_bytes
+    extra = np.zeros(8, W.REQ_DTYPE)
+    n_bf = 4 * (A // 28)
+    while W.staged_region_bytes(16, W.FMT_BF16, n_bf, 5) > A:
+        n_bf -= 4
+    rows = [dict(kind=16, dtype=W.DT_FLOAT, fmt=W.FMT_F32, pe=3, issuer=8, n=A // 4),
+            dict(kind=16, dtype=W.DT_FLOAT, fmt=W.FMT_BF16, pe=20, issuer=5, n=n_bf),
+            dict(kind=15, pe=9, issuer=16, n=A // 32),
+            dict(kind=1, pe=7, issuer=7, n=4096),
+            dict(kind=1, pe=2, issuer=30, n=A // 2),
+            dict(kind=2, pe=11, issuer=4, n=1000),
+            dict(kind=16, dtype=W.DT_INT64, fmt=0, pe=25, issuer=3, n=5000),
+            dict(kind=2, pe=31, issuer=31, n=8)]
+    for r, kw in zip(extra, rows):
+        r["flags"] = 1
+        r["word"] = W.cb64(seed, int(kw["n"]) ^ (kw["pe"] << 32))
+        for k, v in kw.items():
+            r[k] = v
+    for r in extra:
+        assert W.staged_region_bytes(int(r["kind"]), int(r["fmt"]), int(r["n"]), int(r["issuer"])) <= A
+    return np.concatenate([extra[:4], reqs, extra[4:]])
+
+
+def test_staged_served_results_invariant_alone_mix_plain_oracle(sg, heapf, orc):
+    """Requests that stage their own payload (fp32 reductions in place, up to whole-arena
+    regions): served concurrently, one at a time, on the plain path and by the oracle,
+    the results agree; the AMO table ends as the oracle's."""
+    lay = W.serve_layout_staged(arena_bytes=4 << 20, amo_words=4096)
+    Hs = lay.H
+    h = heapf(NPES, Hs)
+    init = np.zeros((NPES, Hs), np.uint8)
+    init[:, :lay.amo_words * 8] = W.cb64_np(17, np.arange(NPES * lay.amo_words, dtype=np.uint64)).view(
+        np.uint8).reshape(NPES, -1)
+    init = init.reshape(-1)
+    reqs = _staged_requests(lay, NPES)
+    cfg = _cfg(sg, lay)
+    stream = torch.cuda.Stream()
+    upload(h, init)
+    srv = sg.Server(cfg, stream)
+    srv.feed(reqs, np.zeros(len(reqs), np.uint64))
+    mix = _by_ticket(_drain(sg, srv, len(reqs)))
+    srv.stop()
+    amo_after_mix = h.partitions()[:, :lay.amo_words * 8].cpu().numpy()
+    assert np.all(mix["status"] == 0), np.unique(mix["status"], return_counts=True)
+    upload(h, init)
+    srv = sg.Server(cfg, stream)
+    alone = np.zeros(len(reqs), sg.COMPLETION_DTYPE)
+    for i in range(len(reqs)):
+        srv.feed(reqs[i:i + 1], np.zeros(1, np.uint64))
+        alone[i] = _drain(sg, srv, 1)[0]
+    srv.stop()
+    assert np.all(alone["status"] == 0)
+    assert np.array_equal(alone["result"], mix["result"])
+    upload(h, init)
+    recs = torch.zeros(len(reqs) * sg.COMPLETION_DTYPE.itemsize, dtype=torch.uint8).pin_memory()
+    sg.plain_feed(reqs, np.zeros(len(reqs), np.uint64), cfg, recs.data_ptr(), stream)
+    stream.synchronize()
+    plain = np.frombuffer(recs.numpy().tobytes(), sg.COMPLETION_DTYPE)
+    assert np.all(plain["seq"] == 1) and np.all(plain["status"] == 0)
+    assert np.array_equal(plain["result"], mix["result"])
+    ref = orc.Heap(NPES, Hs, init)
+    want = np.array([orc.serve_request(ref, r, lay.amo_offset, lay.amo_words, lay.arena_offset, W.serve_payload_words)
+                     & (2**64 - 1) for r in reqs], dtype=np.uint64)
+    bad = np.nonzero(mix["result"] != want)[0]
+    assert len(bad) == 0, [(int(i), int(reqs["kind"][i]), int(reqs["n"][i])) for i in bad[:10]]
+    assert np.array_equal(amo_after_mix.reshape(-1), ref.mem.reshape(NPES, Hs)[:, :lay.amo_words * 8].reshape(-1))
+
+
+def test_staged_admission_refuses_regions_beyond_the_arena(sg, heapf):
+    lay = W.serve_layout_staged(arena_bytes=1 << 20, amo_words=1024)
+    h = heapf(4, lay.H)
+    cfg = _cfg(sg, lay, idle_ns=200_000_000)
+    bad = np.zeros(4, sg.REQ_DTYPE)
+    for r, kw in zip(bad, [dict(kind=16, dtype=W.DT_FLOAT, fmt=W.FMT_F32, pe=0, issuer=2, n=(1 << 18) + 4),  # 4n > arena
+                           dict(kind=15, pe=0, issuer=4, n=(1 << 17) + 16),                                   # 2Pm > arena
+                           dict(kind=5, dtype=W.DT_INT64, word=3, operand=1),                                 # AMOs never stage
+                           dict(kind=16, dtype=W.DT_FLOAT, fmt=W.FMT_F32, pe=0, issuer=4, n=1 << 18)]):       # exactly fits
+        r["flags"] = 1
+        for k, v in kw.items():
+            r[k] = v
+    stream = torch.cuda.Stream()
+    srv = sg.Server(cfg, stream)
+    srv.feed(bad, np.zeros(len(bad), np.uint64))
+    got = _by_ticket(_drain(sg, srv, len(bad)))
+    srv.stop()
+    assert list(got["status"]) == [sg.ERR_OUT_OF_HEAP, sg.ERR_OUT_OF_HEAP, sg.ERR_INVALID_ARG, 0]

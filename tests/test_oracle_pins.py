@@ -808,6 +808,80 @@ def test_serve_request_results_by_kind(orc):
     assert int(h.view(1, lay.amo_offset + 8 * 6, 1, np.int64)[0]) == int(words[70]) + 12345
 
 
+def test_staged_requests_by_kind(orc):
+    """Requests that stage their payload (flags bit 0): the region at the scratch offset is
+    laid out as the request record defines it and the result follows from the payload
+    words alone -- a put/get returns the checksum of the payload bytes, an alltoall that of
+    the payload blocks transposed (numpy), a two-member fp32 reduction that of the
+    elementwise binary32 sum of the two members' payload words (one RNE add), a two-member
+    bf16 reduction that of the binary32 sum of the two dequantised values (Neumaier on two
+    values is their correctly rounded sum), and a one-member reduction returns its own
+    payload (fp32) -- with every PE outside the request untouched."""
+    npes, H, R = 5, 1 << 16, 4096
+    init = np.random.default_rng(21).integers(0, 256, (npes, H), dtype=np.uint8)
+
+    def payload(seed, p, j0, count):
+        return W.serve_payload_words(seed, p, j0, count)
+
+    def req(**kw):
+        r = np.zeros((), W.REQ_DTYPE)
+        r["flags"] = 1
+        r["word"] = 0x1234567
+        for k, v in kw.items():
+            r[k] = v
+        return r
+
+    def run(r):
+        h = orc.Heap(npes, H, init.reshape(-1).copy())
+        got = orc.serve_request(h, r, 0, 1, R, payload)
+        return h, got
+
+    def untouched(h, pes):
+        for p in range(npes):
+            if p not in pes:
+                assert np.array_equal(h.pe(p), init[p]), p
+
+    # put PE 3 -> PE 1 and get by PE 0 from PE 4, 1000 bytes: the payload of the source PE
+    for kind, pe, iss, sp, dp in ((1, 1, 3, 3, 1), (2, 4, 0, 4, 0)):
+        h, got = run(req(kind=kind, pe=pe, issuer=iss, n=1000))
+        want = W.serve_payload_words(0x1234567, sp, 0, 250).view(np.uint8)
+        assert got == orc.checksum32(want)
+        assert np.array_equal(h.pe(dp)[R:R + 1000], want)                      # destination part
+        assert np.array_equal(h.pe(sp)[R + 1008:R + 2008], want)              # source part at R + round16(n)
+        untouched(h, (sp, dp))
+    # alltoall over PEs 1..3, 48 bytes per pair: member j's block i = member i's payload block j
+    P, m = 3, 48
+    h, got = run(req(kind=15, pe=1, issuer=P, n=m))
+    src = [W.serve_payload_words(0x1234567, 1 + i, 0, P * m // 4).view(np.uint8).reshape(P, m) for i in range(P)]
+    want = np.concatenate([np.concatenate([src[i][j] for i in range(P)]) for j in range(P)])
+    assert got == orc.checksum32(want)
+    untouched(h, (1, 2, 3))
+    # fp32 in place over PEs 2..3 (n = 300): one binary32 add per element
+    n = 300
+    h, got = run(req(kind=16, dtype=W.DT_FLOAT, fmt=W.FMT_F32, pe=2, issuer=2, n=n))
+    x = [W.serve_payload_words(0x1234567, p, 0, n).view(np.float32) for p in (2, 3)]
+    want = (x[0] + x[1]).astype(np.float32)
+    assert got == orc.checksum32(want.view(np.uint8))
+    assert np.array_equal(h.view(3, R, n, np.float32), want)
+    # one member: its own payload
+    h, got = run(req(kind=16, dtype=W.DT_FLOAT, fmt=W.FMT_F32, pe=4, issuer=1, n=n))
+    assert got == orc.checksum32(W.serve_payload_words(0x1234567, 4, 0, n).view(np.uint8))
+    # bf16 over PEs 0..1, n = 260 (three blocks): codes at R + 1040, scales at R + 1040 + 528
+    n = 260
+    h, got = run(req(kind=16, dtype=W.DT_FLOAT, fmt=W.FMT_BF16, pe=0, issuer=2, n=n))
+    xs = []
+    for p in (0, 1):
+        w = W.serve_payload_words(0x1234567, p, 0, 528 // 4 + 3)
+        codes = w[:n // 2].view(np.uint16)                                     # little-endian: low code first
+        sc = w[528 // 4:528 // 4 + 3].view(np.float32)
+        dec = (codes.astype(np.uint32) << np.uint32(16)).view(np.float32)
+        xs.append((dec * np.repeat(sc, 128)[:n]).astype(np.float32))
+    want = (xs[0] + xs[1]).astype(np.float32)
+    assert got == orc.checksum32(want.view(np.uint8))
+    assert np.array_equal(h.view(1, R, n, np.float32), want)
+    untouched(h, (0, 1))
+
+
 def _checksum_with(mistake):
     def cs(buf):
         b = np.ascontiguousarray(buf).tobytes()

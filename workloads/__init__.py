@@ -470,7 +470,7 @@ def gen_batch_teams(seed: int = None, n_teams: int = 256, world: int = 128, p_lo
 
 # --------------------------------------------------------------------------- serving
 # One served request = one 64-byte record (same layout as shmemg_req_t).
-REQ_DTYPE = np.dtype([("kind", "<u4"), ("dtype", "u1"), ("fmt", "u1"), ("reserved0", "<u2"), ("pe", "<i4"),
+REQ_DTYPE = np.dtype([("kind", "<u4"), ("dtype", "u1"), ("fmt", "u1"), ("flags", "<u2"), ("pe", "<i4"),
                       ("issuer", "<i4"), ("n", "<u8"), ("word", "<u8"), ("operand", "<i8"), ("cond", "<i8"),
                       ("src", "<u8"), ("ticket", "<u8")])
 assert REQ_DTYPE.itemsize == 64
@@ -497,6 +497,41 @@ def serve_layout(H: int = 32 << 20, amo_words: int = 8192) -> ServeLayout:
                        arena_offset=half, arena_bytes=half)
 
 
+def serve_layout_staged(arena_bytes: int = 32 << 20, amo_words: int = 8192) -> ServeLayout:
+    """Per-PE layout for requests that stage their own payloads: the AMO table, then the
+    page arena (no read-only zone)."""
+    amo = amo_words * 8
+    return ServeLayout(H=amo + arena_bytes, amo_offset=0, amo_words=amo_words, ro_offset=amo, ro_bytes=0,
+                       arena_offset=amo, arena_bytes=arena_bytes)
+
+
+def staged_region_bytes(kind: int, fmt: int, n: int, P: int) -> int:
+    """Bytes of a staged request's region on each PE it touches (shmemg_req_t's staged
+    payloads): the generators size requests to fit the arena with it."""
+    def r16(x):
+        return (x + 15) // 16 * 16
+    if kind in (1, 2):
+        return 2 * r16(n)
+    if kind == 16:
+        if fmt == FMT_BF16:
+            return r16(4 * n) + r16(2 * n) + r16(4 * ((n + 127) // 128))
+        return 4 * n
+    if kind == 15:
+        return 2 * P * n
+    return 0
+
+
+def serve_payload_words(seed: int, pe: int, j0: int, count: int) -> np.ndarray:
+    """Words [j0, j0 + count) of PE pe's staged source part: word j holds two bfloat16
+    codes, of (k1 - 128) / 128 (high half) and (k2 - 128) / 128 (low half), k1 and k2 the
+    top two bytes of cb64(seed, (pe << 40) | j)."""
+    z = cb64_np(seed, np.arange(j0, j0 + count, dtype=np.uint64) + np.uint64(pe << 40))
+
+    def code(k):
+        return ((k.astype(np.int64) - 128).astype(np.float32) / np.float32(128.0)).view(np.uint32) >> np.uint32(16)
+    return (code(z >> np.uint64(56)) << np.uint32(16)) | code((z >> np.uint64(48)) & np.uint64(255))
+
+
 def serve_source_words(seed: int, pe: int, nwords: int) -> np.ndarray:
     """Read-only source zone of one PE: binary32 words (k - 128) / 128, k = top byte of a
     counter draw -- values in [-1, 1) that are also exact in bfloat16 (low 16 bits 0)."""
@@ -517,13 +552,16 @@ def serve_source_words_torch(seed: int, pe: int, nwords: int, device="cuda"):
 def gen_serve_requests(seed: int, count: int, npes: int, lay: ServeLayout, rma_max: int = 4 << 20,
                        red_lo: int = 1 << 16, red_hi: int = 2 << 20, a2a_lo: int = 4096, a2a_hi: int = 256 << 10,
                        p_hi: int = 64, mix=(0.60, 0.25, 0.10, 0.05), distinct_amo_words: bool = False,
-                       bf16_frac: float = 0.5) -> np.ndarray:
+                       bf16_frac: float = 0.5, staged: bool = False) -> np.ndarray:
     """Mixed served requests: put/get of 8 B..rma_max (log-uniform, multiples of 8), int64
     AMOs (fetch_add 50 %, compare_swap 25 %, fetch_xor 25 %), fp32 or bf16-payload sum
     reductions over teams of log-uniform 2..p_hi PEs with red_lo..red_hi elements, and
-    alltoall of a2a_lo..a2a_hi bytes per pair (multiples of 16).  Destination footprints are
-    kept within the arena (alltoall: P*m <= arena/2, reduce: 4n <= arena/2); sources lie in
-    the read-only zone at 16-byte aligned offsets."""
+    alltoall of a2a_lo..a2a_hi bytes per pair (multiples of 16).
+    staged=False: sources lie in the read-only zone at 16-byte aligned offsets, and
+    destination footprints stay within half the arena (alltoall: P*m, reduce: 4n).
+    staged=True: every non-AMO request stages its payload (flags 1, seed in `word`); its
+    region must fit the arena: fp32 reductions in place (4n <= arena), bf16 ones capped at
+    the largest n whose region fits, alltoall 2*P*m <= arena, put/get 2n <= arena."""
     rng = SplitMix64(seed)
     out = np.zeros(count, REQ_DTYPE)
     cum = np.cumsum(mix)
@@ -538,6 +576,12 @@ def gen_serve_requests(seed: int, count: int, npes: int, lay: ServeLayout, rma_m
         span = (ro_hi - ro_lo - nbytes) // 16
         return ro_lo + 16 * rng.below(max(span, 1))
 
+    A = lay.arena_bytes
+
+    def stage(r):
+        r["flags"] = 1
+        r["word"] = rng.next()
+
     for i in range(count):
         u = rng.uniform()
         r = out[i]
@@ -545,6 +589,10 @@ def gen_serve_requests(seed: int, count: int, npes: int, lay: ServeLayout, rma_m
             n = 8 * rng.log_uniform_int(1, rma_max // 8)
             r["kind"] = 1 if rng.below(2) == 0 else 2
             r["pe"], r["issuer"] = rng.below(npes), rng.below(npes)
+            if staged:
+                r["n"] = min(n, 8 * (A // 2 // 8))
+                stage(r)
+                continue
             r["n"] = n
             r["src"] = src_off(n)
         elif u < cum[1]:
@@ -561,12 +609,20 @@ def gen_serve_requests(seed: int, count: int, npes: int, lay: ServeLayout, rma_m
         elif u < cum[2]:
             P = rng.log_uniform_int(2, min(p_hi, npes))
             n = 4 * (rng.log_uniform_int(red_lo, red_hi) // 4)
-            n = min(n, (lay.arena_bytes // 2) // 4)
+            if not staged:
+                n = min(n, (lay.arena_bytes // 2) // 4)
             bf = rng.uniform() < bf16_frac
             r["kind"] = 16
             r["dtype"] = DT_FLOAT
             r["fmt"] = FMT_BF16 if bf else FMT_F32
             r["pe"], r["issuer"] = rng.below(npes - P + 1), P
+            if staged:
+                n = min(n, 4 * (A // 16))
+                while staged_region_bytes(16, int(r["fmt"]), n, P) > A:
+                    n -= 4 * max(1, (staged_region_bytes(16, int(r["fmt"]), n, P) - A) // 28)
+                r["n"] = n
+                stage(r)
+                continue
             r["n"] = n
             r["src"] = src_off(n * (2 if bf else 4))
             if bf:
@@ -578,6 +634,9 @@ def gen_serve_requests(seed: int, count: int, npes: int, lay: ServeLayout, rma_m
             r["kind"] = 15
             r["pe"], r["issuer"] = rng.below(npes - P + 1), P
             r["n"] = m
+            if staged:
+                stage(r)
+                continue
             r["src"] = src_off(m * P)
     return out
 

@@ -1071,20 +1071,32 @@ SERVE_RATES = (1e6, 2e6, 5e6, 1e7, 2e7, 5e7)          # the configuration's arri
 SERVE_SAT_FRACTIONS = (0.1, 0.25, 0.5, 0.75, 1.0, 1.25)  # and fractions of the measured saturation rate
 
 
-def run_serve(torch, sg, nreq=1 << 16, rates=None, npes=512, Hs=32 << 20):
-    """512 PEs x 32 MiB (16 GiB).  Mixed Poisson arrivals: 60 % put/get 8 B-4 MiB, 25 %
-    int64 AMOs, 10 % fp32/bf16 team reductions, 5 % alltoall; served by the persistent
-    engine and by one launch per request, same arrivals; throughput and p50/p99 latency
-    at 1-50 M req/s and at 0.1-1.25 x the saturation rate, `nreq` requests per point."""
-    lay = W.serve_layout(H=Hs, amo_words=8192)
-    heap = sg.Heap(npes, Hs)
-    out = {"npes": npes, "heap_bytes": npes * Hs, "requests_per_point": nreq}
+def served_bytes(reqs):
+    """Bytes each request moves in HBM by definition: its staged payload written, then the
+    operation's reads and writes (put/get n + 2n; reduce P*n_in + P*n_in + P*4n;
+    alltoall 3*P^2*m; an AMO 16)."""
+    k = reqs["kind"].astype(np.int64)
+    n = reqs["n"].astype(np.float64)
+    P = reqs["issuer"].astype(np.float64)
+    bf = (reqs["fmt"] == W.FMT_BF16) & (k == 16)
+    n_in = np.where(bf, 2 * n + 4 * np.ceil(n / 128), 4 * n)
+    return np.select([np.isin(k, (1, 2)), k == 16, k == 15], [3 * n, P * (2 * n_in + 4 * n), 3 * P * P * n], 16.0)
+
+
+def run_serve(torch, sg, nreq=1 << 16, rates=None, npes=512, arena=32 << 20):
+    """512 PEs, each with a 32 MiB page arena (16 GiB) beside its AMO table.  Mixed
+    Poisson arrivals: 60 % put/get 8 B-4 MiB, 25 % int64 AMOs, 10 % fp32/bf16 team
+    reductions of 64 Ki-8 Mi elements, 5 % alltoall of 4-256 KiB per pair, every non-AMO
+    request staging its own payload into its admitted pages; served by the persistent
+    engine and by one launch per request, same arrivals; throughput (req/s, GB/s of the
+    bytes each request moves) and p50/p99 latency at 1-50 M req/s and at 0.1-1.25 x the
+    saturation rate, `nreq` requests per point."""
+    lay = W.serve_layout_staged(arena_bytes=arena, amo_words=8192)
+    heap = sg.Heap(npes, lay.H)
+    out = {"npes": npes, "arena_bytes": npes * arena, "heap_bytes": npes * lay.H, "requests_per_point": nreq,
+           "payloads": "staged (fp32 reductions in place)"}
     try:
         parts = heap.partitions()
-        seed = W.derive_seed("serve-inputs")
-        for p in range(npes):
-            parts[p, lay.ro_offset:lay.ro_offset + lay.ro_bytes].view(torch.float32).copy_(
-                W.serve_source_words_torch(seed, p, lay.ro_bytes // 4))
         parts[:, lay.amo_offset:lay.amo_offset + 8 * lay.amo_words].view(torch.int64).copy_(
             W.cb64_torch(W.derive_seed("serve-amo"), torch.arange(npes * lay.amo_words, device="cuda")).view(
                 npes, lay.amo_words))
@@ -1095,7 +1107,11 @@ def run_serve(torch, sg, nreq=1 << 16, rates=None, npes=512, Hs=32 << 20):
         cfg.amo_offset, cfg.amo_words = lay.amo_offset, lay.amo_words
         cfg.max_ns = 300 * 10**9
         cfg.ring_slots = 1 << 17     # room for a whole point's requests and completions
-        reqs = W.gen_serve_requests(W.derive_seed("serve-reqs"), nreq, npes, lay)
+        reqs = W.gen_serve_requests(W.derive_seed("serve-reqs"), nreq, npes, lay, red_hi=8 << 20, staged=True)
+        req_bytes = served_bytes(reqs)
+        out["mean_request_MB"] = round(float(req_bytes.mean()) / 1e6, 3)
+        out["largest_reduce_elems"] = int(reqs["n"][reqs["kind"] == 16].max())
+        out["largest_alltoall_pair_bytes"] = int(reqs["n"][reqs["kind"] == 15].max())
         mb = float(np.mean(reqs["n"][np.isin(reqs["kind"], (1, 2))])) / 1e6
         out["mix_counts"] = {k: int(v) for k, v in zip(("rma", "amo", "reduce", "alltoall"), (
             np.isin(reqs["kind"], (1, 2)).sum(), np.isin(reqs["kind"], (5, 6, 7)).sum(),
@@ -1132,6 +1148,7 @@ def run_serve(torch, sg, nreq=1 << 16, rates=None, npes=512, Hs=32 << 20):
             return np.frombuffer(rec_t.numpy().tobytes(), sg.COMPLETION_DTYPE).copy(), t0
 
         classes = {"rma": (1, 2), "amo": (5, 6, 7), "reduce": (16,), "alltoall": (15,)}
+        hbm, _ = measured_peaks()
 
         def summarise(recs, t0, arr):
             ok = recs[recs["status"] == 0]
@@ -1146,7 +1163,9 @@ def run_serve(torch, sg, nreq=1 << 16, rates=None, npes=512, Hs=32 << 20):
                     per[cname] = {"p50_us": round(float(np.percentile(lat[m], 50)), 1),
                                   "p99_us": round(float(np.percentile(lat[m], 99)), 1),
                                   "service_p50_us": round(float(np.percentile(svc[m], 50)), 1)}
-            return {"req_per_s": round(len(ok) / span, 1), "p50_us": round(float(np.percentile(lat, 50)), 1),
+            gbps = float(req_bytes[ok["ticket"].astype(np.int64)].sum()) / span / 1e9
+            return {"req_per_s": round(len(ok) / span, 1), "GBps": round(gbps, 1), "frac_of_hbm": round(gbps / hbm, 3),
+                    "p50_us": round(float(np.percentile(lat, 50)), 1),
                     "p99_us": round(float(np.percentile(lat, 99)), 1), "completed": int(len(ok)),
                     "errors": int((recs["status"] != 0).sum()), "per_class": per}
 

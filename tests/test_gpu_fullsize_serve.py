@@ -1,14 +1,17 @@
-"""Full-size parity of the serving engine on the benchmark's workload: 512 PEs x 32 MiB,
-2^16 requests of the configuration's mix (put/get of 8 B-4 MiB, int64 AMOs on shared
-words, fp32 / bf16 team reductions of up to 2 Mi elements, alltoall of up to 256 KiB per
-pair), all submitted at once and served concurrently.
+"""Full-size parity of the serving engine on the benchmark's workload: 512 PEs, each with
+a 32 MiB page arena (16 GiB) beside its AMO table, 2^16 requests of the configuration's
+mix with staged payloads -- put/get of 8 B-4 MiB, int64 AMOs on shared words, fp32 / bf16
+team reductions of 64 Ki-8 Mi elements (fp32 in place; bf16 up to the largest region that
+fits the arena), alltoall of 4-256 KiB per pair -- plus the largest requests of each kind
+(an 8 Mi-element fp32 reduction over 64 PEs, a 64 x 256 KiB alltoall, the largest bf16
+reduction, a put of half the arena), all submitted at once and served concurrently.
   * every put/get, reduction and alltoall result equals the plain launch-per-request
     path's;
   * the AMO requests' fetched values and the final words admit one serial order per word
     (the oracle's serialisation checker);
-  * sampled requests of every non-AMO kind equal the oracle's result, computed on a
-    compact heap that holds only the bytes the request reads (its PEs renumbered from 0,
-    its sources moved to offset 0)."""
+  * the largest requests and sampled ones of every non-AMO kind equal the oracle's
+    result, computed on a compact heap of the request's PEs (renumbered from 0) that the
+    oracle fills from the payload definition itself."""
 import time
 
 import numpy as np
@@ -19,10 +22,10 @@ import workloads as W
 
 pytestmark = pytest.mark.gpu
 
-NPES, HS, NREQ = 512, 32 << 20, 1 << 16
+NPES, ARENA, NREQ = 512, 32 << 20, 1 << 16
 
 
-def _drain(sg, srv, count, timeout=120.0):
+def _drain(sg, srv, count, timeout=300.0):
     out = np.zeros(count, sg.COMPLETION_DTYPE)
     buf = np.zeros(16384, sg.COMPLETION_DTYPE)
     got, t0 = 0, time.time()
@@ -36,52 +39,49 @@ def _drain(sg, srv, count, timeout=120.0):
     return out[np.argsort(out["ticket"])]
 
 
-def _compact(parts, r):
-    """(oracle heap inputs, rewritten request, scratch offset): the request's PEs as 0..k-1,
-    its source bytes at offset 0 of each, the output built above them."""
-    kind, pe, iss, n, src = int(r["kind"]), int(r["pe"]), int(r["issuer"]), int(r["n"]), int(r["src"])
+def _largest(seed):
+    """The largest staged request of each kind the arena holds."""
+    n_bf = 4 * (ARENA // 28)
+    while W.staged_region_bytes(16, W.FMT_BF16, n_bf, 64) > ARENA:
+        n_bf -= 4
+    rows = [dict(kind=16, dtype=W.DT_FLOAT, fmt=W.FMT_F32, pe=100, issuer=64, n=ARENA // 4),
+            dict(kind=15, pe=300, issuer=64, n=256 << 10),
+            dict(kind=16, dtype=W.DT_FLOAT, fmt=W.FMT_BF16, pe=440, issuer=64, n=n_bf),
+            dict(kind=1, pe=7, issuer=500, n=ARENA // 2)]
+    out = np.zeros(len(rows), W.REQ_DTYPE)
+    for i, (r, kw) in enumerate(zip(out, rows)):
+        r["flags"] = 1
+        r["word"] = W.cb64(seed, i)
+        for k, v in kw.items():
+            r[k] = v
+        assert W.staged_region_bytes(int(r["kind"]), int(r["fmt"]), int(r["n"]), int(r["issuer"])) <= ARENA
+    return out
+
+
+def _oracle_result(orc, r):
+    """The oracle's result for a staged request on a compact heap of its PEs."""
+    kind, pe, iss, n = int(r["kind"]), int(r["pe"]), int(r["issuer"]), int(r["n"])
     q = r.copy()
     if kind in (1, 2):
-        sp = iss if kind == 1 else pe
-        pes = [sp] if pe == iss else ([iss, pe])
-        spans = [(src, n)]
-        q["issuer"], q["pe"] = (0, 0) if pe == iss else (0, 1)
+        pes = [pe] if pe == iss else [pe, iss]
+        q["pe"], q["issuer"] = (0, 0) if pe == iss else (0, 1)
     else:
         pes = list(range(pe, pe + iss))
         q["pe"] = 0
-        if kind == 16 and int(r["fmt"]) == 0:
-            spans = [(src, 2 * n), (int(r["cond"]), 4 * ((n + 127) // 128))]
-        elif kind == 16:
-            spans = [(src, 4 * n)]
-        else:
-            spans = [(src, iss * n)]
-    offs, o = [], 0
-    for _, ln in spans:
-        offs.append(o)
-        o = (o + ln + 255) // 256 * 256
-    q["src"] = offs[0]
-    if len(spans) > 1:
-        q["cond"] = offs[1]
-    out_bytes = {1: n, 2: n, 15: iss * n, 16: 4 * n}[kind]
-    scratch = o
-    H = (scratch + out_bytes + 4095) // 4096 * 4096
-    mem = np.zeros((len(pes), H), np.uint8)
-    for i, p in enumerate(pes):
-        for (s0, ln), d0 in zip(spans, offs):
-            mem[i, d0:d0 + ln] = parts[p, s0:s0 + ln].cpu().numpy()
-    return len(pes), H, mem.reshape(-1), q, scratch
+    H = (W.staged_region_bytes(kind, int(r["fmt"]), n, iss) + 4095) // 4096 * 4096
+    ref = orc.Heap(len(pes), H)
+
+    def payload(seed, p, j0, count):
+        return W.serve_payload_words(seed, pes[p], j0, count)
+    return orc.serve_request(ref, q, 0, 1, 0, payload) & (2**64 - 1)
 
 
 def test_serve_full_size(sg, orc):
     torch.cuda.set_device(0)
-    lay = W.serve_layout(H=HS, amo_words=8192)
-    heap = sg.Heap(NPES, HS)
+    lay = W.serve_layout_staged(arena_bytes=ARENA, amo_words=8192)
+    heap = sg.Heap(NPES, lay.H)
     try:
         parts = heap.partitions()
-        seed = W.derive_seed("serve-inputs")
-        for p in range(NPES):
-            parts[p, lay.ro_offset:lay.ro_offset + lay.ro_bytes].view(torch.float32).copy_(
-                W.serve_source_words_torch(seed, p, lay.ro_bytes // 4))
         amo_init = W.cb64_torch(W.derive_seed("serve-amo"), torch.arange(NPES * lay.amo_words, device="cuda"))
         parts[:, lay.amo_offset:lay.amo_offset + 8 * lay.amo_words].view(torch.int64).copy_(
             amo_init.view(NPES, lay.amo_words))
@@ -90,9 +90,11 @@ def test_serve_full_size(sg, orc):
         cfg.page_bytes = lay.page_bytes
         cfg.arena_offset, cfg.arena_bytes = lay.arena_offset, lay.arena_bytes
         cfg.amo_offset, cfg.amo_words = lay.amo_offset, lay.amo_words
-        cfg.max_ns = 300 * 10**9
+        cfg.max_ns = 600 * 10**9
         cfg.ring_slots = 1 << 17
-        reqs = W.gen_serve_requests(W.derive_seed("serve-reqs"), NREQ, NPES, lay)
+        big = _largest(W.derive_seed("serve-largest"))
+        reqs = np.concatenate([W.gen_serve_requests(W.derive_seed("serve-reqs"), NREQ - len(big), NPES, lay,
+                                                    red_hi=8 << 20, staged=True), big])
         stream = torch.cuda.Stream()
         srv = sg.Server(cfg, stream)
         srv.feed(reqs, np.zeros(NREQ, np.uint64))
@@ -102,7 +104,7 @@ def test_serve_full_size(sg, orc):
         amo_final = parts[:, lay.amo_offset:lay.amo_offset + 8 * lay.amo_words].contiguous().view(torch.int64)
         amo_final = amo_final.reshape(-1).cpu().numpy()
         amo_w0 = amo_init.cpu().numpy()
-        # the plain path on the same inputs (the AMO words restored first)
+        # the plain path on the same requests (the AMO words restored first)
         parts[:, lay.amo_offset:lay.amo_offset + 8 * lay.amo_words].view(torch.int64).copy_(
             amo_init.view(NPES, lay.amo_words))
         recs = torch.zeros(NREQ * sg.COMPLETION_DTYPE.itemsize, dtype=torch.uint8).pin_memory()
@@ -118,18 +120,13 @@ def test_serve_full_size(sg, orc):
         got = orc.check_serialisation(w, reqs["kind"][a].astype(np.int32), reqs["operand"][a], reqs["cond"][a],
                                       served["result"][a].view(np.int64), amo_w0[w], amo_final[w])
         assert got == 0 and len(a) > 10000
-        # sampled requests against the oracle
-        picks = []
-        for ks, k in (((1, 2), 20), ((16,), 20), ((15,), 8)):
-            idx = np.nonzero(np.isin(reqs["kind"], ks))[0]
-            order = np.argsort(-reqs["n"][idx].astype(np.int64) * np.maximum(reqs["issuer"][idx], 1))
-            picks += list(idx[order[:2]])   # the largest of the kind
+        # the largest requests and sampled ones against the oracle
+        picks = list(range(NREQ - len(big), NREQ))
+        for ks, k in (((1, 2), 12), ((16,), 8), ((15,), 6)):
+            idx = np.nonzero(np.isin(reqs["kind"][:NREQ - len(big)], ks))[0]
             r = W.cb64_np(W.derive_seed("serve-sample"), np.arange(k, dtype=np.uint64)) % np.uint64(len(idx))
             picks += list(idx[r.astype(np.int64)])
         for i in sorted(set(int(x) for x in picks)):
-            npe, H, mem, q, scratch = _compact(parts, reqs[i])
-            ref = orc.Heap(npe, H, mem)
-            want = orc.serve_request(ref, q, 0, 1, scratch) & (2**64 - 1)
-            assert int(served["result"][i]) == want, (i, int(reqs["kind"][i]))
+            assert int(served["result"][i]) == _oracle_result(orc, reqs[i]), (i, int(reqs["kind"][i]))
     finally:
         heap.close()

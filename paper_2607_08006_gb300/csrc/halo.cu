@@ -60,14 +60,18 @@ __device__ __forceinline__ float jac(float up, float dn, float lf, float rt) {
     return __fmul_rn(0.25f, __fadd_rn(__fadd_rn(up, dn), __fadd_rn(lf, rt)));
 }
 
-// One sweep of this PE's tile (group g: the PE's threads) from tile[p] / halo[p] into
-// tile[p^1]; with `send`, the new boundary values also go to the neighbours' halo[p^1].
+// Rows [R0, R1) of one sweep of this PE's tile (group g: the PE's threads) from tile[p] /
+// halo[p] into tile[p^1]; with `send`, the new boundary values also go to the neighbours'
+// halo[p^1].  edges = false (the interior phase, rows 1 .. ny-2): the west and east
+// halos are not read -- the points of columns 0 and nx-1 get a placeholder left or right
+// value from the tile itself and are recomputed by halo_edges -- so the rows can be swept
+// before the neighbours' halos have arrived.
 // Thread layout: float4 column c4 = rank mod W4, a contiguous run of rows per thread
 // (sliding window of three rows in registers, one new float4 per row).  The grid's
 // update is the same on both paths below; they differ only in where a point's left and
 // right neighbours come from.
 __device__ __forceinline__ void halo_sweep(const HaloArgs &a, shmemg_group g, int me, const int nb[4], int p,
-                                           bool send) {
+                                           bool send, int R0, int R1, bool edges) {
     const shmemg_device_ctx_t &c = a.c;
     const int nx = a.nx, ny = a.ny, W4 = nx / 4;
     const uint64_t tile_elems = (uint64_t)nx * ny, halo_elems = halo_stride(nx, ny);
@@ -87,7 +91,7 @@ __device__ __forceinline__ void halo_sweep(const HaloArgs &a, shmemg_group g, in
     const uint32_t nseg = T / cols;                              // row runs side by side
     if (g.rank >= cols * nseg) return;
     const uint32_t seg = g.rank / cols;
-    const int r0 = (int)((uint64_t)ny * seg / nseg), r1 = (int)((uint64_t)ny * (seg + 1) / nseg);
+    const int r0 = R0 + (int)((uint64_t)(R1 - R0) * seg / nseg), r1 = R0 + (int)((uint64_t)(R1 - R0) * (seg + 1) / nseg);
     if (r0 >= r1) return;
     // every load bypasses L1 (ld.global.cg): neighbours and the PE's other CTAs wrote
     // these values on other SMs since this SM may last have cached them
@@ -97,8 +101,8 @@ __device__ __forceinline__ void halo_sweep(const HaloArgs &a, shmemg_group g, in
         if (send) {  // fused device-initiated puts of the new boundary
             if (i == 0) *reinterpret_cast<float4 *>(to_n + j) = o;
             if (i == ny - 1) *reinterpret_cast<float4 *>(to_s + j) = o;
-            if (c4 == 0) to_w[i] = o.x;
-            if (c4 == W4 - 1) to_e[i] = o.w;
+            if (c4 == 0 && edges) to_w[i] = o.x;
+            if (c4 == W4 - 1 && edges) to_e[i] = o.w;
         }
     };
     auto stencil = [&](const float4 &up, const float4 &mid, const float4 &dn, float lf, float rt) {
@@ -134,10 +138,12 @@ __device__ __forceinline__ void halo_sweep(const HaloArgs &a, shmemg_group g, in
                     const int k = slot(x);
                     const float *q = x < 0 ? h_n + j : x >= ny ? h_s + j : cur + (uint64_t)x * nx + j;
                     halo_cp16(ring + k * blockDim.x, q);
-                    if (x >= r0 && x < r1) {
-                        if (ledge) halo_cp16(edge + 2 * k * nw, c4 == 0 ? h_w + (x & ~3) : cur + (uint64_t)x * nx + j - 4);
+                    if (x >= r0 && x < r1) {   // (edges off: rows 1 .. ny-2, so the side reads stay in the tile)
+                        if (ledge)
+                            halo_cp16(edge + 2 * k * nw, c4 == 0 && edges ? h_w + (x & ~3) : cur + (uint64_t)x * nx + j - 4);
                         if (redge)
-                            halo_cp16(edge + 2 * k * nw + 1, c4 == W4 - 1 ? h_e + (x & ~3) : cur + (uint64_t)x * nx + j + 4);
+                            halo_cp16(edge + 2 * k * nw + 1,
+                                      c4 == W4 - 1 && edges ? h_e + (x & ~3) : cur + (uint64_t)x * nx + j + 4);
                     }
                 }
                 halo_commit();   // an empty group past the end keeps the count
@@ -146,7 +152,7 @@ __device__ __forceinline__ void halo_sweep(const HaloArgs &a, shmemg_group g, in
             halo_wait<HALO_RING - 2>();   // rows r0 - 1 and r0 have landed
             float4 up = ring[slot(r0 - 1) * blockDim.x], mid = ring[slot(r0) * blockDim.x];
             // steady state: pointers and the slot advance by one row per step
-            const bool west = ledge && c4 == 0, east = redge && c4 == W4 - 1;   // lanes on the tile's sides
+            const bool west = ledge && c4 == 0 && edges, east = redge && c4 == W4 - 1 && edges;   // lanes on the tile's sides
             const float *nsrc = cur + (uint64_t)(r0 - 1 + HALO_RING) * nx + j;  // row i - 1 + HALO_RING
             float *dst = nxt + (uint64_t)r0 * nx + j;
             int sl = slot(r0);
@@ -204,8 +210,10 @@ __device__ __forceinline__ void halo_sweep(const HaloArgs &a, shmemg_group g, in
             const float *q = i < 0 ? h_n + j : i >= ny ? h_s + j : cur + (uint64_t)i * nx + j;
             return __ldcg(reinterpret_cast<const float4 *>(q));
         };
-        auto left = [&](int i) { return c4 == 0 ? __ldcg(h_w + i) : __ldcg(cur + (uint64_t)i * nx + j - 1); };
-        auto right = [&](int i) { return c4 == W4 - 1 ? __ldcg(h_e + i) : __ldcg(cur + (uint64_t)i * nx + j + 4); };
+        auto left = [&](int i) { return c4 == 0 && edges ? __ldcg(h_w + i) : __ldcg(cur + (uint64_t)i * nx + j - 1); };
+        auto right = [&](int i) {
+            return c4 == W4 - 1 && edges ? __ldcg(h_e + i) : __ldcg(cur + (uint64_t)i * nx + j + 4);
+        };
         auto emit = [&](int i, const float4 &up, const float4 &mid, const float4 &dn, float lf, float rt) {
             store(i, c4, stencil(up, mid, dn, lf, rt));
         };
@@ -227,6 +235,34 @@ __device__ __forceinline__ void halo_sweep(const HaloArgs &a, shmemg_group g, in
             emit(i, up, mid, dn, left(i), right(i));
             up = mid;
             mid = dn;
+        }
+    }
+}
+
+// Columns 0 and nx-1 of rows 1 .. ny-2 (after an interior phase): the points whose left or
+// right neighbour is in the west or east halo, with their sends.
+__device__ __forceinline__ void halo_edges(const HaloArgs &a, shmemg_group g, int me, const int nb[4], int p,
+                                           bool send) {
+    const shmemg_device_ctx_t &c = a.c;
+    const int nx = a.nx, ny = a.ny;
+    const uint64_t tile_elems = (uint64_t)nx * ny, halo_elems = halo_stride(nx, ny);
+    const float *cur = (const float *)shmemg_d_addr(c, me, a.tiles) + (uint64_t)p * tile_elems;
+    float *nxt = (float *)shmemg_d_addr(c, me, a.tiles) + (uint64_t)(p ^ 1) * tile_elems;
+    const float *hal = (const float *)shmemg_d_addr(c, me, a.halos) + (uint64_t)p * halo_elems;
+    const float *h_w = hal + halo_part(nx, ny, H_W), *h_e = hal + halo_part(nx, ny, H_E);
+    float *to_w = (float *)shmemg_d_addr(c, nb[H_W], a.halos) + (uint64_t)(p ^ 1) * halo_elems + halo_part(nx, ny, H_E);
+    float *to_e = (float *)shmemg_d_addr(c, nb[H_E], a.halos) + (uint64_t)(p ^ 1) * halo_elems + halo_part(nx, ny, H_W);
+    for (uint32_t q = g.rank; q < 2u * (uint32_t)(ny - 2); q += g.size) {
+        const int i = 1 + (int)(q >> 1);
+        const float *row = cur + (uint64_t)i * nx;
+        if ((q & 1) == 0) {  // column 0
+            const float o = jac(__ldcg(row - nx), __ldcg(row + nx), __ldcg(h_w + i), __ldcg(row + 1));
+            nxt[(uint64_t)i * nx] = o;
+            if (send) to_w[i] = o;
+        } else {             // column nx-1
+            const float o = jac(__ldcg(row - nx + nx - 1), __ldcg(row + nx + nx - 1), __ldcg(row + nx - 2), __ldcg(h_e + i));
+            nxt[(uint64_t)i * nx + nx - 1] = o;
+            if (send) to_e[i] = o;
         }
     }
 }
@@ -285,6 +321,11 @@ __global__ void __launch_bounds__(512) k_halo(HaloArgs a, int t0, int t1, int it
         if (leader) halo_signal(a, nb);
     }
     for (int t = t0; t < t1; t++) {
+        const bool send = t + 1 < iters;
+        // interior rows first: they read only this PE's own tile, so they overlap the
+        // wait for the neighbours' halos (rows 0 and ny-1, columns 0 and nx-1 follow it)
+        const bool split = a.ny > 2;
+        if (split) halo_sweep(a, g, me, nb, t & 1, false, 1, a.ny - 1, false);
         if (signals && threadIdx.x == 0) {
             int rc = SHMEMG_SUCCESS;
             if (leader)
@@ -299,8 +340,13 @@ __global__ void __launch_bounds__(512) k_halo(HaloArgs a, int t0, int t1, int it
                              ? shmemg_d_ld_cluster<int>(shmemg_d_cluster_addr(&s_stop, 0))
                              : s_stop;
         if (stop) break;
-        const bool send = t + 1 < iters;
-        halo_sweep(a, g, me, nb, t & 1, send);
+        if (split) {
+            halo_sweep(a, g, me, nb, t & 1, send, 0, 1, true);
+            halo_sweep(a, g, me, nb, t & 1, send, a.ny - 1, a.ny, true);
+            halo_edges(a, g, me, nb, t & 1, send);
+        } else {
+            halo_sweep(a, g, me, nb, t & 1, send, 0, a.ny, true);
+        }
         shmemg_d_pe_sync(c);
         if (signals && send && leader) halo_signal(a, nb);
     }

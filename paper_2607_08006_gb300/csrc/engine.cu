@@ -35,15 +35,32 @@ struct Xfer {
     uint64_t chunk_vec;                // vectors per item
     uint64_t chunks_per_seg;
     uint64_t nitems;                   // items per group
+    int mgroups;                       // broadcast / fcollect: destination members split over this many items
 };
+
+// Item -> (segment, chunk, member group); a replicating item stores to members
+// [mg*size/mgroups, (mg+1)*size/mgroups) of the team.
+struct XItem {
+    uint64_t seg, ch;
+    int r0, r1;
+};
+__device__ __forceinline__ XItem xitem(const Xfer &x, uint64_t item) {
+    XItem t;
+    const uint64_t mg = item % (uint64_t)x.mgroups, rest = item / (uint64_t)x.mgroups;
+    t.seg = rest / x.chunks_per_seg;
+    t.ch = rest - t.seg * x.chunks_per_seg;
+    t.r0 = (int)(mg * (uint64_t)x.size / (uint64_t)x.mgroups);
+    t.r1 = (int)((mg + 1) * (uint64_t)x.size / (uint64_t)x.mgroups);
+    return t;
+}
 
 template <typename V>
 __device__ __forceinline__ void xfer_items(const Xfer &x, uint64_t first, uint64_t step) {
     const int grp = blockIdx.y;
     const int base_pe = x.start + grp * x.gstride;
     for (uint64_t item = first; item < x.nitems; item += step) {
-        uint64_t seg = item / x.chunks_per_seg;
-        uint64_t ch = item - seg * x.chunks_per_seg;
+        const XItem it = xitem(x, item);
+        const uint64_t seg = it.seg, ch = it.ch;
         uint64_t v0 = ch * x.chunk_vec;
         uint64_t nv = x.seg_vec - v0 < x.chunk_vec ? x.seg_vec - v0 : x.chunk_vec;
         const uint64_t segb = x.seg_vec * sizeof(V);
@@ -79,7 +96,7 @@ __device__ __forceinline__ void xfer_items(const Xfer &x, uint64_t first, uint64
                 if (idx < nv) dst[v0 + idx] = buf[u];
             }
         } else {
-            for (int r = 0; r < x.size; r++) {
+            for (int r = it.r0; r < it.r1; r++) {
                 V *d = (V *)(x.heap + (uint64_t)(base_pe + r * x.stride) * x.H + dst_off);
 #pragma unroll
                 for (int u = 0; u < XFER_U; u++) {
@@ -105,14 +122,18 @@ constexpr uint32_t XB_SMEM = XB_STAGES * XB_CHUNK;
 struct XChunk {
     const uint8_t *src;
     uint8_t *dst;        // single destination (copy, alltoall)
-    uint64_t dst_off;    // replicate: byte offset inside every member's partition
+    uint64_t dst_off;    // replicate: byte offset inside the partitions of members [r0, r1)
     uint32_t bytes;
     bool replicate;
+    int r0, r1;
 };
 
 __device__ __forceinline__ XChunk xchunk(const Xfer &x, uint64_t item, int base_pe) {
     XChunk c;
-    const uint64_t seg = item / x.chunks_per_seg, ch = item - seg * x.chunks_per_seg;
+    const XItem it = xitem(x, item);
+    const uint64_t seg = it.seg, ch = it.ch;
+    c.r0 = it.r0;
+    c.r1 = it.r1;
     const uint64_t segb = x.seg_vec, off = ch * XB_CHUNK;
     c.bytes = (uint32_t)(segb - off < XB_CHUNK ? segb - off : XB_CHUNK);
     c.replicate = false;
@@ -169,7 +190,7 @@ __global__ void __launch_bounds__(32) k_xfer_bulk(Xfer x, uint8_t *state, uint64
                          "r"(shmemg_smem_u32(stage)), "r"(c.bytes)
                          : "memory");
         } else {
-            for (int r = 0; r < x.size; r++) {
+            for (int r = c.r0; r < c.r1; r++) {
                 uint8_t *d = x.heap + (uint64_t)(base_pe + r * x.stride) * x.H + c.dst_off;
                 asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(d),
                              "r"(shmemg_smem_u32(stage)), "r"(c.bytes)
@@ -245,6 +266,18 @@ static int vec_width(uint64_t m) {
     return (m & 15) == 0 ? 16 : (m & 7) == 0 ? 8 : (m & 3) == 0 ? 4 : (m & 1) == 0 ? 2 : 1;
 }
 
+// Destination members per item of a replicating transfer (broadcast, fcollect): a
+// launch with fewer segment chunks than resident CTAs splits each chunk's member stores
+// over several items (each reads the chunk -- from L2 after the first), so the stores
+// spread over the GPU instead of one CTA writing every member's copy.
+static int member_groups(const Xfer &x, uint64_t items, uint64_t cap, int ngroups) {
+    if ((x.kind != X_BCAST && x.kind != X_FCOLLECT) || items == 0) return 1;
+    if (ngroups > 1) cap = cap / (uint64_t)ngroups > 0 ? cap / (uint64_t)ngroups : 1;
+    if (items >= cap) return 1;
+    const uint64_t g = (cap + items - 1) / items;
+    return (int)(g < (uint64_t)x.size ? g : (uint64_t)x.size);
+}
+
 template <typename V>
 static int launch_xfer_v(Xfer x, int ngroups, cudaStream_t s, uint64_t *sig, uint64_t val, int op, uint32_t *done) {
     x.seg_vec /= sizeof(V);
@@ -255,7 +288,10 @@ static int launch_xfer_v(Xfer x, int ngroups, cudaStream_t s, uint64_t *sig, uin
     x.nitems = x.seg_vec ? nseg * x.chunks_per_seg : 0;
     if (x.nitems == 0 && !sig) return SHMEMG_SUCCESS;
     const void *kfn = sig ? (const void *)k_put_signal<V> : (const void *)k_xfer<V>;
-    const uint64_t gx = balanced_grid(x.nitems, (uint64_t)ctas_for(kfn, XFER_THREADS, 0), ngroups);
+    const uint64_t cap = (uint64_t)ctas_for(kfn, XFER_THREADS, 0);
+    x.mgroups = member_groups(x, x.nitems, cap, ngroups);
+    x.nitems *= (uint64_t)x.mgroups;
+    const uint64_t gx = balanced_grid(x.nitems, cap, ngroups);
     dim3 grid((unsigned)gx, (unsigned)ngroups);
     if (sig) k_put_signal<V><<<grid, XFER_THREADS, 0, s>>>(x, sig, val, op, done);
     else k_xfer<V><<<grid, XFER_THREADS, 0, s>>>(x);
@@ -281,8 +317,10 @@ static int launch_xfer_bulk(Xfer x, int ngroups, cudaStream_t s) {
     x.chunks_per_seg = (x.seg_vec + XB_CHUNK - 1) / XB_CHUNK;
     const uint64_t nseg = x.kind == X_A2A ? (uint64_t)x.size * x.size : x.kind == X_FCOLLECT ? (uint64_t)x.size : 1;
     x.nitems = nseg * x.chunks_per_seg;
-    dim3 grid((unsigned)balanced_grid(x.nitems, (uint64_t)ctas_for((const void *)k_xfer_bulk, 32, XB_SMEM), ngroups),
-              (unsigned)ngroups);
+    const uint64_t cap = (uint64_t)ctas_for((const void *)k_xfer_bulk, 32, XB_SMEM);
+    x.mgroups = member_groups(x, x.nitems, cap, ngroups);
+    x.nitems *= (uint64_t)x.mgroups;
+    dim3 grid((unsigned)balanced_grid(x.nitems, cap, ngroups), (unsigned)ngroups);
     k_xfer_bulk<<<grid, 32, XB_SMEM, s>>>(x, st().base, st().timeout_ns);
     return cuda_rc(cudaGetLastError());
 }
@@ -308,6 +346,7 @@ static Xfer xfer_base() {
     x.heap = st().heap;
     x.H = st().H;
     x.stride = 1;
+    x.mgroups = 1;
     return x;
 }
 

@@ -830,27 +830,44 @@ def run_amo(torch, sg, nops_log2=30, reps=3):
                 out[f"{dist}_{name}"] = {"GUPS": round(nops / (ms * 1e-3) / 1e9, 3), "ms": round(ms, 3)}
             out[f"{dist}_generation_s"] = round(gen_s, 2)
             del dops, fetched
-        # L2-resident reference: the same kernel on a table of 2^21 words (16 MiB), 2^26 ops
-        small_wpp = (1 << 21) // npes
-        nops = 1 << min(nops_log2, 26)
-        dops = torch.from_numpy(_amo_ops(pool, 5, nops, 21, "uniform").view(np.int32)).cuda()
         pool.shutdown()
-        sg.amo_stream(heap.base, small_wpp, dops, nops, oseed, tseed, None, flags=0)
-        e0, e1 = _events(torch)
-        e0.record(s)
-        for _ in range(reps):
-            sg.amo_stream(heap.base, small_wpp, dops, nops, oseed, tseed, None, flags=0)
-        e1.record(s)
-        torch.cuda.synchronize()
-        l2 = nops / (e0.elapsed_time(e1) / reps * 1e-3) / 1e9
+        # ceilings: the L2 atomic units' rate and the HBM bytes per uniform op, both from the
+        # ncu counters of the stream (profiles/amo_counters.json); and the random-access
+        # rate of DRAM itself over the same table -- PyTorch's gather and scatter of random
+        # 8-byte words (one random read, then one random write per word, like an atomic's
+        # read-modify-write without the atomic)
         hbm, _ = measured_peaks()
-        sector = hbm * 1e9 / (4 + 8 + 64) / 1e9
-        out["l2_resident_GUPS"] = round(l2, 3)
-        out["hbm_sector_ceiling_GUPS"] = round(sector, 2)
-        best = max(out["uniform_plain"]["GUPS"], out["uniform_agg"]["GUPS"])
-        out["uniform_frac_of_l2_resident"] = round(best / l2, 3)
-        out["uniform_frac_of_hbm_sector_ceiling"] = round(best / sector, 3)
-        del dops
+        with open(os.path.join(ROOT, "profiles", "amo_counters.json")) as f:
+            ctr = json.load(f)
+        l2_ceiling = ctr["l2_atomic_ops_per_s"] / 1e9
+        hbm_ceiling = hbm / ctr["uniform_dram_bytes_per_op"]
+        table = parts[:, :wpp * 8].contiguous().view(torch.int64).reshape(-1)   # a copy of the same size
+        nr = 1 << 26
+        gen = torch.Generator(device="cuda")
+        gen.manual_seed(W.derive_seed("amo-probe") & 0x7FFFFFFF)
+        idx = torch.randint(0, table.numel(), (nr,), device="cuda", generator=gen)
+        vals = table[idx]
+        e0, e1, e2 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True), \
+            torch.cuda.Event(enable_timing=True)
+        for _ in range(2):
+            e0.record(s)
+            vals = table[idx]
+            e1.record(s)
+            table.index_put_((idx,), vals)
+            e2.record(s)
+        torch.cuda.synchronize()
+        g_ms, s_ms = e0.elapsed_time(e1), e1.elapsed_time(e2)
+        del table, idx, vals
+        out["random_gather_G_per_s"] = round(nr / (g_ms * 1e-3) / 1e9, 2)
+        out["random_scatter_G_per_s"] = round(nr / (s_ms * 1e-3) / 1e9, 2)
+        out["random_rmw_G_per_s"] = round(nr / ((g_ms + s_ms) * 1e-3) / 1e9, 2)
+        out["l2_atomic_ceiling_GUPS"] = round(l2_ceiling, 1)
+        out["hbm_ceiling_GUPS"] = round(hbm_ceiling, 2)
+        best = max(out["uniform_plain"]["GUPS"], out["uniform_agg"]["GUPS"], out["uniform_combine"]["GUPS"])
+        out["uniform_frac_of_hbm_ceiling"] = round(best / hbm_ceiling, 3)
+        out["uniform_frac_of_l2_atomic_ceiling"] = round(best / l2_ceiling, 3)
+        out["uniform_vs_random_rmw"] = round(best / out["random_rmw_G_per_s"], 3)
+        out["zipf_frac_of_l2_atomic_ceiling"] = round(out["zipf_combine"]["GUPS"] / l2_ceiling, 3)
         # ping-pong: 512 pairs, 10^4 round trips, payload sweep
         sg.get_status()
         sig_off = wpp * 8 + 8192
@@ -1192,7 +1209,7 @@ def run_serve(torch, sg, nreq=1 << 16, rates=None, npes=512, arena=32 << 20):
 
 
 # ----------------------------------------------------------------------------- profiling cases
-PROFILE_CASES = ("interp_ring", "reduce", "reduce_f32", "broadcast", "alltoall", "amo", "amo_l2", "amo_plain", "amo_combine", "amo_combine_zipf", "batch_bf16", "batch_e4m3", "qsum",
+PROFILE_CASES = ("interp_ring", "interp_ops", "reduce", "reduce_f32", "broadcast", "alltoall", "amo", "amo_l2", "amo_plain", "amo_combine", "amo_combine_zipf", "batch_bf16", "batch_e4m3", "qsum",
                  "pingpong_cluster", "cluster_coll", "halo", "halo_plain")
 
 
@@ -1218,6 +1235,16 @@ def run_profile_case(name, launches=4):
         dev = torch.from_numpy(ops.view(np.uint8).copy()).cuda()
         for _ in range(launches):
             sg.run_script(dev, npes + 1, None, s)
+    elif name == "interp_ops":     # 64 PEs of 2-CTA clusters, 640 empty put_nbi ops + quiet (per-op cost)
+        npes = 64
+        heap = sg.Heap(npes, 1 << 20, pe_mode=sg.PE_MODE_CLUSTER, cluster_dim=2)
+        ops = np.zeros(641, W.OP_DTYPE)
+        for k in range(640):
+            ops[k] = (W.OP_PUT_NBI, 0, 0, 0, (k + 1) % npes, k % npes, 1 << 19, 0, 0, 0, 0, 0)
+        ops[640] = (W.OP_QUIET, 0, 0, 0, 0, -1, 0, 0, 0, 0, 0, 0)
+        dev = torch.from_numpy(ops.view(np.uint8).copy()).cuda()
+        for _ in range(launches):
+            sg.run_script(dev, 641, None, s)
     elif name in ("reduce", "reduce_f32"):  # 64 PEs, 1 Mi elements
         n = 1 << 20
         heap = sg.Heap(64, 16 * n)
@@ -1365,7 +1392,7 @@ def leg_summary(name, r):
         uni = [_get(r, "uniform_" + k, "GUPS") for k in ("plain", "agg", "combine")]
         uni = [u for u in uni if u is not None]
         return {"uni_GUPS": max(uni) if uni else None, "zipf_GUPS": _get(r, "zipf_combine", "GUPS"),
-                "zipf_plain_GUPS": _get(r, "zipf_plain", "GUPS"), "uni_frac": r.get("uniform_frac_of_hbm_sector_ceiling"),
+                "zipf_plain_GUPS": _get(r, "zipf_plain", "GUPS"), "uni_frac": r.get("uniform_frac_of_hbm_ceiling"),
                 "pp8_us": _get(r, "pingpong_512_pairs", "8", "half_rtt_us_p50")}
     if name == "cluster":
         return {"pp8_us": [_get(r, "pingpong_512_pairs", "8", m, "half_rtt_us_p50") for m in ("dsmem", "l2")]}

@@ -49,7 +49,7 @@ def _fake_leg(name, args, torch, sg):
         d = {f"{a}_{b}": {"GUPS": 25.0, "ms": 40.0} for a in ("uniform", "zipf") for b in ("plain", "agg", "combine")}
         d["pingpong_512_pairs"] = {str(p): {"half_rtt_us_p50": 1.9, "half_rtt_us_p99": 2.5, "payload_GBps": 1.0}
                                    for p in (8, 64, 512, 4096)}
-        d["uniform_frac_of_hbm_sector_ceiling"] = 0.28
+        d["uniform_frac_of_hbm_ceiling"] = 0.28
         return d
     if name == "batch":
         return {f: {"GBps": 6000.0, "error_vs_fp64": {"normwise_rel_max": 1e-3}} for f in ("fp32", "bf16", "e4m3")}

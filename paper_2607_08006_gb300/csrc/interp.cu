@@ -204,6 +204,22 @@ __device__ __forceinline__ bool op_valid(const shmemg_device_ctx_t &c, const shm
     }
 }
 
+// Whether PE `me` does anything for a valid op: RMA, AMO, put-with-signal and waits only
+// on their issuing PE, quiet / fence on theirs (or on every PE when issuer < 0); barriers
+// and collectives on every PE (membership is decided inside them).
+__device__ __forceinline__ bool op_involves(const shmemg_op_t &o, int me) {
+    switch (o.kind & SHMEMG_OP_KIND_MASK) {
+    case SHMEMG_OP_PUT: case SHMEMG_OP_PUT_NBI: case SHMEMG_OP_GET: case SHMEMG_OP_GET_NBI:
+    case SHMEMG_OP_FETCH_ADD: case SHMEMG_OP_COMPARE_SWAP: case SHMEMG_OP_FETCH_XOR:
+    case SHMEMG_OP_PUT_SIGNAL: case SHMEMG_OP_WAIT_UNTIL:
+        return o.issuer == me;
+    case SHMEMG_OP_QUIET: case SHMEMG_OP_FENCE:
+        return o.issuer == me || o.issuer < 0;
+    default:
+        return true;
+    }
+}
+
 __global__ void __launch_bounds__(INTERP_THREADS) k_interp(shmemg_device_ctx_t c, const shmemg_op_t *ops,
                                                            int64_t nops, int64_t *fetched, int use_bulk) {
     const int me = shmemg_d_my_pe(c);
@@ -216,6 +232,8 @@ __global__ void __launch_bounds__(INTERP_THREADS) k_interp(shmemg_device_ctx_t c
     // the op list is staged through shared memory OP_BATCH records at a time (one
     // coalesced copy per batch instead of a dependent global load per op and thread)
     __shared__ __align__(16) shmemg_op_t s_ops[OP_BATCH];
+    // per op of the batch, decoded once by warp 0: 0 = nothing for this PE, 1 = run, 2 = invalid
+    __shared__ uint8_t s_act[OP_BATCH];
     // shared-team ops of a CTA-mode heap launched in clusters run inside the cluster: the
     // team barrier is the hardware cluster barrier, small collectives are staged in the
     // bulk ring, which then serves as each CTA's DSMEM window (free between ops: every
@@ -268,16 +286,24 @@ __global__ void __launch_bounds__(INTERP_THREADS) k_interp(shmemg_device_ctx_t c
     for (int q = threadIdx.x; q < cnt * 4; q += blockDim.x)
         reinterpret_cast<uint4 *>(s_ops)[q] = __ldcg(reinterpret_cast<const uint4 *>(ops + base) + q);
     __syncthreads();
+    // validity and participation once per op and CTA, not once per op and thread: a PE
+    // then passes the ops of other PEs in a few instructions
+    if (threadIdx.x < 32)
+        for (int k = (int)threadIdx.x; k < cnt; k += 32)
+            s_act[k] = !op_valid(c, s_ops[k]) ? 2 : op_involves(s_ops[k], me) ? 1 : 0;
+    __syncthreads();
     for (int k = 0; k < cnt; k++) {
         const int64_t i = base + k;
+        if (my_ctx) ctx_progress(s_ctx[my_ctx - 1], ctx_ring);  // background transfers advance
+        const int act = s_act[k];
+        if (act == 0 && !failed) continue;
         const shmemg_op_t o = s_ops[k];
         int rc = SHMEMG_SUCCESS;
-        if (my_ctx) ctx_progress(s_ctx[my_ctx - 1], ctx_ring);  // background transfers advance
         if (failed) {  // only in a clustered CTA-mode launch: walk on, through the barriers
             for (int b = cluster_barriers(o); b > 0; b--) shmemg_d_cluster_sync();
             continue;
         }
-        if (!op_valid(c, o)) {  // an invalid op ends the script there, recorded with its index
+        if (act == 2) {  // an invalid op ends the script there, recorded with its index
             if (leader) shmemg_d_set_status(c, SHMEMG_ERR_INVALID_ARG, i);
             failed = true;
             if (dsm) continue;

@@ -49,12 +49,56 @@ struct Neu {
     __device__ __forceinline__ float result() const { return __fadd_rn(sum, c); }
 };
 
+// Pairs of binary32 values in one 64-bit register (the lower-addressed element in the low
+// half) and Blackwell's packed f32x2 arithmetic: two independent IEEE operations, round
+// to nearest even, subnormals kept.
+__device__ __forceinline__ uint64_t f2(float lo, float hi) {
+    return (uint64_t)__float_as_uint(lo) | ((uint64_t)__float_as_uint(hi) << 32);
+}
+__device__ __forceinline__ float f2_lo(uint64_t v) { return __uint_as_float((uint32_t)v); }
+__device__ __forceinline__ float f2_hi(uint64_t v) { return __uint_as_float((uint32_t)(v >> 32)); }
+__device__ __forceinline__ uint64_t f2_add(uint64_t a, uint64_t b) {
+    uint64_t r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ uint64_t f2_sub(uint64_t a, uint64_t b) {
+    uint64_t r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ uint64_t f2_mul(uint64_t a, uint64_t b) {
+    uint64_t r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+
+// Two compensated sums side by side, Neumaier's step on each: t = sum + x, then c gains
+// (a - t) + b with a the larger of sum and x in magnitude (sum when equal) and b the
+// other -- the same operations as Neu, the magnitude ordering per lane, the three adds
+// packed.
+struct Neu2 {
+    uint64_t sum, c;
+    __device__ __forceinline__ void add(uint64_t x) {
+        const uint64_t t = f2_add(sum, x);
+        const float s0 = f2_lo(sum), s1 = f2_hi(sum), x0 = f2_lo(x), x1 = f2_hi(x);
+        const bool g0 = fabsf(s0) >= fabsf(x0), g1 = fabsf(s1) >= fabsf(x1);
+        const uint64_t a = f2(g0 ? s0 : x0, g1 ? s1 : x1), b = f2(g0 ? x0 : s0, g1 ? x1 : s1);
+        c = f2_add(c, f2_add(f2_sub(a, t), b));
+        sum = t;
+    }
+    __device__ __forceinline__ uint64_t result() const { return f2_add(sum, c); }
+};
+
 // Elements per thread of the wide path: one 16-byte code load per member.
 template <int FMT> struct QWide { static constexpr int E = FMT == SHMEMG_FMT_E4M3 ? 16 : 8; };
 
+// The E dequantised values of one 16-byte code load, as E/2 pairs: decoded exactly to
+// binary32, then one RNE multiply by the block scale each (packed).
 template <int FMT>
-__device__ __forceinline__ void qdecode16(uint4 w, float s, float *d) {
+__device__ __forceinline__ void qdecode16(uint4 w, float s, uint64_t *d) {
     const uint32_t v[4] = {w.x, w.y, w.z, w.w};
+    const uint64_t ss = f2(s, s);
     if (FMT == SHMEMG_FMT_E4M3) {
         // hardware conversion of code pairs to f16 (exact: every E4M3 value is an f16
         // value), then to binary32
@@ -63,12 +107,13 @@ __device__ __forceinline__ void qdecode16(uint4 w, float s, float *d) {
             const uint16_t pair = (uint16_t)((v[j >> 2] >> (8 * (j & 3))) & 0xFFFFu);
             uint32_t h2;
             asm("cvt.rn.f16x2.e4m3x2 %0, %1;" : "=r"(h2) : "h"(pair));
-            d[j] = __fmul_rn(__half2float(__ushort_as_half((unsigned short)(h2 & 0xFFFFu))), s);
-            d[j + 1] = __fmul_rn(__half2float(__ushort_as_half((unsigned short)(h2 >> 16))), s);
+            d[j >> 1] = f2_mul(f2(__half2float(__ushort_as_half((unsigned short)(h2 & 0xFFFFu))),
+                                  __half2float(__ushort_as_half((unsigned short)(h2 >> 16)))),
+                               ss);
         }
     } else {
 #pragma unroll
-        for (int j = 0; j < 8; j++) d[j] = __fmul_rn(bf16_decode((v[j >> 1] >> (16 * (j & 1))) & 0xFFFFu), s);
+        for (int j = 0; j < 4; j++) d[j] = f2_mul(f2(bf16_decode(v[j] & 0xFFFFu), __uint_as_float(v[j] & 0xFFFF0000u)), ss);
     }
 }
 
@@ -99,10 +144,10 @@ __device__ __forceinline__ void qsum_wide_acc(const uint8_t *heap, uint64_t H, i
                                               uint64_t q_off, uint64_t s_off, uint64_t e0, float4 *o) {
     constexpr int E = QWide<FMT>::E;
     constexpr uint64_t QS = FMT == SHMEMG_FMT_E4M3 ? 1 : 2;
-    Neu acc[E];
+    Neu2 acc[E / 2];
 #pragma unroll
-    for (int j = 0; j < E; j++) acc[j] = {0.0f, 0.0f};
-    float d[E];
+    for (int j = 0; j < E / 2; j++) acc[j] = {0ull, 0ull};
+    uint64_t d[E / 2];
     int r = 0;
     for (; r + M <= P; r += M) {
         uint4 w[M];
@@ -117,18 +162,20 @@ __device__ __forceinline__ void qsum_wide_acc(const uint8_t *heap, uint64_t H, i
         for (int u = 0; u < M; u++) {
             qdecode16<FMT>(w[u], sc[u], d);
 #pragma unroll
-            for (int j = 0; j < E; j++) acc[j].add(d[j]);
+            for (int j = 0; j < E / 2; j++) acc[j].add(d[j]);
         }
     }
     for (; r < P; r++) {
         const uint8_t *b0 = heap + (uint64_t)(pe0 + r * pstride) * H;
         qdecode16<FMT>(__ldcg((const uint4 *)(b0 + q_off + e0 * QS)), __ldcg((const float *)(b0 + s_off) + e0 / 128), d);
 #pragma unroll
-        for (int j = 0; j < E; j++) acc[j].add(d[j]);
+        for (int j = 0; j < E / 2; j++) acc[j].add(d[j]);
     }
 #pragma unroll
-    for (int k = 0; k < E / 4; k++)
-        o[k] = make_float4(acc[4 * k].result(), acc[4 * k + 1].result(), acc[4 * k + 2].result(), acc[4 * k + 3].result());
+    for (int k = 0; k < E / 4; k++) {
+        const uint64_t a = acc[2 * k].result(), b = acc[2 * k + 1].result();
+        o[k] = make_float4(f2_lo(a), f2_hi(a), f2_lo(b), f2_hi(b));
+    }
 }
 
 // One CTA's chunk of blockDim.x * E elements starting at c0 (full, aligned): every thread

@@ -760,6 +760,36 @@ def run_halo(torch, sg, iters=100, reps=3):
     hbm, _ = measured_peaks()
     best = max(out["cta"]["persistent"]["GBps"], out["cluster2"]["persistent"]["GBps"])
     out["frac_of_hbm"] = round(best / hbm, 4)
+    # a strong-scaling point: the same 19 x 8 PEs with 256 x 256 tiles (the grid fits in
+    # L2), where each sweep is short and the per-sweep synchronisation decides
+    sn, sit = 256, 400
+    shs = sg.halo_stride(sn, sn)
+    st_b, sh_b = 2 * sn * sn * 4, 2 * shs * 4
+    heap = sg.Heap(npes, (st_b + sh_b + 64 + 4095) // 4096 * 4096)
+    try:
+        parts = heap.partitions()
+        parts.zero_()
+        init = torch.randn(npes, sn * sn, device="cuda", generator=torch.Generator(device="cuda").manual_seed(7))
+        tiles, halos, sigs = heap.sym(0, st_b), heap.sym(st_b, sh_b), heap.sym(st_b + sh_b, 32)
+        row, res = {}, {}
+        for variant in ("persistent", "plain"):
+            times = []
+            for _ in range(reps + 1):
+                parts[:, :sn * sn * 4].view(torch.float32).copy_(init)
+                e0, e1 = _events(torch)
+                e0.record(stream)
+                sg.halo_jacobi(tiles, halos, sigs, px, py, sn, sn, sit, stream, plain=variant == "plain")
+                e1.record(stream)
+                torch.cuda.synchronize()
+                times.append(e0.elapsed_time(e1))
+            r0 = (sit & 1) * sn * sn * 4
+            res[variant] = parts[:, r0:r0 + sn * sn * 4].clone()
+            row[variant + "_us_per_sweep"] = round(float(np.median(times[1:])) * 1e3 / sit, 2)
+        row["speedup_vs_plain"] = round(row["plain_us_per_sweep"] / row["persistent_us_per_sweep"], 2)
+        row["results_equal"] = bool(torch.equal(res["persistent"], res["plain"]))
+        out["small_tiles_256"] = row
+    finally:
+        heap.close()
     g = W.normals_np(11, 2048 * 4096).astype(np.float32).reshape(2048, 4096)
     t0 = time.perf_counter()
     orc.halo_jacobi(g, 1)
@@ -1209,7 +1239,7 @@ def run_serve(torch, sg, nreq=1 << 16, rates=None, npes=512, arena=32 << 20):
 
 
 # ----------------------------------------------------------------------------- profiling cases
-PROFILE_CASES = ("interp_ring", "interp_ops", "reduce", "reduce_f32", "broadcast", "alltoall", "amo", "amo_l2", "amo_plain", "amo_combine", "amo_combine_zipf", "batch_bf16", "batch_e4m3", "qsum",
+PROFILE_CASES = ("interp_ring", "interp_ops", "reduce", "reduce_f32", "broadcast", "alltoall", "amo", "amo_l2", "amo_plain", "amo_combine", "amo_combine_zipf", "batch_bf16", "batch_e4m3", "batch_e4m3_teams", "batch_bf16_teams", "qsum",
                  "pingpong_cluster", "cluster_coll", "halo", "halo_plain")
 
 
@@ -1288,6 +1318,22 @@ def run_profile_case(name, launches=4):
         f = torch.empty(nops, dtype=torch.int64, device="cuda")
         for _ in range(launches):
             sg.amo_stream(heap.base, wpp, ops, nops, 1, 2, f, 0 if name == "amo_plain" else 2, s)
+    elif name in ("batch_e4m3_teams", "batch_bf16_teams"):  # 8 teams of all 64 PEs, 1 Mi elements each, tile 8192
+        n, nt = 1 << 20, 8
+        per = 8 * n  # codes (<= 2n) + scales + output (4n), rounded up
+        heap = sg.Heap(64, nt * per)
+        fmt = sg.FMT_E4M3 if name == "batch_e4m3_teams" else sg.FMT_BF16
+        d = []
+        for t in range(nt):
+            o = t * per
+            heap.partitions()[:, o:o + 4 * n].view(torch.float32).normal_()
+            sg.quantize(sg.TEAM_WORLD, heap.base + o + 4 * n, heap.base + o + 6 * n, heap.base + o, fmt, n, s)
+            d.append(sg.CollDesc(0, 64, sg.FLOAT, fmt, n, heap.base + o, heap.base + o + 4 * n, heap.base + o + 6 * n))
+        b = sg.Batch(d, sg.Tune(8192, 0, 0, 0))
+        for _ in range(launches):
+            b.launch(s)
+        torch.cuda.synchronize()
+        b.destroy()
     elif name in ("batch_bf16", "batch_e4m3", "qsum"):   # 64 PEs, bf16 / E4M3 payloads of 1 Mi elements
         n = 1 << 20
         heap = sg.Heap(64, 12 * n)
@@ -1401,7 +1447,7 @@ def leg_summary(name, r):
                 "blocking_GBps": r.get("blocking_GBps")}
     if name == "halo":
         return {"GBps": _get(r, "cta", "persistent", "GBps"), "frac": r.get("frac_of_hbm"),
-                "x_plain": _get(r, "cta", "speedup_vs_plain")}
+                "x_plain": _get(r, "cta", "speedup_vs_plain"), "x_plain_256": _get(r, "small_tiles_256", "speedup_vs_plain")}
     if name == "batch":
         return {f: _get(r, f, "GBps") for f in ("fp32", "bf16", "e4m3")}
     if name == "serve":

@@ -64,7 +64,7 @@ __device__ __forceinline__ float jac(float up, float dn, float lf, float rt) {
 // halo[p] into tile[p^1]; with `send`, the new boundary values also go to the neighbours'
 // halo[p^1].  edges = false (the interior phase, rows 1 .. ny-2): the west and east
 // halos are not read -- the points of columns 0 and nx-1 get a placeholder left or right
-// value from the tile itself and are recomputed by halo_edges -- so the rows can be swept
+// value from the tile itself and are recomputed by halo_boundary -- so the rows can be swept
 // before the neighbours' halos have arrived.
 // Thread layout: float4 column c4 = rank mod W4, a contiguous run of rows per thread
 // (sliding window of three rows in registers, one new float4 per row).  The grid's
@@ -239,30 +239,80 @@ __device__ __forceinline__ void halo_sweep(const HaloArgs &a, shmemg_group g, in
     }
 }
 
-// Columns 0 and nx-1 of rows 1 .. ny-2 (after an interior phase): the points whose left or
-// right neighbour is in the west or east halo, with their sends.
-__device__ __forceinline__ void halo_edges(const HaloArgs &a, shmemg_group g, int me, const int nb[4], int p,
-                                           bool send) {
+// The boundary after an interior phase (ny > 2): rows 0 and ny-1 as float4 chunks, then
+// columns 0 and nx-1 of rows 1 .. ny-2 as single points, with their sends.  Every load of
+// a thread's items is issued before the first result is needed (four edge points per
+// round), so the pass costs about two round trips.
+__device__ __forceinline__ void halo_boundary(const HaloArgs &a, shmemg_group g, int me, const int nb[4], int p,
+                                              bool send) {
     const shmemg_device_ctx_t &c = a.c;
-    const int nx = a.nx, ny = a.ny;
+    const int nx = a.nx, ny = a.ny, W4 = nx / 4;
     const uint64_t tile_elems = (uint64_t)nx * ny, halo_elems = halo_stride(nx, ny);
     const float *cur = (const float *)shmemg_d_addr(c, me, a.tiles) + (uint64_t)p * tile_elems;
     float *nxt = (float *)shmemg_d_addr(c, me, a.tiles) + (uint64_t)(p ^ 1) * tile_elems;
     const float *hal = (const float *)shmemg_d_addr(c, me, a.halos) + (uint64_t)p * halo_elems;
+    const float *h_n = hal + halo_part(nx, ny, H_N), *h_s = hal + halo_part(nx, ny, H_S);
     const float *h_w = hal + halo_part(nx, ny, H_W), *h_e = hal + halo_part(nx, ny, H_E);
-    float *to_w = (float *)shmemg_d_addr(c, nb[H_W], a.halos) + (uint64_t)(p ^ 1) * halo_elems + halo_part(nx, ny, H_E);
-    float *to_e = (float *)shmemg_d_addr(c, nb[H_E], a.halos) + (uint64_t)(p ^ 1) * halo_elems + halo_part(nx, ny, H_W);
-    for (uint32_t q = g.rank; q < 2u * (uint32_t)(ny - 2); q += g.size) {
-        const int i = 1 + (int)(q >> 1);
+    auto nb_halo = [&](int dir, int part) {
+        return (float *)shmemg_d_addr(c, nb[dir], a.halos) + (uint64_t)(p ^ 1) * halo_elems + halo_part(nx, ny, part);
+    };
+    float *to_n = nb_halo(H_N, H_S), *to_s = nb_halo(H_S, H_N), *to_w = nb_halo(H_W, H_E), *to_e = nb_halo(H_E, H_W);
+    for (uint32_t q = g.rank; q < 2u * (uint32_t)W4; q += g.size) {  // a float4 chunk of row 0 or row ny-1
+        const int i = q < (uint32_t)W4 ? 0 : ny - 1, c4 = (int)(q % (uint32_t)W4), j = 4 * c4;
         const float *row = cur + (uint64_t)i * nx;
-        if ((q & 1) == 0) {  // column 0
-            const float o = jac(__ldcg(row - nx), __ldcg(row + nx), __ldcg(h_w + i), __ldcg(row + 1));
-            nxt[(uint64_t)i * nx] = o;
-            if (send) to_w[i] = o;
-        } else {             // column nx-1
-            const float o = jac(__ldcg(row - nx + nx - 1), __ldcg(row + nx + nx - 1), __ldcg(row + nx - 2), __ldcg(h_e + i));
-            nxt[(uint64_t)i * nx + nx - 1] = o;
-            if (send) to_e[i] = o;
+        const float4 up = __ldcg(reinterpret_cast<const float4 *>(i == 0 ? h_n + j : row - nx + j));
+        const float4 mid = __ldcg(reinterpret_cast<const float4 *>(row + j));
+        const float4 dn = __ldcg(reinterpret_cast<const float4 *>(i == ny - 1 ? h_s + j : row + nx + j));
+        const float lf = c4 == 0 ? __ldcg(h_w + i) : __ldcg(row + j - 1);
+        const float rt = c4 == W4 - 1 ? __ldcg(h_e + i) : __ldcg(row + j + 4);
+        float4 o;
+        o.x = jac(up.x, dn.x, lf, mid.y);
+        o.y = jac(up.y, dn.y, mid.x, mid.z);
+        o.z = jac(up.z, dn.z, mid.y, mid.w);
+        o.w = jac(up.w, dn.w, mid.z, rt);
+        *reinterpret_cast<float4 *>(nxt + (uint64_t)i * nx + j) = o;
+        if (send) {
+            *reinterpret_cast<float4 *>((i == 0 ? to_n : to_s) + j) = o;
+            if (c4 == 0) to_w[i] = o.x;
+            if (c4 == W4 - 1) to_e[i] = o.w;
+        }
+    }
+    // edge points e = 0 .. 2(ny-2)-1: row 1 + e/2, column 0 (e even) or nx-1 (e odd)
+    constexpr int U = 4;
+    const uint32_t nedge = 2u * (uint32_t)(ny - 2);
+    for (uint32_t e0 = g.rank; e0 < nedge; e0 += U * g.size) {
+        float v[U][4];
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            const uint32_t e = e0 + (uint32_t)u * g.size;
+            if (e >= nedge) continue;
+            const int i = 1 + (int)(e >> 1);
+            const float *row = cur + (uint64_t)i * nx;
+            if ((e & 1) == 0) {
+                v[u][0] = __ldcg(row - nx);
+                v[u][1] = __ldcg(row + nx);
+                v[u][2] = __ldcg(h_w + i);
+                v[u][3] = __ldcg(row + 1);
+            } else {
+                v[u][0] = __ldcg(row - 1);
+                v[u][1] = __ldcg(row + nx + nx - 1);
+                v[u][2] = __ldcg(row + nx - 2);
+                v[u][3] = __ldcg(h_e + i);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            const uint32_t e = e0 + (uint32_t)u * g.size;
+            if (e >= nedge) continue;
+            const int i = 1 + (int)(e >> 1);
+            const float o = jac(v[u][0], v[u][1], v[u][2], v[u][3]);
+            if ((e & 1) == 0) {
+                nxt[(uint64_t)i * nx] = o;
+                if (send) to_w[i] = o;
+            } else {
+                nxt[(uint64_t)i * nx + nx - 1] = o;
+                if (send) to_e[i] = o;
+            }
         }
     }
 }
@@ -305,6 +355,7 @@ __device__ __forceinline__ void halo_signal(const HaloArgs &a, const int nb[4]) 
 // signals only.  Plain form (signals off): one launch per sweep (t1 = t0 + 1), kernel
 // boundaries order the sweeps and no signal is sent or awaited; both forms run the same
 // sweep code.
+template <bool SPLIT>
 __global__ void __launch_bounds__(512) k_halo(HaloArgs a, int t0, int t1, int iters, int signals) {
     const shmemg_device_ctx_t &c = a.c;
     const int me = shmemg_d_my_pe(c);
@@ -322,10 +373,9 @@ __global__ void __launch_bounds__(512) k_halo(HaloArgs a, int t0, int t1, int it
     }
     for (int t = t0; t < t1; t++) {
         const bool send = t + 1 < iters;
-        // interior rows first: they read only this PE's own tile, so they overlap the
-        // wait for the neighbours' halos (rows 0 and ny-1, columns 0 and nx-1 follow it)
-        const bool split = a.ny > 2;
-        if (split) halo_sweep(a, g, me, nb, t & 1, false, 1, a.ny - 1, false);
+        // SPLIT (the persistent form, ny > 2): the interior rows first -- they read only
+        // this PE's own tile, so they overlap the wait for the neighbours' halos
+        if constexpr (SPLIT) halo_sweep(a, g, me, nb, t & 1, false, 1, a.ny - 1, false);
         if (signals && threadIdx.x == 0) {
             int rc = SHMEMG_SUCCESS;
             if (leader)
@@ -340,13 +390,9 @@ __global__ void __launch_bounds__(512) k_halo(HaloArgs a, int t0, int t1, int it
                              ? shmemg_d_ld_cluster<int>(shmemg_d_cluster_addr(&s_stop, 0))
                              : s_stop;
         if (stop) break;
-        if (split) {
-            halo_sweep(a, g, me, nb, t & 1, send, 0, 1, true);
-            halo_sweep(a, g, me, nb, t & 1, send, a.ny - 1, a.ny, true);
-            halo_edges(a, g, me, nb, t & 1, send);
-        } else {
-            halo_sweep(a, g, me, nb, t & 1, send, 0, a.ny, true);
-        }
+        // then rows 0 and ny-1 and columns 0 and nx-1 (SPLIT), or the whole tile
+        if constexpr (SPLIT) halo_boundary(a, g, me, nb, t & 1, send);
+        else halo_sweep(a, g, me, nb, t & 1, send, 0, a.ny, true);
         shmemg_d_pe_sync(c);
         if (signals && send && leader) halo_signal(a, nb);
     }
@@ -420,7 +466,8 @@ extern "C" int shmemg_halo_jacobi(float *tiles, float *halos, uint64_t *sigs, in
     if (iters == 0) return SHMEMG_SUCCESS;
     int t0 = 0, signals = 1;
     void *args[] = {(void *)&a, (void *)&t0, (void *)&iters, (void *)&iters, (void *)&signals};
-    return halo_launch((const void *)k_halo, args, to_stream(stream));
+    // tiles of more than two rows sweep their interior while the halos are on the way
+    return halo_launch(ny > 2 ? (const void *)k_halo<true> : (const void *)k_halo<false>, args, to_stream(stream));
 }
 
 extern "C" int shmemg_halo_jacobi_plain(float *tiles, float *halos, uint64_t *sigs, int px, int py, int nx, int ny,
@@ -434,7 +481,7 @@ extern "C" int shmemg_halo_jacobi_plain(float *tiles, float *halos, uint64_t *si
     void *args[] = {(void *)&a, (void *)&t, (void *)&t1, (void *)&iters, (void *)&signals};
     for (t = 0; t < iters; t++) {
         t1 = t + 1;
-        if (int rc = halo_launch((const void *)k_halo, args, to_stream(stream))) return rc;
+        if (int rc = halo_launch((const void *)k_halo<false>, args, to_stream(stream))) return rc;
     }
     return SHMEMG_SUCCESS;
 }

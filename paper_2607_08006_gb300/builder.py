@@ -20,6 +20,9 @@ LIB = os.path.join(BUILD, "libshmemg.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-std=c++17", "-O3", "-lineinfo", *ARCH, "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC,
               "-diag-suppress", "549"]
+# per-file flags: the interpreter (one CTA of 512 threads per SM) gets the full 128
+# registers its op walk needs; ptxas's default target for it spills
+FILE_FLAGS = {"interp.cu": ["-maxrregcount=128"]}
 
 
 def _nvcc() -> str:
@@ -54,7 +57,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     def compile_one(job):
         src, obj = job
         tmp = obj + f".{os.getpid()}.tmp"
-        cmd = [nvcc, *NVCC_FLAGS, "-c", src, "-o", tmp]
+        cmd = [nvcc, *NVCC_FLAGS, *FILE_FLAGS.get(os.path.basename(src), []), "-c", src, "-o", tmp]
         if verbose:
             cmd.insert(1, "-Xptxas=-v")
         r = subprocess.run(cmd, capture_output=True, text=True)

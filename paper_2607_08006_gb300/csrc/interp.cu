@@ -17,54 +17,58 @@ namespace shmemg {
 constexpr int INTERP_THREADS = 512;
 constexpr int OP_BATCH = 64;  // op records staged in shared memory at a time
 
-// Large aligned puts and gets (>= SHMEMG_BULK_MIN) run on the bulk (TMA) engine when the
-// launch provides its shared-memory ring (use_bulk): thread 0 of each CTA of the PE
-// streams every ncta-th chunk.
-__device__ __forceinline__ void pe_copy(const shmemg_device_ctx_t &c, shmemg_group g, uint8_t *d, const uint8_t *s,
-                                        uint64_t n, int use_bulk, uint8_t *ring, uint64_t *bars) {
-    if (use_bulk && n >= SHMEMG_BULK_MIN && (((uint64_t)d | (uint64_t)s | n) & 15) == 0) {
-        // the split follows the hardware cluster shape: a launch without clusters (each
-        // CTA its own cluster of one) still copies every chunk
-        const bool cl = c.pe_mode == SHMEMG_PE_MODE_CLUSTER;
-        if (threadIdx.x == 0)
-            shmemg_d_bulk_copy_thread(c, d, s, n, cl ? shmemg_d_cluster_ctarank() : 0u,
-                                      cl ? shmemg_d_cluster_nctarank() : 1u, ring, bars);
-    } else {
-        shmemg_d_copy_group(g, d, s, n);
-    }
+// ---------------------------------------------------------------- the bulk engine
+// Thread 0 of every CTA moves the CTA's bulk (TMA) traffic through one ring of
+// RING_STAGES shared-memory stages of RING_CHUNK bytes: a chunk is loaded global ->
+// shared (cp.async.bulk, completion counted in bytes on the stage's mbarrier), then
+// stored shared -> global (cp.async.bulk, bulk groups).  Two kinds of transfer share
+// the ring, in ring order:
+//  * queue 0, the default context's large aligned puts and gets (>= SHMEMG_BULK_MIN):
+//    blocking -- the op returns once they are written.  The PE's CTAs split the chunks
+//    (every ncta-th chunk) along the hardware cluster shape, so a launch without
+//    clusters still copies every chunk;
+//  * queues 1..3, the explicit contexts (Sec. 6.2: contexts as independent ordering and
+//    completion domains, an optional resource-limited feature beside the default device
+//    context): a context's put_nbi / get_nbi is queued in the PE's leader CTA and moved
+//    in the background -- the engine advances at every op boundary without waiting --
+//    and only quiet / fence on that context (or on all) waits for it.
+// A context alone thus keeps the whole ring in flight, like a blocking copy.  Chunk j of
+// the ring uses stage j % RING_STAGES and completes phase (j / RING_STAGES) & 1 of its
+// mbarrier; a stage is reloaded only after the store of its previous chunk has read it.
+constexpr int RING_STAGES = 6;
+constexpr uint32_t RING_CHUNK = SHMEMG_BULK_CHUNK;
+constexpr size_t RING_SMEM = (size_t)RING_STAGES * RING_CHUNK;
+constexpr int CTX_QCAP = 8;   // queued transfers per context
+constexpr int NQ = SHMEMG_DEVICE_CTX_COUNT;  // queue 0 + one per explicit context
+
+struct DmaXfer {
+    uint64_t dst, src, n;    // generic global addresses, 16-byte multiples
+    uint32_t first, stride;  // chunks first, first + stride, ... of the transfer
+};
+struct DmaState {
+    DmaXfer q[NQ][CTX_QCAP];
+    uint32_t head[NQ], tail[NQ];  // queued transfers; q[k][head] is being loaded
+    uint64_t next[NQ];            // next chunk (in first + i*stride numbering, i counted) of q[k][head]
+    uint64_t last[NQ];            // 1 + ring index of the queue's last chunk issued (0: none)
+    uint64_t ld, st;              // ring chunks whose loads / stores are issued
+    uint64_t st_dst[RING_STAGES];
+    uint32_t st_len[RING_STAGES];
+    uint64_t bar[RING_STAGES];
+    uint32_t rr;                  // next explicit context to serve
+    int dead;                     // a load never landed: nothing is issued any more
+};
+
+__device__ __forceinline__ void dma_init(DmaState &x) {
+    for (int k = 0; k < NQ; k++) x.head[k] = x.tail[k] = 0, x.next[k] = x.last[k] = 0;
+    x.ld = x.st = 0;
+    x.rr = 0;
+    x.dead = 0;
+    for (int k = 0; k < RING_STAGES; k++)
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(shmemg_smem_u32(&x.bar[k])) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
 
-// ---------------------------------------------------------------- explicit contexts
-// Explicit device contexts (Sec. 6.2: contexts as independent ordering and completion
-// domains, an optional resource-limited feature beside the default device context).
-// Context k (1..SHMEMG_DEVICE_CTX_COUNT-1) of a PE is served by one thread of the PE's
-// leader CTA, thread 32*k, with a ring of CTX_STAGES shared-memory stages, one mbarrier
-// per stage and the thread's own bulk-group queue: its put_nbi / get_nbi are queued and
-// moved chunk by chunk with TMA bulk copies (global -> shared -> global) that run while
-// the PE goes on with later ops -- the thread advances them without blocking at every op
-// boundary -- and only quiet / fence on that context (or on all of them) waits for them.
-// Context 0, the default context, completes its non-blocking ops as it issues them.
-constexpr int CTX_STAGES = 2;
-constexpr uint32_t CTX_CHUNK = 12u << 10;
-constexpr int CTX_QCAP = 8;
-constexpr size_t CTX_SMEM = (size_t)(SHMEMG_DEVICE_CTX_COUNT - 1) * CTX_STAGES * CTX_CHUNK;
-
-struct CtxXfer {
-    uint64_t dst, src, n;  // generic global addresses, 16-byte multiples
-};
-// Chunks are numbered across the context's transfers; chunk k uses stage k % CTX_STAGES,
-// its load completes phase (k / CTX_STAGES) & 1 of that stage's mbarrier.
-struct CtxState {
-    CtxXfer q[CTX_QCAP];
-    uint32_t head, tail;              // queued transfers; q[head] is being loaded
-    uint64_t off;                     // bytes of q[head] whose loads are issued
-    uint64_t ld, st;                  // chunks whose loads / stores are issued
-    uint64_t st_dst[CTX_STAGES];      // where each stage's chunk goes, and its length
-    uint32_t st_len[CTX_STAGES];
-    uint64_t bar[CTX_STAGES];
-};
-
-__device__ __forceinline__ bool ctx_mbar_test(uint64_t *bar, uint32_t parity) {
+__device__ __forceinline__ bool dma_test(uint64_t *bar, uint32_t parity) {
     uint32_t done;
     asm volatile("{\n\t.reg .pred p;\n\tmbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
                  : "=r"(done)
@@ -73,69 +77,139 @@ __device__ __forceinline__ bool ctx_mbar_test(uint64_t *bar, uint32_t parity) {
     return done != 0;
 }
 
+// bulk wait_group.read with a run-time count of newer groups allowed to stay pending
+__device__ __forceinline__ void dma_wait_read(uint64_t newer) {
+    switch (newer < RING_STAGES - 1 ? (int)newer : RING_STAGES - 1) {
+    case 0: asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); break;
+    case 1: asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory"); break;
+    case 2: asm volatile("cp.async.bulk.wait_group.read 2;" ::: "memory"); break;
+    case 3: asm volatile("cp.async.bulk.wait_group.read 3;" ::: "memory"); break;
+    case 4: asm volatile("cp.async.bulk.wait_group.read 4;" ::: "memory"); break;
+    default: asm volatile("cp.async.bulk.wait_group.read 5;" ::: "memory"); break;
+    }
+}
+
+// the next queue with a chunk to load: queue 0 first, then the contexts in turn
+__device__ __forceinline__ int dma_pick(DmaState &x) {
+    if (x.head[0] != x.tail[0]) return 0;
+    for (int i = 0; i < NQ - 1; i++) {
+        const int k = 1 + (int)((x.rr + i) % (NQ - 1));
+        if (x.head[k] != x.tail[k]) {
+            x.rr = (uint32_t)(k % (NQ - 1));
+            return k;
+        }
+    }
+    return -1;
+}
+
 // Issues what can be issued now without waiting: stores of chunks whose loads have
 // landed, then loads into stages whose previous chunk's store has read them.
-__device__ __forceinline__ void ctx_progress(CtxState &x, uint8_t *ring) {
+__device__ __noinline__ void dma_progress(DmaState &x, uint8_t *ring) {
     while (x.st < x.ld) {
-        const uint32_t s = (uint32_t)(x.st % CTX_STAGES);
-        if (!ctx_mbar_test(&x.bar[s], (uint32_t)((x.st / CTX_STAGES) & 1))) break;
-        shmemg_bulk_store((void *)x.st_dst[s], ring + (size_t)s * CTX_CHUNK, x.st_len[s]);
+        const uint32_t s = (uint32_t)(x.st % RING_STAGES);
+        if (!dma_test(&x.bar[s], (uint32_t)((x.st / RING_STAGES) & 1))) break;
+        shmemg_bulk_store((void *)x.st_dst[s], ring + (size_t)s * RING_CHUNK, x.st_len[s]);
         x.st++;
     }
-    while (x.head != x.tail && x.ld < x.st + CTX_STAGES) {
-        if (x.ld >= CTX_STAGES) {  // the stage's previous chunk: its store must have read it
-            const uint32_t newer = (uint32_t)(x.st - (x.ld - CTX_STAGES) - 1);
-            if (newer == 0) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
-            else asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");  // CTX_STAGES == 2: newer <= 1
-        }
-        const CtxXfer &t = x.q[x.head % CTX_QCAP];
-        const uint32_t len = (uint32_t)(t.n - x.off < CTX_CHUNK ? t.n - x.off : CTX_CHUNK);
-        const uint32_t s = (uint32_t)(x.ld % CTX_STAGES);
-        x.st_dst[s] = t.dst + x.off;
+    if (x.dead) return;
+    while (x.ld < x.st + RING_STAGES) {
+        const int k = dma_pick(x);
+        if (k < 0) break;
+        if (x.ld >= RING_STAGES) dma_wait_read(x.st - (x.ld - RING_STAGES) - 1);  // stores issued after that chunk's
+        const DmaXfer &t = x.q[k][x.head[k] % CTX_QCAP];
+        const uint64_t off = (t.first + x.next[k] * t.stride) * (uint64_t)RING_CHUNK;
+        const uint32_t len = (uint32_t)(t.n - off < RING_CHUNK ? t.n - off : RING_CHUNK);
+        const uint32_t s = (uint32_t)(x.ld % RING_STAGES);
+        x.st_dst[s] = t.dst + off;
         x.st_len[s] = len;
-        shmemg_bulk_load(ring + (size_t)s * CTX_CHUNK, (const void *)(t.src + x.off), len, &x.bar[s]);
+        shmemg_bulk_load(ring + (size_t)s * RING_CHUNK, (const void *)(t.src + off), len, &x.bar[s]);
         x.ld++;
-        x.off += len;
-        if (x.off == t.n) {
-            x.head++;
-            x.off = 0;
+        x.last[k] = x.ld;
+        if (off + (uint64_t)t.stride * RING_CHUNK >= t.n) {  // that was the transfer's last chunk
+            x.head[k]++;
+            x.next[k] = 0;
+        } else {
+            x.next[k]++;
         }
     }
 }
 
-// Completes every transfer of the context (bounded waits; a load that never lands is
-// recorded as a timeout) and makes its writes visible to generic loads.
-__device__ __forceinline__ void ctx_drain(const shmemg_device_ctx_t &c, CtxState &x, uint8_t *ring) {
+// anything in flight or queued (an inline test before the out-of-line progress call)
+__device__ __forceinline__ bool dma_busy(const DmaState &x) {
+    bool b = x.st != x.ld;
+#pragma unroll
+    for (int k = 0; k < NQ; k++) b |= x.head[k] != x.tail[k];
+    return b;
+}
+
+__device__ __forceinline__ bool dma_queue_done(const DmaState &x, int k) {
+    return x.head[k] == x.tail[k] && x.last[k] <= x.st;
+}
+
+// Completes queue k (k < 0: every queue) -- bounded waits; a load that never lands is
+// recorded as a timeout, and once the other loads in flight have landed (bounded) the
+// engine stops issuing -- then makes the writes visible to generic loads.  No load is
+// left writing the ring when it returns unless the status word says so (detail -4).
+__device__ __noinline__ void dma_drain(const shmemg_device_ctx_t &c, DmaState &x, uint8_t *ring, int k) {
     for (;;) {
-        ctx_progress(x, ring);
-        if (x.head == x.tail && x.st == x.ld) break;
+        dma_progress(x, ring);
+        bool done = true;
+        for (int q = 0; q < NQ; q++)
+            if ((k < 0 || q == k) && !dma_queue_done(x, q)) done = false;
+        if (done || (x.dead && x.st == x.ld)) break;
         if (x.st < x.ld) {
-            const uint32_t s = (uint32_t)(x.st % CTX_STAGES);
-            if (!shmemg_mbar_wait(&x.bar[s], (uint32_t)((x.st / CTX_STAGES) & 1), c.timeout_ns)) {
-                // The other loads in flight land (bounded) before giving up.  The state
-                // stays as it is: a stage is reloaded only after its chunk has been
-                // stored, so a load that lands late overwrites nothing in use, and the
-                // script's final drain waits for it again.
-                bool drained = true;
-                for (uint64_t k = x.st + 1; k < x.ld; k++)
-                    drained = shmemg_mbar_wait(&x.bar[k % CTX_STAGES], (uint32_t)((k / CTX_STAGES) & 1), c.timeout_ns) &&
-                              drained;
+            const uint32_t s = (uint32_t)(x.st % RING_STAGES);
+            if (!shmemg_mbar_wait(&x.bar[s], (uint32_t)((x.st / RING_STAGES) & 1), c.timeout_ns)) {
+                const bool drained = shmemg_bulk_drain_loads(x.bar, RING_STAGES, x.st, x.ld, c.timeout_ns);
                 shmemg_d_set_status(c, SHMEMG_ERR_TIMEOUT, drained ? -3 : -4);
-                break;
+                x.dead = 1;
+                if (!drained) break;
+                x.st = x.ld;  // every load landed: their chunks are abandoned, the ring is free
+                for (int q = 0; q < NQ; q++) x.head[q] = x.tail[q], x.next[q] = 0;
             }
+        } else if (x.dead) {
+            for (int q = 0; q < NQ; q++) x.head[q] = x.tail[q], x.next[q] = 0;  // nothing more is moved
         }
     }
     asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
-    asm volatile("fence.proxy.async.global;" ::: "memory");
+    asm volatile("fence.proxy.async.global;" ::: "memory");  // async-proxy writes -> generic readers
 }
 
-__device__ __forceinline__ void ctx_enqueue(const shmemg_device_ctx_t &c, CtxState &x, uint8_t *ring, uint64_t dst,
-                                            uint64_t src, uint64_t n) {
-    if (x.tail - x.head == CTX_QCAP) ctx_drain(c, x, ring);  // queue full: finish what is queued
-    asm volatile("fence.proxy.async.global;" ::: "memory");    // earlier generic writes -> async proxy
-    x.q[x.tail % CTX_QCAP] = {dst, src, n};
-    x.tail++;
-    ctx_progress(x, ring);
+__device__ __noinline__ void dma_enqueue(const shmemg_device_ctx_t &c, DmaState &x, uint8_t *ring, int k,
+                                            uint64_t dst, uint64_t src, uint64_t n, uint32_t first, uint32_t stride) {
+    if (x.tail[k] - x.head[k] == CTX_QCAP) dma_drain(c, x, ring, k);  // queue full: finish what is queued
+    if ((uint64_t)first * RING_CHUNK >= n) return;                     // no chunk of this transfer is ours
+    asm volatile("fence.proxy.async.global;" ::: "memory");             // earlier generic writes -> async proxy
+    x.q[k][x.tail[k] % CTX_QCAP] = {dst, src, n, first, stride};
+    x.tail[k]++;
+    dma_progress(x, ring);
+}
+
+// Large aligned puts and gets (>= SHMEMG_BULK_MIN) on the default context go through the
+// bulk engine when the launch provides its ring (use_bulk): while no context transfer is
+// queued or in flight the ring is free and the copy runs the lean blocking loop of the
+// device API on it (its own mbarriers, state in registers); otherwise it joins the
+// engine's queue 0 behind the chunks in flight.  The PE's other threads copy smaller or
+// unaligned ones with vector loads and stores.
+__device__ __forceinline__ void pe_copy(const shmemg_device_ctx_t &c, shmemg_group g, uint8_t *d, const uint8_t *s,
+                                        uint64_t n, int use_bulk, uint8_t *ring, DmaState &x, uint64_t *bars) {
+    if (use_bulk && n >= SHMEMG_BULK_MIN && (((uint64_t)d | (uint64_t)s | n) & 15) == 0) {
+        const bool cl = c.pe_mode == SHMEMG_PE_MODE_CLUSTER;
+        const uint32_t first = cl ? shmemg_d_cluster_ctarank() : 0u, stride = cl ? shmemg_d_cluster_nctarank() : 1u;
+        if (threadIdx.x == 0) {
+            if (!dma_busy(x)) {
+                // the engine's last stores were issued; they must have read their stages
+                // before the lean loop loads into them
+                asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+                shmemg_d_bulk_copy_thread(c, d, s, n, first, stride, ring, bars);
+            } else {
+                dma_enqueue(c, x, ring, 0, (uint64_t)d, (uint64_t)s, n, first, stride);
+                dma_drain(c, x, ring, 0);
+            }
+        }
+    } else {
+        shmemg_d_copy_group(g, d, s, n);
+    }
 }
 
 // A context moves a transfer in the background when the bulk engine is on and the bulk
@@ -228,7 +302,7 @@ __global__ void __launch_bounds__(INTERP_THREADS) k_interp(shmemg_device_ctx_t c
     __shared__ int s_wrc[2];
     int n_waits = 0;
     extern __shared__ __align__(128) uint8_t s_ring[];
-    __shared__ __align__(8) uint64_t s_bars[SHMEMG_BULK_STAGES];
+    __shared__ __align__(8) uint64_t s_bars[SHMEMG_BULK_STAGES];  // the lean blocking loop's mbarriers
     // the op list is staged through shared memory OP_BATCH records at a time (one
     // coalesced copy per batch instead of a dependent global load per op and thread)
     __shared__ __align__(16) shmemg_op_t s_ops[OP_BATCH];
@@ -239,21 +313,12 @@ __global__ void __launch_bounds__(INTERP_THREADS) k_interp(shmemg_device_ctx_t c
     // bulk ring, which then serves as each CTA's DSMEM window (free between ops: every
     // bulk copy has drained)
     __shared__ shmemg_cluster_state_t s_cs;
-    // explicit contexts: served by thread 32*k of the leader CTA (with the bulk ring only)
-    __shared__ __align__(16) CtxState s_ctx[SHMEMG_DEVICE_CTX_COUNT - 1];
-    const int my_ctx = (use_bulk && shmemg_d_pe_leader_cta(c) && (threadIdx.x & 31) == 0 && threadIdx.x >= 32 &&
-                        threadIdx.x < 32 * SHMEMG_DEVICE_CTX_COUNT)
-                           ? (int)(threadIdx.x >> 5)
-                           : 0;
-    uint8_t *ctx_ring = my_ctx ? s_ring + SHMEMG_BULK_SMEM + (size_t)(my_ctx - 1) * CTX_STAGES * CTX_CHUNK : nullptr;
-    if (my_ctx) {
-        CtxState &x = s_ctx[my_ctx - 1];
-        x.head = x.tail = 0;
-        x.off = x.ld = x.st = 0;
-        for (int k = 0; k < CTX_STAGES; k++)
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(shmemg_smem_u32(&x.bar[k])) : "memory");
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
+    // the bulk engine (thread 0 only; with the launch's ring): the default context's
+    // large copies and, in the PE's leader CTA, the explicit contexts' queues
+    __shared__ __align__(16) DmaState s_dma;
+    const bool dma = use_bulk && threadIdx.x == 0;
+    const bool ctx_home = use_bulk && shmemg_d_pe_leader_cta(c);  // this CTA serves the PE's contexts
+    if (dma) dma_init(s_dma);
     // (only when the launch really has clusters of cluster_dim CTAs: a launch without
     // them -- a profiler replaying it, say -- runs the shared team on the L2/HBM path and
     // never maps a peer CTA that does not exist)
@@ -294,7 +359,7 @@ __global__ void __launch_bounds__(INTERP_THREADS) k_interp(shmemg_device_ctx_t c
     __syncthreads();
     for (int k = 0; k < cnt; k++) {
         const int64_t i = base + k;
-        if (my_ctx) ctx_progress(s_ctx[my_ctx - 1], ctx_ring);  // background transfers advance
+        if (dma && dma_busy(s_dma)) dma_progress(s_dma, s_ring);  // background transfers advance
         const int act = s_act[k];
         if (act == 0 && !failed) continue;
         const shmemg_op_t o = s_ops[k];
@@ -315,20 +380,27 @@ __global__ void __launch_bounds__(INTERP_THREADS) k_interp(shmemg_device_ctx_t c
         const bool active =
             !warp || (threadIdx.x < 32 && (c.pe_mode != SHMEMG_PE_MODE_CLUSTER || shmemg_d_cluster_ctarank() == 0));
         const shmemg_group gw = warp ? shmemg_d_group_warp() : g;
+        if (staged(o)) {
+            // the ring becomes this CTA's DSMEM window: no background chunk may still be in
+            // it (every CTA of the cluster drains before the collective's entry barrier, so
+            // no peer writes into a window still in use)
+            if (dma) dma_drain(c, s_dma, s_ring, -1);
+            __syncthreads();
+        }
         switch (o.kind & SHMEMG_OP_KIND_MASK) {
         case SHMEMG_OP_PUT:
         case SHMEMG_OP_PUT_NBI:
             if (o.issuer == me && o.kind == SHMEMG_OP_PUT_NBI && o.sub != 0 &&
                 ctx_aligned(c, shmemg_d_addr(c, o.pe, o.dst), shmemg_d_addr(c, me, o.src), o.n, use_bulk)) {
-                if (my_ctx == o.sub)  // queued on its context, moved in the background
-                    ctx_enqueue(c, s_ctx[my_ctx - 1], ctx_ring, (uint64_t)shmemg_d_addr(c, o.pe, o.dst),
-                                (uint64_t)shmemg_d_addr(c, me, o.src), o.n);
+                if (dma && ctx_home)  // queued on its context, moved in the background
+                    dma_enqueue(c, s_dma, s_ring, o.sub, (uint64_t)shmemg_d_addr(c, o.pe, o.dst),
+                                (uint64_t)shmemg_d_addr(c, me, o.src), o.n, 0, 1);
             } else if (o.issuer == me) {
                 if (warp) {
                     if (active) shmemg_d_copy_group(gw, shmemg_d_addr(c, o.pe, o.dst), shmemg_d_addr(c, me, o.src), o.n);
                 } else {
                     pe_copy(c, g, shmemg_d_addr(c, o.pe, o.dst), shmemg_d_addr(c, me, o.src), o.n, use_bulk, s_ring,
-                            s_bars);
+                            s_dma, s_bars);
                     if (o.kind == SHMEMG_OP_PUT) shmemg_d_pe_sync(c);
                 }
             }
@@ -337,15 +409,15 @@ __global__ void __launch_bounds__(INTERP_THREADS) k_interp(shmemg_device_ctx_t c
         case SHMEMG_OP_GET_NBI:
             if (o.issuer == me && o.kind == SHMEMG_OP_GET_NBI && o.sub != 0 &&
                 ctx_aligned(c, shmemg_d_addr(c, me, o.dst), shmemg_d_addr(c, o.pe, o.src), o.n, use_bulk)) {
-                if (my_ctx == o.sub)
-                    ctx_enqueue(c, s_ctx[my_ctx - 1], ctx_ring, (uint64_t)shmemg_d_addr(c, me, o.dst),
-                                (uint64_t)shmemg_d_addr(c, o.pe, o.src), o.n);
+                if (dma && ctx_home)
+                    dma_enqueue(c, s_dma, s_ring, o.sub, (uint64_t)shmemg_d_addr(c, me, o.dst),
+                                (uint64_t)shmemg_d_addr(c, o.pe, o.src), o.n, 0, 1);
             } else if (o.issuer == me) {
                 if (warp) {
                     if (active) shmemg_d_copy_group(gw, shmemg_d_addr(c, me, o.dst), shmemg_d_addr(c, o.pe, o.src), o.n);
                 } else {
                     pe_copy(c, g, shmemg_d_addr(c, me, o.dst), shmemg_d_addr(c, o.pe, o.src), o.n, use_bulk, s_ring,
-                            s_bars);
+                            s_dma, s_bars);
                     if (o.kind == SHMEMG_OP_GET) shmemg_d_pe_sync(c);
                 }
             }
@@ -411,7 +483,7 @@ __global__ void __launch_bounds__(INTERP_THREADS) k_interp(shmemg_device_ctx_t c
         case SHMEMG_OP_QUIET:
         case SHMEMG_OP_FENCE:  // fence on a context completes it too (ordering by completion)
             if (o.issuer == me || o.issuer < 0) {
-                if (my_ctx && (o.sub == SHMEMG_CTX_ALL || o.sub == my_ctx)) ctx_drain(c, s_ctx[my_ctx - 1], ctx_ring);
+                if (dma && ctx_home && o.sub != 0) dma_drain(c, s_dma, s_ring, o.sub == SHMEMG_CTX_ALL ? -1 : o.sub);
                 shmemg_d_quiet_pe(c);
             }
             break;
@@ -462,7 +534,7 @@ __global__ void __launch_bounds__(INTERP_THREADS) k_interp(shmemg_device_ctx_t c
     }
     // every context's transfers complete before the PE ends (none may still read this
     // CTA's shared memory when it exits)
-    if (my_ctx) ctx_drain(c, s_ctx[my_ctx - 1], ctx_ring);
+    if (dma) dma_drain(c, s_dma, s_ring, -1);
     shmemg_d_quiet_pe(c);
     if (dsm) shmemg_d_cluster_end();  // no CTA leaves while a peer may still touch its shared memory
 }
@@ -539,12 +611,12 @@ extern "C" int shmemg_run_script(const shmemg_op_t *ops, int64_t nops, int64_t *
         const char *e = getenv("SHMEMG_BULK");
         bulk = (e && *e == '0') ? 0 : 1;
         if (bulk && cudaFuncSetAttribute((const void *)k_interp, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)(SHMEMG_BULK_SMEM + CTX_SMEM)) != cudaSuccess) {
+                                         (int)RING_SMEM) != cudaSuccess) {
             cudaGetLastError();
             bulk = 0;
         }
     }
     int use_bulk = bulk;
     void *args[] = {(void *)&c, (void *)&ops, (void *)&nops, (void *)&fetched, (void *)&use_bulk};
-    return launch_pe_grid((const void *)k_interp, args, use_bulk ? SHMEMG_BULK_SMEM + CTX_SMEM : 0, to_stream(stream));
+    return launch_pe_grid((const void *)k_interp, args, use_bulk ? RING_SMEM : 0, to_stream(stream));
 }

@@ -247,6 +247,61 @@ __global__ void __launch_bounds__(RED_THREADS) k_reduce(Red x) {
     }
 }
 
+// Integer sum / max / min of few vectors per member: G threads share a 16-byte vector,
+// each combining the members sub, sub + G, ... (integer combining is exact in any order),
+// the G partial results meet by warp shuffles, and the G threads store the result to every
+// G-th member.  A launch of few vectors keeps G times as many loads in flight and needs
+// P / (8G) dependent rounds instead of P / 8.  Requires P >= G.
+template <typename T, typename V, int OP, int G>
+__global__ void __launch_bounds__(RED_THREADS) k_reduce_split(Red x) {
+    constexpr int NL = sizeof(V) / sizeof(T);
+    const int pe0 = x.start + blockIdx.y * x.gstride;
+    const int sub = (int)(threadIdx.x % G);
+    const uint64_t per_cta = blockDim.x / G;
+    auto member = [&](int r, uint64_t off) {
+        return shmemg_ld_cg((const V *)(x.heap + (uint64_t)(pe0 + r * x.stride) * x.H + off));
+    };
+    auto comb = [&](V &a, const V &b) {
+#pragma unroll
+        for (int l = 0; l < NL; l++)
+            reinterpret_cast<T *>(&a)[l] = shmemg_comb<T>(reinterpret_cast<T *>(&a)[l], reinterpret_cast<const T *>(&b)[l], OP);
+    };
+    // warp-uniform loop: every lane runs every round (lanes past the end load vector 0 and
+    // store nothing), so the shuffles always see full warps
+    for (uint64_t vb = blockIdx.x * per_cta; vb < x.nvec; vb += gridDim.x * per_cta) {
+        const uint64_t vi = vb + threadIdx.x / G;
+        const bool act = vi < x.nvec;
+        const uint64_t off = x.src_off + (act ? vi : 0) * sizeof(V);
+        V acc = member(sub, off);
+        int r = sub + G;
+        for (; r + 7 * G < x.size; r += 8 * G) {  // eight members' loads in flight
+            V v[8];
+#pragma unroll
+            for (int u = 0; u < 8; u++) v[u] = member(r + u * G, off);
+#pragma unroll
+            for (int u = 0; u < 8; u++) comb(acc, v[u]);
+        }
+        for (; r < x.size; r += G) comb(acc, member(r, off));
+#pragma unroll
+        for (int m = G / 2; m > 0; m >>= 1) {
+            V o;
+            if constexpr (sizeof(T) == 8) {
+#pragma unroll
+                for (int l = 0; l < NL; l++)
+                    reinterpret_cast<long long *>(&o)[l] = __shfl_xor_sync(0xffffffffu, reinterpret_cast<long long *>(&acc)[l], m);
+            } else {
+#pragma unroll
+                for (int l = 0; l < NL; l++)
+                    reinterpret_cast<int *>(&o)[l] = __shfl_xor_sync(0xffffffffu, reinterpret_cast<int *>(&acc)[l], m);
+            }
+            comb(acc, o);
+        }
+        if (act)
+            for (int q = sub; q < x.size; q += G)
+                *(V *)(x.heap + (uint64_t)(pe0 + q * x.stride) * x.H + x.dst_off + vi * sizeof(V)) = acc;
+    }
+}
+
 // ------------------------------------------------------------------ single-thread ops
 template <typename T>
 __global__ void k_amo(T *addr, int kind, T v, T cond, T *fetched) {
@@ -373,6 +428,24 @@ static int launch_red_v(Red r, int ngroups, cudaStream_t s) {
     r.chunk_vec = (uint64_t)RED_THREADS * RED_U;
     r.nitems = (r.nvec + r.chunk_vec - 1) / r.chunk_vec;
     if (r.nitems == 0) return SHMEMG_SUCCESS;
+    if constexpr (std::is_integral<T>::value && sizeof(V) == 16) {
+        // integer teams with too few vectors to fill the GPU one thread each: several
+        // threads per vector (k_reduce_split)
+        const int G = r.size >= 32 ? 8 : r.size >= 8 ? 4 : 1;
+        const void *kf = G == 8 ? (const void *)k_reduce_split<T, V, OP, 8> : (const void *)k_reduce_split<T, V, OP, 4>;
+        if (G > 1) {
+            const uint64_t cap = (uint64_t)ctas_for(kf, RED_THREADS, 0);
+            const uint64_t ctas = (r.nvec * G + RED_THREADS - 1) / RED_THREADS;
+            // (measured: 4-5x faster up to 64 Ki vectors per member; once the one-per-thread
+            // form has a few hundred items its coalesced member loads win)
+            if (r.nitems * (uint64_t)ngroups * 8 < cap) {
+                dim3 grid((unsigned)balanced_grid(ctas, cap, ngroups), (unsigned)ngroups);
+                if (G == 8) k_reduce_split<T, V, OP, 8><<<grid, RED_THREADS, 0, s>>>(r);
+                else k_reduce_split<T, V, OP, 4><<<grid, RED_THREADS, 0, s>>>(r);
+                return cuda_rc(cudaGetLastError());
+            }
+        }
+    }
     const void *kfn = (const void *)k_reduce<T, V, OP>;
     dim3 grid((unsigned)balanced_grid(r.nitems, (uint64_t)ctas_for(kfn, RED_THREADS, 0), ngroups), (unsigned)ngroups);
     k_reduce<T, V, OP><<<grid, RED_THREADS, 0, s>>>(r);

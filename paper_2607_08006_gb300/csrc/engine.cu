@@ -447,7 +447,12 @@ static int launch_red_v(Red r, int ngroups, cudaStream_t s) {
         }
     }
     const void *kfn = (const void *)k_reduce<T, V, OP>;
-    dim3 grid((unsigned)balanced_grid(r.nitems, (uint64_t)ctas_for(kfn, RED_THREADS, 0), ngroups), (unsigned)ngroups);
+    const uint64_t cap = (uint64_t)ctas_for(kfn, RED_THREADS, 0);
+    if (r.nitems * (uint64_t)ngroups < cap) {  // too few items for the resident CTAs: one vector per thread
+        r.chunk_vec = RED_THREADS;
+        r.nitems = (r.nvec + r.chunk_vec - 1) / r.chunk_vec;
+    }
+    dim3 grid((unsigned)balanced_grid(r.nitems, cap, ngroups), (unsigned)ngroups);
     k_reduce<T, V, OP><<<grid, RED_THREADS, 0, s>>>(r);
     return cuda_rc(cudaGetLastError());
 }

@@ -22,9 +22,9 @@
 namespace shmemg {
 
 constexpr int B_THREADS = 256;
-constexpr int B_TREE_MAXB = 3;   // fp32 tree: 8 members' loads in flight per thread
-constexpr int B_QM_BF16 = 8, B_QM_E4M3 = 4;   // quantised: members loaded ahead
-constexpr int B_MIN_BLOCKS = 4;
+constexpr int B_TREE_MAXB = 4;   // fp32 tree: 16 members' loads in flight per thread
+constexpr int B_QM_BF16 = 8, B_QM_E4M3 = 8;   // quantised: members loaded ahead
+constexpr int B_MIN_BLOCKS = 3;  // 85 registers: 8 members' loads ahead without spills
 enum BKind { BK_F32 = 0, BK_I64 = 1, BK_BF16 = 2, BK_E4M3 = 3 };
 
 struct BTeam {

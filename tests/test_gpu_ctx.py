@@ -90,6 +90,64 @@ def test_context_overlaps_default_context_work(sg, heapf, orc):
     assert _run(sg, h, orc, init, ops) is None
 
 
+@pytest.mark.parametrize("mode,cd", [(0, 1), (1, 2)])
+def test_blocking_bulk_copies_behind_context_chunks(sg, heapf, orc, mode, cd):
+    """Large blocking puts and gets (the bulk engine's queue 0) issued while context
+    transfers are still in the ring: they join the queue behind the chunks in flight and
+    still complete before the op returns (the get reads what the put wrote)."""
+    npes, H = 4, 32 * MiB
+    h = heapf(npes, H, pe_mode=mode, cluster_dim=cd)
+    init = random_heap(npes, H, 63 + mode)
+    upload(h, init)
+    ops = []
+    for p in range(npes):
+        ops += [_rec(kind=W.OP_PUT_NBI, sub=1, pe=(p + 1) % npes, issuer=p, dst=16 * MiB, src=0, n=10 * MiB),
+                _rec(kind=W.OP_GET_NBI, sub=3, pe=(p + 3) % npes, issuer=p, dst=27 * MiB, src=MiB, n=2 * MiB)]
+    for p in range(npes):   # blocking bulk copies while the contexts' chunks are in flight
+        ops += [_rec(kind=W.OP_PUT, pe=(p + 2) % npes, issuer=p, dst=12 * MiB + MiB * p, src=11 * MiB, n=MiB),
+                _rec(kind=W.OP_GET, pe=(p + 2) % npes, issuer=p, dst=30 * MiB, src=12 * MiB + MiB * p, n=MiB)]
+    ops += [_rec(kind=W.OP_QUIET, sub=ALL, issuer=p) for p in range(npes)]
+    ops.append(_rec(kind=W.OP_BARRIER_ALL))
+    assert _run(sg, h, orc, init, ops) is None
+
+
+def test_context_chunks_drain_before_a_staged_cluster_collective(sg, heapf, orc):
+    """CTA PEs in clusters of 4: context transfers in flight when a shared-team collective
+    stages its data in the same shared-memory ring (its DSMEM window); the ring drains
+    first, and both the transfers and the collectives come out right."""
+    npes, H = 8, 8 * MiB
+    h = heapf(npes, H, pe_mode=0, cluster_dim=4)
+    init = random_heap(npes, H, 71)
+    upload(h, init)
+    ops = []
+    for p in range(npes):
+        ops.append(_rec(kind=W.OP_PUT_NBI, sub=2, pe=(p + 4) % npes, issuer=p, dst=4 * MiB, src=0, n=3 * MiB))
+    ops += [_rec(kind=W.OP_REDUCE, dtype=W.DT_INT64, sub=W.RED_SUM, team=1, dst=7 * MiB, src=3 * MiB + 4096, n=2048),
+            _rec(kind=W.OP_BCAST, team=1, pe=2, dst=7 * MiB + 65536, src=3 * MiB, n=8192),
+            _rec(kind=W.OP_FCOLLECT, team=1, dst=7 * MiB + 131072, src=3 * MiB + 16384, n=4096)]
+    ops += [_rec(kind=W.OP_QUIET, sub=2, issuer=p) for p in range(npes)]
+    ops.append(_rec(kind=W.OP_BARRIER_ALL))
+    ops = np.array(ops, dtype=W.OP_DTYPE)
+    dev = torch.from_numpy(ops.view(np.uint8).copy()).cuda()
+    sg.clear_status()
+    sg.run_script(dev, len(ops), None)
+    torch.cuda.synchronize()
+    assert sg.get_status()[0] == 0
+    # the oracle's form: each shared-team op once per cluster (explicit teams 1 + g)
+    eops = []
+    for o in ops:
+        if o["kind"] in W.COLLECTIVE_KINDS and o["kind"] != W.OP_BARRIER_ALL and o["team"] == 1:
+            for g in range(npes // 4):
+                e = o.copy()
+                e["team"] = 1 + g
+                eops.append(e)
+        else:
+            eops.append(o)
+    ref = orc.Heap(npes, H, init)
+    ref.run_script(np.array(eops, dtype=W.OP_DTYPE), teams=[(0, 1, npes)] + [(4 * g, 1, 4) for g in range(npes // 4)])
+    assert first_diff(download(h), ref.mem) is None
+
+
 @pytest.mark.parametrize("bad", [
     dict(kind=W.OP_PUT_NBI, sub=4, pe=1, issuer=0, dst=0, src=4096, n=64),     # no context 4
     dict(kind=W.OP_QUIET, sub=7, issuer=0),                                     # no context 7

@@ -306,8 +306,11 @@ __global__ void __launch_bounds__(INTERP_THREADS) k_interp(shmemg_device_ctx_t c
     // the op list is staged through shared memory OP_BATCH records at a time (one
     // coalesced copy per batch instead of a dependent global load per op and thread)
     __shared__ __align__(16) shmemg_op_t s_ops[OP_BATCH];
-    // per op of the batch, decoded once by warp 0: 0 = nothing for this PE, 1 = run, 2 = invalid
+    // per op of the batch, decoded once by warp 0: 0 = nothing for this PE, 1 = run, 2 = invalid;
+    // and the indices of the ops with a nonzero code, in order
     __shared__ uint8_t s_act[OP_BATCH];
+    __shared__ uint8_t s_list[OP_BATCH];
+    __shared__ int s_nact;
     // shared-team ops of a CTA-mode heap launched in clusters run inside the cluster: the
     // team barrier is the hardware cluster barrier, small collectives are staged in the
     // bulk ring, which then serves as each CTA's DSMEM window (free between ops: every
@@ -351,17 +354,43 @@ __global__ void __launch_bounds__(INTERP_THREADS) k_interp(shmemg_device_ctx_t c
     for (int q = threadIdx.x; q < cnt * 4; q += blockDim.x)
         reinterpret_cast<uint4 *>(s_ops)[q] = __ldcg(reinterpret_cast<const uint4 *>(ops + base) + q);
     __syncthreads();
-    // validity and participation once per op and CTA, not once per op and thread: a PE
-    // then passes the ops of other PEs in a few instructions
-    if (threadIdx.x < 32)
-        for (int k = (int)threadIdx.x; k < cnt; k += 32)
-            s_act[k] = !op_valid(c, s_ops[k]) ? 2 : op_involves(s_ops[k], me) ? 1 : 0;
+    // validity and participation once per op and CTA, not once per op and thread, and the
+    // batch's ops this PE takes part in as a compact list (in order): the PE walks only
+    // those, and the ops of other PEs cost it nothing
+    if (threadIdx.x < 32) {
+        const int lane = (int)threadIdx.x;
+        int nact = 0;
+        for (int k0 = 0; k0 < cnt; k0 += 32) {
+            const int k = k0 + lane;
+            int a = 0;
+            if (k < cnt) {
+                a = !op_valid(c, s_ops[k]) ? 2 : op_involves(s_ops[k], me) ? 1 : 0;
+                s_act[k] = (uint8_t)a;
+            }
+            const unsigned m = __ballot_sync(0xffffffffu, a != 0);
+            if (a != 0) s_list[nact + __popc(m & ((1u << lane) - 1u))] = (uint8_t)k;
+            nact += __popc(m);
+        }
+        if (lane == 0) s_nact = nact;
+    }
     __syncthreads();
-    for (int k = 0; k < cnt; k++) {
+    if (dma && dma_busy(s_dma)) dma_progress(s_dma, s_ring);  // background transfers advance
+    const int nact = s_nact;
+    // the PE's ops in order; once failed (only in a clustered CTA-mode launch) every
+    // remaining op of the script, for its cluster barriers
+    for (int qi = 0, k_next = 0;;) {
+        int k;
+        if (!failed) {
+            if (qi >= nact) break;
+            k = s_list[qi++];
+        } else {
+            if (!dsm || k_next >= cnt) break;
+            k = k_next;
+        }
+        k_next = k + 1;
         const int64_t i = base + k;
         if (dma && dma_busy(s_dma)) dma_progress(s_dma, s_ring);  // background transfers advance
         const int act = s_act[k];
-        if (act == 0 && !failed) continue;
         const shmemg_op_t o = s_ops[k];
         int rc = SHMEMG_SUCCESS;
         if (failed) {  // only in a clustered CTA-mode launch: walk on, through the barriers

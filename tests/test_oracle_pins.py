@@ -866,6 +866,15 @@ def test_staged_requests_by_kind(orc):
     # one member: its own payload
     h, got = run(req(kind=16, dtype=W.DT_FLOAT, fmt=W.FMT_F32, pe=4, issuer=1, n=n))
     assert got == orc.checksum32(W.serve_payload_words(0x1234567, 4, 0, n).view(np.uint8))
+    # int64 in place over PEs 1..2, n = 50: word pairs as little-endian int64, summed with
+    # two's-complement wraparound
+    n = 50
+    h, got = run(req(kind=16, dtype=W.DT_INT64, fmt=0, pe=1, issuer=2, n=n))
+    x = [W.serve_payload_words(0x1234567, p, 0, 2 * n).view(np.int64) for p in (1, 2)]
+    with np.errstate(over="ignore"):
+        want = (x[0] + x[1]).astype(np.int64)
+    assert got == orc.checksum32(want.view(np.uint8))
+    assert np.array_equal(h.view(2, R, n, np.int64), want)
     # bf16 over PEs 0..1, n = 260 (three blocks): codes at R + 1040, scales at R + 1040 + 528
     n = 260
     h, got = run(req(kind=16, dtype=W.DT_FLOAT, fmt=W.FMT_BF16, pe=0, issuer=2, n=n))

@@ -225,3 +225,51 @@ def test_staged_admission_refuses_regions_beyond_the_arena(sg, heapf):
     got = _by_ticket(_drain(sg, srv, len(bad)))
     srv.stop()
     assert list(got["status"]) == [sg.ERR_OUT_OF_HEAP, sg.ERR_OUT_OF_HEAP, sg.ERR_INVALID_ARG, 0]
+
+
+def test_staged_ragged_and_degenerate_requests(sg, heapf, orc):
+    """Staged requests at ragged and degenerate sizes: reductions of 4..8188 elements (a
+    ragged last tile, a ragged last 128-element block for bf16 scales, one-member teams),
+    puts and gets of 8 B and of one RMA tile plus 8 B, self puts, alltoalls of 16 B and of
+    one chunk plus 16 B per pair with teams of 1-3; each result alone = plain = oracle."""
+    npes = 8
+    lay = W.serve_layout_staged(arena_bytes=2 << 20, amo_words=256)
+    h = heapf(npes, lay.H)
+    init = np.zeros(npes * lay.H, np.uint8)
+    rows = []
+    for n in (4, 12, 20, 124, 132, 8188, 8196):
+        for fmt, dt in ((W.FMT_F32, W.DT_FLOAT), (W.FMT_BF16, W.DT_FLOAT), (0, W.DT_INT64)):
+            for P in (1, 3):
+                rows.append(dict(kind=16, dtype=dt, fmt=fmt, pe=npes - P, issuer=P, n=n))
+    for n in (8, 24, (64 << 10) + 8):
+        rows += [dict(kind=1, pe=2, issuer=5, n=n), dict(kind=2, pe=6, issuer=1, n=n), dict(kind=1, pe=3, issuer=3, n=n)]
+    for m in (16, 48, (32 << 10) + 16):
+        for P in (1, 2, 3):
+            rows.append(dict(kind=15, pe=1, issuer=P, n=m))
+    reqs = np.zeros(len(rows), W.REQ_DTYPE)
+    for i, (r, kw) in enumerate(zip(reqs, rows)):
+        r["flags"] = 1
+        r["word"] = W.cb64(77, i)
+        for k, v in kw.items():
+            r[k] = v
+    cfg = _cfg(sg, lay)
+    stream = torch.cuda.Stream()
+    upload(h, init)
+    srv = sg.Server(cfg, stream)
+    alone = np.zeros(len(reqs), sg.COMPLETION_DTYPE)
+    for i in range(len(reqs)):
+        srv.feed(reqs[i:i + 1], np.zeros(1, np.uint64))
+        alone[i] = _drain(sg, srv, 1)[0]
+    srv.stop()
+    assert np.all(alone["status"] == 0), [(rows[i], int(alone["status"][i])) for i in np.nonzero(alone["status"])[0][:5]]
+    recs = torch.zeros(len(reqs) * sg.COMPLETION_DTYPE.itemsize, dtype=torch.uint8).pin_memory()
+    sg.plain_feed(reqs, np.zeros(len(reqs), np.uint64), cfg, recs.data_ptr(), stream)
+    stream.synchronize()
+    plain = np.frombuffer(recs.numpy().tobytes(), sg.COMPLETION_DTYPE)
+    assert np.all(plain["status"] == 0)
+    assert np.array_equal(plain["result"], alone["result"])
+    ref = orc.Heap(npes, lay.H, init)
+    want = np.array([orc.serve_request(ref, r, lay.amo_offset, lay.amo_words, lay.arena_offset, W.serve_payload_words)
+                     & (2**64 - 1) for r in reqs], dtype=np.uint64)
+    bad = np.nonzero(alone["result"] != want)[0]
+    assert len(bad) == 0, [rows[i] for i in bad[:8]]

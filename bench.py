@@ -1239,7 +1239,7 @@ def run_serve(torch, sg, nreq=1 << 16, rates=None, npes=512, arena=32 << 20):
 
 
 # ----------------------------------------------------------------------------- profiling cases
-PROFILE_CASES = ("interp_ring", "interp_ops", "reduce", "reduce_mid", "reduce_f32", "broadcast", "alltoall", "amo", "amo_l2", "amo_plain", "amo_combine", "amo_combine_zipf", "batch_bf16", "batch_e4m3", "batch_e4m3_teams", "batch_bf16_teams", "qsum",
+PROFILE_CASES = ("interp_ring", "interp_ops", "reduce", "reduce_mid", "reduce_big", "reduce_f32", "broadcast", "alltoall", "amo", "amo_l2", "amo_plain", "amo_combine", "amo_combine_zipf", "batch_bf16", "batch_e4m3", "batch_e4m3_teams", "batch_bf16_teams", "qsum",
                  "pingpong_cluster", "cluster_coll", "halo", "halo_plain")
 
 
@@ -1275,13 +1275,14 @@ def run_profile_case(name, launches=4):
         dev = torch.from_numpy(ops.view(np.uint8).copy()).cuda()
         for _ in range(launches):
             sg.run_script(dev, 641, None, s)
-    elif name == "reduce_mid":     # 64 PEs, int32 sum of 1 Mi elements (the split form: 8 threads per vector)
-        n = 1 << 20
+    elif name in ("reduce_mid", "reduce_big"):  # 64 PEs, int32 sum: 1 Mi elements (4 MiB per member,
+        # the bulk ring k_reduce_bulk) or 8 Mi (32 MiB per member, the register form k_reduce)
+        n = 1 << 20 if name == "reduce_mid" else 8 << 20
         heap = sg.Heap(64, 8 * n)
         heap.partitions().random_(0, 255)
         for _ in range(launches):
             sg.reduce(sg.TEAM_WORLD, heap.base + 4 * n, heap.base, n, sg.INT32, sg.SUM, s)
-    elif name in ("reduce", "reduce_f32"):  # 64 PEs, 1 Mi elements
+    elif name in ("reduce", "reduce_f32"):  # 64 PEs, 1 Mi elements (int64: the bulk ring)
         n = 1 << 20
         heap = sg.Heap(64, 16 * n)
         heap.partitions().random_(0, 255)

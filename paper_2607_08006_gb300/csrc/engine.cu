@@ -10,8 +10,11 @@
 // from every member, combines, and writes the result to every member.
 #include <cuda_runtime.h>
 
+#include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <type_traits>
+#include <unordered_map>
 
 #include "internal.h"
 
@@ -234,6 +237,7 @@ struct Red {
     uint64_t nvec;        // vectors (V) per member
     uint64_t chunk_vec;
     uint64_t nitems;
+    uint32_t rb_chunk, rb_stages;  // k_reduce_bulk: bytes per member per chunk, ring stages
 };
 
 template <typename T, typename V, int OP>
@@ -299,6 +303,123 @@ __global__ void __launch_bounds__(RED_THREADS) k_reduce_split(Red x) {
         if (act)
             for (int q = sub; q < x.size; q += G)
                 *(V *)(x.heap + (uint64_t)(pe0 + q * x.stride) * x.H + x.dst_off + vi * sizeof(V)) = acc;
+    }
+}
+
+// Integer sum / max / min over many vectors per member, one CTA per SM: the CTA streams
+// its chunks of the members' slices (x.rb_chunk bytes of each member per chunk) through an
+// x.rb_stages-deep shared-memory ring.  The lanes of warp 0 issue the chunk's P bulk loads
+// (one per member, all completing on the stage's mbarrier); the threads combine a stage
+// column by column (a column is one 16-byte vector; the members are split over `nparts`
+// thread groups whose partial results meet in shared memory), and each group stores the
+// result to its share of the members.  The loads of later chunks are in flight while
+// earlier chunks are combined and stored, so reads and writes overlap from the first chunk
+// on, which the one-vector-per-thread form does not do at a few chunks per CTA.
+//
+// Measured on GB300 (see rb_shape): a bulk copy costs the SM's copy engine about 65-70
+// cycles whatever its size below a few KiB, so the per-member pieces must be >= 1 KiB to
+// keep the engine under its limit at the HBM rate; three stages of P x 1 KiB fill the
+// 192 KiB ring at P = 64.  Teams of 48..64 members with 128 KiB .. 16 MiB per member take
+// the ring: at 64 members it measured 1.03-1.4x the register form from 128 KiB to 8 MiB per
+// member, equal at 16 MiB, and from 1% faster to 3% slower above (int64 max the slowest).  Smaller teams with wider pieces measured slower than the register form above
+// 512 KiB per member; larger teams (512 B pieces) are bound by the copy engine.
+constexpr int RB_THREADS = 256;
+constexpr int RB_MAX_STAGES = 4;
+constexpr uint32_t RB_RING = 192u << 10;
+constexpr uint32_t RB_SMEM = RB_RING + 2 * RB_THREADS * 16;
+constexpr uint64_t RB_MAX_BYTES = 16ull << 20;  // per member
+
+// bulk load of `bytes` into shared memory, completing on `bar` (whose expected byte count
+// the caller has already raised)
+__device__ __forceinline__ void rb_load(void *smem, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     shmemg_smem_u32(smem)),
+                 "l"(src), "r"(bytes), "r"(shmemg_smem_u32(bar))
+                 : "memory");
+}
+
+template <typename T, typename V, int OP>
+__global__ void __launch_bounds__(RB_THREADS, 1) k_reduce_bulk(Red x, uint8_t *state, uint64_t timeout_ns) {
+    extern __shared__ __align__(128) uint8_t rb[];
+    __shared__ __align__(8) uint64_t bars[RB_MAX_STAGES];
+    constexpr int NL = sizeof(V) / sizeof(T);
+    const int P = x.size;
+    const int pe0 = x.start + blockIdx.y * x.gstride;
+    const uint32_t C = x.rb_chunk, S = x.rb_stages, ncol = C / 16, nparts = RB_THREADS / ncol;
+    const uint64_t SB = (uint64_t)P * C;  // stage bytes
+    const uint32_t col = threadIdx.x % ncol, part = threadIdx.x / ncol, lane = threadIdx.x & 31;
+    const uint64_t bytes = x.nvec * sizeof(V);  // per member
+    const uint64_t nchunks = (bytes + C - 1) / C;
+    if (nchunks <= blockIdx.x) return;  // (uniform over the CTA)
+    const uint64_t count = (nchunks - blockIdx.x + gridDim.x - 1) / gridDim.x;
+    V *partial = (V *)(rb + RB_RING);
+    auto chunk_bytes = [&](uint64_t c) { return (uint32_t)(bytes - c * C < C ? bytes - c * C : C); };
+    auto issue = [&](uint64_t j) {  // warp 0: chunk j's member loads into stage j % S
+        const uint64_t c = blockIdx.x + j * gridDim.x;
+        const uint32_t b = chunk_bytes(c), s = (uint32_t)(j % S);
+        uint8_t *stage = rb + s * SB;
+        if (lane == 0)
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(shmemg_smem_u32(&bars[s])),
+                         "r"(b * (uint32_t)P)
+                         : "memory");
+        __syncwarp();
+        for (int r = (int)lane; r < P; r += 32)
+            rb_load(stage + (uint64_t)r * C, x.heap + (uint64_t)(pe0 + r * x.stride) * x.H + x.src_off + c * C, b,
+                    &bars[s]);
+    };
+    auto comb = [&](V &a, const V &b) {
+#pragma unroll
+        for (int l = 0; l < NL; l++)
+            reinterpret_cast<T *>(&a)[l] = shmemg_comb<T>(reinterpret_cast<T *>(&a)[l], reinterpret_cast<const T *>(&b)[l], OP);
+    };
+    if (threadIdx.x == 0) {
+        for (uint32_t s = 0; s < S; s++)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(shmemg_smem_u32(&bars[s])) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.global;" ::: "memory");
+    }
+    __syncthreads();
+    if (threadIdx.x < 32)
+        for (uint64_t j = 0; j < count && j < S; j++) issue(j);
+    for (uint64_t j = 0; j < count; j++) {
+        const uint32_t s = (uint32_t)(j % S);
+        const bool ok = shmemg_mbar_wait(&bars[s], (uint32_t)((j / S) & 1), timeout_ns);
+        const uint64_t c = blockIdx.x + j * gridDim.x;
+        const uint32_t nc = chunk_bytes(c) / 16;
+        V *pb = partial + (j & 1) * RB_THREADS;  // (double-buffered: chunk j + 2 writes after barrier j + 1)
+        if (ok && col < nc) {
+            const uint8_t *stage = rb + s * SB + (uint64_t)col * 16;
+            V acc = *(const V *)(stage + (uint64_t)part * C);
+            int r = (int)(part + nparts);
+            for (; r + 3 * (int)nparts < P; r += 4 * (int)nparts) {
+                V v[4];
+#pragma unroll
+                for (int u = 0; u < 4; u++) v[u] = *(const V *)(stage + (uint64_t)(r + u * (int)nparts) * C);
+#pragma unroll
+                for (int u = 0; u < 4; u++) comb(acc, v[u]);
+            }
+            for (; r < P; r += (int)nparts) comb(acc, *(const V *)(stage + (uint64_t)r * C));
+            pb[threadIdx.x] = acc;
+        }
+        if (__syncthreads_or(!ok)) {  // a stage never landed: every thread stops here
+            if (threadIdx.x == 0) {
+                // no load of the ring may still be writing shared memory when the CTA exits
+                const bool drained = shmemg_bulk_drain_loads(bars, S, j, count, timeout_ns);
+                int *st = (int *)(state + SHMEMG_STATUS_OFF);
+                if (atomicCAS(st, 0, SHMEMG_ERR_TIMEOUT) == 0)
+                    *(volatile int64_t *)(state + SHMEMG_STATUS_OFF + 8) = drained ? -3 : -4;
+            }
+            break;
+        }
+        // every thread has read stage s: warp 0 refills it while the groups store chunk j
+        if (threadIdx.x < 32 && j + S < count) issue(j + S);
+        if (col < nc) {
+            V acc = pb[col];
+            for (uint32_t q = 1; q < nparts; q++) comb(acc, pb[q * ncol + col]);
+            const uint64_t doff = x.dst_off + c * C + (uint64_t)col * 16;
+            for (int r = (int)part; r < P; r += (int)nparts)
+                *(V *)(x.heap + (uint64_t)(pe0 + r * x.stride) * x.H + doff) = acc;
+        }
     }
 }
 
@@ -422,6 +543,38 @@ static int rma(void *dst, const void *src, uint64_t n, int dst_pe, int src_pe, v
     return launch_xfer(x, 1, doff | soff, to_stream(stream));
 }
 
+// bytes per member from which integer reductions take the bulk ring (SHMEMG_RED_BULK_MIN
+// overrides; a value above any partition turns the ring off)
+static uint64_t red_bulk_min() {
+    static uint64_t v = [] {
+        const char *e = getenv("SHMEMG_RED_BULK_MIN");
+        return (e && *e) ? (uint64_t)strtoull(e, nullptr, 10) : (uint64_t)(128u << 10);
+    }();
+    return v;
+}
+
+// ring shape for a P-member team: 1 KiB per member per chunk, three stages; only teams of
+// 48..64 members (the measured range where the ring beats the register form; see
+// k_reduce_bulk)
+static bool rb_shape(int P, uint32_t *chunk, uint32_t *stages) {
+    *chunk = 1024;
+    *stages = 3;
+    return P >= 48 && P <= 64;
+}
+
+// the ring's shared memory granted to kernel `k` (once per instantiation)
+static bool red_bulk_ready(const void *k) {
+    static std::mutex mu;
+    static std::unordered_map<const void *, bool> ok;
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = ok.find(k);
+    if (it != ok.end()) return it->second;
+    const bool g = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, RB_SMEM) == cudaSuccess;
+    if (!g) cudaGetLastError();
+    ok[k] = g;
+    return g;
+}
+
 template <typename V, typename T, int OP>
 static int launch_red_v(Red r, int ngroups, cudaStream_t s) {
     r.nvec /= (sizeof(V) / sizeof(T));
@@ -429,6 +582,16 @@ static int launch_red_v(Red r, int ngroups, cudaStream_t s) {
     r.nitems = (r.nvec + r.chunk_vec - 1) / r.chunk_vec;
     if (r.nitems == 0) return SHMEMG_SUCCESS;
     if constexpr (std::is_integral<T>::value && sizeof(V) == 16) {
+        // integer teams of 48..64 members with 128 KiB .. 16 MiB per member: the bulk ring
+        // (above 16 MiB both forms run at the HBM rate and the register form is the steadier)
+        if ((r.H & 15) == 0 && r.nvec * sizeof(V) >= red_bulk_min() && r.nvec * sizeof(V) <= RB_MAX_BYTES &&
+            rb_shape(r.size, &r.rb_chunk, &r.rb_stages) && red_bulk_ready((const void *)k_reduce_bulk<T, V, OP>)) {
+            const uint64_t C = r.rb_chunk, nchunks = (r.nvec * sizeof(V) + C - 1) / C;
+            const uint64_t cap = (uint64_t)ctas_for((const void *)k_reduce_bulk<T, V, OP>, RB_THREADS, RB_SMEM);
+            dim3 grid((unsigned)balanced_grid(nchunks, cap, ngroups), (unsigned)ngroups);
+            k_reduce_bulk<T, V, OP><<<grid, RB_THREADS, RB_SMEM, s>>>(r, st().base, st().timeout_ns);
+            return cuda_rc(cudaGetLastError());
+        }
         // integer teams with too few vectors to fill the GPU one thread each: several
         // threads per vector (k_reduce_split)
         const int G = r.size >= 32 ? 8 : r.size >= 8 ? 4 : 1;

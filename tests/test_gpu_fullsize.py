@@ -65,10 +65,13 @@ def test_ring_256MiB(sg, orc, step, kind):
         assert np.array_equal(b[p].reshape(-1), ref.pe(p)[w:]), p
 
 
-@pytest.mark.parametrize("dt,op", [("int32", "sum"), ("int64", "sum"), ("int32", "max"), ("int64", "max")])
-def test_reduce_16Mi(sg, orc, step, dt, op):
+@pytest.mark.parametrize("dt,op,n", [("int32", "sum", 1 << 24), ("int64", "sum", 1 << 24), ("int32", "max", 1 << 24),
+                                     ("int64", "max", 1 << 24), ("int32", "sum", 1 << 20), ("int64", "max", 1 << 20),
+                                     ("int32", "max", 1 << 22)])
+def test_reduce_full_points(sg, orc, step, dt, op, n):
+    """The largest reduce points (16 Mi elements: the one-vector-per-thread kernel) and the
+    1 Mi / 4 Mi points the bulk ring runs (4-16 MiB per member)."""
     bench, g, s = step
-    n = 1 << 24
     _run(bench, g, s, f"reduce_{dt}_{op}", "reduce", n)
     parts = g.heap.partitions()
     es = 4 if dt == "int32" else 8

@@ -206,7 +206,9 @@ int shmemg_query_capabilities(shmemg_team_t team, shmemg_caps_t *out);
  * For SHMEMG_ERR_TIMEOUT of a bulk (TMA) ring: -2 a device-initiated copy, -3 a
  * host-issued bulk transfer or an explicit context's queue, each after the loads still
  * in flight have landed; -4 a load that did not land even then (the launch's results are
- * void and the ring was not used again).  Synchronises the device. */
+ * void and the ring was not used again); -5 a context agent that saw no post, no progress
+ * of its PE and no end of the script for 8 x the wait timeout and left (a quiet on its
+ * contexts then times out with the op index as detail).  Synchronises the device. */
 int shmemg_get_status(int *code, int64_t *detail);
 int shmemg_clear_status(void *stream);
 const char *shmemg_strerror(int code);
@@ -318,9 +320,13 @@ enum {
  * default device context, 1..SHMEMG_DEVICE_CTX_COUNT-1 explicit contexts; `sub` of
  * quiet / fence picks the context it completes, or SHMEMG_CTX_ALL.  Each explicit
  * context is an independent completion domain: its non-blocking transfers move in the
- * background (TMA bulk copies advanced at every later op of the PE) and only quiet or
- * fence on that context -- or on all -- waits for them; barriers and collectives quiet
- * the default context only.  Every context is complete when the script ends.
+ * background and only quiet or fence on that context -- or on all -- waits for them;
+ * barriers and collectives quiet the default context only.  Every context is complete
+ * when the script ends.  With CTA PEs and no hardware clusters, when the GPU holds two
+ * CTAs per PE, shmemg_run_script launches a context agent per PE (a second CTA whose TMA
+ * bulk copies run while the PE goes on; set SHMEMG_CTX_AGENTS=0 to turn the agents off);
+ * otherwise the PE's own bulk engine advances them at every later op of the PE.  One
+ * script runs at a time (concurrent scripts share the agents' mailboxes).
  * Transfers whose addresses or length are not 16-byte multiples (or with the bulk
  * engine off) complete at once, as on the default context. */
 #define SHMEMG_DEVICE_CTX_COUNT 4

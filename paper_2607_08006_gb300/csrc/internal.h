@@ -54,9 +54,11 @@ int ctas_for(const void *kernel, int threads, size_t smem);
 uint64_t balanced_grid(uint64_t nitems, uint64_t cap, int ngroups = 1);
 
 // cooperative launch with one CTA per PE (pe_mode CTA) or one cluster of cluster_dim CTAs
-// per PE, `threads` per CTA (0: the interpreter's count); SHMEMG_ERR_UNSUPPORTED if the
-// GPU cannot hold every PE at once
-int launch_pe_grid(const void *kernel, void **args, size_t smem, cudaStream_t s, int threads = 0);
+// per PE, `threads` per CTA (0: the interpreter's count), the grid grid_mult times that
+// (the interpreter's context agents: CTA npes + p serves PE p); SHMEMG_ERR_UNSUPPORTED if
+// the GPU cannot hold every CTA at once
+int launch_pe_grid(const void *kernel, void **args, size_t smem, cudaStream_t s, int threads = 0, int grid_mult = 1);
+int interp_threads();
 
 // splitmix64 (Steele, Lea, Flood, OOPSLA 2014): first output of the stream started at
 // state seed ^ i -- the counter-based draw of the AMO stream and of staged payloads.

@@ -30,8 +30,9 @@ constexpr int OP_BATCH = 64;  // op records staged in shared memory at a time
 //  * queues 1..3, the explicit contexts (Sec. 6.2: contexts as independent ordering and
 //    completion domains, an optional resource-limited feature beside the default device
 //    context): a context's put_nbi / get_nbi is queued in the PE's leader CTA and moved
-//    in the background -- the engine advances at every op boundary without waiting --
-//    and only quiet / fence on that context (or on all) waits for it.
+//    in the background -- the engine advances at every op boundary -- and only quiet /
+//    fence on that context (or on all) waits for it.  Where the GPU holds a second CTA
+//    per PE, the contexts run on that CTA instead (the context agents below).
 // A context alone thus keeps the whole ring in flight, like a blocking copy.  Chunk j of
 // the ring uses stage j % RING_STAGES and completes phase (j / RING_STAGES) & 1 of its
 // mbarrier; a stage is reloaded only after the store of its previous chunk has read it.
@@ -220,6 +221,133 @@ __device__ __forceinline__ bool ctx_aligned(const shmemg_device_ctx_t &, const v
     return use_bulk && n > 0 && (((uint64_t)d | (uint64_t)s | n) & 15) == 0;
 }
 
+// ---------------------------------------------------------------- context agents
+// A context's engine on the PE's own CTA advances only between the PE's ops and stalls the
+// PE whenever the SM's copy engine is busy (its stores are read out at the SM's store
+// rate, and a reload or a new bulk instruction waits for them), so it hands back in stalls
+// what it gains in overlap.  When the GPU holds two CTAs per PE (CTA PEs without hardware
+// clusters), each PE gets a context agent instead: a second CTA, on another SM with its
+// own copy engine, whose thread 0 runs the engine above for the PE's contexts 1..3.  The
+// PE posts a context's transfer to its mailbox (the descriptor, then a release of the
+// context's posted count) and goes on at once; the agent takes it (acquire), moves it
+// through its own ring, and once a context's transfers are all written (bulk wait_group
+// 0, then the async-proxy fence) releases the context's done count.  Quiet / fence on a
+// context waits (bounded) until done reaches what the PE has posted.  The PE releases
+// `exit` with the launch's epoch when its script ends; the agent leaves when every
+// transfer is done and exit is set.
+constexpr int AGENT_MAX_PES = 128;
+// Counts are tagged with the launch's epoch in their upper 32 bits, so a mailbox needs no
+// reset between launches: a count left by an earlier launch reads as 0.
+struct CtxMailbox {
+    DmaXfer q[NQ - 1][CTX_QCAP];  // contexts 1..NQ-1; slot = count % CTX_QCAP
+    uint64_t posted[NQ - 1];      // epoch:count, released by the PE
+    uint64_t done[NQ - 1];        // epoch:count, released by the agent
+    uint32_t exit;                // the launch's epoch, released by the PE at its end
+    uint32_t beat;                // the PE's op batch, written as it walks (the agent's sign of life)
+};
+__device__ CtxMailbox g_mbox[AGENT_MAX_PES];
+// The epoch of a launch with agents is g_agent_epoch + 1 (never 0): every CTA reads it at
+// its start, and the last CTA to finish stores it back, so the next launch -- stream
+// ordered after this one, a graph replay included -- uses the next epoch.
+__device__ uint32_t g_agent_epoch, g_agent_exits;
+
+__device__ __forceinline__ uint32_t mb_count(const uint64_t *p, uint32_t epoch) {
+    const uint64_t v = shmemg_d_ld_acquire_u64(p);
+    return (uint32_t)(v >> 32) == epoch ? (uint32_t)v : 0u;
+}
+__device__ __forceinline__ void mb_set(uint64_t *p, uint32_t epoch, uint32_t n) {
+    shmemg_d_st_release_u64(p, ((uint64_t)epoch << 32) | n);
+}
+
+// The agent (thread 0 of the PE's agent CTA; the CTA's other threads have left).  Waits
+// are bounded: a load that never lands ends in dma_drain's timeout (status set, the
+// transfers abandoned and still counted done, so no quiet waits forever), and an agent
+// that sees no post, no new op batch of its PE and no exit flag for 8 x timeout_ns (longer
+// than any bounded wait of the PE) records a timeout (detail -5) and leaves; a later quiet
+// on it then times out in the PE.
+__device__ __noinline__ void ctx_agent(const shmemg_device_ctx_t &c, CtxMailbox *mb, uint32_t epoch, DmaState &x,
+                                       uint8_t *ring) {
+    dma_init(x);
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+    uint32_t taken[NQ - 1] = {}, reported[NQ - 1] = {}, beat = 0, nap = 128;
+    uint64_t idle_since = 0;
+    for (;;) {
+        bool got = false;
+        for (int k = 0; k < NQ - 1; k++) {
+            const uint32_t p = mb_count(&mb->posted[k], epoch);
+            for (; taken[k] != p; taken[k]++) {
+                const DmaXfer d = mb->q[k][taken[k] % CTX_QCAP];
+                dma_enqueue(c, x, ring, k + 1, d.dst, d.src, d.n, 0, 1);  // (drains queue k + 1 if it is full)
+                got = true;
+            }
+        }
+        if (dma_busy(x)) dma_drain(c, x, ring, -1);  // every queued transfer written (or abandoned)
+        bool pending = false;
+        for (int k = 0; k < NQ - 1; k++) pending |= reported[k] != taken[k];
+        if (pending) {  // dma_drain ended with wait_group 0 and the async-proxy fence
+            for (int k = 0; k < NQ - 1; k++)
+                if (reported[k] != taken[k]) mb_set(&mb->done[k], epoch, reported[k] = taken[k]);
+            idle_since = 0;
+            nap = 128;
+            continue;
+        }
+        if (got) {
+            nap = 128;
+            continue;
+        }
+        if (shmemg_d_ld_acquire_u32(&mb->exit) == epoch) break;
+        const uint64_t now = shmemg_d_globaltimer();
+        const uint32_t b = *(volatile uint32_t *)&mb->beat;
+        if (idle_since == 0 || b != beat) idle_since = now, beat = b;
+        else if (now - idle_since > 8 * c.timeout_ns) {
+            shmemg_d_set_status(c, SHMEMG_ERR_TIMEOUT, -5);
+            break;
+        }
+        __nanosleep(nap);  // idle: poll less often (a post, or the end, waits at most ~1 us)
+        if (nap < 1024) nap *= 2;
+    }
+}
+
+// The PE's side (thread 0): post a context transfer; false if the mailbox stayed full
+// for timeout_ns (status set; the transfer is not made)
+__device__ __noinline__ bool agent_post(const shmemg_device_ctx_t &c, CtxMailbox *mb, uint32_t epoch, uint32_t *posted,
+                                        int k, uint64_t dst, uint64_t src, uint64_t n, int64_t op_index) {
+    const int q = k - 1;
+    uint64_t t0 = 0;
+    while (posted[q] - mb_count(&mb->done[q], epoch) >= CTX_QCAP) {
+        const uint64_t now = shmemg_d_globaltimer();
+        if (t0 == 0) t0 = now;
+        else if (now - t0 > c.timeout_ns) {
+            shmemg_d_set_status(c, SHMEMG_ERR_TIMEOUT, op_index);
+            return false;
+        }
+        __nanosleep(128);
+    }
+    mb->q[q][posted[q] % CTX_QCAP] = {dst, src, n, 0, 1};
+    __threadfence();  // the descriptor, and the PE's writes before this op, before the count
+    mb_set(&mb->posted[q], epoch, ++posted[q]);
+    return true;
+}
+
+// The PE's side (thread 0): wait until context k (k = SHMEMG_CTX_ALL: every context) has
+// written everything posted to it; bounded by timeout_ns (status set)
+__device__ __noinline__ void agent_quiet(const shmemg_device_ctx_t &c, CtxMailbox *mb, uint32_t epoch,
+                                         const uint32_t *posted, int k, int64_t op_index) {
+    uint64_t t0 = 0;
+    for (int q = 0; q < NQ - 1; q++) {
+        if (k != SHMEMG_CTX_ALL && q != k - 1) continue;
+        while (mb_count(&mb->done[q], epoch) != posted[q]) {
+            const uint64_t now = shmemg_d_globaltimer();
+            if (t0 == 0) t0 = now;
+            else if (now - t0 > c.timeout_ns) {
+                shmemg_d_set_status(c, SHMEMG_ERR_TIMEOUT, op_index);
+                return;
+            }
+            __nanosleep(64);
+        }
+    }
+}
+
 // Device-side check of one op (the same rules as the host's argument checks): PEs in
 // range, byte ranges inside a partition, AMO alignment, live teams.  Every thread of
 // every PE evaluates it on the same record, so the verdict is uniform.
@@ -294,8 +422,10 @@ __device__ __forceinline__ bool op_involves(const shmemg_op_t &o, int me) {
     }
 }
 
+// with_agents: the launch has 2 x npes CTAs, CTA npes + p being PE p's context agent
 __global__ void __launch_bounds__(INTERP_THREADS) k_interp(shmemg_device_ctx_t c, const shmemg_op_t *ops,
-                                                           int64_t nops, int64_t *fetched, int use_bulk) {
+                                                           int64_t nops, int64_t *fetched, int use_bulk,
+                                                           int with_agents) {
     const int me = shmemg_d_my_pe(c);
     const shmemg_group g = shmemg_d_group_pe(c);
     const bool leader = shmemg_d_pe_leader(c);
@@ -319,6 +449,29 @@ __global__ void __launch_bounds__(INTERP_THREADS) k_interp(shmemg_device_ctx_t c
     // the bulk engine (thread 0 only; with the launch's ring): the default context's
     // large copies and, in the PE's leader CTA, the explicit contexts' queues
     __shared__ __align__(16) DmaState s_dma;
+    uint32_t agent_epoch = 0;
+    if (with_agents) {
+        agent_epoch = *(volatile uint32_t *)&g_agent_epoch + 1u;
+        if (agent_epoch == 0) agent_epoch = 1;
+    }
+    // (thread 0 of each CTA, at its end: the last one moves the epoch on)
+    auto agent_exit = [&]() {
+        __threadfence();
+        if (atomicAdd(&g_agent_exits, 1u) == gridDim.x - 1) {
+            g_agent_exits = 0;
+            g_agent_epoch = agent_epoch;
+            __threadfence();
+        }
+    };
+    if (with_agents && blockIdx.x >= (uint32_t)c.npes) {  // a context agent, not a PE
+        if (threadIdx.x == 0) {
+            ctx_agent(c, &g_mbox[blockIdx.x - (uint32_t)c.npes], agent_epoch, s_dma, s_ring);
+            agent_exit();
+        }
+        return;
+    }
+    CtxMailbox *const mb = with_agents ? &g_mbox[me] : nullptr;  // this PE's contexts go to its agent
+    uint32_t ag_posted[NQ - 1] = {};                              // (thread 0's counts)
     const bool dma = use_bulk && threadIdx.x == 0;
     const bool ctx_home = use_bulk && shmemg_d_pe_leader_cta(c);  // this CTA serves the PE's contexts
     if (dma) dma_init(s_dma);
@@ -350,6 +503,7 @@ __global__ void __launch_bounds__(INTERP_THREADS) k_interp(shmemg_device_ctx_t c
     bool failed = false;
     for (int64_t base = 0; base < nops && (!failed || dsm); base += OP_BATCH) {
     const int cnt = (int)(nops - base < OP_BATCH ? nops - base : OP_BATCH);
+    if (mb && threadIdx.x == 0) *(volatile uint32_t *)&mb->beat = (uint32_t)(base / OP_BATCH) + 1;
     __syncthreads();
     for (int q = threadIdx.x; q < cnt * 4; q += blockDim.x)
         reinterpret_cast<uint4 *>(s_ops)[q] = __ldcg(reinterpret_cast<const uint4 *>(ops + base) + q);
@@ -421,9 +575,14 @@ __global__ void __launch_bounds__(INTERP_THREADS) k_interp(shmemg_device_ctx_t c
         case SHMEMG_OP_PUT_NBI:
             if (o.issuer == me && o.kind == SHMEMG_OP_PUT_NBI && o.sub != 0 &&
                 ctx_aligned(c, shmemg_d_addr(c, o.pe, o.dst), shmemg_d_addr(c, me, o.src), o.n, use_bulk)) {
-                if (dma && ctx_home)  // queued on its context, moved in the background
+                if (mb) {  // posted to the PE's agent
+                    if (threadIdx.x == 0)
+                        agent_post(c, mb, agent_epoch, ag_posted, o.sub, (uint64_t)shmemg_d_addr(c, o.pe, o.dst),
+                                   (uint64_t)shmemg_d_addr(c, me, o.src), o.n, i);
+                } else if (dma && ctx_home) {  // queued on its context, moved in the background
                     dma_enqueue(c, s_dma, s_ring, o.sub, (uint64_t)shmemg_d_addr(c, o.pe, o.dst),
                                 (uint64_t)shmemg_d_addr(c, me, o.src), o.n, 0, 1);
+                }
             } else if (o.issuer == me) {
                 if (warp) {
                     if (active) shmemg_d_copy_group(gw, shmemg_d_addr(c, o.pe, o.dst), shmemg_d_addr(c, me, o.src), o.n);
@@ -438,9 +597,14 @@ __global__ void __launch_bounds__(INTERP_THREADS) k_interp(shmemg_device_ctx_t c
         case SHMEMG_OP_GET_NBI:
             if (o.issuer == me && o.kind == SHMEMG_OP_GET_NBI && o.sub != 0 &&
                 ctx_aligned(c, shmemg_d_addr(c, me, o.dst), shmemg_d_addr(c, o.pe, o.src), o.n, use_bulk)) {
-                if (dma && ctx_home)
+                if (mb) {
+                    if (threadIdx.x == 0)
+                        agent_post(c, mb, agent_epoch, ag_posted, o.sub, (uint64_t)shmemg_d_addr(c, me, o.dst),
+                                   (uint64_t)shmemg_d_addr(c, o.pe, o.src), o.n, i);
+                } else if (dma && ctx_home) {
                     dma_enqueue(c, s_dma, s_ring, o.sub, (uint64_t)shmemg_d_addr(c, me, o.dst),
                                 (uint64_t)shmemg_d_addr(c, o.pe, o.src), o.n, 0, 1);
+                }
             } else if (o.issuer == me) {
                 if (warp) {
                     if (active) shmemg_d_copy_group(gw, shmemg_d_addr(c, me, o.dst), shmemg_d_addr(c, o.pe, o.src), o.n);
@@ -512,7 +676,11 @@ __global__ void __launch_bounds__(INTERP_THREADS) k_interp(shmemg_device_ctx_t c
         case SHMEMG_OP_QUIET:
         case SHMEMG_OP_FENCE:  // fence on a context completes it too (ordering by completion)
             if (o.issuer == me || o.issuer < 0) {
-                if (dma && ctx_home && o.sub != 0) dma_drain(c, s_dma, s_ring, o.sub == SHMEMG_CTX_ALL ? -1 : o.sub);
+                if (mb) {
+                    if (threadIdx.x == 0 && o.sub != 0) agent_quiet(c, mb, agent_epoch, ag_posted, o.sub, i);
+                } else if (dma && ctx_home && o.sub != 0) {
+                    dma_drain(c, s_dma, s_ring, o.sub == SHMEMG_CTX_ALL ? -1 : o.sub);
+                }
                 shmemg_d_quiet_pe(c);
             }
             break;
@@ -562,10 +730,12 @@ __global__ void __launch_bounds__(INTERP_THREADS) k_interp(shmemg_device_ctx_t c
     }
     }
     // every context's transfers complete before the PE ends (none may still read this
-    // CTA's shared memory when it exits)
+    // CTA's shared memory when it exits); the agent finishes its own before it leaves
     if (dma) dma_drain(c, s_dma, s_ring, -1);
+    if (mb && threadIdx.x == 0) shmemg_d_st_release_u32(&mb->exit, agent_epoch);
     shmemg_d_quiet_pe(c);
     if (dsm) shmemg_d_cluster_end();  // no CTA leaves while a peer may still touch its shared memory
+    if (with_agents && threadIdx.x == 0) agent_exit();
 }
 
 int interp_threads() {
@@ -578,13 +748,14 @@ int interp_threads() {
     return t;
 }
 
-// Cooperative launch of `kernel` with one CTA (or cluster) per PE; `threads` per CTA
-// (0: the interpreter's count).
-int launch_pe_grid(const void *kernel, void **args, size_t smem, cudaStream_t s, int threads) {
+// Cooperative launch of `kernel` with one CTA (or cluster) per PE, grid_mult times over;
+// `threads` per CTA (0: the interpreter's count).
+int launch_pe_grid(const void *kernel, void **args, size_t smem, cudaStream_t s, int threads, int grid_mult) {
     State &S = st();
     if (threads <= 0) threads = interp_threads();
     const int cd = S.cluster_dim;
-    const unsigned grid = S.pe_mode == SHMEMG_PE_MODE_CLUSTER ? (unsigned)(S.npes * cd) : (unsigned)S.npes;
+    const unsigned grid =
+        (S.pe_mode == SHMEMG_PE_MODE_CLUSTER ? (unsigned)(S.npes * cd) : (unsigned)S.npes) * (unsigned)grid_mult;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
     cfg.blockDim = dim3(threads);
@@ -646,6 +817,19 @@ extern "C" int shmemg_run_script(const shmemg_op_t *ops, int64_t nops, int64_t *
         }
     }
     int use_bulk = bulk;
-    void *args[] = {(void *)&c, (void *)&ops, (void *)&nops, (void *)&fetched, (void *)&use_bulk};
-    return launch_pe_grid((const void *)k_interp, args, use_bulk ? RING_SMEM : 0, to_stream(stream));
+    // context agents: CTA PEs without hardware clusters, when the GPU holds two CTAs per PE
+    // (SHMEMG_CTX_AGENTS=0 keeps the contexts on the PE's own engine)
+    static int agents = -1;
+    if (agents < 0) {
+        const char *e = getenv("SHMEMG_CTX_AGENTS");
+        agents = (e && *e == '0') ? 0 : 1;
+    }
+    State &S = st();
+    int with_agents = 0;
+    if (agents && use_bulk && S.pe_mode == SHMEMG_PE_MODE_CTA && S.cluster_dim == 1 && S.npes <= AGENT_MAX_PES &&
+        ctas_for((const void *)k_interp, interp_threads(), RING_SMEM) >= 2 * S.npes)
+        with_agents = 1;
+    void *args[] = {(void *)&c, (void *)&ops, (void *)&nops, (void *)&fetched, (void *)&use_bulk, (void *)&with_agents};
+    return launch_pe_grid((const void *)k_interp, args, use_bulk ? RING_SMEM : 0, to_stream(stream), 0,
+                          with_agents ? 2 : 1);
 }

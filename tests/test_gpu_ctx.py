@@ -161,3 +161,66 @@ def test_invalid_contexts_rejected(sg, heapf, bad):
     code, detail = sg.get_status()
     assert code == sg.ERR_INVALID_ARG and detail == 1
     sg.clear_status()
+
+
+@pytest.mark.parametrize("npes", [96, 6])
+def test_contexts_with_and_without_agents(sg, heapf, orc, npes):
+    """CTA PEs without clusters: 6 PEs get a context agent each (a second CTA), 96 PEs do
+    not fit twice on the GPU and keep their contexts on their own engine.  Both: three
+    contexts per PE with transfers interleaved with blocking puts, a quiet on one context
+    while the others still move (context independence), a get of what a quieted context
+    delivered, and transfers left for the script's end."""
+    H = 4 * MiB
+    h = heapf(npes, H)
+    init = random_heap(npes, H, 90 + npes)
+    upload(h, init)
+    ops = []
+    for p in range(npes):
+        ops += [_rec(kind=W.OP_PUT_NBI, sub=1, pe=(p + 1) % npes, issuer=p, dst=2 * MiB, src=0, n=768 * KiB),
+                _rec(kind=W.OP_GET_NBI, sub=2, pe=(p + 2) % npes, issuer=p, dst=3 * MiB, src=256 * KiB, n=256 * KiB),
+                _rec(kind=W.OP_PUT, pe=(p + 3) % npes, issuer=p, dst=3 * MiB + 512 * KiB + 64 * p, src=64, n=64),
+                _rec(kind=W.OP_PUT_NBI, sub=3, pe=(p + 1) % npes, issuer=p, dst=3 * MiB + 768 * KiB, src=512 * KiB,
+                     n=128 * KiB + 16)]
+    for p in range(npes):
+        ops.append(_rec(kind=W.OP_QUIET, sub=2, issuer=p))
+    ops.append(_rec(kind=W.OP_BARRIER_ALL))
+    for p in range(npes):   # what context 2 delivered, read back after its quiet and a barrier
+        ops.append(_rec(kind=W.OP_GET, pe=(p + 1) % npes, issuer=p, dst=3 * MiB + 640 * KiB, src=3 * MiB, n=64 * KiB))
+    assert _run(sg, h, orc, init, ops) is None
+
+
+def test_context_agents_across_graph_replays(sg, heapf, orc):
+    """A script with context transfers captured once in a CUDA graph and replayed: each
+    replay adds to a word, moves the block holding it on context 1, quiets, and reads the
+    neighbour's copy back; after three replays the heap equals three runs of the oracle
+    (every replay's quiet waited for that replay's transfer)."""
+    npes, H = 6, 2 * MiB
+    h = heapf(npes, H)
+    init = random_heap(npes, H, 101)
+    upload(h, init)
+    W0, D, E = 0, 512 * KiB, 1 * MiB
+    ops = []
+    for p in range(npes):
+        ops += [_rec(kind=W.OP_FADD, dtype=W.DT_INT64, pe=p, issuer=p, dst=W0, operand=1 + p),
+                _rec(kind=W.OP_PUT_NBI, sub=1, pe=(p + 1) % npes, issuer=p, dst=D, src=W0, n=256 * KiB),
+                _rec(kind=W.OP_QUIET, sub=1, issuer=p)]
+    ops.append(_rec(kind=W.OP_BARRIER_ALL))
+    for p in range(npes):
+        ops.append(_rec(kind=W.OP_GET, pe=(p + 1) % npes, issuer=p, dst=E, src=D, n=64 * KiB))
+    ops.append(_rec(kind=W.OP_BARRIER_ALL))
+    ops = np.array(ops, dtype=W.OP_DTYPE)
+    dev = torch.from_numpy(ops.view(np.uint8).copy()).cuda()
+    sg.clear_status()
+    s = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(g, stream=s):
+            sg.run_script(dev, len(ops), None, s)
+    for _ in range(3):
+        g.replay()
+    torch.cuda.synchronize()
+    assert sg.get_status()[0] == 0
+    ref = orc.Heap(npes, H, init)
+    for _ in range(3):
+        ref.run_script(ops)
+    assert first_diff(download(h), ref.mem) is None

@@ -1070,7 +1070,7 @@ def run_batch(torch, sg, reps=5, check_teams=32, check_elems=4096):
                          "frac_of_hbm": round(ab / (tuned * 1e-3) / 1e9 / hbm, 3),
                          "untuned_ms": round(untuned, 3), "launch_per_team_ms": round(per_team, 3),
                          "speedup_vs_launch_per_team": round(per_team / tuned, 2),
-                         "tune": {"tile_elems": tune.tile_elems, "ctas_per_sm": tune.ctas_per_sm},
+                         "tune": {"tile_elems": tune.tile_elems, "ctas_per_sm": tune.ctas_per_sm, "deep": tune.deep},
                          "algorithmic_bytes": ab, "error_vs_fp64": err}
             b.destroy()
     finally:

@@ -452,7 +452,8 @@ typedef struct {
     int32_t tile_elems;   /* elements per work item; 0 = autotune */
     int32_t ctas_per_sm;  /* 0 = occupancy maximum */
     int32_t threads;      /* threads per CTA, 0 = 256 */
-    int32_t reserved0;
+    int32_t deep;         /* 0: the kernel held to 3 CTAs per SM; 1: the one held to 2 CTAs
+                             per SM whose quantised sums load 16 members ahead, not 8 */
 } shmemg_tune_t;
 typedef struct shmemg_batch_s *shmemg_batch_t;
 /* Validates and uploads the descriptors, plans work items largest-first and captures

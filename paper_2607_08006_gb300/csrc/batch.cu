@@ -22,9 +22,13 @@
 namespace shmemg {
 
 constexpr int B_THREADS = 256;
-constexpr int B_TREE_MAXB = 4;   // fp32 tree: 16 members' loads in flight per thread
-constexpr int B_QM_BF16 = 8, B_QM_E4M3 = 8;   // quantised: members loaded ahead
-constexpr int B_MIN_BLOCKS = 3;  // 85 registers: 8 members' loads ahead without spills
+constexpr int B_DEEP_QM = 16;
+// Two kernels (the plan's `deep` picks one): the lean one holds 85 registers for 3 CTAs per
+// SM, with 16 members' loads in flight in the fp32 tree and 8 quantised members loaded
+// ahead; the deep one holds 128 registers for 2 CTAs per SM and loads further ahead.
+template <int MINB> struct BShape;
+template <> struct BShape<3> { static constexpr int TREE_MAXB = 4, QM = 8; };
+template <> struct BShape<2> { static constexpr int TREE_MAXB = 4, QM = B_DEEP_QM; };
 enum BKind { BK_F32 = 0, BK_I64 = 1, BK_BF16 = 2, BK_E4M3 = 3 };
 
 struct BTeam {
@@ -45,11 +49,10 @@ struct BArgs {
 // quantised tile: full chunks of blockDim x E elements accumulate into shared memory (two
 // buffers, alternated across the CTA's chunks) and are bulk-stored to every member (bit 1
 // of t.vec: 16-byte aligned codes and outputs); the rest runs E (or 4) elements per thread
-template <int FMT>
+template <int FMT, int M>
 __device__ __forceinline__ void batch_qsum(const BArgs &a, const BTeam &t, uint64_t e0, uint64_t e1, float (*s_out)[B_THREADS * 16],
                                            int &buf) {
     constexpr int E = QWide<FMT>::E;
-    constexpr int M = FMT == SHMEMG_FMT_E4M3 ? B_QM_E4M3 : B_QM_BF16;
     const uint64_t CH = (uint64_t)blockDim.x * E;
     uint64_t f0 = e0;
     if (t.vec & 2) {
@@ -70,22 +73,24 @@ __device__ __forceinline__ void batch_qsum(const BArgs &a, const BTeam &t, uint6
     }
 }
 
+template <int MINB>
 __device__ __forceinline__ void batch_item(const BArgs &a, const BTeam &t, uint64_t e0, uint64_t e1, float (*s_out)[B_THREADS * 16],
                                            int &buf) {
     const shmemg_group g = {threadIdx.x, blockDim.x};
     if (t.kind == BK_F32) {
-        shmemg_d_reduce_elems_t<float, float4, B_TREE_MAXB>(g, a.heap, a.H, t.start, 1, t.size, t.d_off, t.s_off, e0, e1,
+        shmemg_d_reduce_elems_t<float, float4, BShape<MINB>::TREE_MAXB>(g, a.heap, a.H, t.start, 1, t.size, t.d_off, t.s_off, e0, e1,
                                                          SHMEMG_SUM);
     } else if (t.kind == BK_I64) {
         shmemg_d_reduce_elems_t<int64_t, longlong2>(g, a.heap, a.H, t.start, 1, t.size, t.d_off, t.s_off, e0, e1,
                                                     SHMEMG_SUM);
     } else {
-        if (t.kind == BK_E4M3) batch_qsum<SHMEMG_FMT_E4M3>(a, t, e0, e1, s_out, buf);
-        else batch_qsum<SHMEMG_FMT_BF16>(a, t, e0, e1, s_out, buf);
+        if (t.kind == BK_E4M3) batch_qsum<SHMEMG_FMT_E4M3, BShape<MINB>::QM>(a, t, e0, e1, s_out, buf);
+        else batch_qsum<SHMEMG_FMT_BF16, BShape<MINB>::QM>(a, t, e0, e1, s_out, buf);
     }
 }
 
-__global__ void __launch_bounds__(B_THREADS, B_MIN_BLOCKS) k_batch(BArgs a) {
+template <int MINB>
+__global__ void __launch_bounds__(B_THREADS, MINB) k_batch(BArgs a) {
     __shared__ uint32_t s_item;
     __shared__ __align__(128) float s_out[2][B_THREADS * 16];  // two quantised chunks (E <= 16), alternated
     int buf = 0;
@@ -99,7 +104,7 @@ __global__ void __launch_bounds__(B_THREADS, B_MIN_BLOCKS) k_batch(BArgs a) {
         const BTeam t = a.teams[item.x];
         const uint64_t e0 = (uint64_t)item.y * a.tile;
         const uint64_t e1 = e0 + a.tile < t.n ? e0 + a.tile : t.n;
-        batch_item(a, t, e0, e1, s_out, buf);
+        batch_item<MINB>(a, t, e0, e1, s_out, buf);
     }
     if (threadIdx.x == 0) {
         asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");  // this CTA's bulk stores are done
@@ -159,7 +164,8 @@ static int plan_and_capture(shmemg_batch_s *b) {
         return rc;
     b->nitems = (uint32_t)items.size();
     int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch, B_THREADS, 0);
+    const void *kfn = b->tune.deep ? (const void *)k_batch<2> : (const void *)k_batch<3>;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kfn, B_THREADS, 0);
     if (per_sm < 1) per_sm = 1;
     int want = b->tune.ctas_per_sm > 0 ? std::min(b->tune.ctas_per_sm, per_sm) : per_sm;
     b->grid = want * S.sm_count;
@@ -177,7 +183,8 @@ static int plan_and_capture(shmemg_batch_s *b) {
     a.counter = b->d_counter;
     rc = cuda_rc(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
     if (!rc) {
-        k_batch<<<b->grid, B_THREADS, 0, cs>>>(a);
+        if (b->tune.deep) k_batch<2><<<b->grid, B_THREADS, 0, cs>>>(a);
+        else k_batch<3><<<b->grid, B_THREADS, 0, cs>>>(a);
         cudaError_t le = cudaGetLastError();
         cudaError_t ee = cudaStreamEndCapture(cs, &b->graph);
         rc = cuda_rc(le != cudaSuccess ? le : ee);
@@ -227,6 +234,7 @@ int shmemg_batch_create(const shmemg_coll_desc_t *descs, int count, const shmemg
     b->tune.tile_elems = tune && tune->tile_elems > 0 ? tune->tile_elems : 16384;
     b->tune.ctas_per_sm = tune ? tune->ctas_per_sm : 0;
     b->tune.threads = B_THREADS;
+    b->tune.deep = tune && tune->deep ? 1 : 0;
     if (b->tune.tile_elems % 128) { delete b; return SHMEMG_ERR_INVALID_ARG; }
     int rc = cuda_rc(cudaMalloc(&b->d_teams, sizeof(BTeam) * b->teams.size()));
     if (!rc) rc = cuda_rc(cudaMemcpy(b->d_teams, b->teams.data(), sizeof(BTeam) * b->teams.size(), cudaMemcpyHostToDevice));
@@ -251,8 +259,8 @@ int shmemg_batch_autotune(shmemg_batch_t b, void *stream, shmemg_tune_t *chosen)
     if (int rc = check_init()) return rc;
     if (!b) return SHMEMG_ERR_INVALID_ARG;
     cudaStream_t s = to_stream(stream);
-    const int tiles[] = {2048, 8192, 32768, 131072};
-    const int ctas[] = {1, 2, 0};
+    const int tiles[] = {2048, 4096, 8192, 32768, 131072};
+    const int ctas[] = {1, 2, 0, -1};  // (-1: the deep kernel at its 2 CTAs per SM)
     shmemg_tune_t best = b->tune;
     float best_ms = 1e30f;
     cudaEvent_t e0, e1;
@@ -262,7 +270,8 @@ int shmemg_batch_autotune(shmemg_batch_t b, void *stream, shmemg_tune_t *chosen)
     for (int t : tiles) {
         for (int c : ctas) {
             b->tune.tile_elems = t;
-            b->tune.ctas_per_sm = c;
+            b->tune.ctas_per_sm = c < 0 ? 0 : c;
+            b->tune.deep = c < 0 ? 1 : 0;
             if ((rc = plan_and_capture(b))) break;
             cudaGraphLaunch(b->exec, s);  // warm-up
             cudaEventRecord(e0, s);
@@ -402,8 +411,8 @@ extern "C" int shmemg_batch_reduce_noalloc(const shmemg_coll_desc_t *descs, int 
     a.nitems = k;
     a.tile = tile;
     a.counter = d->counter;
-    int grid = ctas_for((const void *)k_batch, B_THREADS, 0);
+    int grid = ctas_for((const void *)k_batch<3>, B_THREADS, 0);
     if ((uint32_t)grid > k) grid = (int)k;
-    k_batch<<<grid, B_THREADS, 0, s>>>(a);
+    k_batch<3><<<grid, B_THREADS, 0, s>>>(a);
     return cuda_rc(cudaGetLastError());
 }

@@ -72,7 +72,7 @@ class CollDesc(C.Structure):
 
 class Tune(C.Structure):
     _fields_ = [("tile_elems", C.c_int32), ("ctas_per_sm", C.c_int32), ("threads", C.c_int32),
-                ("reserved0", C.c_int32)]
+                ("deep", C.c_int32)]
 
 
 class Req(C.Structure):

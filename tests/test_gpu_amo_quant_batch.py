@@ -218,9 +218,17 @@ def test_batch_engine_bitexact_and_replay(sg, heapf, orc):
     torch.cuda.synchronize()
     assert first_diff(download(h), ref.mem) is None
     tune = b.autotune()
-    assert tune.tile_elems in (2048, 8192, 32768, 131072)
+    assert tune.tile_elems in (2048, 4096, 8192, 32768, 131072) and tune.deep in (0, 1)
     h.partitions().copy_(torch.from_numpy(init.reshape(world, H)).cuda())
     b.launch()
     torch.cuda.synchronize()
     assert first_diff(download(h), ref.mem) is None
+    # the deep kernel (2 CTAs per SM, 16 quantised members loaded ahead) on the same plan
+    for tile in (4096, 8192):
+        bd = sg.Batch(descs, sg.Tune(tile, 0, 0, 1))
+        h.partitions().copy_(torch.from_numpy(init.reshape(world, H)).cuda())
+        bd.launch()
+        torch.cuda.synchronize()
+        assert first_diff(download(h), ref.mem) is None, tile
+        bd.destroy()
     b.destroy()

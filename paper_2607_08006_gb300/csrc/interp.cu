@@ -9,6 +9,9 @@
 #include <cuda_runtime.h>
 
 #include <cstdlib>
+#include <map>
+#include <mutex>
+#include <tuple>
 
 #include "internal.h"
 
@@ -772,20 +775,38 @@ int launch_pe_grid(const void *kernel, void **args, size_t smem, cudaStream_t s,
         attr[na].val.clusterDim.y = 1;
         attr[na].val.clusterDim.z = 1;
         na++;
-        int nclusters = 0;
-        cudaLaunchConfig_t q = cfg;
-        q.attrs = attr + 1;
-        q.numAttrs = 1;
-        if (cudaOccupancyMaxActiveClusters(&nclusters, kernel, &q) != cudaSuccess) {
-            cudaGetLastError();
-            return SHMEMG_ERR_UNSUPPORTED;
-        }
-        if ((int64_t)nclusters * cd < (int64_t)grid) return SHMEMG_ERR_UNSUPPORTED;
-    } else {
-        int per_sm = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem);
-        if ((int64_t)per_sm * S.sm_count < (int64_t)grid) return SHMEMG_ERR_UNSUPPORTED;
     }
+    // whether the GPU holds the whole grid at once: an occupancy query per kernel shape,
+    // cached (a query per launch cost more host time than a small script runs)
+    static std::mutex mu;
+    static std::map<std::tuple<const void *, int, size_t, int, unsigned, int>, bool> fits;
+    const auto key = std::make_tuple(kernel, threads, smem, cd, grid, S.device);
+    bool ok;
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        auto it = fits.find(key);
+        if (it != fits.end()) {
+            ok = it->second;
+        } else {
+            if (cd > 1) {
+                int nclusters = 0;
+                cudaLaunchConfig_t q = cfg;
+                q.attrs = attr + 1;
+                q.numAttrs = 1;
+                if (cudaOccupancyMaxActiveClusters(&nclusters, kernel, &q) != cudaSuccess) {
+                    cudaGetLastError();
+                    nclusters = 0;
+                }
+                ok = (int64_t)nclusters * cd >= (int64_t)grid;
+            } else {
+                int per_sm = 0;
+                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem);
+                ok = (int64_t)per_sm * S.sm_count >= (int64_t)grid;
+            }
+            fits[key] = ok;
+        }
+    }
+    if (!ok) return SHMEMG_ERR_UNSUPPORTED;
     cfg.attrs = attr;
     cfg.numAttrs = na;
     cudaError_t e = cudaLaunchKernelExC(&cfg, kernel, args);

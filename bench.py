@@ -1239,7 +1239,7 @@ def run_serve(torch, sg, nreq=1 << 16, rates=None, npes=512, arena=32 << 20):
 
 
 # ----------------------------------------------------------------------------- profiling cases
-PROFILE_CASES = ("interp_ring", "interp_ops", "reduce", "reduce_mid", "reduce_big", "reduce_f32", "broadcast", "alltoall", "amo", "amo_l2", "amo_plain", "amo_combine", "amo_combine_zipf", "batch_bf16", "batch_e4m3", "batch_e4m3_teams", "batch_bf16_teams", "qsum",
+PROFILE_CASES = ("interp_ring", "interp_ops", "reduce", "reduce_mid", "reduce_big", "reduce_f32", "broadcast", "alltoall", "amo", "amo_l2", "amo_plain", "amo_combine", "amo_combine_zipf", "batch_bf16", "batch_e4m3", "batch_e4m3_teams", "batch_bf16_teams", "qsum", "serve_reduce", "serve_a2a",
                  "pingpong_cluster", "cluster_coll", "halo", "halo_plain")
 
 
@@ -1291,6 +1291,28 @@ def run_profile_case(name, launches=4):
             heap.partitions()[:, :8 * n].view(torch.float32).normal_()
         for _ in range(launches):
             sg.reduce(sg.TEAM_WORLD, heap.base + 8 * n, heap.base, n, dt, sg.SUM, s)
+    elif name in ("serve_reduce", "serve_a2a"):  # the serving tiles on the plain path: one staged
+        # request per launch pair (staging launch, then the operation's): an fp32 reduction of
+        # 4 Mi elements over 32 PEs in place, or a 32 x 256 KiB alltoall
+        lay = W.serve_layout_staged(arena_bytes=32 * MiB, amo_words=1024)
+        heap = sg.Heap(32, lay.H)
+        cfg = sg.ServerCfg()
+        cfg.page_bytes = lay.page_bytes
+        cfg.arena_offset, cfg.arena_bytes = lay.arena_offset, lay.arena_bytes
+        cfg.amo_offset, cfg.amo_words = lay.amo_offset, lay.amo_words
+        cfg.max_ns = 60 * 10**9
+        req = np.zeros(1, sg.REQ_DTYPE)
+        req["flags"], req["pe"], req["issuer"], req["word"] = 1, 0, 32, 12345
+        if name == "serve_reduce":
+            req["kind"], req["dtype"], req["fmt"], req["n"] = W.OP_REDUCE, W.DT_FLOAT, W.FMT_F32, 4 << 20
+        else:
+            req["kind"], req["n"] = W.OP_ALLTOALL, 256 * KiB
+        recs = torch.zeros(launches * sg.COMPLETION_DTYPE.itemsize, dtype=torch.uint8).pin_memory()
+        reqs = np.repeat(req, launches)
+        sg.plain_feed(reqs, np.zeros(launches, np.uint64), cfg, recs.data_ptr(), s)
+        s.synchronize()
+        done = np.frombuffer(recs.numpy().tobytes(), sg.COMPLETION_DTYPE)
+        assert np.all(done["status"] == 0), done["status"]
     elif name == "broadcast":      # 64 PEs, 8 MiB
         m = 8 * MiB
         heap = sg.Heap(64, 2 * m)

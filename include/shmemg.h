@@ -526,10 +526,13 @@ int shmemg_batch_reduce_noalloc(const shmemg_coll_desc_t *descs, int count, int 
  *              are 4n and 2n rounded up to 16
  *   ALLTOALL   [R, R + P*n) destination blocks, [R + P*n, R + 2*P*n) source blocks
  * The request first writes its source on every source PE p: 32-bit word j of the source
- * part (at byte 4j from its start) is w(j) = (b(z >> 56) << 16) | b((z >> 48) & 255),
+ * part (at byte 4j from its start) is
+ *   w(j) = (b((z >> (56 - 16q)) & 255) << 16) | b((z >> (48 - 16q)) & 255),  q = j mod 4,
  * where z is the first output of Steele, Lea and Flood's SplitMix64 stream started at
- * state seed ^ ((p << 40) | j), and b(k) the bfloat16 code of (k - 128) / 128; then it
- * runs the operation on that source like any other request.
+ * state seed ^ ((p << 40) | floor(j / 4)) -- one draw gives four words, two of its bytes
+ * each, high bytes first -- and b(k) = ((k & 128) << 8) | 0x3F80 | (k & 127), the
+ * bfloat16 code of (-1)^(k >> 7) * (1 + (k & 127) / 128); then it runs the operation on
+ * that source like any other request.
  *
  * The result is the fetched value (AMO) or a checksum of the output:
  * sum over its little-endian 32-bit words w_i (members' outputs concatenated in team

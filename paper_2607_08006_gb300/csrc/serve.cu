@@ -276,17 +276,20 @@ __device__ __forceinline__ uint64_t copy_ck(uint8_t *dst, const uint8_t *src, ui
 }
 
 // ------------------------------------------------------------------ staged payloads
-// Word j of PE p's staged source: two bfloat16 codes of (k - 128) / 128 from the top two
-// bytes of the counter draw (shmemg_req_t's staged payloads).
-__device__ __forceinline__ uint32_t payload_bf16(uint32_t k) {
-    return __float_as_uint((float)((int)k - 128) * 0.0078125f) >> 16;  // exact: k - 128 has <= 8 bits
+// Staged payload words (shmemg_req_t's definition): word q (0..3) of the counter draw z
+// holds bytes 7 - 2q and 6 - 2q of z as two bfloat16 codes b(k) = sign of k's top bit,
+// exponent 127, mantissa k's low 7 bits -- (-1)^(k >> 7) * (1 + (k & 127) / 128) --
+// built with integer operations on both halves at once.
+__device__ __forceinline__ uint32_t payload_of(uint64_t z, uint32_t q) {
+    const uint32_t t = (uint32_t)(z >> (48 - 16 * q)) & 0xFFFFu;  // the word's two bytes
+    const uint32_t u = ((t & 0xFF00u) << 8) | (t & 0xFFu);        // one per half-word
+    return ((u & 0x00800080u) << 8) | 0x3F803F80u | (u & 0x007F007Fu);
 }
 __device__ __forceinline__ uint32_t payload_word(uint64_t seed, int p, uint64_t j) {
-    const uint64_t z = cb64(seed, ((uint64_t)p << 40) | j);
-    return (payload_bf16((uint32_t)(z >> 56)) << 16) | payload_bf16((uint32_t)(z >> 48) & 255u);
+    return payload_of(cb64(seed, ((uint64_t)p << 40) | (j >> 2)), (uint32_t)(j & 3));
 }
 // words [j0, j1) of PE p's source part, which starts at `part` (16-byte aligned): four
-// words per 16-byte store where the range allows, single words at its ends
+// words -- one draw -- per 16-byte store where the range allows, single words at its ends
 __device__ void stage_words(uint8_t *part, uint64_t seed, int p, uint64_t j0, uint64_t j1) {
     uint32_t *w = (uint32_t *)part;
     const uint64_t a0 = (j0 + 3) & ~(uint64_t)3, a1 = j1 & ~(uint64_t)3;
@@ -296,9 +299,8 @@ __device__ void stage_words(uint8_t *part, uint64_t seed, int p, uint64_t j0, ui
     }
     for (uint64_t j = j0 + threadIdx.x; j < a0; j += blockDim.x) w[j] = payload_word(seed, p, j);
     for (uint64_t q = a0 / 4 + threadIdx.x; q < a1 / 4; q += blockDim.x) {
-        const uint64_t j = 4 * q;
-        ((uint4 *)part)[q] = make_uint4(payload_word(seed, p, j), payload_word(seed, p, j + 1),
-                                        payload_word(seed, p, j + 2), payload_word(seed, p, j + 3));
+        const uint64_t z = cb64(seed, ((uint64_t)p << 40) | q);
+        ((uint4 *)part)[q] = make_uint4(payload_of(z, 0), payload_of(z, 1), payload_of(z, 2), payload_of(z, 3));
     }
     for (uint64_t j = a1 + threadIdx.x; j < j1; j += blockDim.x) w[j] = payload_word(seed, p, j);
 }

@@ -37,6 +37,24 @@ def test_splitmix64_published_outputs(orc):
     assert np.array_equal(W.cb64_np(77, idx), np.array([orc.cb64(77, int(i)) for i in idx], np.uint64))
 
 
+def test_staged_payload_word_layout():
+    """Staged payload words follow the request record's definition: four words per
+    SplitMix64 draw of (seed, PE, word // 4), word q taking bytes 7 - 2q (high bfloat16) and
+    6 - 2q (low) of the draw, each byte k coded as the bfloat16 of
+    (-1)^(k >> 7) * (1 + (k & 127) / 128) -- checked word by word from the published first
+    output and from the bytes' values."""
+    seed, pe = 0x1234567, 5
+    w = W.serve_payload_words(seed, pe, 0, 4 * 7 + 3)
+    for j in range(len(w)):
+        z = W.SplitMix64(seed ^ ((pe << 40) | (j // 4))).next()
+        hi, lo = (z >> (56 - 16 * (j % 4))) & 255, (z >> (48 - 16 * (j % 4))) & 255
+        for k, half in ((hi, int(w[j]) >> 16), (lo, int(w[j]) & 0xFFFF)):
+            v = np.array([half << 16], np.uint32).view(np.float32)[0]   # the bfloat16 as binary32
+            assert v == (-1.0 if k >> 7 else 1.0) * (1 + (k & 127) / 128.0), (j, k, half)
+    # an offset start gives the same words (word j's draw depends on j alone)
+    assert np.array_equal(W.serve_payload_words(seed, pe, 6, 20), w[6:26])
+
+
 def test_torch_generator_matches_numpy():
     torch = pytest.importorskip("torch")
     idx = np.arange(5000, dtype=np.int64) * 7919

@@ -523,13 +523,19 @@ def staged_region_bytes(kind: int, fmt: int, n: int, P: int) -> int:
 
 def serve_payload_words(seed: int, pe: int, j0: int, count: int) -> np.ndarray:
     """Words [j0, j0 + count) of PE pe's staged source part: word j holds two bfloat16
-    codes, of (k1 - 128) / 128 (high half) and (k2 - 128) / 128 (low half), k1 and k2 the
-    top two bytes of cb64(seed, (pe << 40) | j)."""
-    z = cb64_np(seed, np.arange(j0, j0 + count, dtype=np.uint64) + np.uint64(pe << 40))
+    codes b(k1) (high half) and b(k2) (low half), where k1, k2 are bytes 7 - 2q and 6 - 2q
+    (q = j mod 4) of the draw cb64(seed, (pe << 40) | j // 4) -- one draw, four words --
+    and b(k) = ((k & 128) << 8) | 0x3F80 | (k & 127), the bfloat16 code of
+    (-1)^(k >> 7) * (1 + (k & 127) / 128)."""
+    j = np.arange(j0, j0 + count, dtype=np.uint64)
+    z = cb64_np(seed, (j >> np.uint64(2)) + np.uint64(pe << 40))
+    sh = np.uint64(16) * (j & np.uint64(3))
 
     def code(k):
-        return ((k.astype(np.int64) - 128).astype(np.float32) / np.float32(128.0)).view(np.uint32) >> np.uint32(16)
-    return (code(z >> np.uint64(56)) << np.uint32(16)) | code((z >> np.uint64(48)) & np.uint64(255))
+        k = k.astype(np.uint32)
+        return ((k & np.uint32(128)) << np.uint32(8)) | np.uint32(0x3F80) | (k & np.uint32(127))
+    return (code((z >> (np.uint64(56) - sh)) & np.uint64(255)) << np.uint32(16)) | \
+        code((z >> (np.uint64(48) - sh)) & np.uint64(255))
 
 
 def serve_source_words(seed: int, pe: int, nwords: int) -> np.ndarray:

@@ -297,17 +297,22 @@ static __device__ __forceinline__ bool shmemg_bulk_drain_loads(uint64_t *bars, u
 }
 
 /* Thread-scope bulk copy of the chunks first, first+stride, ... of (dst <- src, n bytes);
- * dst, src and n multiples of 16.  smem: SHMEMG_BULK_SMEM bytes (128-byte aligned);
- * bars: SHMEMG_BULK_STAGES mbarriers.  Returns once the data is written (blocking put
+ * dst, src and n multiples of 16.  smem: STAGES x SHMEMG_BULK_CHUNK bytes (128-byte
+ * aligned); bars: STAGES mbarriers.  Returns once the data is written (blocking put
  * semantics); SHMEMG_ERR_TIMEOUT (recorded in the status word) if a stage never fills, after
- * waiting (bounded) for the loads still in flight (shmemg_bulk_drain_loads). */
-static __device__ int shmemg_d_bulk_copy_thread(const shmemg_device_ctx_t &c, uint8_t *dst, const uint8_t *src,
-                                                uint64_t n, uint32_t first, uint32_t stride, uint8_t *smem,
-                                                uint64_t *bars) {
+ * waiting (bounded) for the loads still in flight (shmemg_bulk_drain_loads).
+ * A stage is refilled one chunk behind: after chunk j's store is issued, the stage of
+ * chunk j - 1 takes chunk j - 1 + STAGES once that older store has read it (bulk
+ * wait_group.read 1), so the wait rarely blocks and STAGES - 1 loads stay in flight. */
+template <int STAGES>
+static __device__ int shmemg_d_bulk_copy_thread_n(const shmemg_device_ctx_t &c, uint8_t *dst, const uint8_t *src,
+                                                  uint64_t n, uint32_t first, uint32_t stride, uint8_t *smem,
+                                                  uint64_t *bars) {
+    static_assert(STAGES >= 2, "a chunk is refilled one stage behind");
     const uint64_t nch = (n + SHMEMG_BULK_CHUNK - 1) / SHMEMG_BULK_CHUNK;
     if (first >= nch) return SHMEMG_SUCCESS;
     const uint32_t count = (uint32_t)((nch - first + stride - 1) / stride);
-    for (int s = 0; s < SHMEMG_BULK_STAGES; s++)
+    for (int s = 0; s < STAGES; s++)
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(shmemg_smem_u32(&bars[s])) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.global;" ::: "memory");  /* earlier generic writes -> async proxy */
@@ -316,16 +321,19 @@ static __device__ int shmemg_d_bulk_copy_thread(const shmemg_device_ctx_t &c, ui
         const uint64_t left = n - *off;
         return (uint32_t)(left < SHMEMG_BULK_CHUNK ? left : SHMEMG_BULK_CHUNK);
     };
-    for (uint32_t j = 0; j < count && j < SHMEMG_BULK_STAGES; j++) {
+    for (uint32_t j = 0; j < count && j < STAGES; j++) {
         uint64_t off;
         const uint32_t b = chunk(j, &off);
         shmemg_bulk_load(smem + (uint64_t)j * SHMEMG_BULK_CHUNK, src + off, b, &bars[j]);
     }
     int rc = SHMEMG_SUCCESS;
     for (uint32_t j = 0; j < count; j++) {
-        const uint32_t s = j % SHMEMG_BULK_STAGES;
-        if (!shmemg_mbar_wait(&bars[s], (j / SHMEMG_BULK_STAGES) & 1u, c.timeout_ns)) {
-            const bool drained = shmemg_bulk_drain_loads(bars, SHMEMG_BULK_STAGES, j, count, c.timeout_ns);
+        const uint32_t s = j % STAGES;
+        if (!shmemg_mbar_wait(&bars[s], (j / STAGES) & 1u, c.timeout_ns)) {
+            /* loads issued so far: chunks 0 .. j + STAGES - 2 (the refill of iteration j - 1
+             * took chunk j - 2 + STAGES); those from j on are still in flight */
+            const uint32_t issued = j + STAGES - 1 < count ? j + STAGES - 1 : count;
+            const bool drained = shmemg_bulk_drain_loads(bars, STAGES, j, issued, c.timeout_ns);
             shmemg_d_set_status(c, SHMEMG_ERR_TIMEOUT, drained ? -2 : -4);
             rc = SHMEMG_ERR_TIMEOUT;
             break;
@@ -333,17 +341,23 @@ static __device__ int shmemg_d_bulk_copy_thread(const shmemg_device_ctx_t &c, ui
         uint64_t off;
         const uint32_t b = chunk(j, &off);
         shmemg_bulk_store(dst + off, smem + (uint64_t)s * SHMEMG_BULK_CHUNK, b);
-        if (j + SHMEMG_BULK_STAGES < count) {
-            /* the stage is refilled once the store just issued has read it */
-            asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+        if (j >= 1 && j - 1 + STAGES < count) {
+            /* the stage of chunk j - 1, once its store (the group before this one) has read it */
+            asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
+            const uint32_t sp = (j - 1) % STAGES;
             uint64_t off2;
-            const uint32_t b2 = chunk(j + SHMEMG_BULK_STAGES, &off2);
-            shmemg_bulk_load(smem + (uint64_t)s * SHMEMG_BULK_CHUNK, src + off2, b2, &bars[s]);
+            const uint32_t b2 = chunk(j - 1 + STAGES, &off2);
+            shmemg_bulk_load(smem + (uint64_t)sp * SHMEMG_BULK_CHUNK, src + off2, b2, &bars[sp]);
         }
     }
     asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
     asm volatile("fence.proxy.async.global;" ::: "memory");  /* async-proxy writes -> generic readers */
     return rc;
+}
+static __device__ int shmemg_d_bulk_copy_thread(const shmemg_device_ctx_t &c, uint8_t *dst, const uint8_t *src,
+                                                uint64_t n, uint32_t first, uint32_t stride, uint8_t *smem,
+                                                uint64_t *bars) {
+    return shmemg_d_bulk_copy_thread_n<SHMEMG_BULK_STAGES>(c, dst, src, n, first, stride, smem, bars);
 }
 
 /* ------------------------------------------------------------------ RMA (Sec. 2.1) */

@@ -205,7 +205,7 @@ __device__ __forceinline__ void pe_copy(const shmemg_device_ctx_t &c, shmemg_gro
                 // the engine's last stores were issued; they must have read their stages
                 // before the lean loop loads into them
                 asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
-                shmemg_d_bulk_copy_thread(c, d, s, n, first, stride, ring, bars);
+                shmemg_d_bulk_copy_thread_n<RING_STAGES>(c, d, s, n, first, stride, ring, bars);
             } else {
                 dma_enqueue(c, x, ring, 0, (uint64_t)d, (uint64_t)s, n, first, stride);
                 dma_drain(c, x, ring, 0);
@@ -435,7 +435,7 @@ __global__ void __launch_bounds__(INTERP_THREADS) k_interp(shmemg_device_ctx_t c
     __shared__ int s_wrc[2];
     int n_waits = 0;
     extern __shared__ __align__(128) uint8_t s_ring[];
-    __shared__ __align__(8) uint64_t s_bars[SHMEMG_BULK_STAGES];  // the lean blocking loop's mbarriers
+    __shared__ __align__(8) uint64_t s_bars[RING_STAGES];  // the lean blocking loop's mbarriers
     // the op list is staged through shared memory OP_BATCH records at a time (one
     // coalesced copy per batch instead of a dependent global load per op and thread)
     __shared__ __align__(16) shmemg_op_t s_ops[OP_BATCH];

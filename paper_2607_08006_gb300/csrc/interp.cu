@@ -298,7 +298,14 @@ __device__ __noinline__ void ctx_agent(const shmemg_device_ctx_t &c, CtxMailbox 
             nap = 128;
             continue;
         }
-        if (shmemg_d_ld_acquire_u32(&mb->exit) == epoch) break;
+        if (shmemg_d_ld_acquire_u32(&mb->exit) == epoch) {
+            // the PE's posts before its exit are visible now: any the loop above did not
+            // see yet are taken first
+            bool late = false;
+            for (int k = 0; k < NQ - 1; k++) late |= mb_count(&mb->posted[k], epoch) != taken[k];
+            if (!late) break;
+            continue;
+        }
         const uint64_t now = shmemg_d_globaltimer();
         const uint32_t b = *(volatile uint32_t *)&mb->beat;
         if (idle_since == 0 || b != beat) idle_since = now, beat = b;

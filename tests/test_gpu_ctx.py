@@ -224,3 +224,19 @@ def test_context_agents_across_graph_replays(sg, heapf, orc):
     for _ in range(3):
         ref.run_script(ops)
     assert first_diff(download(h), ref.mem) is None
+
+
+def test_context_transfer_as_each_pes_last_op(sg, heapf, orc):
+    """Each PE's last op is a context transfer with no quiet, barrier or later op: the
+    script's end alone must complete it (the PE leaves right after posting it to its
+    agent, which must still take it).  Repeated with new data, so a transfer the agent
+    missed would leave a stale destination."""
+    npes, H = 6, 1 * MiB
+    h = heapf(npes, H)
+    for it in range(12):
+        init = random_heap(npes, H, 500 + it)
+        upload(h, init)
+        ops = [_rec(kind=W.OP_PUT, pe=(p + 2) % npes, issuer=p, dst=768 * KiB, src=0, n=4096) for p in range(npes)]
+        ops += [_rec(kind=W.OP_PUT_NBI, sub=1 + p % 3, pe=(p + 1) % npes, issuer=p, dst=256 * KiB, src=0,
+                     n=64 * KiB + 16 * it) for p in range(npes)]
+        assert _run(sg, h, orc, init, ops) is None, it

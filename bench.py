@@ -34,8 +34,9 @@ import workloads as W  # noqa: E402
 
 KiB, MiB, GiB = 1 << 10, 1 << 20, 1 << 30
 NPES = 64
-H = 512 * MiB               # grown from 64 MiB to hold the largest sweep points (256 MiB src + dst)
+H = 768 * MiB               # the largest sweep points (256 MiB src + dst) and a second source region
 A_OFF, B_OFF = 0, 256 * MiB  # sources live in region A, destinations in region B
+A2_OFF = 512 * MiB           # the end-to-end leg's second source region (its steps alternate A / A2)
 I32_OFF = 128 * MiB          # int32 sources: A[128 MiB, 192 MiB); int64 sources: A[0, 128 MiB)
 METRIC = "collective & bulk-RMA GB/s vs HBM peak; AMO GUPS; served p50/p99 op latency"
 WORKLOAD = ("64 virtual PEs x 512 MiB sweep: int32/int64 sum+max reduce and fcollect 1Ki-16Mi elements; "
@@ -65,14 +66,14 @@ def sweep_points():
     return pts
 
 
-def ring_script(kind, m):
+def ring_script(kind, m, a_off=A_OFF):
     ops = np.zeros(NPES + 1, W.OP_DTYPE)
     for p in range(NPES):
         q = (p + 1) % NPES
         if kind == "put":   # PE p: its A -> PE q's B
-            ops[p] = (W.OP_PUT_NBI, 0, 0, 0, q, p, B_OFF, A_OFF, m, 0, 0, 0)
+            ops[p] = (W.OP_PUT_NBI, 0, 0, 0, q, p, B_OFF, a_off, m, 0, 0, 0)
         else:               # PE p: PE q's A -> its own B
-            ops[p] = (W.OP_GET_NBI, 0, 0, 0, q, p, B_OFF, A_OFF, m, 0, 0, 0)
+            ops[p] = (W.OP_GET_NBI, 0, 0, 0, q, p, B_OFF, a_off, m, 0, 0, 0)
     ops[NPES] = (W.OP_QUIET, 0, 0, 0, 0, -1, 0, 0, 0, 0, 0, 0)
     return ops
 
@@ -134,7 +135,8 @@ class GpuStep:
         self.scripts = {}
         for name, fam, m, _ in self.pts:
             if fam in ("put", "get"):
-                self.scripts[(fam, m)] = torch.from_numpy(ring_script(fam, m).view(np.uint8).copy()).cuda()
+                for reg, a_off in ((0, A_OFF), (1, A2_OFF)):
+                    self.scripts[(fam, m, reg)] = torch.from_numpy(ring_script(fam, m, a_off).view(np.uint8).copy()).cuda()
         self.fill_inputs()
 
     def fill_inputs(self):
@@ -155,23 +157,26 @@ class GpuStep:
     def launches_per_step(self):
         return len(self.pts)
 
-    def run_point(self, name, fam, m):
+    def run_point(self, name, fam, m, region=0):
+        """One sweep point; region 1 reads the second source region (A2) instead of A."""
         sg, s = self.sg, self.stream
+        A = self.A + (A2_OFF - A_OFF if region else 0)
+        A32 = self.A32 + (A2_OFF - A_OFF if region else 0)
         if fam == "reduce":
             _, dt, op = name.split("_")
             dtype = sg.INT32 if dt == "int32" else sg.INT64
-            src = self.A32 if dt == "int32" else self.A
+            src = A32 if dt == "int32" else A
             sg.reduce(sg.TEAM_WORLD, self.B, src, m, dtype, sg.SUM if op == "sum" else sg.MAX, s)
         elif fam == "fcollect":
             es = 4 if name.endswith("int32") else 8
-            src = self.A32 if es == 4 else self.A
+            src = A32 if es == 4 else A
             sg.fcollectmem(sg.TEAM_WORLD, self.B, src, m * es, s)
         elif fam == "alltoall":
-            sg.alltoallmem(sg.TEAM_WORLD, self.B, self.A, m, s)
+            sg.alltoallmem(sg.TEAM_WORLD, self.B, A, m, s)
         elif fam == "broadcast":
-            sg.broadcastmem(sg.TEAM_WORLD, self.B, self.A, m, NPES - 1, s)
+            sg.broadcastmem(sg.TEAM_WORLD, self.B, A, m, NPES - 1, s)
         else:
-            sg.run_script(self.scripts[(fam, m)], NPES + 1, None, s)
+            sg.run_script(self.scripts[(fam, m, region)], NPES + 1, None, s)
 
     def step(self, events=None):
         for i, (name, fam, m, _) in enumerate(self.pts):
@@ -353,11 +358,14 @@ def point_reads(name, fam, m):
 
 def run_e2e(torch, sg, g, stream, args, world):
     """Same step through the public API with the inputs on the HOST: every step copies
-    region A of every PE from pinned host memory, runs the sweep, and reads PE 0's
-    destination region B back.  The copy is pipelined with the work: region A moves in
-    32 MiB chunks on a copy stream in E2E_CHUNK_ORDER, and each point runs once the chunks
-    it reads have landed (points in order of readiness, the sweep's order among equals)."""
-    steps = max(1, min(args.steps, 2))
+    the sources of every PE from pinned host memory, runs the sweep on them, and reads PE
+    0's destination region B back.  The copies are pipelined with the work: a step's
+    sources move in 32 MiB chunks on a copy stream in E2E_CHUNK_ORDER, and each point runs
+    once the chunks it reads have landed (points in order of readiness, the sweep's order
+    among equals).  Steps alternate between source regions A and A2, so the next step's
+    copies start as soon as this step's are done (they wait only for the step before this
+    one to have finished reading the region they overwrite): the copy stream never idles."""
+    steps = max(1, min(args.steps, 3))
     parts = g.heap.partitions()
     host_in = torch.empty((NPES, 256 * MiB), dtype=torch.uint8, pin_memory=True)
     for p in range(NPES):
@@ -365,38 +373,51 @@ def run_e2e(torch, sg, g, stream, args, world):
     host_out = torch.empty(256 * MiB, dtype=torch.uint8, pin_memory=True)
     copy_stream = torch.cuda.Stream()
     pos = {c: k for k, c in enumerate(E2E_CHUNK_ORDER)}
+    regions = (A_OFF, A2_OFF)
 
     def ready_after(pt):
         lo, hi = point_reads(pt[0], pt[1], pt[2])
         return max(pos[c] for c in range(lo // E2E_CHUNK, (hi + E2E_CHUNK - 1) // E2E_CHUNK))
 
     order = sorted(range(len(g.pts)), key=lambda k: (ready_after(g.pts[k]), k))
-    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    barrier(world)
-    torch.cuda.synchronize()
-    t0.record(stream)
-    for _ in range(steps):
-        step_start = torch.cuda.Event()
-        step_start.record(stream)
-        copy_stream.wait_event(step_start)  # the previous step has finished reading region A
+    done = [None, None]  # per region: the event after the last step that read it
+
+    def issue_copies(k):
+        reg = k % 2
+        if done[reg] is not None:
+            copy_stream.wait_event(done[reg])  # that step has finished reading the region
         landed = []
         with torch.cuda.stream(copy_stream):
             for c in E2E_CHUNK_ORDER:
-                lo = A_OFF + c * E2E_CHUNK
+                lo = regions[reg] + c * E2E_CHUNK
                 for p in range(NPES):
                     parts[p, lo:lo + E2E_CHUNK].copy_(host_in[p, c * E2E_CHUNK:(c + 1) * E2E_CHUNK],
                                                       non_blocking=True)
                 ev = torch.cuda.Event()
                 ev.record(copy_stream)
                 landed.append(ev)
+        return landed
+
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier(world)
+    torch.cuda.synchronize()
+    t0.record(stream)
+    copy_stream.wait_event(t0)
+    landed = issue_copies(0)
+    for k in range(steps):
+        nxt = issue_copies(k + 1) if k + 1 < steps else None
         waited = -1
-        for k in order:
-            need = ready_after(g.pts[k])
+        for i in order:
+            need = ready_after(g.pts[i])
             if need > waited:
                 stream.wait_event(landed[need])
                 waited = need
-            g.run_point(*g.pts[k][:3])
+            g.run_point(*g.pts[i][:3], region=k % 2)
         host_out.copy_(parts[0, B_OFF:B_OFF + 256 * MiB], non_blocking=True)
+        ev = torch.cuda.Event()
+        ev.record(stream)
+        done[k % 2] = ev
+        landed = nxt
     t1.record(stream)
     torch.cuda.synchronize()
     ms = max_over_ranks(t0.elapsed_time(t1), world) / steps
@@ -404,7 +425,8 @@ def run_e2e(torch, sg, g, stream, args, world):
     return {"value": round(world * bytes_step / (ms * 1e-3) / 1e9, 1), "unit": "GB/s",
             "h2d_bytes_per_step": NPES * 256 * MiB, "d2h_bytes_per_step": 256 * MiB,
             "ms_per_step": round(ms, 3), "steps": steps,
-            "pipeline": "32 MiB chunks of region A on a copy stream; each point waits for the chunks it reads"}
+            "pipeline": "32 MiB chunks on a copy stream, each point waits for the chunks it reads; "
+                        "steps alternate two source regions, so the next step's copies overlap this step"}
 
 
 # ----------------------------------------------------------------------------- CPU oracle arm

@@ -1,4 +1,4 @@
-"""Full-size parity of the benchmark's own workload (64 PEs x 512 MiB, PEs = clusters of
+"""Full-size parity of the benchmark's own workload (64 PEs x 768 MiB, PEs = clusters of
 2 CTAs, the launch configuration bench.py times): the largest point of every op family
 runs once and sampled outputs are compared with the oracle applied to the sampled
 inputs (a small heap holding only the sampled positions)."""

@@ -233,8 +233,8 @@ __device__ __forceinline__ bool ctx_aligned(const shmemg_device_ctx_t &, const v
 // own copy engine, whose thread 0 runs the engine above for the PE's contexts 1..3.  The
 // PE posts a context's transfer to its mailbox (the descriptor, then a release of the
 // context's posted count) and goes on at once; the agent takes it (acquire), moves it
-// through its own ring, and once a context's transfers are all written (bulk wait_group
-// 0, then the async-proxy fence) releases the context's done count.  Quiet / fence on a
+// through its own ring with the lean bulk loop, and once it is written (bulk wait_group 0,
+// then the async-proxy fence) releases the context's done count.  Quiet / fence on a
 // context waits (bounded) until done reaches what the PE has posted.  The PE releases
 // `exit` with the launch's epoch when its script ends; the agent leaves when every
 // transfer is done and exit is set.
@@ -262,17 +262,18 @@ __device__ __forceinline__ void mb_set(uint64_t *p, uint32_t epoch, uint32_t n) 
     shmemg_d_st_release_u64(p, ((uint64_t)epoch << 32) | n);
 }
 
-// The agent (thread 0 of the PE's agent CTA; the CTA's other threads have left).  Waits
-// are bounded: a load that never lands ends in dma_drain's timeout (status set, the
-// transfers abandoned and still counted done, so no quiet waits forever), and an agent
-// that sees no post, no new op batch of its PE and no exit flag for 8 x timeout_ns (longer
-// than any bounded wait of the PE) records a timeout (detail -5) and leaves; a later quiet
-// on it then times out in the PE.
-__device__ __noinline__ void ctx_agent(const shmemg_device_ctx_t &c, CtxMailbox *mb, uint32_t epoch, DmaState &x,
-                                       uint8_t *ring) {
-    dma_init(x);
-    asm volatile("fence.proxy.async.global;" ::: "memory");
-    uint32_t taken[NQ - 1] = {}, reported[NQ - 1] = {}, beat = 0, nap = 128;
+// The agent (thread 0 of the PE's agent CTA; the CTA's other threads have left) moves the
+// posted transfers in order, each through the device API's lean bulk loop on the CTA's
+// whole ring (the same loop as a blocking copy), and releases its context's done count
+// after each one.  Waits are bounded: a load that never lands ends the lean loop with a
+// timeout (status set); the ring is then left alone and later transfers are counted done
+// without being moved, so no quiet waits forever.  An agent that sees no post, no new op
+// batch of its PE and no exit flag for 8 x timeout_ns (longer than any bounded wait of the
+// PE) records a timeout (detail -5) and leaves; a later quiet on it then times out in the PE.
+__device__ __noinline__ void ctx_agent(const shmemg_device_ctx_t &c, CtxMailbox *mb, uint32_t epoch, uint8_t *ring,
+                                       uint64_t *bars) {
+    uint32_t taken[NQ - 1] = {}, beat = 0, nap = 128;
+    bool dead = false;
     uint64_t idle_since = 0;
     for (;;) {
         bool got = false;
@@ -280,21 +281,15 @@ __device__ __noinline__ void ctx_agent(const shmemg_device_ctx_t &c, CtxMailbox 
             const uint32_t p = mb_count(&mb->posted[k], epoch);
             for (; taken[k] != p; taken[k]++) {
                 const DmaXfer d = mb->q[k][taken[k] % CTX_QCAP];
-                dma_enqueue(c, x, ring, k + 1, d.dst, d.src, d.n, 0, 1);  // (drains queue k + 1 if it is full)
+                if (!dead && shmemg_d_bulk_copy_thread_n<RING_STAGES>(c, (uint8_t *)d.dst, (const uint8_t *)d.src, d.n,
+                                                                       0, 1, ring, bars) != SHMEMG_SUCCESS)
+                    dead = true;  // (the lean loop waited, bounded, for its loads in flight)
+                mb_set(&mb->done[k], epoch, taken[k] + 1);
                 got = true;
             }
         }
-        if (dma_busy(x)) dma_drain(c, x, ring, -1);  // every queued transfer written (or abandoned)
-        bool pending = false;
-        for (int k = 0; k < NQ - 1; k++) pending |= reported[k] != taken[k];
-        if (pending) {  // dma_drain ended with wait_group 0 and the async-proxy fence
-            for (int k = 0; k < NQ - 1; k++)
-                if (reported[k] != taken[k]) mb_set(&mb->done[k], epoch, reported[k] = taken[k]);
-            idle_since = 0;
-            nap = 128;
-            continue;
-        }
         if (got) {
+            idle_since = 0;
             nap = 128;
             continue;
         }
@@ -475,7 +470,7 @@ __global__ void __launch_bounds__(INTERP_THREADS) k_interp(shmemg_device_ctx_t c
     };
     if (with_agents && blockIdx.x >= (uint32_t)c.npes) {  // a context agent, not a PE
         if (threadIdx.x == 0) {
-            ctx_agent(c, &g_mbox[blockIdx.x - (uint32_t)c.npes], agent_epoch, s_dma, s_ring);
+            ctx_agent(c, &g_mbox[blockIdx.x - (uint32_t)c.npes], agent_epoch, s_ring, s_bars);
             agent_exit();
         }
         return;

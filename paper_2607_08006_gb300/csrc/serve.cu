@@ -249,6 +249,16 @@ __device__ __forceinline__ uint64_t copy_ck(uint8_t *dst, const uint8_t *src, ui
         uint4 *d = (uint4 *)dst;
         uint64_t v = b0 / 16 + threadIdx.x;
         const uint64_t e = b1 / 16, st = blockDim.x;
+        for (; v + 7 * st < e; v += 8 * st) {  // eight 16-byte loads in flight per thread
+            uint4 x[8];
+#pragma unroll
+            for (int u = 0; u < 8; u++) x[u] = __ldcg(s + v + u * st);
+#pragma unroll
+            for (int u = 0; u < 8; u++) {
+                d[v + u * st] = x[u];
+                acc += ck4(x[u], wbase + 4 * (v + u * st));
+            }
+        }
         for (; v + 3 * st < e; v += 4 * st) {
             uint4 a = __ldcg(s + v), b = __ldcg(s + v + st), c = __ldcg(s + v + 2 * st), f = __ldcg(s + v + 3 * st);
             d[v] = a;

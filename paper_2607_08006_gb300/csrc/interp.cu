@@ -230,7 +230,7 @@ __device__ __forceinline__ bool ctx_aligned(const shmemg_device_ctx_t &, const v
 // rate, and a reload or a new bulk instruction waits for them), so it hands back in stalls
 // what it gains in overlap.  When the GPU holds two CTAs per PE (CTA PEs without hardware
 // clusters), each PE gets a context agent instead: a second CTA, on another SM with its
-// own copy engine, whose thread 0 runs the engine above for the PE's contexts 1..3.  The
+// own copy engine, whose thread 0 moves the PE's context 1..3 transfers.  The
 // PE posts a context's transfer to its mailbox (the descriptor, then a release of the
 // context's posted count) and goes on at once; the agent takes it (acquire), moves it
 // through its own ring with the lean bulk loop, and once it is written (bulk wait_group 0,

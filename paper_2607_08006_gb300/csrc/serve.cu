@@ -308,8 +308,21 @@ __device__ void stage_words(uint8_t *part, uint64_t seed, int p, uint64_t j0, ui
         return;
     }
     for (uint64_t j = j0 + threadIdx.x; j < a0; j += blockDim.x) w[j] = payload_word(seed, p, j);
-    for (uint64_t q = a0 / 4 + threadIdx.x; q < a1 / 4; q += blockDim.x) {
-        const uint64_t z = cb64(seed, ((uint64_t)p << 40) | q);
+    // four independent draws per thread and pass: a draw is one serial chain of 64-bit
+    // multiplies, so one chain per thread leaves the schedulers waiting on its latency
+    const uint64_t nq = a1 / 4, bd = blockDim.x, hi = (uint64_t)p << 40;
+    uint64_t q = a0 / 4 + threadIdx.x;
+    for (; q + 3 * bd < nq; q += 4 * bd) {
+        uint64_t z[4];
+#pragma unroll
+        for (int u = 0; u < 4; u++) z[u] = cb64(seed, hi | (q + u * bd));
+#pragma unroll
+        for (int u = 0; u < 4; u++)
+            ((uint4 *)part)[q + u * bd] =
+                make_uint4(payload_of(z[u], 0), payload_of(z[u], 1), payload_of(z[u], 2), payload_of(z[u], 3));
+    }
+    for (; q < nq; q += bd) {
+        const uint64_t z = cb64(seed, hi | q);
         ((uint4 *)part)[q] = make_uint4(payload_of(z, 0), payload_of(z, 1), payload_of(z, 2), payload_of(z, 3));
     }
     for (uint64_t j = a1 + threadIdx.x; j < j1; j += blockDim.x) w[j] = payload_word(seed, p, j);

@@ -1073,14 +1073,15 @@ static __device__ __forceinline__ int shmemg_d_alltoallmem_warp(const shmemg_dev
 }
 
 /* ------------------------------------------------------------------ cluster collectives */
-/* Shared-team collectives staged through DSMEM (CTA-mode heaps, the team = the launch's
- * cluster).  `win` is a shared-memory window of `win_bytes` at the same offset in every
- * CTA (16-byte aligned).  After the entry barrier (a quiet and a team barrier) each
- * member copies what the others need into its own window, the cluster synchronises,
- * and each member builds ITS OWN destination from the members' windows read through
- * DSMEM; an exit barrier keeps every window until all have read it.  The only HBM
- * traffic is each member's own source read and destination write; every byte that
- * moves between PEs crosses the cluster's DSMEM. */
+/* Shared-team alltoall staged through DSMEM (CTA-mode heaps, the team = the launch's
+ * cluster).  `win` is a shared-memory window at the same offset in every CTA (16-byte
+ * aligned).  After the entry barrier (a quiet and a team barrier) each member copies its
+ * P blocks into its own window, the cluster synchronises, and each member builds ITS OWN
+ * destination from the members' windows read through DSMEM; an exit barrier keeps every
+ * window until all have read it.  The only HBM traffic is each member's own source read
+ * and destination write.  Staging pays for small blocks only: it copies every byte twice
+ * and takes a third cluster barrier, so the other shared-team collectives (and larger
+ * alltoalls) move their data through L2 between two cluster barriers. */
 
 /* group-wide copies between global memory and a cluster peer's shared memory: the
  * peer's copy of the shared object at `local` in cluster rank `rank` */
@@ -1139,89 +1140,6 @@ static __device__ __forceinline__ void shmemg_d_copy_to_cluster(shmemg_group g, 
     }
 }
 
-/* the rank-pairwise tree (the fixed float order above) over P <= 8 members, values from
- * a loader ld(r) */
-template <int L, typename V, typename Ld>
-static __device__ __forceinline__ V shmemg_tree_block_ld(const Ld &ld, int r0) {
-    if constexpr (L == 0) {
-        return ld(r0);
-    } else {
-        V a = shmemg_tree_block_ld<L - 1, V>(ld, r0);
-        V b = shmemg_tree_block_ld<L - 1, V>(ld, r0 + (1 << (L - 1)));
-        return shmemg_vadd<V>::add(a, b);
-    }
-}
-template <typename V, typename Ld>
-static __device__ __forceinline__ V shmemg_tree_sum8(const Ld &ld, int P) {
-    V acc{};
-    bool have = false;
-#define SHMEMG_TB8(b)                                                    \
-    if (P & (1 << b)) {                                                  \
-        V t = shmemg_tree_block_ld<b, V>(ld, P & ~((2 << b) - 1));       \
-        acc = have ? shmemg_vadd<V>::add(t, acc) : t;                    \
-        have = true;                                                     \
-    }
-    SHMEMG_TB8(0) SHMEMG_TB8(1) SHMEMG_TB8(2) SHMEMG_TB8(3)
-#undef SHMEMG_TB8
-    return acc;
-}
-
-/* Slice-owner combination from the windows: this member owns vectors [v0, v1); each is
- * read from the P members' windows through DSMEM (team-rank order; the fixed tree for
- * float sums), combined, and stored to the P members' destinations. */
-template <typename T, typename V, int OP>
-static __device__ __forceinline__ void shmemg_d_cluster_reduce_vecs(const uint8_t *win, int P, uint8_t *heap,
-                                                                   uint64_t H, int pe0, uint64_t dst_off, uint64_t v0,
-                                                                   uint64_t v1) {
-    constexpr int NL = sizeof(V) / sizeof(T);
-    const uint32_t w0 = shmemg_d_cluster_addr(win, 0);
-    const uint32_t wstride = shmemg_d_cluster_addr(win, 1) - w0;  /* windows of consecutive ranks */
-    for (uint64_t vi = v0 + threadIdx.x; vi < v1; vi += blockDim.x) {
-        auto ld = [&](int r) { return shmemg_d_ld_cluster<V>(w0 + (uint32_t)r * wstride + (uint32_t)(vi * sizeof(V))); };
-        V acc;
-        if constexpr (OP == SHMEMG_SUM && std::is_floating_point<T>::value) {
-            acc = shmemg_tree_sum8<V>(ld, P);
-        } else {
-            auto comb = [&](const V &x) {
-#pragma unroll
-                for (int l = 0; l < NL; l++) {
-                    T &s = reinterpret_cast<T *>(&acc)[l];
-                    s = shmemg_comb<T>(s, reinterpret_cast<const T *>(&x)[l], OP);
-                }
-            };
-            acc = ld(0);
-            int r = 1;
-            for (; r + 3 < P; r += 4) {  /* four members' loads in flight */
-                const V a = ld(r), b = ld(r + 1), d = ld(r + 2), e = ld(r + 3);
-                comb(a);
-                comb(b);
-                comb(d);
-                comb(e);
-            }
-            for (; r < P; r++) comb(ld(r));
-        }
-        for (int r = 0; r < P; r++) *(V *)(heap + (uint64_t)(pe0 + r) * H + dst_off + vi * sizeof(V)) = acc;
-    }
-}
-template <typename T, typename V16>
-static __device__ __forceinline__ void shmemg_d_cluster_reduce_t(const uint8_t *win, int P, int r, uint8_t *heap,
-                                                                uint64_t H, int pe0, uint64_t dst_off, uint64_t nelems,
-                                                                int op) {
-    const bool v16 = ((dst_off | (nelems * sizeof(T)) | H) & 15) == 0;
-    const uint64_t nv = v16 ? nelems * sizeof(T) / 16 : nelems;
-    uint64_t lo, hi;
-    shmemg_d_slice(nv, r, P, 1, &lo, &hi);
-    if (v16) {
-        if (op == SHMEMG_SUM) shmemg_d_cluster_reduce_vecs<T, V16, SHMEMG_SUM>(win, P, heap, H, pe0, dst_off, lo, hi);
-        else if (op == SHMEMG_MAX) shmemg_d_cluster_reduce_vecs<T, V16, SHMEMG_MAX>(win, P, heap, H, pe0, dst_off, lo, hi);
-        else shmemg_d_cluster_reduce_vecs<T, V16, SHMEMG_MIN>(win, P, heap, H, pe0, dst_off, lo, hi);
-    } else {
-        if (op == SHMEMG_SUM) shmemg_d_cluster_reduce_vecs<T, T, SHMEMG_SUM>(win, P, heap, H, pe0, dst_off, lo, hi);
-        else if (op == SHMEMG_MAX) shmemg_d_cluster_reduce_vecs<T, T, SHMEMG_MAX>(win, P, heap, H, pe0, dst_off, lo, hi);
-        else shmemg_d_cluster_reduce_vecs<T, T, SHMEMG_MIN>(win, P, heap, H, pe0, dst_off, lo, hi);
-    }
-}
-
 /* Gather of nj blocks of nv vectors: block b (rank j0 + b) of the members' windows at
  * byte offset woff -> dst + b * blk.  Four blocks' loads are in flight per thread. */
 template <typename V>
@@ -1261,58 +1179,6 @@ static __device__ __forceinline__ void shmemg_d_cluster_gather(uint8_t *dst, uin
     }
 }
 
-/* Bytes a staged collective needs in each member's window (0: too large to stage). */
-static __device__ __forceinline__ uint64_t shmemg_d_cluster_stage_bytes(int kind, uint64_t n, int dtype, int P) {
-    switch (kind) {
-    case SHMEMG_OP_REDUCE: return n * (dtype == SHMEMG_INT64 ? 8 : 4);
-    case SHMEMG_OP_BROADCAST: case SHMEMG_OP_FCOLLECT: return n;
-    case SHMEMG_OP_ALLTOALL: return n * (uint64_t)P;
-    default: return 0;
-    }
-}
-
-static __device__ __noinline__ int shmemg_d_cluster_reduce_pe(const shmemg_device_ctx_t &c, shmemg_cluster_state_t &cs,
-                                                              uint8_t *win, uint64_t dst_off, uint64_t src_off,
-                                                              uint64_t nelems, int dtype, int op, int64_t detail) {
-    const int me = shmemg_d_my_pe(c), P = (int)shmemg_d_cluster_nctarank(), r = (int)shmemg_d_cluster_ctarank();
-    int rc = shmemg_d_cluster_sync_pe(c, cs, true, detail);
-    if (rc) return rc;
-    shmemg_d_copy_group(shmemg_d_group_block(), win, shmemg_d_addr(c, me, src_off),
-                        shmemg_d_cluster_stage_bytes(SHMEMG_OP_REDUCE, nelems, dtype, P));
-    if ((rc = shmemg_d_cluster_sync_pe(c, cs, false, detail))) return rc;
-    const int pe0 = me - r;
-    if (dtype == SHMEMG_INT32) shmemg_d_cluster_reduce_t<int32_t, int4>(win, P, r, c.heap, c.pe_stride, pe0, dst_off, nelems, op);
-    else if (dtype == SHMEMG_INT64) shmemg_d_cluster_reduce_t<int64_t, longlong2>(win, P, r, c.heap, c.pe_stride, pe0, dst_off, nelems, op);
-    else shmemg_d_cluster_reduce_t<float, float4>(win, P, r, c.heap, c.pe_stride, pe0, dst_off, nelems, op);
-    return shmemg_d_cluster_sync_pe(c, cs, false, detail);
-}
-/* root (team rank) stages n bytes; every member copies the root's window */
-static __device__ __noinline__ int shmemg_d_cluster_broadcastmem_pe(const shmemg_device_ctx_t &c,
-                                                                    shmemg_cluster_state_t &cs, uint8_t *win,
-                                                                    uint64_t dst_off, uint64_t src_off, uint64_t n,
-                                                                    int root, int64_t detail) {
-    const int me = shmemg_d_my_pe(c);
-    int rc = shmemg_d_cluster_sync_pe(c, cs, true, detail);
-    if (rc) return rc;
-    if ((int)shmemg_d_cluster_ctarank() == root)
-        shmemg_d_copy_group(shmemg_d_group_block(), win, shmemg_d_addr(c, me, src_off), n);
-    if ((rc = shmemg_d_cluster_sync_pe(c, cs, false, detail))) return rc;
-    shmemg_d_cluster_gather(shmemg_d_addr(c, me, dst_off), n, win, 0, root, 1);
-    return shmemg_d_cluster_sync_pe(c, cs, false, detail);
-}
-/* each member stages its n bytes; member r's dst block j = member j's window */
-static __device__ __noinline__ int shmemg_d_cluster_fcollectmem_pe(const shmemg_device_ctx_t &c,
-                                                                   shmemg_cluster_state_t &cs, uint8_t *win,
-                                                                   uint64_t dst_off, uint64_t src_off, uint64_t n,
-                                                                   int64_t detail) {
-    const int me = shmemg_d_my_pe(c), P = (int)shmemg_d_cluster_nctarank();
-    int rc = shmemg_d_cluster_sync_pe(c, cs, true, detail);
-    if (rc) return rc;
-    shmemg_d_copy_group(shmemg_d_group_block(), win, shmemg_d_addr(c, me, src_off), n);
-    if ((rc = shmemg_d_cluster_sync_pe(c, cs, false, detail))) return rc;
-    shmemg_d_cluster_gather(shmemg_d_addr(c, me, dst_off), n, win, 0, 0, P);
-    return shmemg_d_cluster_sync_pe(c, cs, false, detail);
-}
 /* each member stages its P blocks; member r's dst block j = block r of member j's window */
 static __device__ __noinline__ int shmemg_d_cluster_alltoallmem_pe(const shmemg_device_ctx_t &c,
                                                                    shmemg_cluster_state_t &cs, uint8_t *win,

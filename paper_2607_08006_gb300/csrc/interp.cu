@@ -19,6 +19,11 @@ namespace shmemg {
 
 constexpr int INTERP_THREADS = 512;
 constexpr int OP_BATCH = 64;  // op records staged in shared memory at a time
+// shared-team alltoalls staged through the DSMEM windows: at most this many bytes per
+// member (P blocks).  Measured on a cluster of 8 PEs: staged 3.96 / 4.48 / 4.91 us per op
+// at 64 B / 512 B / 1 KiB blocks against 5.53-5.58 us through L2, and behind from 2 KiB
+// blocks (5.74 against 5.59 us)
+constexpr uint64_t DSM_A2A_MAX = 8u << 10;
 
 // ---------------------------------------------------------------- the bulk engine
 // Thread 0 of every CTA moves the CTA's bulk (TMA) traffic through one ring of
@@ -447,7 +452,7 @@ __global__ void __launch_bounds__(INTERP_THREADS) k_interp(shmemg_device_ctx_t c
     __shared__ uint8_t s_list[OP_BATCH];
     __shared__ int s_nact;
     // shared-team ops of a CTA-mode heap launched in clusters run inside the cluster: the
-    // team barrier is the hardware cluster barrier, small collectives are staged in the
+    // team barrier is the hardware cluster barrier, small alltoalls are staged in the
     // bulk ring, which then serves as each CTA's DSMEM window (free between ops: every
     // bulk copy has drained)
     __shared__ shmemg_cluster_state_t s_cs;
@@ -488,10 +493,16 @@ __global__ void __launch_bounds__(INTERP_THREADS) k_interp(shmemg_device_ctx_t c
     shmemg_cluster_state_t *cs = dsm ? &s_cs : nullptr;
     const uint64_t win_bytes = use_bulk ? SHMEMG_BULK_SMEM : 0;
     if (dsm) shmemg_d_cluster_begin(s_cs);
+    // Which shared-team collectives are staged through the DSMEM windows: alltoalls of at
+    // most DSM_A2A_MAX bytes per member.  Every other shared-team collective moves its data
+    // through L2 between cluster barriers -- measured faster at every size, because a staged
+    // op copies its source twice (into the window, then out of the peers' windows over the
+    // SM-to-SM network, whose per-SM port a broadcast's root serialises) and needs a third
+    // cluster barrier, while the hardware barrier is what makes the shared team fast.
     auto staged = [&](const shmemg_op_t &o) {
-        if (!dsm || o.team != SHMEMG_TEAM_SHARED || (o.kind & SHMEMG_OP_WARP)) return false;
-        const uint64_t b = shmemg_d_cluster_stage_bytes(o.kind, o.n, o.dtype, c.cluster_dim);
-        return b > 0 && b <= win_bytes;
+        if (!dsm || o.team != SHMEMG_TEAM_SHARED || o.kind != SHMEMG_OP_ALLTOALL) return false;
+        const uint64_t b = o.n * (uint64_t)c.cluster_dim;
+        return b > 0 && b <= DSM_A2A_MAX && b <= win_bytes;
     };
     // Hardware cluster barriers an op runs on the shared team (a fixed count per op
     // record): a CTA that has failed still passes them for every op it skips, so the
@@ -699,20 +710,17 @@ __global__ void __launch_bounds__(INTERP_THREADS) k_interp(shmemg_device_ctx_t c
             break;
         }
         case SHMEMG_OP_BROADCAST:
-            if (staged(o)) rc = shmemg_d_cluster_broadcastmem_pe(c, s_cs, s_ring, o.dst, o.src, o.n, o.pe, i);
-            else if (active) rc = shmemg_d_broadcastmem_scoped(c, o.team, o.dst, o.src, o.n, o.pe, i, cs, warp);
+            if (active) rc = shmemg_d_broadcastmem_scoped(c, o.team, o.dst, o.src, o.n, o.pe, i, cs, warp);
             break;
         case SHMEMG_OP_FCOLLECT:
-            if (staged(o)) rc = shmemg_d_cluster_fcollectmem_pe(c, s_cs, s_ring, o.dst, o.src, o.n, i);
-            else if (active) rc = shmemg_d_fcollectmem_scoped(c, o.team, o.dst, o.src, o.n, i, cs, warp);
+            if (active) rc = shmemg_d_fcollectmem_scoped(c, o.team, o.dst, o.src, o.n, i, cs, warp);
             break;
         case SHMEMG_OP_ALLTOALL:
             if (staged(o)) rc = shmemg_d_cluster_alltoallmem_pe(c, s_cs, s_ring, o.dst, o.src, o.n, i);
             else if (active) rc = shmemg_d_alltoallmem_scoped(c, o.team, o.dst, o.src, o.n, i, cs, warp);
             break;
         case SHMEMG_OP_REDUCE:
-            if (staged(o)) rc = shmemg_d_cluster_reduce_pe(c, s_cs, s_ring, o.dst, o.src, o.n, o.dtype, o.sub, i);
-            else if (active) rc = shmemg_d_reduce_scoped(c, o.team, o.dst, o.src, o.n, o.dtype, o.sub, i, cs, warp);
+            if (active) rc = shmemg_d_reduce_scoped(c, o.team, o.dst, o.src, o.n, o.dtype, o.sub, i, cs, warp);
             break;
         default:
             if (leader) shmemg_d_set_status(c, SHMEMG_ERR_INVALID_ARG, i);

@@ -1,7 +1,8 @@
 """GPU parity of the cluster-resident shared-team path: device-initiated scripts whose
-shared-team collectives and barriers go through distributed shared memory (CTA-mode
-heaps launched in clusters), and the DSMEM put-with-signal ping-pong.  The oracle runs
-each shared-team op once per cluster group, as an explicit team."""
+shared-team barriers are the hardware cluster barrier and whose small shared-team
+alltoalls are staged through distributed shared memory (CTA-mode heaps launched in
+clusters), and the DSMEM put-with-signal ping-pong.  The oracle runs each shared-team op
+once per cluster group, as an explicit team."""
 import numpy as np
 import pytest
 import torch
@@ -38,9 +39,9 @@ class _Dst:
 
 
 def _cluster_script(npes, cd, H):
-    """Shared-team reduce / broadcast / fcollect / alltoall / team_sync of sizes that
-    are staged through the windows (<= 128 KiB per member) and that are not, at aligned
-    and unaligned offsets, mixed with world ops."""
+    """Shared-team reduce / broadcast / fcollect / alltoall / team_sync, alltoalls both
+    staged through the DSMEM windows (up to 8 KiB per member) and not, at aligned and
+    unaligned offsets, mixed with world ops."""
     d = _Dst(H)
     ops = []
     P = cd
@@ -114,8 +115,8 @@ def test_cluster_shared_script_bitexact(sg, heapf, orc, cd):
 
 
 def test_cluster_script_repeated_launches(sg, heapf, orc):
-    """Many shared-team barriers and staged reductions in one launch and across
-    launches (barrier generations start afresh in every launch)."""
+    """Many shared-team barriers, reductions and staged alltoalls in one launch and
+    across launches (barrier generations start afresh in every launch)."""
     npes, H, cd = 8, 4 * MiB, 4
     h = heapf(npes, H, pe_mode=sg.PE_MODE_CTA, cluster_dim=cd)
     init = _init_heap(npes, H, 7)
@@ -125,6 +126,8 @@ def test_cluster_script_repeated_launches(sg, heapf, orc):
         ops.append(_rec(kind=W.OP_REDUCE, dtype=W.DT_INT64, sub=W.RED_SUM, team=SHARED,
                         dst=DST0 + (k % 50) * 4096, src=SRC_INT + 8 * k, n=64 + k))
         ops.append(_rec(kind=W.OP_TEAM_SYNC, team=SHARED))
+        ops.append(_rec(kind=W.OP_ALLTOALL, team=SHARED, dst=2 * MiB + (k % 50) * 4096, src=SRC_INT + 16 * k,
+                        n=16 + (k % 8) * 16))
     ops = np.array(ops, dtype=W.OP_DTYPE)
     dev = torch.from_numpy(ops.view(np.uint8).copy()).cuda()
     ref = orc.Heap(npes, H, init)
@@ -213,6 +216,7 @@ def test_cluster_failed_pe_keeps_barrier_sequence(sg, heapf):
            _rec(kind=W.OP_BCAST, team=SHARED, pe=2, dst=524288, src=4096, n=3000),
            _rec(kind=W.OP_BARRIER_ALL),
            _rec(kind=W.OP_ALLTOALL, team=SHARED, dst=600000, src=4096, n=64),
+           _rec(kind=W.OP_ALLTOALL, team=SHARED, dst=700000, src=4096, n=4096),
            _rec(kind=W.OP_TEAM_SYNC, team=SHARED)]
     ops = np.array(ops, dtype=W.OP_DTYPE)
     sg.clear_status()

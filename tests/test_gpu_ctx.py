@@ -111,10 +111,11 @@ def test_blocking_bulk_copies_behind_context_chunks(sg, heapf, orc, mode, cd):
     assert _run(sg, h, orc, init, ops) is None
 
 
-def test_context_chunks_drain_before_a_staged_cluster_collective(sg, heapf, orc):
-    """CTA PEs in clusters of 4: context transfers in flight when a shared-team collective
-    stages its data in the same shared-memory ring (its DSMEM window); the ring drains
-    first, and both the transfers and the collectives come out right."""
+def test_context_chunks_drain_before_a_staged_cluster_alltoall(sg, heapf, orc):
+    """CTA PEs in clusters of 4: context transfers in flight when a shared-team alltoall
+    stages its blocks in the same shared-memory ring (its DSMEM window); the ring drains
+    first, and the transfers, the staged alltoall and the collectives after it (through
+    L2 between cluster barriers) come out right."""
     npes, H = 8, 8 * MiB
     h = heapf(npes, H, pe_mode=0, cluster_dim=4)
     init = random_heap(npes, H, 71)
@@ -122,7 +123,8 @@ def test_context_chunks_drain_before_a_staged_cluster_collective(sg, heapf, orc)
     ops = []
     for p in range(npes):
         ops.append(_rec(kind=W.OP_PUT_NBI, sub=2, pe=(p + 4) % npes, issuer=p, dst=4 * MiB, src=0, n=3 * MiB))
-    ops += [_rec(kind=W.OP_REDUCE, dtype=W.DT_INT64, sub=W.RED_SUM, team=1, dst=7 * MiB, src=3 * MiB + 4096, n=2048),
+    ops += [_rec(kind=W.OP_ALLTOALL, team=1, dst=7 * MiB + 262144, src=3 * MiB + 32768, n=1024),
+            _rec(kind=W.OP_REDUCE, dtype=W.DT_INT64, sub=W.RED_SUM, team=1, dst=7 * MiB, src=3 * MiB + 4096, n=2048),
             _rec(kind=W.OP_BCAST, team=1, pe=2, dst=7 * MiB + 65536, src=3 * MiB, n=8192),
             _rec(kind=W.OP_FCOLLECT, team=1, dst=7 * MiB + 131072, src=3 * MiB + 16384, n=4096)]
     ops += [_rec(kind=W.OP_QUIET, sub=2, issuer=p) for p in range(npes)]

@@ -514,8 +514,10 @@ static __device__ __forceinline__ int shmemg_d_signal_wait_until(const shmemg_de
             }
             if (shmemg_d_get_status(c) != 0) return SHMEMG_ERR_DEVICE;  /* another PE failed */
         }
-        __nanosleep(ns);
-        if (ns < 1024) ns <<= 1;
+        if (it >= 256) {  /* spin first (a signal usually comes within a few round trips), then back off */
+            __nanosleep(ns);
+            if (ns < 1024) ns <<= 1;
+        }
     }
 }
 

@@ -59,7 +59,9 @@ def _cluster_script(npes, cd, H):
     ops.append(_rec(kind=W.OP_BARRIER_ALL))
     for n in (3000, 140000, 1 << 17):
         ops.append(_rec(kind=W.OP_FCOLLECT, team=SHARED, dst=d.take(n * P), src=SRC_INT + 16, n=n))
-    for n in (1000, 20000, 24):
+    # (at P = 8: 1024-byte blocks are exactly the 8 KiB per member that is still staged,
+    # 1040-byte blocks the first size past it)
+    for n in (1000, 20000, 24, 1024, 1040):
         ops.append(_rec(kind=W.OP_ALLTOALL, team=SHARED, dst=d.take(n * P), src=SRC_INT + 32, n=n))
     ops.append(_rec(kind=W.OP_REDUCE, dtype=W.DT_FLOAT, sub=W.RED_SUM, team=0, dst=d.take(4 * 3000), src=SRC_FLT, n=3000))
     ops.append(_rec(kind=W.OP_TEAM_SYNC, team=SHARED))
